@@ -1,0 +1,73 @@
+"""The stencil programs of this library in the textual stencil-program form.
+
+The form restates the paper's stencil dialect (§IV): ``input`` fields are
+loaded (stencil.load), each ``stage`` is one stencil.apply whose body reads
+earlier values at constant offsets (stencil.access) and returns its results
+(stencil.return), ``column ... = thomas(a, b, c, d...)`` solves a tridiagonal
+system along k in every (i, j) column, and ``output`` values are stored over
+the domain (stencil.store). ``kpos`` is the level index relative to the
+domain's lower k bound and ``ksize`` the domain's extent in k.
+
+``oec_program_create`` recognises these three programs (by structure, not by
+text) and runs them with the hand-written kernels; other programs go through
+the generic code generator.
+"""
+
+# Horizontal diffusion (the shape Table II lists as hdiffsa): 5-point Laplacian,
+# i/j fluxes with a sign limiter, flux divergence.
+HDIFF = """
+input in, coeff
+stage lap = 4.0*in - in[-1,0,0] - in[1,0,0] - in[0,-1,0] - in[0,1,0]
+stage flx = { let f = lap[1,0,0] - lap; return select(f*(in[1,0,0] - in) > 0.0, 0.0, f) }
+stage fly = { let f = lap[0,1,0] - lap; return select(f*(in[0,1,0] - in) > 0.0, 0.0, f) }
+stage out = in - coeff*((flx - flx[-1,0,0]) + (fly - fly[0,-1,0]))
+output out
+"""
+
+
+def _hdiff_of(x, tag):
+    return f"""
+stage lap{tag} = 4.0*{x} - {x}[-1,0,0] - {x}[1,0,0] - {x}[0,-1,0] - {x}[0,1,0]
+stage flx{tag} = {{ let f = lap{tag}[1,0,0] - lap{tag}; return select(f*({x}[1,0,0] - {x}) > 0.0, 0.0, f) }}
+stage fly{tag} = {{ let f = lap{tag}[0,1,0] - lap{tag}; return select(f*({x}[0,1,0] - {x}) > 0.0, 0.0, f) }}
+stage {x}d = {x} - coeff*((flx{tag} - flx{tag}[-1,0,0]) + (fly{tag} - fly{tag}[0,-1,0]))
+"""
+
+
+# Horizontal diffusion of u and v followed by implicit vertical advection: one
+# tridiagonal system per (i, j) column (staggered wind wf = (w + w(i+1))/2),
+# solved by the Thomas algorithm (§VII-B) for both right-hand sides.
+HDIFF_VADVC = ("""
+input u, v, w, coeff
+param dtr
+""" + _hdiff_of("u", "u") + _hdiff_of("v", "v") + """
+stage wf = 0.5*(w + w[1,0,0])
+stage a = select(kpos > 0.0, -0.25*wf, 0.0)
+stage c = select(kpos < ksize - 1.0, 0.25*wf[0,0,1], 0.0)
+stage b = dtr + abs(a) + abs(c)
+stage du = dtr*ud - 0.5*(select(kpos > 0.0, a*(ud[0,0,-1] - ud), 0.0) + select(kpos < ksize - 1.0, c*(ud[0,0,1] - ud), 0.0))
+stage dv = dtr*vd - 0.5*(select(kpos > 0.0, a*(vd[0,0,-1] - vd), 0.0) + select(kpos < ksize - 1.0, c*(vd[0,0,1] - vd), 0.0))
+column u_out, v_out = thomas(a, b, c, du, dv)
+output u_out, v_out
+""")
+
+# Fastwaves-like program (the shape Table II lists as fastwavesuv: six applies,
+# nine inputs, two outputs, no control flow): vertical pressure interpolation,
+# its k difference, terrain-following pressure gradients in i and j, a
+# fourth-order divergence, and the wind update.
+FASTWAVES = """
+input u_in, v_in, utens, vtens, pp, rho, wgtfac, hhl, fx
+param dt, alpha
+stage ppgk = wgtfac*pp + (1.0 - wgtfac)*pp[0,0,-1]
+stage ppgc = ppgk[0,0,1] - ppgk
+stage ppgu = (pp[1,0,0] - pp) + 0.25*(ppgc[1,0,0] + ppgc)*((hhl[0,0,1] + hhl) - (hhl[1,0,1] + hhl[1,0,0])) / ((hhl[0,0,1] - hhl) + (hhl[1,0,1] - hhl[1,0,0]))
+stage ppgv = (pp[0,1,0] - pp) + 0.25*(ppgc[0,1,0] + ppgc)*((hhl[0,0,1] + hhl) - (hhl[0,1,1] + hhl[0,1,0])) / ((hhl[0,0,1] - hhl) + (hhl[0,1,1] - hhl[0,1,0]))
+stage div = (-u_in[2,0,0] + 8.0*u_in[1,0,0] - 8.0*u_in[-1,0,0] + u_in[-2,0,0])/12.0 + (-v_in[0,2,0] + 8.0*v_in[0,1,0] - 8.0*v_in[0,-1,0] + v_in[0,-2,0])/12.0
+stage u_out, v_out = { return u_in + dt*((utens - ppgu*2.0*fx/(rho[1,0,0] + rho)) + alpha*(div[1,0,0] - div)), v_in + dt*((vtens - ppgv*2.0*fx/(rho[0,1,0] + rho)) + alpha*(div[0,1,0] - div)) }
+output u_out, v_out
+"""
+
+BUILTIN = {"hdiff": HDIFF, "hdiff_vadvc": HDIFF_VADVC, "fastwaves": FASTWAVES}
+
+# default scalar parameters of the synthetic workloads
+PARAMS = {"hdiff": [], "hdiff_vadvc": [2.0], "fastwaves": [0.5, 0.0625]}
