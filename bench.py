@@ -1,0 +1,333 @@
+"""Benchmark: horizontal diffusion + vertical advection (Thomas), FP64, interior
+128x128x80 with halo 3 - the workload the grid-points/s metric is quoted on.
+
+One step = one application of the whole program (hdiff of u and v, tridiagonal
+build, Thomas sweep) to one set of synthetic fields, through the C ABI.
+Inputs rotate over several resident sets whose total exceeds the L2 cache, so
+every step reads its fields from HBM.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0). --impl reference times the CPU FP64 oracle on
+the host cores instead (bounded column samples of the same workload).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "hdiff_vadvc"
+N = (128, 128, 80)
+H = 3
+DTR = 2.0
+# algorithmic floating-point operations per interior point of hdiff(u), hdiff(v),
+# the tridiagonal build and the Thomas sweep (each add, sub, mul, div, compare
+# counted once; derivation in the design notes)
+FLOPS_PER_POINT = 71
+METRIC = "grid-points/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def mark(self):
+        return len(self.lines)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, start=0):
+        rows = []
+        for l in self.lines[start:] or self.lines:
+            parts = [x.strip() for x in l.split(",")]
+            if len(parts) >= 7 and parts[0].isdigit():
+                rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(float(r[0]) for r in rows), "sm_max_mhz": float(rows[0][1]),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _kernel_source_hash():
+    h = hashlib.sha256()
+    for name in ("k_vadvc.cu", "kcommon.cuh"):
+        with open(os.path.join(ROOT, "paper_2005_13014_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _ncu_traffic(kernel_hash):
+    """DRAM bytes per launch of the timed kernel from the committed ncu summary,
+    if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "hdiff_vadvc_fused_f64_128x128x80.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+    t = re.search(r"dram_bytes_per_launch:\s*([0-9]+)", text)
+    if not m or not t or m.group(1) != kernel_hash:
+        return None
+    return int(t.group(1))
+
+
+def cpu_oracle_rate(seconds=10.0, sub=None):
+    """Points/s of the CPU FP64 oracle on the workload (or a column sample)."""
+    from oracle import stencils as S
+    from paper_2005_13014_gb300 import inputs
+    f = inputs.hdiff_vadvc_fields(*N, H)
+    G = {k: S.Grid.storage(v, H) for k, v in f.items()}
+    ub = sub or N
+    pts = ub[0] * ub[1] * ub[2]
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        S.hdiff_vadvc(G["u"], G["v"], G["w"], G["coeff"], (0, 0, 0), ub, DTR)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return pts * reps / el, reps
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    from oracle import stencils as S
+    from paper_2005_13014_gb300 import inputs
+    f = inputs.hdiff_vadvc_fields(*N, H)
+    G = {k: S.Grid.storage(v, H) for k, v in f.items()}
+    sub = (32, 32, N[2])            # one step: a 32x32-column sample of the domain
+    pts = sub[0] * sub[1] * sub[2]
+    for _ in range(args.warmup):
+        S.hdiff_vadvc(G["u"], G["v"], G["w"], G["coeff"], (0, 0, 0), sub, DTR)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        S.hdiff_vadvc(G["u"], G["v"], G["w"], G["coeff"], (0, 0, 0), sub, DTR)
+    el = time.perf_counter() - t0
+    value = pts * args.steps / el
+    line = {"metric": METRIC, "value": value, "unit": "grid-points/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": "hdiff+vadvc FP64 128x128x80 halo 3 (32x32x80 column sample per step)",
+                       "program": WORKLOAD},
+            "cpu_baseline": {"value": value, "unit": "grid-points/s", "cores": 1, "kind": "oracle",
+                             "sample": "numpy FP64 oracle, 32x32x80 columns of the 128x128x80 domain per step"},
+            "e2e": {"value": value, "unit": "grid-points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2005_13014_gb300 import inputs, programs
+    from paper_2005_13014_gb300.api import Program, device_field
+
+    prog = Program(programs.HDIFF_VADVC, "f64")
+    if args.schedule:
+        prog.set_schedule(**json.loads(args.schedule))
+    lb, ub, halo = (0, 0, 0), N, (H, H, H)
+    points = N[0] * N[1] * N[2]
+    f = inputs.hdiff_vadvc_fields(*N, H)
+    set_bytes = 6 * f["u"].nbytes
+    l2 = torch.cuda.get_device_properties(local).L2_cache_size if hasattr(
+        torch.cuda.get_device_properties(local), "L2_cache_size") else 128 << 20
+    n_sets = max(2, int(np.ceil(3 * l2 / set_bytes)))
+    sets = []
+    for s in range(n_sets):
+        fs = f if s == 0 else inputs.hdiff_vadvc_fields(*N, H, seed=inputs.SEED + 100 * s)
+        d = [device_field(fs[k], H, "f64") for k in ("u", "v", "w", "coeff")]
+        o = [device_field(np.zeros_like(fs["u"]), H, "f64") for _ in range(2)]
+        sets.append((d, o))
+    stream = torch.cuda.Stream()
+    sched = prog.schedule
+
+    def step(s):
+        d, o = sets[s % n_sets]
+        prog.apply(d, o, lb, ub, halo, [DTR], stream=stream)
+
+    with torch.cuda.stream(stream):
+        for w in range(max(args.warmup, 3)):
+            step(w)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        time.sleep(0.2)
+        # keep the GPU busy while the sampler starts, then time exactly K steps
+        with torch.cuda.stream(stream):
+            for w in range(args.warmup):
+                step(w)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        mark = clk.mark()
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            t_start.record(stream)
+            for s in range(args.steps):
+                ev[s][0].record(stream)
+                step(s)
+                ev[s][1].record(stream)
+            t_end.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        total_ms = t_start.elapsed_time(t_end)
+        time.sleep(0.1)
+        clocks = clk.summary(mark)
+    kern_ms = [a.elapsed_time(b) for a, b in ev]
+    kern_avg_ms = float(np.mean(kern_ms))
+    tmax = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    total_ms = float(tmax.item())
+    value = points * args.steps * ws / (total_ms * 1e-3)
+
+    # end to end through the same ABI call: pinned host inputs -> device, apply,
+    # outputs -> pinned host, every step inside the timed region
+    host_in = [torch.from_numpy(f[k]).pin_memory() for k in ("u", "v", "w", "coeff")]
+    host_out = [torch.empty_like(host_in[0]).pin_memory() for _ in range(2)]
+    d0, o0 = sets[0]
+    h2d = sum(t.numel() * t.element_size() for t in host_in)
+    d2h = sum(t.numel() * t.element_size() for t in host_out)
+    e2e_steps = max(10, min(args.steps, 200))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(e2e_steps):
+            for t_h, fd in zip(host_in, d0):
+                fd.tensor.copy_(t_h, non_blocking=True)
+            prog.apply(d0, o0, lb, ub, halo, [DTR], stream=stream)
+            for t_h, fd in zip(host_out, o0):
+                t_h.copy_(fd.tensor, non_blocking=True)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    e2e_value = points * ws / (e2e_ms * 1e-3)
+
+    alg_bytes = prog.algorithmic_bytes(lb, ub)
+    peaks = _peaks()
+    fp64_peak = 1250.0        # GFLOP/s, GB300 nominal dense FP64
+    achieved_gflops = FLOPS_PER_POINT * points / (kern_avg_ms * 1e-3) / 1e9
+    achieved_gbs = alg_bytes / (kern_avg_ms * 1e-3) / 1e9
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    khash = _kernel_source_hash()
+    traffic = _ncu_traffic(khash)
+    line = {
+        "metric": METRIC, "value": value, "unit": "grid-points/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "hdiff+vadvc FP64 interior 128x128x80 halo 3 (u,v,w ~ U[-1,1], coeff ~ U[0,0.1], dtr=2)",
+                   "program": WORKLOAD, "schedule": sched,
+                   "l2": f"rotating {n_sets} resident input/output sets ({n_sets * set_bytes / 1e6:.0f} MB > L2 {l2 / 1e6:.0f} MB)",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
+        "roofline": {"bound": "alu", "achieved": achieved_gflops, "peak": fp64_peak, "unit": "GFLOP/s (FP64)",
+                     "frac": achieved_gflops / fp64_peak, "traffic": traffic,
+                     "kernel": "hv_fused_kernel", "flops_per_point": FLOPS_PER_POINT,
+                     "peak_source": "GB300 nominal dense FP64 1.25 TFLOP/s (profiling recipe table)"},
+        "roofline_hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": achieved_gbs / hbm_peak,
+                         "algorithmic_bytes_per_launch": alg_bytes, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"},
+        "kernel_ms": {"mean": kern_avg_ms, "median": float(np.median(kern_ms)),
+                      "q1": float(np.percentile(kern_ms, 25)), "q3": float(np.percentile(kern_ms, 75))},
+        "e2e": {"value": e2e_value, "unit": "grid-points/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": args.steps * (1 if sched["fusion"] == 0 else 3),
+        "clocks": clocks,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        rate, reps = cpu_oracle_rate(args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": "grid-points/s", "cores": 1, "kind": "oracle",
+                                "sample": f"numpy FP64 oracle on the full 128x128x80 domain, {reps} repetitions"}
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="oec", choices=["oec", "reference"])
+    ap.add_argument("--schedule", default=None, help="JSON schedule override")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,206 @@
+/*
+ * oec.h - C ABI of liboec, a GB300 (sm_103a) runtime for stencil programs.
+ *
+ * A stencil program (paper §IV, "Stencil Programs") loads input fields, applies
+ * a chain of stencil operators (stencil.apply) that read their inputs at
+ * constant offsets (stencil.access), and stores results to output fields over
+ * a domain given as a range with an inclusive lower and an exclusive upper
+ * bound (paper §IV, "Shapes & Domains"). The library parses a textual form of
+ * such a program, infers the access range of every input (paper §V-B, shape
+ * inference), and runs it on the GPU, fused into one kernel per program
+ * (stencil inlining, paper §V-A) or stage by stage with temporaries in device
+ * memory (the paper's "original" optimisation level, §VII-C).
+ *
+ * Conventions used by every call:
+ *  - Coordinates are (i, j, k); i is the contiguous dimension.
+ *  - Every pointer to device memory is owned by the caller; the library never
+ *    frees it. Program and batch handles, compiled modules and scratch
+ *    temporaries are owned by the library and freed by the matching destroy.
+ *  - Functions return OEC_OK (0) or a negative OEC_ERR_* code; the message of
+ *    the last error on the calling thread is returned by oec_last_error().
+ *    No C++ exception crosses this interface.
+ *  - Apply calls are asynchronous: they enqueue work on the caller's CUDA
+ *    stream (a cudaStream_t passed as void*, NULL = legacy default stream)
+ *    and never synchronise with the host.
+ */
+#ifndef OEC_H
+#define OEC_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define OEC_API __attribute__((visibility("default")))
+#else
+#define OEC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------- */
+#define OEC_OK 0
+#define OEC_ERR_INVALID_ARG (-1)   /* null pointer, bad count, empty or inverted domain  */
+#define OEC_ERR_PARSE (-2)         /* program text does not parse or verify              */
+#define OEC_ERR_SHAPE (-3)         /* a field's storage does not hold its inferred range  */
+#define OEC_ERR_HALO (-4)          /* inferred input range exceeds the caller's halo      */
+#define OEC_ERR_ALIAS (-5)         /* an output range overlaps an input or other output   */
+#define OEC_ERR_DTYPE (-6)         /* field element type differs from the program's       */
+#define OEC_ERR_UNSUPPORTED (-7)   /* valid request this build cannot run                 */
+#define OEC_ERR_COMPILE (-8)       /* run-time compilation of a generated kernel failed    */
+#define OEC_ERR_CUDA (-9)          /* a CUDA runtime call failed                          */
+#define OEC_ERR_TIMEOUT (-10)      /* a bounded device-side wait gave up                  */
+
+/* ---- element types (paper §IV: fields hold f32 or f64) ------------------ */
+typedef enum { OEC_F32 = 0, OEC_F64 = 1 } oec_dtype;
+
+/*
+ * A field: caller-owned storage of a 1-, 2- or 3-D grid (paper §IV,
+ * !stencil.field). Element (i, j, k) of the logical grid lives at
+ *   data + ((origin[0]+i)*stride[0] + (origin[1]+j)*stride[1] + (origin[2]+k)*stride[2]) elements,
+ * valid for 0 <= origin[d] + x_d < size[d]. Logical (0,0,0) is the origin of
+ * the computation domain (paper §IV, range notation). stride[0] must be 1.
+ * Unused trailing dimensions of 1-/2-D fields have size 1 and stride 0.
+ */
+typedef struct oec_field_desc {
+  void* data;          /* device pointer to element (0,0,0) of the storage    */
+  int32_t dtype;       /* oec_dtype                                           */
+  int32_t ndim;        /* 1..3                                                */
+  int64_t size[3];     /* storage extents (halo and padding included), i,j,k  */
+  int64_t stride[3];   /* element strides                                     */
+  int64_t origin[3];   /* storage index of logical point (0,0,0)              */
+} oec_field_desc;
+
+/* ---- schedules (paper §V-A: inlining and unrolling; §VI: grid mapping) --- */
+typedef enum {
+  OEC_FUSE_INLINE = 0,   /* all producers inlined into one kernel (paper §V-A)          */
+  OEC_FUSE_NONE = 1      /* one kernel per stage, temporaries in device memory         */
+} oec_fusion;
+
+typedef enum {
+  OEC_STAGE_REGS = 0,    /* every thread recomputes what it reads (paper's model)      */
+  OEC_STAGE_SMEM = 1     /* overlapped tile in shared memory, no redundant compute     */
+} oec_staging;
+
+typedef struct oec_schedule {
+  int32_t fusion;        /* oec_fusion                                                   */
+  int32_t staging;       /* oec_staging (fused kernels only)                             */
+  int32_t tile_i;        /* CTA tile extent along i, in points (16..256)                 */
+  int32_t tile_j;        /* CTA tile extent along j, in points (1..16)                   */
+  int32_t unroll;        /* points per thread along the unroll dimension (1, 2 or 4)     */
+  int32_t k_chunk;       /* levels per CTA for horizontal programs (0 = whole column)    */
+  int32_t reserved[6];   /* zero                                                          */
+} oec_schedule;
+
+/* ---- programs ----------------------------------------------------------- */
+typedef struct oec_program* oec_program_t;
+
+#define OEC_OPT_GENERIC 1      /* never use a hand-written kernel for this program */
+
+typedef struct oec_program_options {
+  int32_t dtype;         /* oec_dtype of every field of the program             */
+  int32_t flags;         /* OEC_OPT_* bits                                      */
+  int32_t reserved[6];   /* zero                                                */
+} oec_program_options;
+
+/* What kind of kernel runs a program (oec_program_info.kind). */
+#define OEC_KIND_GENERIC 0
+#define OEC_KIND_HDIFF 1
+#define OEC_KIND_HDIFF_VADVC 2
+#define OEC_KIND_FASTWAVES 3
+
+typedef struct oec_program_info {
+  int32_t kind;          /* OEC_KIND_*                                           */
+  int32_t n_inputs;      /* fields named by `input`, in order                    */
+  int32_t n_outputs;     /* values named by `output`, in order                   */
+  int32_t n_params;      /* scalars named by `param`, in order                   */
+  int32_t n_stages;      /* stencil.apply statements (+ column solves)           */
+  int32_t dtype;         /* oec_dtype                                            */
+} oec_program_info;
+
+/*
+ * Parse and verify a program in the textual stencil form (paper §IV):
+ *   input a, b            loaded fields          (stencil.load)
+ *   param p               scalar parameters
+ *   stage x = expr        one stencil.apply; reads name[di,dj,dk] (stencil.access)
+ *   stage x, y = { let t = expr; return e1, e2 }   multi-result apply
+ *   column x = thomas(a, b, c, d)                  tridiagonal solve along k
+ *   output x              stored values           (stencil.store)
+ * Expressions: + - * / unary -, min, max, abs, select(x > y, a, b) (also <, >=,
+ * <=), numbers, params, `kpos` (k minus the domain's lower k) and `ksize`.
+ * On success *out receives a handle. No GPU work happens here.
+ * Errors: OEC_ERR_INVALID_ARG, OEC_ERR_PARSE (message gives the position).
+ */
+OEC_API int oec_program_create(const char* source, const oec_program_options* opts, oec_program_t* out);
+
+/* Free a program, its scratch temporaries and compiled modules (NULL is a no-op).
+ * The caller must ensure no apply of this program is still running. */
+OEC_API void oec_program_destroy(oec_program_t p);
+
+/* Counts and kind of a program. Errors: OEC_ERR_INVALID_ARG. */
+OEC_API int oec_program_get_info(oec_program_t p, oec_program_info* info);
+
+/* Name of input `index` (0-based, declaration order) copied into buf (NUL
+ * terminated, truncated to len). Errors: OEC_ERR_INVALID_ARG. */
+OEC_API int oec_program_input_name(oec_program_t p, int index, char* buf, int len);
+
+/*
+ * Inferred access range of input `index` for the domain [lb, ub) (paper §V-B:
+ * the bounding box of all extents its consumers read), returned as the
+ * half-open box [range_lo, range_hi) in logical coordinates. An input that
+ * no output depends on gets an empty box (range_lo == range_hi == lb).
+ * Errors: OEC_ERR_INVALID_ARG.
+ */
+OEC_API int oec_program_input_range(oec_program_t p, int index, const int64_t lb[3], const int64_t ub[3],
+                            int64_t range_lo[3], int64_t range_hi[3]);
+
+/*
+ * Select the schedule used by later applies (fusion, staging, tile, unroll,
+ * k-chunk). Values outside the supported set give OEC_ERR_UNSUPPORTED and
+ * leave the schedule unchanged. A new program starts with the library's
+ * default schedule for its kind.
+ */
+OEC_API int oec_program_set_schedule(oec_program_t p, const oec_schedule* s);
+OEC_API int oec_program_get_schedule(oec_program_t p, oec_schedule* s);
+
+/*
+ * Run the program over the domain [lb, ub) (paper §IV range notation, logical
+ * coordinates).
+ *   in[n_in]    input fields in `input` order (device memory, caller-owned)
+ *   out[n_out]  output fields in `output` order; written over [lb, ub) only
+ *   halo[3]     cells around [lb, ub) (per side, per dimension) that hold valid
+ *               input data; the inferred range of every input must stay inside
+ *               [lb - halo, ub + halo) (OEC_ERR_HALO) and inside the field's
+ *               storage (OEC_ERR_SHAPE)
+ *   params      the program's scalars in `param` order (n_params of them)
+ *   cuda_stream cudaStream_t (void*); NULL = legacy default stream
+ * Inputs may alias each other; an output's written range may overlap no
+ * input's storage and no other output's range (OEC_ERR_ALIAS; paper §IV
+ * requires alias-free program arguments). All fields of one program must
+ * share the program's dtype (OEC_ERR_DTYPE) and the same j and k strides
+ * (OEC_ERR_UNSUPPORTED). The first apply at a new domain size may allocate
+ * scratch temporaries (unfused schedules, column solves); later applies at
+ * that size reuse them. Asynchronous: returns after enqueueing.
+ * Errors: OEC_ERR_INVALID_ARG, OEC_ERR_SHAPE, OEC_ERR_HALO, OEC_ERR_ALIAS,
+ * OEC_ERR_DTYPE, OEC_ERR_UNSUPPORTED, OEC_ERR_COMPILE, OEC_ERR_CUDA.
+ */
+OEC_API int oec_program_apply(oec_program_t p, const oec_field_desc* in, int n_in, const oec_field_desc* out,
+                      int n_out, const int64_t lb[3], const int64_t ub[3], const int64_t halo[3],
+                      const double* params, int n_params, void* cuda_stream);
+
+/*
+ * Algorithmic device-memory bytes of one apply over [lb, ub): the sum over
+ * inputs of the inferred range volume plus the sum over outputs of the domain
+ * volume, times the element size. Temporaries are not counted (a fused
+ * kernel keeps them on chip). Errors: OEC_ERR_INVALID_ARG.
+ */
+OEC_API int oec_program_algorithmic_bytes(oec_program_t p, const int64_t lb[3], const int64_t ub[3], int64_t* bytes);
+
+/* Message of the last error on the calling thread ("" if none). The pointer
+ * stays valid until the thread's next liboec call. */
+OEC_API const char* oec_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

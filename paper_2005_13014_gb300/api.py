@@ -1,0 +1,146 @@
+"""Python face of liboec: argument marshalling between torch tensors and the C
+ABI. Every step of a stencil program runs in liboec's CUDA kernels; there is no
+Python or CPU execution path. torch provides device memory and streams only.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib as L
+
+_DTYPES = {"f32": L.F32, "f64": L.F64}
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class Field:
+    """A device field: a torch tensor indexed [k, j, i] plus the storage index
+    (i, j, k) of the logical origin (paper §IV range notation)."""
+
+    def __init__(self, tensor, origin):
+        torch = _torch()
+        if tensor.dim() != 3:
+            raise ValueError("fields are 3-D tensors indexed [k, j, i]")
+        if tensor.dtype not in (torch.float32, torch.float64):
+            raise ValueError("fields hold float32 or float64")
+        self.tensor = tensor
+        self.origin = tuple(int(x) for x in origin)
+
+    @property
+    def dtype_code(self):
+        return L.F64 if self.tensor.dtype == _torch().float64 else L.F32
+
+    def desc(self) -> L.FieldDesc:
+        t = self.tensor
+        d = L.FieldDesc()
+        d.data = t.data_ptr()
+        d.dtype = self.dtype_code
+        d.ndim = 3
+        d.size = L.I64x3(t.shape[2], t.shape[1], t.shape[0])
+        d.stride = L.I64x3(t.stride(2), t.stride(1), t.stride(0))
+        d.origin = L.I64x3(*self.origin)
+        return d
+
+    def interior(self, lb, ub):
+        """View of the tensor over the logical box [lb, ub)."""
+        oi, oj, ok = self.origin
+        return self.tensor[ok + lb[2]:ok + ub[2], oj + lb[1]:oj + ub[1], oi + lb[0]:oi + ub[0]]
+
+
+def device_field(arr: np.ndarray, h, dtype="f64", device="cuda", align_bytes=0, pad_i=0):
+    """Copy a host storage array [k, j, i] with halo ``h`` (int or (hi, hj, hk))
+    to the device. With ``align_bytes`` > 0 the i-rows are padded in front so
+    that the first interior point of every row starts on that boundary; ``pad_i``
+    extra elements are appended to every row."""
+    torch = _torch()
+    hi = h if np.isscalar(h) else h[0]
+    hj = h if np.isscalar(h) else h[1]
+    hk = h if np.isscalar(h) else h[2]
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    es = 8 if dtype == "f64" else 4
+    front = 0
+    if align_bytes:
+        a = align_bytes // es
+        front = (-hi) % a
+    nk, nj, ni = arr.shape
+    row = front + ni + pad_i
+    if align_bytes:
+        row = -(-row // (align_bytes // es)) * (align_bytes // es)
+    host = np.zeros((nk, nj, row), dtype=np.float64 if dtype == "f64" else np.float32)
+    host[:, :, front:front + ni] = arr
+    t = torch.from_numpy(host).to(device)
+    return Field(t, (front + hi, hj, hk))
+
+
+class Program:
+    """A compiled stencil program (liboec handle)."""
+
+    def __init__(self, source: str, dtype: str = "f64", generic: bool = False):
+        self._h = None
+        opts = L.ProgramOptions()
+        opts.dtype = _DTYPES[dtype]
+        opts.flags = 1 if generic else 0
+        h = C.c_void_p()
+        L.check(L.lib().oec_program_create(source.encode(), C.byref(opts), C.byref(h)))
+        self._h = h
+        self.dtype = dtype
+        info = L.ProgramInfo()
+        L.check(L.lib().oec_program_get_info(h, C.byref(info)))
+        self.kind = L.KIND_NAMES.get(info.kind, "?")
+        self.n_inputs, self.n_outputs, self.n_params = info.n_inputs, info.n_outputs, info.n_params
+        self.n_stages = info.n_stages
+        buf = C.create_string_buffer(256)
+        names = []
+        for x in range(self.n_inputs):
+            L.check(L.lib().oec_program_input_name(h, x, buf, 256))
+            names.append(buf.value.decode())
+        self.input_names = names
+
+    def __del__(self):
+        if getattr(self, "_h", None) is not None:
+            L.lib().oec_program_destroy(self._h)
+            self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def schedule(self) -> dict:
+        s = L.Schedule()
+        L.check(L.lib().oec_program_get_schedule(self._h, C.byref(s)))
+        return {"fusion": s.fusion, "staging": s.staging, "tile_i": s.tile_i, "tile_j": s.tile_j,
+                "unroll": s.unroll, "k_chunk": s.k_chunk}
+
+    def set_schedule(self, fusion=0, staging=0, tile_i=64, tile_j=4, unroll=1, k_chunk=0):
+        s = L.Schedule(fusion, staging, tile_i, tile_j, unroll, k_chunk)
+        L.check(L.lib().oec_program_set_schedule(self._h, C.byref(s)))
+
+    def input_range(self, index, lb, ub):
+        lo, hi = L.I64x3(), L.I64x3()
+        L.check(L.lib().oec_program_input_range(self._h, index, L.I64x3(*lb), L.I64x3(*ub), lo, hi))
+        return tuple(lo), tuple(hi)
+
+    def algorithmic_bytes(self, lb, ub) -> int:
+        b = C.c_int64()
+        L.check(L.lib().oec_program_algorithmic_bytes(self._h, L.I64x3(*lb), L.I64x3(*ub), C.byref(b)))
+        return b.value
+
+    def apply(self, inputs, outputs, lb, ub, halo, params=(), stream=None):
+        """Enqueue the program on ``stream`` (torch.cuda.Stream or raw handle;
+        default: torch's current stream). Fields are ``Field`` objects."""
+        ins = (L.FieldDesc * max(1, len(inputs)))(*[f.desc() for f in inputs])
+        outs = (L.FieldDesc * max(1, len(outputs)))(*[f.desc() for f in outputs])
+        par = (C.c_double * max(1, len(params)))(*params)
+        if stream is None:
+            stream = _torch().cuda.current_stream().cuda_stream
+        elif hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        L.check(L.lib().oec_program_apply(self._h, ins, len(inputs), outs, len(outputs), L.I64x3(*lb),
+                                          L.I64x3(*ub), L.I64x3(*halo), par, len(params), C.c_void_p(stream)))

@@ -1,0 +1,332 @@
+// api.cpp - the C ABI of liboec (include/oec.h): program handles, validation of
+// field descriptors against the inferred ranges (paper §V-B), schedule
+// selection and dispatch to the hand-written kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/oec.h"
+#include "api_internal.h"
+#include "builtin_programs.h"
+#include "ir.h"
+#include "kernels.h"
+
+namespace oec {
+
+namespace {
+thread_local std::string g_err;
+}
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  std::vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+void clear_error() { g_err.clear(); }
+
+int cuda_fail(cudaError_t e, const char* where) {
+  return fail(OEC_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+static const std::string& builtin_canon(int kind) {
+  static std::string c[4];
+  static std::once_flag once;
+  std::call_once(once, [] {
+    const char* src[4] = {nullptr, kBuiltin_hdiff, kBuiltin_hdiff_vadvc, kBuiltin_fastwaves};
+    for (int k = 1; k < 4; ++k) {
+      Program p;
+      std::string err;
+      if (parse(src[k], p, err)) c[k] = canonical(p);
+    }
+  });
+  return c[kind];
+}
+
+oec_schedule default_schedule(int kind) {
+  oec_schedule s{};
+  s.fusion = OEC_FUSE_INLINE;
+  s.unroll = 1;
+  switch (kind) {
+    case OEC_KIND_HDIFF:
+      s.staging = OEC_STAGE_SMEM;
+      s.tile_i = 64;
+      s.tile_j = 4;
+      s.k_chunk = 2;
+      break;
+    case OEC_KIND_HDIFF_VADVC:
+      s.staging = OEC_STAGE_SMEM;
+      s.tile_i = 32;
+      s.tile_j = 2;
+      break;
+    case OEC_KIND_FASTWAVES:
+      s.staging = OEC_STAGE_REGS;
+      s.tile_i = 64;
+      s.tile_j = 4;
+      s.unroll = 2;
+      break;
+    default:
+      s.staging = OEC_STAGE_REGS;
+      s.tile_i = 64;
+      s.tile_j = 4;
+      break;
+  }
+  return s;
+}
+
+bool schedule_ok(int kind, const oec_schedule& s, std::string& why) {
+  for (int r : s.reserved)
+    if (r != 0) { why = "reserved schedule fields must be zero"; return false; }
+  switch (kind) {
+    case OEC_KIND_HDIFF: return hdiff_schedule_ok(s, why);
+    case OEC_KIND_HDIFF_VADVC: return hdiff_vadvc_schedule_ok(s, why);
+    case OEC_KIND_FASTWAVES: return fastwaves_schedule_ok(s, why);
+    default: return generic_schedule_ok(s, why);
+  }
+}
+
+size_t elem_size(int dtype) { return dtype == OEC_F64 ? 8 : 4; }
+
+// Byte interval [lo, hi] touched by `f` over the box [blo, bhi) (non-empty).
+static void byte_span(const oec_field_desc& f, const int64_t blo[3], const int64_t bhi[3], size_t es, uintptr_t& lo,
+                      uintptr_t& hi) {
+  int64_t a = 0, b = 0;
+  for (int d = 0; d < 3; ++d) {
+    const int64_t s = f.stride[d];
+    const int64_t x0 = (f.origin[d] + blo[d]) * s, x1 = (f.origin[d] + bhi[d] - 1) * s;
+    a += std::min(x0, x1);
+    b += std::max(x0, x1);
+  }
+  lo = (uintptr_t)f.data + a * (int64_t)es;
+  hi = (uintptr_t)f.data + b * (int64_t)es + es - 1;
+}
+
+int validate_fields(const oec_program* p, const oec_field_desc* in, int n_in, const oec_field_desc* out, int n_out,
+                    const int64_t lb[3], const int64_t ub[3], const int64_t halo[3], std::vector<Box>& ranges) {
+  const Program& ir = p->ir;
+  const size_t es = elem_size(p->dtype);
+  std::string err;
+  if (!infer_ranges(ir, lb, ub, ranges, err)) return fail(OEC_ERR_SHAPE, "%s", err.c_str());
+  auto check_desc = [&](const oec_field_desc& f, const char* role, int idx) -> int {
+    if (!f.data) return fail(OEC_ERR_INVALID_ARG, "%s %d: null data pointer", role, idx);
+    if (f.dtype != p->dtype) return fail(OEC_ERR_DTYPE, "%s %d: dtype %d, program dtype %d", role, idx, f.dtype, p->dtype);
+    if (f.ndim < 1 || f.ndim > 3) return fail(OEC_ERR_INVALID_ARG, "%s %d: ndim must be 1..3", role, idx);
+    if (f.stride[0] != 1) return fail(OEC_ERR_UNSUPPORTED, "%s %d: stride[0] must be 1", role, idx);
+    for (int d = 0; d < 3; ++d)
+      if (f.size[d] < 1) return fail(OEC_ERR_INVALID_ARG, "%s %d: size[%d] < 1", role, idx, d);
+    return OEC_OK;
+  };
+  for (int x = 0; x < n_in; ++x) {
+    int rc = check_desc(in[x], "input", x);
+    if (rc) return rc;
+    const Box& r = ranges[ir.inputs[x]];
+    if (!r.valid) continue;
+    for (int d = 0; d < 3; ++d) {
+      if (r.lo[d] < lb[d] - halo[d] || r.hi[d] > ub[d] + halo[d])
+        return fail(OEC_ERR_HALO, "input '%s': inferred range [%lld, %lld) in dim %d exceeds halo %lld around [%lld, %lld)",
+                    ir.values[ir.inputs[x]].name.c_str(), (long long)r.lo[d], (long long)r.hi[d], d,
+                    (long long)halo[d], (long long)lb[d], (long long)ub[d]);
+      if (in[x].origin[d] + r.lo[d] < 0 || in[x].origin[d] + r.hi[d] > in[x].size[d])
+        return fail(OEC_ERR_SHAPE, "input '%s': storage does not hold inferred range [%lld, %lld) in dim %d",
+                    ir.values[ir.inputs[x]].name.c_str(), (long long)r.lo[d], (long long)r.hi[d], d);
+    }
+  }
+  for (int x = 0; x < n_out; ++x) {
+    int rc = check_desc(out[x], "output", x);
+    if (rc) return rc;
+    for (int d = 0; d < 3; ++d)
+      if (out[x].origin[d] + lb[d] < 0 || out[x].origin[d] + ub[d] > out[x].size[d])
+        return fail(OEC_ERR_SHAPE, "output %d: storage does not hold the domain in dim %d", x, d);
+  }
+  // alias: an output's written bytes may not meet any input's storage or another output
+  for (int x = 0; x < n_out; ++x) {
+    uintptr_t olo, ohi;
+    byte_span(out[x], lb, ub, es, olo, ohi);
+    for (int y = 0; y < n_in; ++y) {
+      int64_t slo[3], shi[3];
+      for (int d = 0; d < 3; ++d) { slo[d] = -in[y].origin[d]; shi[d] = in[y].size[d] - in[y].origin[d]; }
+      uintptr_t ilo, ihi;
+      byte_span(in[y], slo, shi, es, ilo, ihi);
+      if (olo <= ihi && ilo <= ohi) return fail(OEC_ERR_ALIAS, "output %d overlaps input %d", x, y);
+    }
+    for (int y = 0; y < x; ++y) {
+      uintptr_t plo, phi;
+      byte_span(out[y], lb, ub, es, plo, phi);
+      if (olo <= phi && plo <= ohi) return fail(OEC_ERR_ALIAS, "output %d overlaps output %d", x, y);
+    }
+  }
+  return OEC_OK;
+}
+
+int ensure_scratch(oec_program* p, size_t bytes) {
+  if (bytes == 0) return OEC_OK;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (p->scratch && p->scratch_bytes >= bytes && p->scratch_dev == dev) return OEC_OK;
+  if (p->scratch) {
+    int cur = dev;
+    cudaSetDevice(p->scratch_dev);
+    cudaFree(p->scratch);                    // waits for work that may still use it
+    cudaSetDevice(cur);
+    p->scratch = nullptr;
+    p->scratch_bytes = 0;
+  }
+  e = cudaMalloc(&p->scratch, bytes);
+  if (e != cudaSuccess) {
+    p->scratch = nullptr;
+    return cuda_fail(e, "cudaMalloc(scratch)");
+  }
+  p->scratch_bytes = bytes;
+  p->scratch_dev = dev;
+  return OEC_OK;
+}
+
+}  // namespace oec
+
+using namespace oec;
+
+extern "C" {
+
+const char* oec_last_error(void) { return g_err.c_str(); }
+
+int oec_program_create(const char* source, const oec_program_options* opts, oec_program_t* out) {
+  clear_error();
+  if (!source || !out) return fail(OEC_ERR_INVALID_ARG, "null source or output handle");
+  *out = nullptr;
+  const int dtype = opts ? opts->dtype : OEC_F64;
+  if (dtype != OEC_F32 && dtype != OEC_F64) return fail(OEC_ERR_DTYPE, "dtype must be OEC_F32 or OEC_F64");
+  oec_program* p = new (std::nothrow) oec_program();
+  if (!p) return fail(OEC_ERR_INVALID_ARG, "out of host memory");
+  std::string err;
+  if (!parse(source, p->ir, err)) {
+    delete p;
+    return fail(OEC_ERR_PARSE, "%s", err.c_str());
+  }
+  p->dtype = dtype;
+  p->kind = OEC_KIND_GENERIC;
+  if (!(opts && (opts->flags & OEC_OPT_GENERIC))) {
+    const std::string c = canonical(p->ir);
+    for (int k = 1; k < 4; ++k)
+      if (c == builtin_canon(k)) p->kind = k;
+  }
+  p->sched = default_schedule(p->kind);
+  *out = p;
+  return OEC_OK;
+}
+
+void oec_program_destroy(oec_program_t p) {
+  if (!p) return;
+  if (p->scratch) {
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(p->scratch_dev);
+    cudaFree(p->scratch);
+    cudaSetDevice(cur);
+  }
+  generic_release(p);
+  delete p;
+}
+
+int oec_program_get_info(oec_program_t p, oec_program_info* info) {
+  clear_error();
+  if (!p || !info) return fail(OEC_ERR_INVALID_ARG, "null argument");
+  info->kind = p->kind;
+  info->n_inputs = (int)p->ir.inputs.size();
+  info->n_outputs = (int)p->ir.outputs.size();
+  info->n_params = (int)p->ir.params.size();
+  info->n_stages = (int)p->ir.stmts.size();
+  info->dtype = p->dtype;
+  return OEC_OK;
+}
+
+int oec_program_input_name(oec_program_t p, int index, char* buf, int len) {
+  clear_error();
+  if (!p || !buf || len < 1) return fail(OEC_ERR_INVALID_ARG, "null argument");
+  if (index < 0 || index >= (int)p->ir.inputs.size()) return fail(OEC_ERR_INVALID_ARG, "input index out of range");
+  std::snprintf(buf, (size_t)len, "%s", p->ir.values[p->ir.inputs[index]].name.c_str());
+  return OEC_OK;
+}
+
+int oec_program_input_range(oec_program_t p, int index, const int64_t lb[3], const int64_t ub[3], int64_t lo[3],
+                            int64_t hi[3]) {
+  clear_error();
+  if (!p || !lb || !ub || !lo || !hi) return fail(OEC_ERR_INVALID_ARG, "null argument");
+  if (index < 0 || index >= (int)p->ir.inputs.size()) return fail(OEC_ERR_INVALID_ARG, "input index out of range");
+  std::vector<Box> r;
+  std::string err;
+  if (!infer_ranges(p->ir, lb, ub, r, err)) return fail(OEC_ERR_SHAPE, "%s", err.c_str());
+  const Box& b = r[p->ir.inputs[index]];
+  for (int d = 0; d < 3; ++d) {
+    lo[d] = b.valid ? b.lo[d] : lb[d];
+    hi[d] = b.valid ? b.hi[d] : lb[d];
+  }
+  return OEC_OK;
+}
+
+int oec_program_set_schedule(oec_program_t p, const oec_schedule* s) {
+  clear_error();
+  if (!p || !s) return fail(OEC_ERR_INVALID_ARG, "null argument");
+  std::string why;
+  if (!schedule_ok(p->kind, *s, why)) return fail(OEC_ERR_UNSUPPORTED, "schedule: %s", why.c_str());
+  p->sched = *s;
+  return OEC_OK;
+}
+
+int oec_program_get_schedule(oec_program_t p, oec_schedule* s) {
+  clear_error();
+  if (!p || !s) return fail(OEC_ERR_INVALID_ARG, "null argument");
+  *s = p->sched;
+  return OEC_OK;
+}
+
+int oec_program_algorithmic_bytes(oec_program_t p, const int64_t lb[3], const int64_t ub[3], int64_t* bytes) {
+  clear_error();
+  if (!p || !lb || !ub || !bytes) return fail(OEC_ERR_INVALID_ARG, "null argument");
+  std::vector<Box> r;
+  std::string err;
+  if (!infer_ranges(p->ir, lb, ub, r, err)) return fail(OEC_ERR_SHAPE, "%s", err.c_str());
+  int64_t elems = 0;
+  for (int v : p->ir.inputs) elems += r[v].volume();
+  int64_t dom = 1;
+  for (int d = 0; d < 3; ++d) dom *= std::max<int64_t>(0, ub[d] - lb[d]);
+  elems += dom * (int64_t)p->ir.outputs.size();
+  *bytes = elems * (int64_t)elem_size(p->dtype);
+  return OEC_OK;
+}
+
+int oec_program_apply(oec_program_t p, const oec_field_desc* in, int n_in, const oec_field_desc* out, int n_out,
+                      const int64_t lb[3], const int64_t ub[3], const int64_t halo[3], const double* params,
+                      int n_params, void* cuda_stream) {
+  clear_error();
+  if (!p || !lb || !ub || !halo) return fail(OEC_ERR_INVALID_ARG, "null argument");
+  const Program& ir = p->ir;
+  if (n_in != (int)ir.inputs.size() || (n_in && !in))
+    return fail(OEC_ERR_INVALID_ARG, "program has %zu inputs, got %d", ir.inputs.size(), n_in);
+  if (n_out != (int)ir.outputs.size() || !out)
+    return fail(OEC_ERR_INVALID_ARG, "program has %zu outputs, got %d", ir.outputs.size(), n_out);
+  if (n_params != (int)ir.params.size() || (n_params && !params))
+    return fail(OEC_ERR_INVALID_ARG, "program has %zu params, got %d", ir.params.size(), n_params);
+  for (int d = 0; d < 3; ++d) {
+    if (ub[d] < lb[d]) return fail(OEC_ERR_INVALID_ARG, "inverted domain in dim %d", d);
+    if (halo[d] < 0) return fail(OEC_ERR_INVALID_ARG, "negative halo");
+    if (ub[d] - lb[d] > (1 << 30)) return fail(OEC_ERR_UNSUPPORTED, "domain extent above 2^30");
+  }
+  if (ub[0] == lb[0] || ub[1] == lb[1] || ub[2] == lb[2]) return OEC_OK;   // empty domain: nothing to do
+  std::vector<Box> ranges;
+  int rc = validate_fields(p, in, n_in, out, n_out, lb, ub, halo, ranges);
+  if (rc) return rc;
+  return dispatch_apply(p, in, out, lb, ub, params, (cudaStream_t)cuda_stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,47 @@
+// api_internal.h - the program handle and helpers shared by the ABI sources.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/oec.h"
+#include "ir.h"
+
+struct oec_generic_state;   // generic code generator state (codegen.cpp)
+
+struct oec_program {
+  oec::Program ir;
+  int dtype = OEC_F64;
+  int kind = OEC_KIND_GENERIC;
+  oec_schedule sched{};
+  void* scratch = nullptr;       // library-owned temporaries (device memory)
+  size_t scratch_bytes = 0;
+  int scratch_dev = -1;
+  oec_generic_state* gen = nullptr;
+};
+
+namespace oec {
+
+int fail(int code, const char* fmt, ...);
+void clear_error();
+int cuda_fail(cudaError_t e, const char* where);
+size_t elem_size(int dtype);
+oec_schedule default_schedule(int kind);
+bool schedule_ok(int kind, const oec_schedule& s, std::string& why);
+int ensure_scratch(oec_program* p, size_t bytes);
+int validate_fields(const oec_program* p, const oec_field_desc* in, int n_in, const oec_field_desc* out, int n_out,
+                    const int64_t lb[3], const int64_t ub[3], const int64_t halo[3], std::vector<Box>& ranges);
+
+// dispatch.cpp: run a validated apply
+int dispatch_apply(oec_program* p, const oec_field_desc* in, const oec_field_desc* out, const int64_t lb[3],
+                   const int64_t ub[3], const double* params, cudaStream_t st);
+
+// codegen.cpp: generic programs
+bool generic_schedule_ok(const oec_schedule& s, std::string& why);
+void generic_release(oec_program* p);
+int generic_apply(oec_program* p, const oec_field_desc* in, const oec_field_desc* out, const int64_t lb[3],
+                  const int64_t ub[3], const double* params, cudaStream_t st);
+
+}  // namespace oec

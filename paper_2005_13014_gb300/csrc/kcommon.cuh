@@ -1,0 +1,35 @@
+// kcommon.cuh - helpers shared by the hand-written stencil kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace oec {
+
+// Read-only load through the non-coherent path (inputs never alias outputs,
+// paper §IV, so the texture/L1 path is safe).
+template <typename T>
+__device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
+
+// Stage bodies of the horizontal-diffusion program, written once and used by
+// every kernel variant (fused, unfused, batched, and inside the column sweep).
+// Laplacian: 4*c - w - e - s - n, in that order.
+template <typename T>
+__device__ __forceinline__ T hd_lap(T c, T w, T e, T s, T n) {
+  return T(4) * c - w - e - s - n;
+}
+// Flux with the sign limiter: 0 where the flux points down the input gradient.
+template <typename T>
+__device__ __forceinline__ T hd_flux(T lap_hi, T lap_lo, T in_hi, T in_lo) {
+  T f = lap_hi - lap_lo;
+  return (f * (in_hi - in_lo) > T(0)) ? T(0) : f;
+}
+// Output: in - coeff*((flx - flx(i-1)) + (fly - fly(j-1))).
+template <typename T>
+__device__ __forceinline__ T hd_out(T in, T coeff, T flx, T flx_m, T fly, T fly_m) {
+  return in - coeff * ((flx - flx_m) + (fly - fly_m));
+}
+
+__host__ __device__ inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+}  // namespace oec

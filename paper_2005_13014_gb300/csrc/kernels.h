@@ -1,0 +1,52 @@
+// kernels.h - host-side interface of the hand-written kernels. Every launcher
+// takes pointers already offset to the domain's lower corner (logical lb), the
+// domain extents, the fields' shared j/k strides (elements), a scratch buffer
+// of at least *_scratch_bytes() bytes (may be null when that is 0) and the
+// caller's stream, and returns the launch status.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+#include "../../include/oec.h"
+
+namespace oec {
+
+struct Dom {
+  int ni, nj, nk;        // domain extents
+  int64_t sj, sk;        // element strides shared by all fields
+};
+
+// ---- horizontal diffusion: in, coeff -> out --------------------------------
+bool hdiff_schedule_ok(const oec_schedule& s, std::string& why);
+size_t hdiff_scratch_bytes(const oec_schedule& s, int dtype, const Dom& d);
+cudaError_t hdiff_launch(const oec_schedule& s, int dtype, const Dom& d, const void* in, const void* coeff,
+                         void* out, void* scratch, cudaStream_t st);
+// Fused schedules only: output written with its own strides (osj, osk).
+cudaError_t hdiff_launch_strided(const oec_schedule& s, int dtype, const Dom& d, const void* in, const void* coeff,
+                                 void* out, int64_t osj, int64_t osk, cudaStream_t st);
+
+// ---- horizontal diffusion of u, v + vertical advection (Thomas) -------------
+bool hdiff_vadvc_schedule_ok(const oec_schedule& s, std::string& why);
+size_t hdiff_vadvc_scratch_bytes(const oec_schedule& s, int dtype, const Dom& d);
+cudaError_t hdiff_vadvc_launch(const oec_schedule& s, int dtype, const Dom& d, const void* u, const void* v,
+                               const void* w, const void* coeff, void* u_out, void* v_out, double dtr,
+                               void* scratch, cudaStream_t st);
+
+// ---- fastwaves-like program -------------------------------------------------
+struct FastwavesPtrs {
+  const void* u_in; const void* v_in; const void* utens; const void* vtens; const void* pp;
+  const void* rho; const void* wgtfac; const void* hhl; const void* fx;
+  void* u_out; void* v_out;
+};
+bool fastwaves_schedule_ok(const oec_schedule& s, std::string& why);
+size_t fastwaves_scratch_bytes(const oec_schedule& s, int dtype, const Dom& d);
+cudaError_t fastwaves_launch(const oec_schedule& s, int dtype, const Dom& d, const FastwavesPtrs& f, double dt,
+                             double alpha, void* scratch, cudaStream_t st);
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace oec

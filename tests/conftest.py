@@ -23,3 +23,19 @@ def rel_err(x, r):
 
 # tolerances on the normwise relative error against the FP64 oracle
 TOL = {"f64": 1e-13, "f32": 1e-5}
+
+
+@pytest.fixture(scope="session")
+def liboec():
+    """Build (if stale) and load the CUDA library; no GPU is needed to load it."""
+    from paper_2005_13014_gb300 import build, _lib
+    build.build()
+    return _lib.lib()
+
+
+def has_gpu():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False

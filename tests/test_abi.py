@@ -1,0 +1,123 @@
+"""Host-side tests of liboec's C ABI: every declared symbol is exported, the
+builtin programs are recognised by structure, shape inference agrees with the
+oracle's independent implementation (paper §V-B), and validation rejects bad
+calls before any GPU work (fake device pointers are never dereferenced)."""
+
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from oracle import program as OP
+from paper_2005_13014_gb300 import _lib as L
+from paper_2005_13014_gb300 import inputs, programs
+
+
+def test_every_declared_symbol_is_exported(liboec):
+    names = L.declared_symbols()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(liboec, n), n
+
+
+def _prog(src, dtype="f64", generic=False):
+    from paper_2005_13014_gb300.api import Program
+    return Program(src, dtype=dtype, generic=generic)
+
+
+def test_builtin_programs_recognised(liboec):
+    assert _prog(programs.HDIFF).kind == "hdiff"
+    assert _prog(programs.HDIFF_VADVC).kind == "hdiff_vadvc"
+    assert _prog(programs.FASTWAVES, "f32").kind == "fastwaves"
+    assert _prog(programs.HDIFF, generic=True).kind == "generic"
+    renamed = (programs.HDIFF.replace("lap", "L0").replace("coeff", "kappa").replace("flx", "fx")
+               .replace(" in", " phi").replace("(in", "(phi").replace("*in", "*phi").replace(",in", ",phi"))
+    assert _prog("# renamed\n" + renamed).kind == "hdiff"
+    changed = programs.HDIFF.replace("4.0*in", "4.5*in")
+    assert _prog(changed).kind == "generic"
+
+
+def test_parse_errors_are_reported(liboec):
+    for bad in ["input a\nstage b = a[1,0]\noutput b", "input a\nstage b = c\noutput b", "input a\nstage b = a\n",
+                "input a\nstage b = a\nstage b = a\noutput b", "input a\nstage b = a $\noutput b"]:
+        with pytest.raises(L.OecError) as e:
+            _prog(bad)
+        assert e.value.name == "PARSE"
+        assert "line" in str(e.value)
+
+
+def _oracle_ranges(src, lb, ub):
+    prog = OP.parse(src)
+    r = OP.infer_ranges(prog, lb, ub)
+    out = []
+    for n in prog.inputs:
+        if n in r:
+            out.append((tuple(x[0] for x in r[n]), tuple(x[1] for x in r[n])))
+        else:
+            out.append((tuple(lb), tuple(lb)))
+    return out
+
+
+@pytest.mark.parametrize("src", [programs.HDIFF, programs.HDIFF_VADVC, programs.FASTWAVES]
+                         + [inputs.random_dag(s) for s in range(10000, 10030)])
+def test_input_ranges_match_oracle_shape_inference(liboec, src):
+    p = _prog(src)
+    lb, ub = (3, -2, 1), (40, 17, 9)
+    want = _oracle_ranges(src, lb, ub)
+    for x in range(p.n_inputs):
+        assert p.input_range(x, lb, ub) == want[x]
+
+
+def test_algorithmic_bytes_hdiff_64():
+    p = _prog(programs.HDIFF)
+    # in over [-2,66)^2 x 60, coeff and out over the 64x64x60 interior
+    assert p.algorithmic_bytes((0, 0, 0), (64, 64, 60)) == 8 * (68 * 68 * 60 + 2 * 64 * 64 * 60)
+
+
+def _fake(addr, shape, origin, dtype=L.F64):
+    d = L.FieldDesc()
+    d.data = addr
+    d.dtype = dtype
+    d.ndim = 3
+    ni, nj, nk = shape
+    d.size = L.I64x3(ni, nj, nk)
+    d.stride = L.I64x3(1, ni, ni * nj)
+    d.origin = L.I64x3(*origin)
+    return d
+
+
+def _apply(p, ins, outs, lb, ub, halo, params=()):
+    a = (L.FieldDesc * len(ins))(*ins)
+    b = (L.FieldDesc * len(outs))(*outs)
+    par = (C.c_double * max(1, len(params)))(*params)
+    return L.lib().oec_program_apply(p.handle, a, len(ins), b, len(outs), L.I64x3(*lb), L.I64x3(*ub),
+                                     L.I64x3(*halo), par, len(params), None)
+
+
+def test_validation_errors_without_gpu(liboec):
+    p = _prog(programs.HDIFF)
+    n, h = (16, 12, 5), 2
+    shp = (n[0] + 2 * h, n[1] + 2 * h, n[2] + 2 * h)
+    GB = 1 << 30
+    fin, fco, fout = _fake(1 * GB, shp, (h, h, h)), _fake(2 * GB, shp, (h, h, h)), _fake(3 * GB, shp, (h, h, h))
+    lb, ub = (0, 0, 0), n
+    assert _apply(p, [fin, fco], [fout], lb, ub, (1, 1, 0)) == -4            # HALO: needs 2
+    small = _fake(1 * GB, (n[0] + 2, n[1] + 4, n[2] + 4), (1, 2, 2))
+    assert _apply(p, [small, fco], [fout], lb, ub, (2, 2, 0)) == -3          # SHAPE
+    assert _apply(p, [fin, fco], [_fake(1 * GB, shp, (h, h, h))], lb, ub, (2, 2, 0)) == -5   # ALIAS
+    assert _apply(p, [fin, fco], [_fake(3 * GB, shp, (h, h, h), L.F32)], lb, ub, (2, 2, 0)) == -6   # DTYPE
+    assert _apply(p, [fin], [fout], lb, ub, (2, 2, 0)) == -1                 # wrong input count
+    assert _apply(p, [fin, fco], [fout], (0, 0, 0), (16, 12, 0), (2, 2, 0)) == 0   # empty domain: no work
+    assert _apply(p, [fin, fco], [fout], (0, 5, 0), (16, 4, 5), (2, 2, 0)) == -1   # inverted
+    msg = L.lib().oec_last_error().decode()
+    assert "inverted" in msg
+
+
+def test_bad_schedule_rejected(liboec):
+    p = _prog(programs.HDIFF)
+    with pytest.raises(L.OecError):
+        p.set_schedule(fusion=0, staging=1, tile_i=48, tile_j=4)
+    with pytest.raises(L.OecError):
+        p.set_schedule(fusion=0, staging=0, tile_i=64, tile_j=3, unroll=2)
+    p.set_schedule(fusion=0, staging=0, tile_i=64, tile_j=4, unroll=2)
+    assert p.schedule["unroll"] == 2

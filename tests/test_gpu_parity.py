@@ -1,0 +1,188 @@
+"""GPU parity: every hand-written kernel variant against the FP64 oracle,
+element by element, through the C ABI. Sizes span several tiles with ragged
+tails, and the full workload sizes; tolerances are the normwise relative
+errors 1e-13 (FP64) and 1e-5 (FP32 fields, oracle fed the FP32-rounded inputs).
+Poisoned halos check that no kernel reads outside the inferred input ranges or
+writes outside the domain."""
+
+import numpy as np
+import pytest
+
+from conftest import TOL, rel_err
+from oracle import stencils as S
+from paper_2005_13014_gb300 import inputs, programs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _round(arr, dtype):
+    return arr.astype(np.float32).astype(np.float64) if dtype == "f32" else arr
+
+
+def _dev(arr, h, dtype, align=0):
+    from paper_2005_13014_gb300.api import device_field
+    return device_field(arr, h, dtype, align_bytes=align)
+
+
+def _prog(src, dtype, sched=None):
+    from paper_2005_13014_gb300.api import Program
+    p = Program(src, dtype)
+    if sched:
+        p.set_schedule(**sched)
+    return p
+
+
+HDIFF_SCHEDS = (
+    [dict(fusion=1)]
+    + [dict(fusion=0, staging=1, tile_i=a, tile_j=b, k_chunk=kc)
+       for (a, b) in [(32, 4), (32, 8), (64, 2), (64, 4), (64, 8), (128, 2), (128, 4)] for kc in (0, 3)]
+    + [dict(fusion=0, staging=0, tile_i=a, tile_j=b, unroll=u, k_chunk=kc)
+       for (a, b, u) in [(32, 4, 1), (64, 4, 2), (32, 8, 4), (128, 4, 4), (64, 1, 1)] for kc in (0, 2)]
+)
+
+
+def _hdiff_case(n, h, dtype, sched, align=0, lb=None, ub=None, poison=True):
+    f = inputs.hdiff_fields(*n, h, seed=31)
+    fin = _round(f["in"], dtype)
+    fco = _round(f["coeff"], dtype)
+    lb = lb or (0, 0, 0)
+    ub = ub or n
+    if poison:
+        # NaN outside the inferred input range: [lb-2, ub+2) in i/j for in, [lb, ub) for coeff
+        pin = np.full_like(fin, np.nan)
+        sl = (slice(h + lb[2], h + ub[2]), slice(h + lb[1] - 2, h + ub[1] + 2), slice(h + lb[0] - 2, h + ub[0] + 2))
+        pin[sl] = fin[sl]
+        pco = np.full_like(fco, np.nan)
+        sl2 = (slice(h + lb[2], h + ub[2]), slice(h + lb[1], h + ub[1]), slice(h + lb[0], h + ub[0]))
+        pco[sl2] = fco[sl2]
+    else:
+        pin, pco = fin, fco
+    p = _prog(programs.HDIFF, dtype, sched)
+    din, dco = _dev(pin, h, dtype, align), _dev(pco, h, dtype, align)
+    sentinel = 12345.0
+    dout = _dev(np.full_like(fin, sentinel), h, dtype, align)
+    p.apply([din, dco], [dout], lb, ub, (h, h, h))
+    torch.cuda.synchronize()
+    full = dout.tensor.cpu().numpy().astype(np.float64)
+    oi, oj, ok = dout.origin
+    got = full[ok + lb[2]:ok + ub[2], oj + lb[1]:oj + ub[1], oi + lb[0]:oi + ub[0]]
+    ref = S.hdiff(S.Grid.storage(fin, h), S.Grid.storage(fco, h), lb, ub)
+    assert np.all(np.isfinite(got))
+    mask = np.ones(full.shape, bool)
+    mask[ok + lb[2]:ok + ub[2], oj + lb[1]:oj + ub[1], oi + lb[0]:oi + ub[0]] = False
+    assert np.all(full[mask] == sentinel), "write outside the domain"
+    return rel_err(got, ref)
+
+
+@pytest.mark.parametrize("sched", HDIFF_SCHEDS, ids=str)
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_hdiff_ragged(sched, dtype):
+    assert _hdiff_case((37, 29, 5), 2, dtype, sched) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("sched", [dict(fusion=1), dict(fusion=0, staging=1, tile_i=64, tile_j=4, k_chunk=2),
+                                   dict(fusion=0, staging=0, tile_i=64, tile_j=4, unroll=2)], ids=str)
+def test_hdiff_config_64x64x60_f64(sched):
+    assert _hdiff_case((64, 64, 60), 2, "f64", sched) <= TOL["f64"]
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_hdiff_256x256x80_halo3(dtype):
+    assert _hdiff_case((256, 256, 80), 3, dtype, None, poison=False) <= TOL[dtype]
+
+
+def test_hdiff_subdomain_and_aligned_rows():
+    assert _hdiff_case((40, 30, 6), 3, "f64", None, lb=(5, 3, 1), ub=(33, 27, 5)) <= TOL["f64"]
+    assert _hdiff_case((40, 30, 6), 2, "f32", dict(fusion=0, staging=0, tile_i=32, tile_j=4, unroll=4),
+                       align=128) <= TOL["f32"]
+
+
+def test_hdiff_single_point_and_line():
+    assert _hdiff_case((1, 1, 1), 2, "f64", None) <= TOL["f64"]
+    assert _hdiff_case((130, 1, 2), 2, "f64", dict(fusion=0, staging=0, tile_i=64, tile_j=4, unroll=4)) <= TOL["f64"]
+
+
+# ---------------------------------------------------------------- hdiff+vadvc
+
+HV_SCHEDS = [dict(fusion=1)] + [dict(fusion=0, staging=1, tile_i=a, tile_j=b)
+                                for a, b in [(32, 1), (32, 2), (32, 4), (64, 1), (64, 2), (128, 1)]]
+
+
+def _hv_case(n, h, dtype, sched, dtr=2.0):
+    f = inputs.hdiff_vadvc_fields(*n, h, seed=32)
+    g = {k: _round(v, dtype) for k, v in f.items()}
+    p = _prog(programs.HDIFF_VADVC, dtype, sched)
+    d = {k: _dev(v, h, dtype) for k, v in g.items()}
+    uo = _dev(np.full_like(g["u"], 777.0), h, dtype)
+    vo = _dev(np.full_like(g["u"], 777.0), h, dtype)
+    p.apply([d["u"], d["v"], d["w"], d["coeff"]], [uo, vo], (0, 0, 0), n, (h, h, h), [dtr])
+    torch.cuda.synchronize()
+    G = {k: S.Grid.storage(v, h) for k, v in g.items()}
+    ru, rv = S.hdiff_vadvc(G["u"], G["v"], G["w"], G["coeff"], (0, 0, 0), n, dtr)
+    gu = uo.interior((0, 0, 0), n).cpu().numpy().astype(np.float64)
+    gv = vo.interior((0, 0, 0), n).cpu().numpy().astype(np.float64)
+    full = uo.tensor.cpu().numpy()
+    oi, oj, ok = uo.origin
+    mask = np.ones(full.shape, bool)
+    mask[ok:ok + n[2], oj:oj + n[1], oi:oi + n[0]] = False
+    assert np.all(full[mask] == 777.0)
+    return max(rel_err(gu, ru), rel_err(gv, rv))
+
+
+@pytest.mark.parametrize("sched", HV_SCHEDS, ids=str)
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_hdiff_vadvc_ragged(sched, dtype):
+    assert _hv_case((37, 23, 11), 3, dtype, sched) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("nk", [1, 2, 3])
+def test_hdiff_vadvc_short_columns(nk):
+    assert _hv_case((33, 5, nk), 3, "f64", None) <= TOL["f64"]
+    assert _hv_case((33, 5, nk), 3, "f64", dict(fusion=1)) <= TOL["f64"]
+
+
+@pytest.mark.parametrize("sched", [None, dict(fusion=1)], ids=str)
+def test_hdiff_vadvc_config_128x128x80_f64(sched):
+    assert _hv_case((128, 128, 80), 3, "f64", sched) <= TOL["f64"]
+
+
+def test_hdiff_vadvc_config_128x128x137_f32():
+    assert _hv_case((128, 128, 137), 3, "f32", None) <= TOL["f32"]
+
+
+# ------------------------------------------------------------------ fastwaves
+
+FW_SCHEDS = ([dict(fusion=1)]
+             + [dict(fusion=0, staging=1, tile_i=a, tile_j=b, k_chunk=kc)
+                for (a, b) in [(32, 4), (32, 8), (64, 2), (64, 4), (128, 2)] for kc in (0, 3)]
+             + [dict(fusion=0, staging=0, tile_i=a, tile_j=b, unroll=u)
+                for (a, b, u) in [(32, 4, 1), (64, 4, 2), (32, 8, 4), (128, 2, 4)]])
+
+
+def _fw_case(n, h, dtype, sched, dt=0.5, alpha=0.0625):
+    f = inputs.fastwaves_fields(*n, h, seed=33)
+    g = {k: _round(v, dtype) for k, v in f.items()}
+    p = _prog(programs.FASTWAVES, dtype, sched)
+    d = [_dev(g[name], h, dtype) for name in inputs.FASTWAVES_NAMES]
+    uo = _dev(np.full_like(g["pp"], 555.0), h, dtype)
+    vo = _dev(np.full_like(g["pp"], 555.0), h, dtype)
+    p.apply(d, [uo, vo], (0, 0, 0), n, (h, h, h), [dt, alpha])
+    torch.cuda.synchronize()
+    G = {k: S.Grid.storage(v, h) for k, v in g.items()}
+    ru, rv = S.fastwaves(G, (0, 0, 0), n, dt, alpha)
+    gu = uo.interior((0, 0, 0), n).cpu().numpy().astype(np.float64)
+    gv = vo.interior((0, 0, 0), n).cpu().numpy().astype(np.float64)
+    return max(rel_err(gu, ru), rel_err(gv, rv))
+
+
+@pytest.mark.parametrize("sched", FW_SCHEDS, ids=str)
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_fastwaves_ragged(sched, dtype):
+    assert _fw_case((37, 29, 7), 3, dtype, sched) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_fastwaves_config_256x256x80(dtype):
+    assert _fw_case((256, 256, 80), 3, dtype, None) <= TOL[dtype]
