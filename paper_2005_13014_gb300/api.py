@@ -53,11 +53,11 @@ class Field:
         return self.tensor[ok + lb[2]:ok + ub[2], oj + lb[1]:oj + ub[1], oi + lb[0]:oi + ub[0]]
 
 
-def device_field(arr: np.ndarray, h, dtype="f64", device="cuda", align_bytes=0, pad_i=0):
+def device_field(arr: np.ndarray, h, dtype="f64", device="cuda", align_bytes=0, pad_i=0, pad_value=0.0):
     """Copy a host storage array [k, j, i] with halo ``h`` (int or (hi, hj, hk))
     to the device. With ``align_bytes`` > 0 the i-rows are padded in front so
     that the first interior point of every row starts on that boundary; ``pad_i``
-    extra elements are appended to every row."""
+    extra elements are appended to every row; padding holds ``pad_value``."""
     torch = _torch()
     hi = h if np.isscalar(h) else h[0]
     hj = h if np.isscalar(h) else h[1]
@@ -72,7 +72,7 @@ def device_field(arr: np.ndarray, h, dtype="f64", device="cuda", align_bytes=0, 
     row = front + ni + pad_i
     if align_bytes:
         row = -(-row // (align_bytes // es)) * (align_bytes // es)
-    host = np.zeros((nk, nj, row), dtype=np.float64 if dtype == "f64" else np.float32)
+    host = np.full((nk, nj, row), pad_value, dtype=np.float64 if dtype == "f64" else np.float32)
     host[:, :, front:front + ni] = arr
     t = torch.from_numpy(host).to(device)
     return Field(t, (front + hi, hj, hk))

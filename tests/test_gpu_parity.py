@@ -21,9 +21,9 @@ def _round(arr, dtype):
     return arr.astype(np.float32).astype(np.float64) if dtype == "f32" else arr
 
 
-def _dev(arr, h, dtype, align=0):
+def _dev(arr, h, dtype, align=0, pad_value=0.0):
     from paper_2005_13014_gb300.api import device_field
-    return device_field(arr, h, dtype, align_bytes=align)
+    return device_field(arr, h, dtype, align_bytes=align, pad_value=pad_value)
 
 
 def _prog(src, dtype, sched=None):
@@ -62,7 +62,7 @@ def _hdiff_case(n, h, dtype, sched, align=0, lb=None, ub=None, poison=True):
     p = _prog(programs.HDIFF, dtype, sched)
     din, dco = _dev(pin, h, dtype, align), _dev(pco, h, dtype, align)
     sentinel = 12345.0
-    dout = _dev(np.full_like(fin, sentinel), h, dtype, align)
+    dout = _dev(np.full_like(fin, sentinel), h, dtype, align, pad_value=sentinel)
     p.apply([din, dco], [dout], lb, ub, (h, h, h))
     torch.cuda.synchronize()
     full = dout.tensor.cpu().numpy().astype(np.float64)
