@@ -196,6 +196,35 @@ OEC_API int oec_program_apply(oec_program_t p, const oec_field_desc* in, int n_i
  */
 OEC_API int oec_program_algorithmic_bytes(oec_program_t p, const int64_t lb[3], const int64_t ub[3], int64_t* bytes);
 
+/*
+ * hdiff+vadvc without any device allocation. There is no counterpart in the
+ * paper; this entry point exists for callers that cannot allocate device
+ * memory while they run the program: code running while its stream is being
+ * captured into a CUDA graph (an allocation is not captured work and can
+ * break the capture), code that must stay inside a device-memory budget owned
+ * by another allocator, and latency-critical loops where cudaMalloc/cudaFree
+ * may synchronise the device. oec_program_apply allocates scratch on its first
+ * apply at a new size; this call never does: it runs the fused column sweep
+ * with its Thomas scratch in a fixed 32 MiB array inside the library's device
+ * image (held on every GPU where the library's device code is loaded, until
+ * the process exits).
+ *   dtype   OEC_F32 or OEC_F64 (all six fields)
+ *   in[4]   u, v, w, coeff; u and v must hold [lb-2, ub+2) in i and j, w must
+ *           hold [lb, ub+1) in i, coeff the domain
+ *   out[2]  u_out, v_out, written over [lb, ub)
+ *   dtr     the scalar parameter of the vertical advection
+ * Limit: 24 bytes of scratch per grid point, so at most 1,398,101 points
+ * (OEC_ERR_UNSUPPORTED above that). The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current; make
+ * that first call before any stream capture. All calls share the one array and
+ * it keeps the last call's contents (nothing in it needs to start at zero:
+ * every value is written before it is read): calls whose kernels overlap on
+ * the GPU race and corrupt each other's results, so serialise them (one
+ * stream, or events). Returns as oec_program_apply does.
+ */
+OEC_API int oec_hdiff_vadvc_apply_noalloc(int32_t dtype, const oec_field_desc* in, const oec_field_desc* out,
+                                          const int64_t lb[3], const int64_t ub[3], double dtr, void* cuda_stream);
+
 /* Message of the last error on the calling thread ("" if none). The pointer
  * stays valid until the thread's next liboec call. */
 OEC_API const char* oec_last_error(void);

@@ -77,6 +77,8 @@ def lib():
         "oec_program_apply": (C.c_int, [P, C.POINTER(FieldDesc), C.c_int, C.POINTER(FieldDesc), C.c_int,
                                         I64x3, I64x3, I64x3, C.POINTER(C.c_double), C.c_int, P]),
         "oec_program_algorithmic_bytes": (C.c_int, [P, I64x3, I64x3, C.POINTER(C.c_int64)]),
+        "oec_hdiff_vadvc_apply_noalloc": (C.c_int, [C.c_int32, C.POINTER(FieldDesc), C.POINTER(FieldDesc), I64x3,
+                                                    I64x3, C.c_double, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
