@@ -89,8 +89,19 @@ typedef struct oec_schedule {
   int32_t tile_j;        /* CTA tile extent along j, in points (1..16)                   */
   int32_t unroll;        /* points per thread along the unroll dimension (1, 2 or 4)     */
   int32_t k_chunk;       /* levels per CTA for horizontal programs (0 = whole column)    */
-  int32_t reserved[6];   /* zero                                                          */
+  int32_t arith;         /* OEC_ARITH_*                                                   */
+  int32_t reserved[5];   /* zero                                                          */
 } oec_schedule;
+
+/* Arithmetic of a schedule. OEC_ARITH_NATIVE evaluates in the dtype's own
+ * IEEE arithmetic (FP32 programs keep their column recurrence in native FP64).
+ * OEC_ARITH_DOUBLE_FLOAT evaluates FP64 values as pairs of floats (~48
+ * significant bits, Dekker/Knuth error-free transformations) on the FP32 pipes,
+ * which GB300 runs ~70x faster than its FP64 pipe: for FP64 programs every
+ * operation, for FP32 programs the column recurrence. Results stay within the
+ * FP64 tolerance (normwise 1e-13) for values of magnitude 2^-74..2^128. */
+#define OEC_ARITH_NATIVE 0
+#define OEC_ARITH_DOUBLE_FLOAT 1
 
 /* ---- programs ----------------------------------------------------------- */
 typedef struct oec_program* oec_program_t;
@@ -195,6 +206,41 @@ OEC_API int oec_program_apply(oec_program_t p, const oec_field_desc* in, int n_i
  * kernel keeps them on chip). Errors: OEC_ERR_INVALID_ARG.
  */
 OEC_API int oec_program_algorithmic_bytes(oec_program_t p, const int64_t lb[3], const int64_t ub[3], int64_t* bytes);
+
+/* ---- batched ensembles (no counterpart in the paper's compiler; the paper's
+ * programs run one domain per launch) ------------------------------------- */
+typedef struct oec_batch* oec_batch_t;
+
+typedef struct oec_batch_member {
+  const oec_field_desc* in;    /* the program's inputs for this member (device memory)  */
+  const oec_field_desc* out;   /* its outputs                                           */
+  int64_t lb[3], ub[3];        /* the member's domain [lb, ub)                          */
+  int64_t halo[3];             /* valid cells around the domain (as oec_program_apply)  */
+} oec_batch_member;
+
+/*
+ * Prepare one launch over an ensemble of domains of different sizes (currently
+ * hdiff+vadvc programs): every member is validated as oec_program_apply would
+ * validate it, the members' column tiles become one work list (tallest
+ * columns first), and a persistent kernel - one CTA per resident slot on every
+ * SM - pulls (member, tile) items from an atomic counter and runs the fused
+ * column sweep with the program's current schedule (tile shape, arithmetic).
+ * The counter reset and the launch are captured once into a CUDA graph.
+ * Device memory: the work table, the counter and per-CTA scratch, owned by the
+ * batch. The program and every member's fields must outlive the batch.
+ * params: the program's scalars. Errors: as oec_program_apply, and
+ * OEC_ERR_UNSUPPORTED for other program kinds.
+ */
+OEC_API int oec_batch_create(oec_program_t p, const oec_batch_member* members, int n_members, const double* params,
+                             int n_params, oec_batch_t* out);
+/* Launch the captured graph on cuda_stream (asynchronous). */
+OEC_API int oec_batch_apply(oec_batch_t b, void* cuda_stream);
+/* Launch the persistent kernel directly (no graph) on cuda_stream. */
+OEC_API int oec_batch_apply_direct(oec_batch_t b, void* cuda_stream);
+/* Work items (tiles) and persistent CTAs of a batch. */
+OEC_API int oec_batch_info(oec_batch_t b, int* n_items, int* n_ctas);
+/* Free the batch (NULL is a no-op); waits for its device work to finish. */
+OEC_API void oec_batch_destroy(oec_batch_t b);
 
 /*
  * hdiff+vadvc without any device allocation. There is no counterpart in the

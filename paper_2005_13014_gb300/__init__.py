@@ -10,7 +10,7 @@ from . import programs  # noqa: F401  (program texts; no compute)
 def __getattr__(name):
     # the binding is imported lazily so that `inputs` and `programs` load
     # without the CUDA library
-    if name in ("Program", "Field", "device_field"):
+    if name in ("Program", "Field", "Batch", "device_field"):
         from . import api
         return getattr(api, name)
     raise AttributeError(name)

@@ -15,6 +15,7 @@ ERRORS = {-1: "INVALID_ARG", -2: "PARSE", -3: "SHAPE", -4: "HALO", -5: "ALIAS", 
           -7: "UNSUPPORTED", -8: "COMPILE", -9: "CUDA", -10: "TIMEOUT"}
 F32, F64 = 0, 1
 FUSE_INLINE, FUSE_NONE = 0, 1
+ARITH_NATIVE, ARITH_DOUBLE_FLOAT = 0, 1
 STAGE_REGS, STAGE_SMEM = 0, 1
 KIND_NAMES = {0: "generic", 1: "hdiff", 2: "hdiff_vadvc", 3: "fastwaves"}
 
@@ -28,7 +29,7 @@ class FieldDesc(C.Structure):
 
 class Schedule(C.Structure):
     _fields_ = [("fusion", C.c_int32), ("staging", C.c_int32), ("tile_i", C.c_int32), ("tile_j", C.c_int32),
-                ("unroll", C.c_int32), ("k_chunk", C.c_int32), ("reserved", C.c_int32 * 6)]
+                ("unroll", C.c_int32), ("k_chunk", C.c_int32), ("arith", C.c_int32), ("reserved", C.c_int32 * 5)]
 
 
 class ProgramOptions(C.Structure):
@@ -38,6 +39,11 @@ class ProgramOptions(C.Structure):
 class ProgramInfo(C.Structure):
     _fields_ = [("kind", C.c_int32), ("n_inputs", C.c_int32), ("n_outputs", C.c_int32),
                 ("n_params", C.c_int32), ("n_stages", C.c_int32), ("dtype", C.c_int32)]
+
+
+class BatchMember(C.Structure):
+    _fields_ = [("in_", C.POINTER(FieldDesc)), ("out", C.POINTER(FieldDesc)), ("lb", I64x3), ("ub", I64x3),
+                ("halo", I64x3)]
 
 
 class OecError(RuntimeError):
@@ -79,6 +85,12 @@ def lib():
         "oec_program_algorithmic_bytes": (C.c_int, [P, I64x3, I64x3, C.POINTER(C.c_int64)]),
         "oec_hdiff_vadvc_apply_noalloc": (C.c_int, [C.c_int32, C.POINTER(FieldDesc), C.POINTER(FieldDesc), I64x3,
                                                     I64x3, C.c_double, P]),
+        "oec_batch_create": (C.c_int, [P, C.POINTER(BatchMember), C.c_int, C.POINTER(C.c_double), C.c_int,
+                                       C.POINTER(P)]),
+        "oec_batch_apply": (C.c_int, [P, P]),
+        "oec_batch_apply_direct": (C.c_int, [P, P]),
+        "oec_batch_info": (C.c_int, [P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+        "oec_batch_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)

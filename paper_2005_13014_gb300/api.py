@@ -116,10 +116,10 @@ class Program:
         s = L.Schedule()
         L.check(L.lib().oec_program_get_schedule(self._h, C.byref(s)))
         return {"fusion": s.fusion, "staging": s.staging, "tile_i": s.tile_i, "tile_j": s.tile_j,
-                "unroll": s.unroll, "k_chunk": s.k_chunk}
+                "unroll": s.unroll, "k_chunk": s.k_chunk, "arith": s.arith}
 
-    def set_schedule(self, fusion=0, staging=0, tile_i=64, tile_j=4, unroll=1, k_chunk=0):
-        s = L.Schedule(fusion, staging, tile_i, tile_j, unroll, k_chunk)
+    def set_schedule(self, fusion=0, staging=0, tile_i=64, tile_j=4, unroll=1, k_chunk=0, arith=0):
+        s = L.Schedule(fusion, staging, tile_i, tile_j, unroll, k_chunk, arith)
         L.check(L.lib().oec_program_set_schedule(self._h, C.byref(s)))
 
     def input_range(self, index, lb, ub):
@@ -144,3 +144,45 @@ class Program:
             stream = stream.cuda_stream
         L.check(L.lib().oec_program_apply(self._h, ins, len(inputs), outs, len(outputs), L.I64x3(*lb),
                                           L.I64x3(*ub), L.I64x3(*halo), par, len(params), C.c_void_p(stream)))
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return _torch().cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+
+
+class Batch:
+    """An ensemble of domains run by one persistent launch (replayed from a
+    CUDA graph). ``members``: list of (inputs, outputs, lb, ub, halo)."""
+
+    def __init__(self, program: Program, members, params=()):
+        self._h = None
+        self.program = program
+        self._keep = []
+        arr = (L.BatchMember * len(members))()
+        for x, (ins, outs, lb, ub, halo) in enumerate(members):
+            di = (L.FieldDesc * len(ins))(*[f.desc() for f in ins])
+            do = (L.FieldDesc * len(outs))(*[f.desc() for f in outs])
+            self._keep += [di, do, ins, outs]
+            arr[x].in_ = C.cast(di, C.POINTER(L.FieldDesc))
+            arr[x].out = C.cast(do, C.POINTER(L.FieldDesc))
+            arr[x].lb = L.I64x3(*lb)
+            arr[x].ub = L.I64x3(*ub)
+            arr[x].halo = L.I64x3(*halo)
+        par = (C.c_double * max(1, len(params)))(*params)
+        h = C.c_void_p()
+        L.check(L.lib().oec_batch_create(program.handle, arr, len(members), par, len(params), C.byref(h)))
+        self._h = h
+        ni, nc = C.c_int(), C.c_int()
+        L.check(L.lib().oec_batch_info(h, C.byref(ni), C.byref(nc)))
+        self.n_items, self.n_ctas = ni.value, nc.value
+
+    def apply(self, stream=None, graph=True):
+        fn = L.lib().oec_batch_apply if graph else L.lib().oec_batch_apply_direct
+        L.check(fn(self._h, C.c_void_p(_stream_handle(stream))))
+
+    def __del__(self):
+        if getattr(self, "_h", None) is not None:
+            L.lib().oec_batch_destroy(self._h)
+            self._h = None

@@ -63,17 +63,20 @@ oec_schedule default_schedule(int kind) {
       s.tile_i = 64;
       s.tile_j = 4;
       s.k_chunk = 2;
+      s.arith = OEC_ARITH_DOUBLE_FLOAT;
       break;
     case OEC_KIND_HDIFF_VADVC:
       s.staging = OEC_STAGE_SMEM;
-      s.tile_i = 32;
-      s.tile_j = 2;
+      s.tile_i = 16;
+      s.tile_j = 4;
+      s.arith = OEC_ARITH_DOUBLE_FLOAT;
       break;
     case OEC_KIND_FASTWAVES:
       s.staging = OEC_STAGE_REGS;
       s.tile_i = 64;
       s.tile_j = 4;
       s.unroll = 2;
+      s.arith = OEC_ARITH_DOUBLE_FLOAT;
       break;
     default:
       s.staging = OEC_STAGE_REGS;

@@ -1,0 +1,90 @@
+// arith.cuh - arithmetic policies of the hand-written kernels and the few
+// generic operations the stencil bodies need, for float, double and df64.
+//
+//   policy   storage S   stencil compute C   column recurrence R
+//   P32      float       float               double  (FP64 recurrence)
+//   P32D     float       float               df64    (FP64-class recurrence on FP32 pipes)
+//   P64      double      double              double  (native FP64)
+//   P64D     double      df64                df64    (FP64-class, FP32 pipes)
+#pragma once
+
+#include "df64.cuh"
+
+namespace oec {
+
+struct P32 { typedef float S; typedef float C; typedef double R; };
+struct P32D { typedef float S; typedef float C; typedef df64 R; };
+struct P64 { typedef double S; typedef double C; typedef double R; };
+struct P64D { typedef double S; typedef df64 C; typedef df64 R; };
+
+// ---- conversions -------------------------------------------------------------
+template <class To> __device__ __forceinline__ To cvt(float x);
+template <class To> __device__ __forceinline__ To cvt(double x);
+template <class To> __device__ __forceinline__ To cvt(df64 x);
+template <> __device__ __forceinline__ float cvt<float>(float x) { return x; }
+template <> __device__ __forceinline__ double cvt<double>(float x) { return (double)x; }
+template <> __device__ __forceinline__ df64 cvt<df64>(float x) { return df64{x, 0.0f}; }
+template <> __device__ __forceinline__ float cvt<float>(double x) { return (float)x; }
+template <> __device__ __forceinline__ double cvt<double>(double x) { return x; }
+template <> __device__ __forceinline__ df64 cvt<df64>(double x) { return df_from_double(x); }
+template <> __device__ __forceinline__ float cvt<float>(df64 x) { return x.hi + x.lo; }
+template <> __device__ __forceinline__ double cvt<double>(df64 x) { return df_to_double(x); }
+template <> __device__ __forceinline__ df64 cvt<df64>(df64 x) { return x; }
+
+// ---- constants and small operations ------------------------------------------
+template <class T> __device__ __forceinline__ T kc(float v) { return cvt<T>(v); }
+
+// multiplication by a constant that is a power of two (exact in every type)
+__device__ __forceinline__ float mul_p2(float a, float c) { return a * c; }
+__device__ __forceinline__ double mul_p2(double a, float c) { return a * (double)c; }
+__device__ __forceinline__ df64 mul_p2(df64 a, float c) { return df_scale(a, c); }
+// multiplication by any float constant
+__device__ __forceinline__ float mul_c(float a, float c) { return a * c; }
+__device__ __forceinline__ double mul_c(double a, float c) { return a * (double)c; }
+__device__ __forceinline__ df64 mul_c(df64 a, float c) { return df_mulf(a, c); }
+
+__device__ __forceinline__ float abs_(float a) { return fabsf(a); }
+__device__ __forceinline__ double abs_(double a) { return fabs(a); }
+__device__ __forceinline__ df64 abs_(df64 a) { return df_abs(a); }
+
+__device__ __forceinline__ bool gt0(float a) { return a > 0.0f; }
+__device__ __forceinline__ bool gt0(double a) { return a > 0.0; }
+__device__ __forceinline__ bool gt0(df64 a) { return df_gt0(a); }
+
+// a*b > 0 (the limiter's test): for df64 decided from the signs, which are
+// exact for normalised pairs
+__device__ __forceinline__ bool prod_gt0(float a, float b) { return a * b > 0.0f; }
+__device__ __forceinline__ bool prod_gt0(double a, double b) { return a * b > 0.0; }
+__device__ __forceinline__ bool prod_gt0(df64 a, df64 b) {
+  return (a.hi > 0.0f && b.hi > 0.0f) || (a.hi < 0.0f && b.hi < 0.0f);
+}
+
+__device__ __forceinline__ float rcp_(float a) { return 1.0f / a; }
+__device__ __forceinline__ double rcp_(double a) { return 1.0 / a; }
+__device__ __forceinline__ df64 rcp_(df64 a) { return df_rcp(a); }
+
+template <class T> __device__ __forceinline__ T zero_() { return kc<T>(0.0f); }
+
+// a double-precision constant in the compute type
+template <class T> __device__ __forceinline__ T kd(double v) { return cvt<T>(v); }
+
+// x / 12 (division for the IEEE types, multiplication by the double-float
+// reciprocal for df64)
+__device__ __forceinline__ float div12(float x) { return x / 12.0f; }
+__device__ __forceinline__ double div12(double x) { return x / 12.0; }
+__device__ __forceinline__ df64 div12(df64 x) { return x * df_from_double(1.0 / 12.0); }
+
+// ---- stage bodies of horizontal diffusion (any compute type) ------------------
+// Laplacian 4c - w - e - s - n; flux with the sign limiter; flux divergence.
+template <class T> __device__ __forceinline__ T hlap(T c, T w, T e, T s, T n) {
+  return mul_p2(c, 4.0f) - w - e - s - n;
+}
+template <class T> __device__ __forceinline__ T hflux(T lap_hi, T lap_lo, T in_hi, T in_lo) {
+  const T f = lap_hi - lap_lo;
+  return prod_gt0(f, in_hi - in_lo) ? zero_<T>() : f;
+}
+template <class T> __device__ __forceinline__ T hout(T in, T coeff, T flx, T flx_m, T fly, T fly_m) {
+  return in - coeff * ((flx - flx_m) + (fly - fly_m));
+}
+
+}  // namespace oec

@@ -19,6 +19,8 @@
 //     level on the tile plus one row/column (the execution model of overlapped
 //     tiling + k-streaming, paper §VII-D);
 //   unfused: one kernel per stage, temporaries over their inferred ranges.
+// Templated on an arithmetic policy (arith.cuh): S storage, C compute type.
+#include "arith.cuh"
 #include "kcommon.cuh"
 #include "kernels.h"
 
@@ -33,44 +35,55 @@ struct FW {
   int64_t sj, sk;
 };
 
-template <typename T>
-__device__ __forceinline__ T fw_ppgk(T wg, T pp, T pp_km1) { return wg * pp + (T(1) - wg) * pp_km1; }
-template <typename T>
-__device__ __forceinline__ T fw_pgrad(T pp_n, T pp, T pc_n, T pc, T h_k1, T h, T hn_k1, T hn) {
-  return (pp_n - pp) + T(0.25) * (pc_n + pc) * ((h_k1 + h) - (hn_k1 + hn)) / ((h_k1 - h) + (hn_k1 - hn));
+template <class C>
+__device__ __forceinline__ C fw_ppgk(C wg, C pp, C pp_km1) { return wg * pp + (kc<C>(1.0f) - wg) * pp_km1; }
+template <class C>
+__device__ __forceinline__ C fw_pgrad(C pp_n, C pp, C pc_n, C pc, C h_k1, C h, C hn_k1, C hn) {
+  return (pp_n - pp) + mul_p2(pc_n + pc, 0.25f) * ((h_k1 + h) - (hn_k1 + hn)) / ((h_k1 - h) + (hn_k1 - hn));
 }
-template <typename T>
-__device__ __forceinline__ T fw_d4(T m2, T m1, T p1, T p2) { return (-p2 + T(8) * p1 - T(8) * m1 + m2) / T(12); }
-template <typename T>
-__device__ __forceinline__ T fw_out(T uin, T dt, T tens, T pg, T fx, T rho_n, T rho, T alpha, T div_n, T div) {
-  return uin + dt * ((tens - pg * T(2) * fx / (rho_n + rho)) + alpha * (div_n - div));
+template <class C>
+__device__ __forceinline__ C fw_d4(C m2, C m1, C p1, C p2) {
+  return div12(-p2 + mul_p2(p1, 8.0f) - mul_p2(m1, 8.0f) + m2);
 }
-
-template <typename T>
-__device__ __forceinline__ T ppgk_at(const FW<T>& p, int64_t o) {
-  return fw_ppgk(ldg(p.wgtfac + o), ldg(p.pp + o), ldg(p.pp + o - p.sk));
-}
-template <typename T>
-__device__ __forceinline__ T div_at(const FW<T>& p, int64_t o) {
-  const T* u = p.u_in + o;
-  const T* v = p.v_in + o;
-  return fw_d4(ldg(u - 2), ldg(u - 1), ldg(u + 1), ldg(u + 2)) + fw_d4(ldg(v - 2 * p.sj), ldg(v - p.sj), ldg(v + p.sj), ldg(v + 2 * p.sj));
+template <class C>
+__device__ __forceinline__ C fw_out(C uin, C dt, C tens, C pg, C fx, C rho_n, C rho, C alpha, C div_n, C div) {
+  return uin + dt * ((tens - mul_p2(pg, 2.0f) * fx / (rho_n + rho)) + alpha * (div_n - div));
 }
 
-template <typename T>
-__device__ __forceinline__ void fw_point(const FW<T>& p, int64_t o, T pc, T pc_e, T pc_n, T dv, T dv_e, T dv_n, T dt,
-                                         T alpha) {
+template <class P>
+__device__ __forceinline__ typename P::C ld(const typename P::S* q) { return cvt<typename P::C>(ldg(q)); }
+
+template <class P>
+__device__ __forceinline__ typename P::C ppgk_at(const FW<typename P::S>& p, int64_t o) {
+  return fw_ppgk(ld<P>(p.wgtfac + o), ld<P>(p.pp + o), ld<P>(p.pp + o - p.sk));
+}
+template <class P>
+__device__ __forceinline__ typename P::C div_at(const FW<typename P::S>& p, int64_t o) {
+  const typename P::S* u = p.u_in + o;
+  const typename P::S* v = p.v_in + o;
+  return fw_d4(ld<P>(u - 2), ld<P>(u - 1), ld<P>(u + 1), ld<P>(u + 2)) +
+         fw_d4(ld<P>(v - 2 * p.sj), ld<P>(v - p.sj), ld<P>(v + p.sj), ld<P>(v + 2 * p.sj));
+}
+
+template <class P>
+__device__ __forceinline__ void fw_point(const FW<typename P::S>& p, int64_t o, typename P::C pc, typename P::C pc_e,
+                                         typename P::C pc_n, typename P::C dv, typename P::C dv_e, typename P::C dv_n,
+                                         typename P::C dt, typename P::C alpha) {
+  typedef typename P::C C;
+  typedef typename P::S S;
   const int64_t sj = p.sj, sk = p.sk;
-  const T pp = ldg(p.pp + o), h = ldg(p.hhl + o), h1 = ldg(p.hhl + o + sk);
-  const T ppgu = fw_pgrad(ldg(p.pp + o + 1), pp, pc_e, pc, h1, h, ldg(p.hhl + o + 1 + sk), ldg(p.hhl + o + 1));
-  const T ppgv = fw_pgrad(ldg(p.pp + o + sj), pp, pc_n, pc, h1, h, ldg(p.hhl + o + sj + sk), ldg(p.hhl + o + sj));
-  const T fx = ldg(p.fx + o), rho = ldg(p.rho + o);
-  p.u_out[o] = fw_out(ldg(p.u_in + o), dt, ldg(p.utens + o), ppgu, fx, ldg(p.rho + o + 1), rho, alpha, dv_e, dv);
-  p.v_out[o] = fw_out(ldg(p.v_in + o), dt, ldg(p.vtens + o), ppgv, fx, ldg(p.rho + o + sj), rho, alpha, dv_n, dv);
+  const C pp = ld<P>(p.pp + o), h = ld<P>(p.hhl + o), h1 = ld<P>(p.hhl + o + sk);
+  const C ppgu = fw_pgrad(ld<P>(p.pp + o + 1), pp, pc_e, pc, h1, h, ld<P>(p.hhl + o + 1 + sk), ld<P>(p.hhl + o + 1));
+  const C ppgv = fw_pgrad(ld<P>(p.pp + o + sj), pp, pc_n, pc, h1, h, ld<P>(p.hhl + o + sj + sk), ld<P>(p.hhl + o + sj));
+  const C fx = ld<P>(p.fx + o), rho = ld<P>(p.rho + o);
+  p.u_out[o] = cvt<S>(fw_out(ld<P>(p.u_in + o), dt, ld<P>(p.utens + o), ppgu, fx, ld<P>(p.rho + o + 1), rho, alpha, dv_e, dv));
+  p.v_out[o] = cvt<S>(fw_out(ld<P>(p.v_in + o), dt, ld<P>(p.vtens + o), ppgv, fx, ld<P>(p.rho + o + sj), rho, alpha, dv_n, dv));
 }
 
-template <typename T, int U>
-__global__ void fw_regs_kernel(FW<T> p, T dt, T alpha) {
+template <class P, int U>
+__global__ void fw_regs_kernel(FW<typename P::S> p, double dt_d, double alpha_d) {
+  typedef typename P::C T;
+  const T dt = kd<T>(dt_d), alpha = kd<T>(alpha_d);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int kb = blockIdx.z * U;
@@ -80,22 +93,24 @@ __global__ void fw_regs_kernel(FW<T> p, T dt, T alpha) {
 #pragma unroll
   for (int r = 0; r <= U; ++r) {
     const int64_t o = (int64_t)min(kb + r, p.nk) * p.sk + col;   // clamp: levels past nk unused
-    pk[r] = ppgk_at(p, o);
-    pk_e[r] = ppgk_at(p, o + 1);
-    pk_n[r] = ppgk_at(p, o + p.sj);
+    pk[r] = ppgk_at<P>(p, o);
+    pk_e[r] = ppgk_at<P>(p, o + 1);
+    pk_n[r] = ppgk_at<P>(p, o + p.sj);
   }
 #pragma unroll
   for (int r = 0; r < U; ++r) {
     if (kb + r < p.nk) {
       const int64_t o = (int64_t)(kb + r) * p.sk + col;
-      fw_point(p, o, pk[r + 1] - pk[r], pk_e[r + 1] - pk_e[r], pk_n[r + 1] - pk_n[r], div_at(p, o), div_at(p, o + 1),
-               div_at(p, o + p.sj), dt, alpha);
+      fw_point<P>(p, o, pk[r + 1] - pk[r], pk_e[r + 1] - pk_e[r], pk_n[r + 1] - pk_n[r], div_at<P>(p, o),
+                  div_at<P>(p, o + 1), div_at<P>(p, o + p.sj), dt, alpha);
     }
   }
 }
 
-template <typename T, int TI, int TJ>
-__global__ void __launch_bounds__(TI * TJ) fw_smem_kernel(FW<T> p, T dt, T alpha, int kchunk) {
+template <class P, int TI, int TJ>
+__global__ void __launch_bounds__(TI * TJ) fw_smem_kernel(FW<typename P::S> p, double dt_d, double alpha_d, int kchunk) {
+  typedef typename P::C T;
+  const T dt = kd<T>(dt_d), alpha = kd<T>(alpha_d);
   constexpr int NT = TI * TJ, PI = TI + 1, PJ = TJ + 1;
   __shared__ T s_pk[2][PJ][PI];
   __shared__ T s_pc[PJ][PI];
@@ -108,7 +123,7 @@ __global__ void __launch_bounds__(TI * TJ) fw_smem_kernel(FW<T> p, T dt, T alpha
   int cur = 0;
   for (int idx = tid; idx < PI * PJ; idx += NT) {
     const int b = idx / PI, a = idx - b * PI;
-    if (a < vi + 1 && b < vj + 1) s_pk[cur][b][a] = ppgk_at(p, (int64_t)k0 * p.sk + tile + (int64_t)b * p.sj + a);
+    if (a < vi + 1 && b < vj + 1) s_pk[cur][b][a] = ppgk_at<P>(p, (int64_t)k0 * p.sk + tile + (int64_t)b * p.sj + a);
   }
   for (int k = k0; k < k1; ++k) {
     __syncthreads();
@@ -116,17 +131,17 @@ __global__ void __launch_bounds__(TI * TJ) fw_smem_kernel(FW<T> p, T dt, T alpha
       const int b = idx / PI, a = idx - b * PI;
       if (a < vi + 1 && b < vj + 1) {
         const int64_t o = (int64_t)k * p.sk + tile + (int64_t)b * p.sj + a;
-        const T pk1 = ppgk_at(p, o + p.sk);
+        const T pk1 = ppgk_at<P>(p, o + p.sk);
         s_pc[b][a] = pk1 - s_pk[cur][b][a];
         s_pk[cur ^ 1][b][a] = pk1;
-        s_dv[b][a] = div_at(p, o);
+        s_dv[b][a] = div_at<P>(p, o);
       }
     }
     __syncthreads();
     if (tx < vi && ty < vj) {
       const int64_t o = (int64_t)k * p.sk + tile + (int64_t)ty * p.sj + tx;
-      fw_point(p, o, s_pc[ty][tx], s_pc[ty][tx + 1], s_pc[ty + 1][tx], s_dv[ty][tx], s_dv[ty][tx + 1], s_dv[ty + 1][tx],
-               dt, alpha);
+      fw_point<P>(p, o, s_pc[ty][tx], s_pc[ty][tx + 1], s_pc[ty + 1][tx], s_dv[ty][tx], s_dv[ty][tx + 1],
+                  s_dv[ty + 1][tx], dt, alpha);
     }
     cur ^= 1;
   }
@@ -136,21 +151,21 @@ __global__ void __launch_bounds__(TI * TJ) fw_smem_kernel(FW<T> p, T dt, T alpha
 // temporaries: pk  [0,ni+1) x [0,nj+1) x [0,nk+1)   pitch ni+1, plane (ni+1)(nj+1)
 //              pc, dv [0,ni+1) x [0,nj+1) x [0,nk)
 //              pu, pv domain                        pitch ni, plane ni*nj
-template <typename T>
-__global__ void fw_s1(FW<T> p, T* pk) {
+template <class P, class T = typename P::C>
+__global__ void fw_s1(FW<typename P::S> p, T* pk) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y, k = blockIdx.z;
   if (i > p.ni || j > p.nj) return;
-  pk[((int64_t)k * (p.nj + 1) + j) * (p.ni + 1) + i] = ppgk_at(p, (int64_t)k * p.sk + (int64_t)j * p.sj + i);
+  pk[((int64_t)k * (p.nj + 1) + j) * (p.ni + 1) + i] = ppgk_at<P>(p, (int64_t)k * p.sk + (int64_t)j * p.sj + i);
 }
-template <typename T>
-__global__ void fw_s2(FW<T> p, const T* __restrict__ pk, T* __restrict__ pc) {
+template <class P, class T = typename P::C>
+__global__ void fw_s2(FW<typename P::S> p, const T* __restrict__ pk, T* __restrict__ pc) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y, k = blockIdx.z;
   if (i > p.ni || j > p.nj) return;
   const int64_t plane = (int64_t)(p.nj + 1) * (p.ni + 1), o = ((int64_t)k * (p.nj + 1) + j) * (p.ni + 1) + i;
-  pc[o] = ldg(pk + o + plane) - ldg(pk + o);
+  pc[o] = pk[o + plane] - pk[o];
 }
-template <typename T, int DIR>
-__global__ void fw_s34(FW<T> p, const T* __restrict__ pc, T* __restrict__ pg) {
+template <class P, int DIR, class T = typename P::C>
+__global__ void fw_s34(FW<typename P::S> p, const T* __restrict__ pc, T* __restrict__ pg) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y, k = blockIdx.z;
   if (i >= p.ni || j >= p.nj) return;
   const int64_t o = (int64_t)k * p.sk + (int64_t)j * p.sj + i;
@@ -158,34 +173,35 @@ __global__ void fw_s34(FW<T> p, const T* __restrict__ pc, T* __restrict__ pg) {
   const int64_t t = ((int64_t)k * (p.nj + 1) + j) * (p.ni + 1) + i;
   const int64_t tn = DIR == 0 ? 1 : (p.ni + 1);          // neighbour in the temporary
   pg[((int64_t)k * p.nj + j) * p.ni + i] =
-      fw_pgrad(ldg(p.pp + o + n), ldg(p.pp + o), ldg(pc + t + tn), ldg(pc + t), ldg(p.hhl + o + p.sk), ldg(p.hhl + o),
-               ldg(p.hhl + o + n + p.sk), ldg(p.hhl + o + n));
+      fw_pgrad(ld<P>(p.pp + o + n), ld<P>(p.pp + o), pc[t + tn], pc[t], ld<P>(p.hhl + o + p.sk), ld<P>(p.hhl + o),
+               ld<P>(p.hhl + o + n + p.sk), ld<P>(p.hhl + o + n));
 }
-template <typename T>
-__global__ void fw_s5(FW<T> p, T* dv) {
+template <class P, class T = typename P::C>
+__global__ void fw_s5(FW<typename P::S> p, T* dv) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y, k = blockIdx.z;
   if (i > p.ni || j > p.nj) return;
-  dv[((int64_t)k * (p.nj + 1) + j) * (p.ni + 1) + i] = div_at(p, (int64_t)k * p.sk + (int64_t)j * p.sj + i);
+  dv[((int64_t)k * (p.nj + 1) + j) * (p.ni + 1) + i] = div_at<P>(p, (int64_t)k * p.sk + (int64_t)j * p.sj + i);
 }
-template <typename T>
-__global__ void fw_s6(FW<T> p, const T* __restrict__ pu, const T* __restrict__ pv, const T* __restrict__ dv, T dt,
-                      T alpha) {
+template <class P, class T = typename P::C>
+__global__ void fw_s6(FW<typename P::S> p, const T* __restrict__ pu, const T* __restrict__ pv, const T* __restrict__ dv,
+                      double dt_d, double alpha_d) {
+  typedef typename P::S S;
+  const T dt = kd<T>(dt_d), alpha = kd<T>(alpha_d);
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y, k = blockIdx.z;
   if (i >= p.ni || j >= p.nj) return;
   const int64_t o = (int64_t)k * p.sk + (int64_t)j * p.sj + i;
   const int64_t t = ((int64_t)k * (p.nj + 1) + j) * (p.ni + 1) + i;
   const int64_t d = ((int64_t)k * p.nj + j) * p.ni + i;
-  const T fx = ldg(p.fx + o), rho = ldg(p.rho + o), dvc = ldg(dv + t);
-  p.u_out[o] = fw_out(ldg(p.u_in + o), dt, ldg(p.utens + o), ldg(pu + d), fx, ldg(p.rho + o + 1), rho, alpha, ldg(dv + t + 1), dvc);
-  p.v_out[o] = fw_out(ldg(p.v_in + o), dt, ldg(p.vtens + o), ldg(pv + d), fx, ldg(p.rho + o + p.sj), rho, alpha,
-                      ldg(dv + t + (p.ni + 1)), dvc);
+  const T fx = ld<P>(p.fx + o), rho = ld<P>(p.rho + o), dvc = dv[t];
+  p.u_out[o] = cvt<S>(fw_out(ld<P>(p.u_in + o), dt, ld<P>(p.utens + o), pu[d], fx, ld<P>(p.rho + o + 1), rho, alpha, dv[t + 1], dvc));
+  p.v_out[o] = cvt<S>(fw_out(ld<P>(p.v_in + o), dt, ld<P>(p.vtens + o), pv[d], fx, ld<P>(p.rho + o + p.sj), rho, alpha,
+                             dv[t + (p.ni + 1)], dvc));
 }
 
 struct Tmp {
   size_t pk, pc, dv, pu, pv, total;
 };
-Tmp tmp_layout(int dtype, const Dom& d) {
-  const size_t e = dtype == OEC_F64 ? 8 : 4;
+Tmp tmp_layout(size_t e, const Dom& d) {
   const size_t plane1 = size_t(d.ni + 1) * (d.nj + 1), dom = size_t(d.ni) * d.nj * d.nk;
   Tmp t;
   t.pk = 0;
@@ -201,22 +217,23 @@ int kchunk_of(const oec_schedule& s, int nk) { return (s.k_chunk <= 0 || s.k_chu
 
 #define OEC_FW_TILES(X) X(32, 4) X(32, 8) X(64, 2) X(64, 4) X(128, 2)
 
-template <typename T>
-cudaError_t dispatch(const oec_schedule& s, const Dom& d, const FW<T>& p, T dt, T alpha, char* scratch,
-                     cudaStream_t st) {
+template <class P>
+cudaError_t dispatch(const oec_schedule& s, const Dom& d, const FW<typename P::S>& p, double dt, double alpha,
+                     char* scratch, cudaStream_t st) {
+  typedef typename P::C T;
   if (s.fusion == OEC_FUSE_NONE) {
-    Tmp t = tmp_layout(sizeof(T) == 8 ? OEC_F64 : OEC_F32, d);
+    Tmp t = tmp_layout(sizeof(T), d);
     T *pk = (T*)(scratch + t.pk), *pc = (T*)(scratch + t.pc), *dv = (T*)(scratch + t.dv);
     T *pu = (T*)(scratch + t.pu), *pv = (T*)(scratch + t.pv);
     dim3 b(32, 8);
     dim3 g1(ceil_div(d.ni + 1, 32), ceil_div(d.nj + 1, 8), d.nk + 1), g(ceil_div(d.ni + 1, 32), ceil_div(d.nj + 1, 8), d.nk);
     dim3 gd(ceil_div(d.ni, 32), ceil_div(d.nj, 8), d.nk);
-    fw_s1<T><<<g1, b, 0, st>>>(p, pk);
-    fw_s2<T><<<g, b, 0, st>>>(p, pk, pc);
-    fw_s34<T, 0><<<gd, b, 0, st>>>(p, pc, pu);
-    fw_s34<T, 1><<<gd, b, 0, st>>>(p, pc, pv);
-    fw_s5<T><<<g, b, 0, st>>>(p, dv);
-    fw_s6<T><<<gd, b, 0, st>>>(p, pu, pv, dv, dt, alpha);
+    fw_s1<P><<<g1, b, 0, st>>>(p, pk);
+    fw_s2<P><<<g, b, 0, st>>>(p, pk, pc);
+    fw_s34<P, 0><<<gd, b, 0, st>>>(p, pc, pu);
+    fw_s34<P, 1><<<gd, b, 0, st>>>(p, pc, pv);
+    fw_s5<P><<<g, b, 0, st>>>(p, dv);
+    fw_s6<P><<<gd, b, 0, st>>>(p, pu, pv, dv, dt, alpha);
     return cudaGetLastError();
   }
   if (s.staging == OEC_STAGE_SMEM) {
@@ -224,7 +241,7 @@ cudaError_t dispatch(const oec_schedule& s, const Dom& d, const FW<T>& p, T dt, 
 #define X(a, b)                                                                                 \
   if (s.tile_i == a && s.tile_j == b) {                                                         \
     dim3 g(ceil_div(d.ni, a), ceil_div(d.nj, b), ceil_div(d.nk, kc));                           \
-    fw_smem_kernel<T, a, b><<<g, a * b, 0, st>>>(p, dt, alpha, kc);                              \
+    fw_smem_kernel<P, a, b><<<g, a * b, 0, st>>>(p, dt, alpha, kc);                              \
     return cudaGetLastError();                                                                  \
   }
     OEC_FW_TILES(X)
@@ -234,9 +251,9 @@ cudaError_t dispatch(const oec_schedule& s, const Dom& d, const FW<T>& p, T dt, 
   dim3 b(s.tile_i, s.tile_j);
   dim3 g(ceil_div(d.ni, s.tile_i), ceil_div(d.nj, s.tile_j), ceil_div(d.nk, s.unroll));
   switch (s.unroll) {
-    case 1: fw_regs_kernel<T, 1><<<g, b, 0, st>>>(p, dt, alpha); break;
-    case 2: fw_regs_kernel<T, 2><<<g, b, 0, st>>>(p, dt, alpha); break;
-    case 4: fw_regs_kernel<T, 4><<<g, b, 0, st>>>(p, dt, alpha); break;
+    case 1: fw_regs_kernel<P, 1><<<g, b, 0, st>>>(p, dt, alpha); break;
+    case 2: fw_regs_kernel<P, 2><<<g, b, 0, st>>>(p, dt, alpha); break;
+    case 4: fw_regs_kernel<P, 4><<<g, b, 0, st>>>(p, dt, alpha); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -245,6 +262,7 @@ cudaError_t dispatch(const oec_schedule& s, const Dom& d, const FW<T>& p, T dt, 
 }  // namespace
 
 bool fastwaves_schedule_ok(const oec_schedule& s, std::string& why) {
+  if (s.arith != 0 && s.arith != 1) { why = "arith must be 0 (native) or 1 (double-float)"; return false; }
   if (s.fusion == OEC_FUSE_NONE) return true;
   if (s.fusion != OEC_FUSE_INLINE) { why = "fusion must be OEC_FUSE_INLINE or OEC_FUSE_NONE"; return false; }
   if (s.k_chunk < 0) { why = "k_chunk must be >= 0"; return false; }
@@ -265,7 +283,7 @@ bool fastwaves_schedule_ok(const oec_schedule& s, std::string& why) {
 }
 
 size_t fastwaves_scratch_bytes(const oec_schedule& s, int dtype, const Dom& d) {
-  return s.fusion == OEC_FUSE_NONE ? tmp_layout(dtype, d).total : 0;
+  return s.fusion == OEC_FUSE_NONE ? tmp_layout(dtype == OEC_F64 ? 8 : 4, d).total : 0;
 }
 
 cudaError_t fastwaves_launch(const oec_schedule& s, int dtype, const Dom& d, const FastwavesPtrs& f, double dt,
@@ -275,13 +293,14 @@ cudaError_t fastwaves_launch(const oec_schedule& s, int dtype, const Dom& d, con
     FW<T> p{(const T*)f.u_in, (const T*)f.v_in, (const T*)f.utens, (const T*)f.vtens, (const T*)f.pp,
             (const T*)f.rho, (const T*)f.wgtfac, (const T*)f.hhl, (const T*)f.fx, (T*)f.u_out, (T*)f.v_out,
             d.ni, d.nj, d.nk, d.sj, d.sk};
-    return dispatch<T>(s, d, p, T(dt), T(alpha), (char*)scratch, st);
+    if (s.arith == 1) return dispatch<P64D>(s, d, p, dt, alpha, (char*)scratch, st);
+    return dispatch<P64>(s, d, p, dt, alpha, (char*)scratch, st);
   }
   typedef float T;
   FW<T> p{(const T*)f.u_in, (const T*)f.v_in, (const T*)f.utens, (const T*)f.vtens, (const T*)f.pp,
           (const T*)f.rho, (const T*)f.wgtfac, (const T*)f.hhl, (const T*)f.fx, (T*)f.u_out, (T*)f.v_out,
           d.ni, d.nj, d.nk, d.sj, d.sk};
-  return dispatch<T>(s, d, p, T(dt), T(alpha), (char*)scratch, st);
+  return dispatch<P32>(s, d, p, dt, alpha, (char*)scratch, st);
 }
 
 }  // namespace oec

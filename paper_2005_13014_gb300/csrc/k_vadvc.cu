@@ -6,207 +6,440 @@
 // d_k = dtr*phi_k - (a_k (phi_{k-1} - phi_k) + c_k (phi_{k+1} - phi_k))/2 with
 // the column-end terms left out, solved by the Thomas algorithm (forward
 // elimination, back substitution; the paper names Thomas for vertical implicit
-// integration in §VII-B) for phi = hdiff(u) and hdiff(v) with one matrix.
+// integration, §VII-B) for phi = hdiff(u) and hdiff(v) with one matrix.
 //
-// T is the storage/stencil type, R the type of the Thomas recurrence (double
-// in both precisions: FP32 fields keep the recurrence in FP64).
-//
-// Fused form: one CTA owns TI x TJ columns, a thread per column. Marching up
-// the column, the CTA evaluates hdiff of u and v one level ahead in shared
-// memory (the producer inlined into the sweep, paper §V-A), builds row k and
-// eliminates it; c'_k, d'_k go to a scratch array (R, layout [3][k][column])
-// that the back substitution reads on the way down.
-// Staged form: the hdiff kernel writes hdiff(u), hdiff(v) to scratch over the
-// domain, then a column kernel runs the sweep.
+// Fused form (the producer inlined into the column sweep, paper §V-A): one CTA
+// owns TI x TJ columns and walks up them in chunks of KC levels. Per chunk all
+// 2*TI*TJ threads evaluate hdiff of u and v for the chunk's levels on an
+// overlapped tile in shared memory; then one thread per column runs the
+// chunk's elimination steps (lagging one level, since row k needs phi_{k+1}).
+// c'_k, d'_k go to a per-tile scratch slot ([k][3][column]) that the back
+// substitution reads on the way down.
+// Staged form: hdiff writes hdiff(u), hdiff(v) to scratch, then a column
+// kernel runs the sweep.
+// Batched form: a persistent kernel pulls (member, tile) items of an ensemble
+// of domains from an atomic counter and runs the fused tile sweep on each.
+#include "arith.cuh"
 #include "kcommon.cuh"
 #include "kernels.h"
+#include "k_vadvc.cuh"
 
 namespace oec {
 namespace {
 
-template <typename T>
-struct HV {
-  const T* u; const T* v; const T* w; const T* coeff;
-  T* uo; T* vo;
-  int ni, nj, nk;
-  int64_t sj, sk;
-};
-
-// One row of the system and its right-hand sides for both fields.
-template <typename T>
-__device__ __forceinline__ void hv_row(bool lo, bool hi, T wf_c, T wf_p, T dtr, T um, T uc, T up, T vm, T vc, T vp,
-                                       T& a, T& b, T& c, T& du, T& dv) {
-  a = lo ? T(-0.25) * wf_c : T(0);
-  c = hi ? T(0.25) * wf_p : T(0);
-  b = dtr + fabs(a) + fabs(c);
+// One row of the system and its right-hand sides for both fields (compute type C).
+template <class C>
+__device__ __forceinline__ void hv_row(bool lo, bool hi, C wf_c, C wf_p, C dtr, C um, C uc, C up, C vm, C vc, C vp,
+                                       C& a, C& b, C& c, C& du, C& dv) {
+  a = lo ? -mul_p2(wf_c, 0.25f) : zero_<C>();
+  c = hi ? mul_p2(wf_p, 0.25f) : zero_<C>();
+  b = dtr + abs_(a) + abs_(c);
+  const C tu = dtr * uc, tv = dtr * vc;
   if (lo && hi) {
-    du = dtr * uc - T(0.5) * (a * (um - uc) + c * (up - uc));
-    dv = dtr * vc - T(0.5) * (a * (vm - vc) + c * (vp - vc));
+    du = tu - mul_p2(a * (um - uc) + c * (up - uc), 0.5f);
+    dv = tv - mul_p2(a * (vm - vc) + c * (vp - vc), 0.5f);
   } else if (hi) {
-    du = dtr * uc - T(0.5) * (c * (up - uc));
-    dv = dtr * vc - T(0.5) * (c * (vp - vc));
+    du = tu - mul_p2(c * (up - uc), 0.5f);
+    dv = tv - mul_p2(c * (vp - vc), 0.5f);
   } else if (lo) {
-    du = dtr * uc - T(0.5) * (a * (um - uc));
-    dv = dtr * vc - T(0.5) * (a * (vm - vc));
+    du = tu - mul_p2(a * (um - uc), 0.5f);
+    dv = tv - mul_p2(a * (vm - vc), 0.5f);
   } else {
-    du = dtr * uc;
-    dv = dtr * vc;
+    du = tu;
+    dv = tv;
   }
 }
 
-template <typename T, typename R, int TI, int TJ>
-__global__ void __launch_bounds__(TI * TJ)
-hv_fused_kernel(HV<T> p, T dtr, R* __restrict__ scr) {
-  constexpr int NT = TI * TJ, WI = TI + 4, WJ = TJ + 4;
-  __shared__ T s_in[2][WJ][WI];
-  __shared__ T s_lap[2][TJ + 2][TI + 2];
-  __shared__ T s_flx[2][TJ][TI + 1];
-  __shared__ T s_fly[2][TJ + 1][TI];
-  const int tid = threadIdx.x, tx = tid % TI, ty = tid / TI;
-  const int i0 = blockIdx.x * TI, j0 = blockIdx.y * TJ;
+template <class P, int TI, int TJ, int KC>
+struct HVSmem {
+  typedef typename P::S S;
+  typedef typename P::C C;
+  static constexpr int WI = TI + 4, WJ = TJ + 4, NC = TI * TJ, NT = 2 * NC, RING = KC + 2;
+  // raw storage values of one chunk: u, v windows, the w rows (TI+1 wide) and coeff
+  static constexpr int N_WIN = 2 * KC * WJ * WI, N_W = KC * TJ * (TI + 1), N_CF = KC * NC;
+  static constexpr int N_LOAD = N_WIN + N_W + N_CF;
+  static constexpr int PF = (N_LOAD + NT - 1) / NT;   // prefetch registers per thread
+  C win[2][KC][WJ][WI];
+  C lap[2][KC][TJ + 2][TI + 2];
+  C flx[2][KC][TJ][TI + 1];
+  C fly[2][KC][TJ + 1][TI];
+  C ring[2][RING][NC];
+  S wrow[KC][TJ][TI + 1];
+  S cf[KC][NC];
+  C wf[KC][NC];
+  int item;
+};
+
+// Global loads of chunk [k0, k0+nl): element e of the chunk's load list.
+template <class P, int TI, int TJ, int KC>
+__device__ __forceinline__ const typename P::S* hv_load_addr(const HV<typename P::S>& p, int i0, int j0, int k0, int nl,
+                                                             int e) {
+  typedef HVSmem<P, TI, TJ, KC> SM;
+  constexpr int WI = SM::WI, WJ = SM::WJ, NC = SM::NC;
+  if (e < 2 * nl * WJ * WI) {
+    const int c = e % WI, r = (e / WI) % WJ, l = (e / (WI * WJ)) % nl, f = e / (WI * WJ * nl);
+    return (f ? p.v : p.u) + (int64_t)(k0 + l) * p.sk + (int64_t)(j0 - 2 + r) * p.sj + (i0 - 2 + c);
+  }
+  e -= 2 * nl * WJ * WI;
+  if (e < nl * TJ * (TI + 1)) {
+    const int c = e % (TI + 1), r = (e / (TI + 1)) % TJ, l = e / ((TI + 1) * TJ);
+    return p.w + (int64_t)(k0 + l) * p.sk + (int64_t)(j0 + r) * p.sj + (i0 + c);
+  }
+  e -= nl * TJ * (TI + 1);
+  const int q = e % NC, l = e / NC;
+  return p.coeff + (int64_t)(k0 + l) * p.sk + (int64_t)(j0 + q / TI) * p.sj + (i0 + q % TI);
+}
+template <class P, int TI, int TJ, int KC>
+__device__ __forceinline__ bool hv_load_valid(int vi, int vj, int nl, int e) {
+  typedef HVSmem<P, TI, TJ, KC> SM;
+  constexpr int WI = SM::WI, WJ = SM::WJ, NC = SM::NC;
+  if (e < 2 * nl * WJ * WI) return e % WI < vi + 4 && (e / WI) % WJ < vj + 4;
+  e -= 2 * nl * WJ * WI;
+  if (e < nl * TJ * (TI + 1)) return e % (TI + 1) < vi + 1 && (e / (TI + 1)) % TJ < vj;
+  e -= nl * TJ * (TI + 1);
+  if (e >= nl * NC) return false;
+  const int q = e % NC;
+  return q % TI < vi && q / TI < vj;
+}
+template <class P, int TI, int TJ, int KC>
+__device__ __forceinline__ void hv_load_store(HVSmem<P, TI, TJ, KC>& sm, int nl, int e, typename P::S v) {
+  typedef HVSmem<P, TI, TJ, KC> SM;
+  typedef typename P::C C;
+  constexpr int WI = SM::WI, WJ = SM::WJ, NC = SM::NC;
+  if (e < 2 * nl * WJ * WI) {
+    const int c = e % WI, r = (e / WI) % WJ, l = (e / (WI * WJ)) % nl, f = e / (WI * WJ * nl);
+    sm.win[f][l][r][c] = cvt<C>(v);
+    return;
+  }
+  e -= 2 * nl * WJ * WI;
+  if (e < nl * TJ * (TI + 1)) {
+    sm.wrow[e / ((TI + 1) * TJ)][(e / (TI + 1)) % TJ][e % (TI + 1)] = v;
+    return;
+  }
+  e -= nl * TJ * (TI + 1);
+  sm.cf[e / NC][e % NC] = v;
+}
+
+// The fused sweep of one tile (all 2*TI*TJ threads of the CTA call it).
+template <class P, int TI, int TJ, int KC>
+__device__ void hv_tile(const HV<typename P::S>& p, int i0, int j0, typename P::R* __restrict__ slot,
+                        typename P::C dtr, HVSmem<P, TI, TJ, KC>& sm) {
+  typedef typename P::S S;
+  typedef typename P::C C;
+  typedef typename P::R R;
+  typedef HVSmem<P, TI, TJ, KC> SM;
+  constexpr int NC = SM::NC, NT = SM::NT, RING = SM::RING, PF = SM::PF;
+  const int tid = threadIdx.x;
   const int vi = min(TI, p.ni - i0), vj = min(TJ, p.nj - j0);
-  const bool active = tx < vi && ty < vj;
-  const int i = i0 + tx, j = j0 + ty;
   const int nk = p.nk;
-  const int64_t ncol = (int64_t)p.ni * p.nj, col = (int64_t)j * p.ni + i;
-  const int64_t plane = ncol * nk;
+  // column state (threads tid < NC)
+  const int tx = tid % TI, ty = tid / TI;
+  const bool col = tid < NC && tx < vi && ty < vj;
+  const int64_t cbase = (int64_t)(j0 + ty) * p.sj + (i0 + tx);
+  C um = zero_<C>(), uc = zero_<C>(), vm = zero_<C>(), vc = zero_<C>(), wf_c = zero_<C>();
+  R cp = cvt<R>(0.0f), dpu = cvt<R>(0.0f), dpv = cvt<R>(0.0f);
+  int knext = 0;   // next elimination step
 
-  // hdiff of u and v at level k for every column of the tile (all threads call)
-  auto level = [&](int k, T& ud, T& vd) {
-    const int64_t base = (int64_t)k * p.sk + (int64_t)(j0 - 2) * p.sj + (i0 - 2);
-    for (int idx = tid; idx < 2 * WI * WJ; idx += NT) {
-      const int f = idx / (WI * WJ), rem = idx - f * WI * WJ, r = rem / WI, c = rem - r * WI;
-      if (c < vi + 4 && r < vj + 4) s_in[f][r][c] = ldg((f ? p.v : p.u) + base + (int64_t)r * p.sj + c);
+  // prefetch registers: the next chunk's raw values, loaded across phase B
+  S pf[PF];
+  auto issue = [&](int k0, int nl) {
+#pragma unroll
+    for (int x = 0; x < PF; ++x) {
+      const int e = tid + x * NT;
+      if (e < SM::N_LOAD && hv_load_valid<P, TI, TJ, KC>(vi, vj, nl, e))
+        pf[x] = ldg(hv_load_addr<P, TI, TJ, KC>(p, i0, j0, k0, nl, e));
     }
-    __syncthreads();
-    for (int idx = tid; idx < 2 * (TI + 2) * (TJ + 2); idx += NT) {
-      const int f = idx / ((TI + 2) * (TJ + 2)), rem = idx - f * (TI + 2) * (TJ + 2);
-      const int r = rem / (TI + 2), c = rem - r * (TI + 2);
-      if (c < vi + 2 && r < vj + 2)
-        s_lap[f][r][c] = hd_lap(s_in[f][r + 1][c + 1], s_in[f][r + 1][c], s_in[f][r + 1][c + 2], s_in[f][r][c + 1],
-                                s_in[f][r + 2][c + 1]);
-    }
-    __syncthreads();
-    for (int idx = tid; idx < 2 * (TI + 1) * TJ; idx += NT) {
-      const int f = idx / ((TI + 1) * TJ), rem = idx - f * (TI + 1) * TJ, r = rem / (TI + 1), c = rem - r * (TI + 1);
-      if (c < vi + 1 && r < vj)
-        s_flx[f][r][c] = hd_flux(s_lap[f][r + 1][c + 1], s_lap[f][r + 1][c], s_in[f][r + 2][c + 2], s_in[f][r + 2][c + 1]);
-    }
-    for (int idx = tid; idx < 2 * TI * (TJ + 1); idx += NT) {
-      const int f = idx / (TI * (TJ + 1)), rem = idx - f * TI * (TJ + 1), r = rem / TI, c = rem - r * TI;
-      if (c < vi && r < vj + 1)
-        s_fly[f][r][c] = hd_flux(s_lap[f][r + 1][c + 1], s_lap[f][r][c + 1], s_in[f][r + 2][c + 2], s_in[f][r + 1][c + 2]);
-    }
-    __syncthreads();
-    if (active) {
-      const T cf = ldg(p.coeff + (int64_t)k * p.sk + (int64_t)j * p.sj + i);
-      ud = hd_out(s_in[0][ty + 2][tx + 2], cf, s_flx[0][ty][tx + 1], s_flx[0][ty][tx], s_fly[0][ty + 1][tx], s_fly[0][ty][tx]);
-      vd = hd_out(s_in[1][ty + 2][tx + 2], cf, s_flx[1][ty][tx + 1], s_flx[1][ty][tx], s_fly[1][ty + 1][tx], s_fly[1][ty][tx]);
-    }
-    __syncthreads();
   };
-  auto wf = [&](int k) -> T {
-    if (!active) return T(0);
-    const T* q = p.w + (int64_t)k * p.sk + (int64_t)j * p.sj + i;
-    return T(0.5) * (ldg(q) + ldg(q + 1));
+  auto land = [&](int nl) {
+#pragma unroll
+    for (int x = 0; x < PF; ++x) {
+      const int e = tid + x * NT;
+      if (e < SM::N_LOAD && hv_load_valid<P, TI, TJ, KC>(vi, vj, nl, e)) hv_load_store<P, TI, TJ, KC>(sm, nl, e, pf[x]);
+    }
   };
+  issue(0, min(KC, nk));
+  land(min(KC, nk));
+  __syncthreads();
 
-  T um = 0, uc = 0, up = 0, vm = 0, vc = 0, vp = 0;
-  level(0, uc, vc);
-  if (nk > 1) level(1, up, vp);
-  T wf_c = wf(0), wf_p = nk > 1 ? wf(1) : T(0);
-  R cp = 0, dpu = 0, dpv = 0;
-  for (int k = 0; k < nk; ++k) {
-    T a, b, c, du, dv;
-    hv_row(k > 0, k < nk - 1, wf_c, wf_p, dtr, um, uc, up, vm, vc, vp, a, b, c, du, dv);
-    const R m = k == 0 ? R(b) : R(b) - R(a) * cp;
-    const R inv = R(1) / m;
-    cp = R(c) * inv;
-    dpu = (R(du) - R(a) * dpu) * inv;
-    dpv = (R(dv) - R(a) * dpv) * inv;
-    if (active) {
-      R* s = scr + (int64_t)k * ncol + col;
-      s[0] = cp;
-      s[plane] = dpu;
-      s[2 * plane] = dpv;
+  for (int k0 = 0; k0 < nk; k0 += KC) {
+    const int nl = min(KC, nk - k0);
+    // ---- phase A: hdiff of u and v (and wf) for levels [k0, k0+nl) ----------
+    for (int idx = tid; idx < 2 * nl * (TJ + 2) * (TI + 2); idx += NT) {
+      const int c = idx % (TI + 2), r = (idx / (TI + 2)) % (TJ + 2), l = (idx / ((TI + 2) * (TJ + 2))) % nl;
+      const int f = idx / ((TI + 2) * (TJ + 2) * nl);
+      if (c < vi + 2 && r < vj + 2) {
+        const auto& W = sm.win[f][l];
+        sm.lap[f][l][r][c] = hlap(W[r + 1][c + 1], W[r + 1][c], W[r + 1][c + 2], W[r][c + 1], W[r + 2][c + 1]);
+      }
     }
-    um = uc; uc = up; vm = vc; vc = vp;
-    wf_c = wf_p;
-    if (k + 2 < nk) {
-      level(k + 2, up, vp);
-      wf_p = wf(k + 2);
+    for (int idx = tid; idx < nl * NC; idx += NT) {
+      const int q = idx % NC, l = idx / NC, x = q % TI, y = q / TI;
+      if (x < vi && y < vj) sm.wf[l][q] = mul_p2(cvt<C>(sm.wrow[l][y][x]) + cvt<C>(sm.wrow[l][y][x + 1]), 0.5f);
+    }
+    __syncthreads();
+    for (int idx = tid; idx < 2 * nl * TJ * (TI + 1); idx += NT) {
+      const int c = idx % (TI + 1), r = (idx / (TI + 1)) % TJ, l = (idx / ((TI + 1) * TJ)) % nl, f = idx / ((TI + 1) * TJ * nl);
+      if (c < vi + 1 && r < vj) {
+        const auto& W = sm.win[f][l];
+        const auto& L = sm.lap[f][l];
+        sm.flx[f][l][r][c] = hflux(L[r + 1][c + 1], L[r + 1][c], W[r + 2][c + 2], W[r + 2][c + 1]);
+      }
+    }
+    for (int idx = tid; idx < 2 * nl * (TJ + 1) * TI; idx += NT) {
+      const int c = idx % TI, r = (idx / TI) % (TJ + 1), l = (idx / (TI * (TJ + 1))) % nl, f = idx / (TI * (TJ + 1) * nl);
+      if (c < vi && r < vj + 1) {
+        const auto& W = sm.win[f][l];
+        const auto& L = sm.lap[f][l];
+        sm.fly[f][l][r][c] = hflux(L[r + 1][c + 1], L[r][c + 1], W[r + 2][c + 2], W[r + 1][c + 2]);
+      }
+    }
+    __syncthreads();
+    for (int idx = tid; idx < 2 * nl * NC; idx += NT) {
+      const int q = idx % NC, l = (idx / NC) % nl, f = idx / (NC * nl);
+      const int x = q % TI, y = q / TI;
+      if (x < vi && y < vj)
+        sm.ring[f][(k0 + l) % RING][q] = hout(sm.win[f][l][y + 2][x + 2], cvt<C>(sm.cf[l][q]), sm.flx[f][l][y][x + 1],
+                                              sm.flx[f][l][y][x], sm.fly[f][l][y + 1][x], sm.fly[f][l][y][x]);
+    }
+    __syncthreads();
+    // the next chunk's loads fly while this chunk's elimination steps run
+    const int k0n = k0 + KC, nln = min(KC, nk - k0n);
+    if (k0n < nk) issue(k0n, nln);
+    // ---- phase B: elimination steps whose rows are now complete -------------
+    const int last_avail = k0 + nl - 1;
+    const int kend = last_avail == nk - 1 ? nk - 1 : last_avail - 1;
+    if (col) {
+      if (knext == 0) wf_c = sm.wf[0][tid];
+      for (int k = knext; k <= kend; ++k) {
+        if (k == 0) {
+          uc = sm.ring[0][0][tid];
+          vc = sm.ring[1][0][tid];
+        }
+        const bool hi = k + 1 < nk;
+        const C up = hi ? sm.ring[0][(k + 1) % RING][tid] : zero_<C>();
+        const C vp = hi ? sm.ring[1][(k + 1) % RING][tid] : zero_<C>();
+        const C wf_p = hi ? sm.wf[k + 1 - k0][tid] : zero_<C>();
+        C a, b, c, du, dv;
+        hv_row(k > 0, hi, wf_c, wf_p, dtr, um, uc, up, vm, vc, vp, a, b, c, du, dv);
+        const R ra = cvt<R>(a);
+        const R m = k == 0 ? cvt<R>(b) : cvt<R>(b) - ra * cp;
+        const R inv = rcp_(m);
+        cp = cvt<R>(c) * inv;
+        dpu = (cvt<R>(du) - ra * dpu) * inv;
+        dpv = (cvt<R>(dv) - ra * dpv) * inv;
+        R* s = slot + (int64_t)k * 3 * NC + tid;
+        s[0] = cp;
+        s[NC] = dpu;
+        s[2 * NC] = dpv;
+        um = uc; uc = up; vm = vc; vc = vp;
+        wf_c = wf_p;
+      }
+    }
+    knext = kend + 1;
+    __syncthreads();
+    if (k0n < nk) {
+      land(nln);
+      __syncthreads();
     }
   }
-  if (!active) return;
-  R xu = dpu, xv = dpv;
-  int64_t o = (int64_t)(nk - 1) * p.sk + (int64_t)j * p.sj + i;
-  p.uo[o] = T(xu);
-  p.vo[o] = T(xv);
-  for (int k = nk - 2; k >= 0; --k) {
-    const R* s = scr + (int64_t)k * ncol + col;
-    const R ck = s[0];
-    xu = s[plane] - ck * xu;
-    xv = s[2 * plane] - ck * xv;
-    o -= p.sk;
-    p.uo[o] = T(xu);
-    p.vo[o] = T(xv);
+  // ---- back substitution, loads batched BK levels at a time ---------------
+  if (col) {
+    constexpr int BK = 8;
+    R xu = dpu, xv = dpv;
+    int64_t o = (int64_t)(nk - 1) * p.sk + cbase;
+    p.uo[o] = cvt<S>(xu);
+    p.vo[o] = cvt<S>(xv);
+    for (int kt = nk - 2; kt >= 0; kt -= BK) {
+      R c_[BK], du_[BK], dv_[BK];
+#pragma unroll
+      for (int x = 0; x < BK; ++x) {
+        if (kt - x >= 0) {
+          const R* s = slot + (int64_t)(kt - x) * 3 * NC + tid;
+          c_[x] = s[0];
+          du_[x] = s[NC];
+          dv_[x] = s[2 * NC];
+        }
+      }
+#pragma unroll
+      for (int x = 0; x < BK; ++x) {
+        if (kt - x >= 0) {
+          xu = du_[x] - c_[x] * xu;
+          xv = dv_[x] - c_[x] * xv;
+          o -= p.sk;
+          p.uo[o] = cvt<S>(xu);
+          p.vo[o] = cvt<S>(xv);
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+template <class P, int TI, int TJ, int KC>
+__global__ void __launch_bounds__(2 * TI * TJ)
+hv_fused_kernel(HV<typename P::S> p, double dtr, typename P::R* __restrict__ scr) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  auto& sm = *reinterpret_cast<HVSmem<P, TI, TJ, KC>*>(smem_raw);
+  const int tile = blockIdx.y * gridDim.x + blockIdx.x;
+  hv_tile<P, TI, TJ, KC>(p, blockIdx.x * TI, blockIdx.y * TJ, scr + (int64_t)tile * 3 * p.nk * TI * TJ,
+                         cvt<typename P::C>(dtr), sm);
+}
+
+template <class P, int TI, int TJ, int KC>
+__global__ void __launch_bounds__(2 * TI * TJ)
+hv_batch_kernel(const HVMember* __restrict__ members, int n_members, int total_items, int* __restrict__ counter,
+                double dtr, typename P::R* __restrict__ scr, int64_t slot_elems) {
+  typedef typename P::S S;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  auto& sm = *reinterpret_cast<HVSmem<P, TI, TJ, KC>*>(smem_raw);
+  typename P::R* slot = scr + (int64_t)blockIdx.x * slot_elems;
+  for (;;) {
+    if (threadIdx.x == 0) sm.item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int item = sm.item;
+    __syncthreads();
+    if (item >= total_items) break;
+    int m = 0;
+    while (m + 1 < n_members && members[m + 1].tile_begin <= item) ++m;
+    const HVMember& mb = members[m];
+    const int t = item - mb.tile_begin;
+    HV<S> p{(const S*)mb.u, (const S*)mb.v, (const S*)mb.w, (const S*)mb.coeff, (S*)mb.uo, (S*)mb.vo,
+            mb.ni, mb.nj, mb.nk, mb.sj, mb.sk};
+    hv_tile<P, TI, TJ, KC>(p, (t % mb.tiles_i) * TI, (t / mb.tiles_i) * TJ, slot, cvt<typename P::C>(dtr), sm);
   }
 }
 
 // Staged form, second kernel: the column sweep over precomputed hdiff(u),
-// hdiff(v) (ud, vd: domain layout, pitch ni, plane ni*nj).
-template <typename T, typename R>
-__global__ void vadvc_kernel(HV<T> p, const T* __restrict__ ud, const T* __restrict__ vd, T dtr, R* __restrict__ scr) {
+// hdiff(v) held in the compute type (domain layout, pitch ni, plane ni*nj).
+template <class P>
+__global__ void vadvc_kernel(HV<typename P::S> p, const typename P::C* __restrict__ ud,
+                             const typename P::C* __restrict__ vd, double dtr_d, typename P::R* __restrict__ scr) {
+  typedef typename P::S S;
+  typedef typename P::C C;
+  typedef typename P::R R;
   const int64_t ncol = (int64_t)p.ni * p.nj;
   const int64_t col = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (col >= ncol) return;
   const int i = int(col % p.ni), j = int(col / p.ni);
   const int nk = p.nk;
-  const int64_t plane = ncol * nk;
-  auto wf = [&](int k) -> T {
-    const T* q = p.w + (int64_t)k * p.sk + (int64_t)j * p.sj + i;
-    return T(0.5) * (ldg(q) + ldg(q + 1));
+  const C dtr = cvt<C>(dtr_d);
+  const int64_t cbase = (int64_t)j * p.sj + i;
+  auto wf = [&](int k) -> C {
+    const S* q = p.w + (int64_t)k * p.sk + cbase;
+    return mul_p2(cvt<C>(ldg(q)) + cvt<C>(ldg(q + 1)), 0.5f);
   };
-  T um = 0, uc = ldg(ud + col), up = nk > 1 ? ldg(ud + ncol + col) : T(0);
-  T vm = 0, vc = ldg(vd + col), vp = nk > 1 ? ldg(vd + ncol + col) : T(0);
-  T wf_c = wf(0), wf_p = nk > 1 ? wf(1) : T(0);
-  R cp = 0, dpu = 0, dpv = 0;
+  C um = zero_<C>(), uc = ud[col], vm = zero_<C>(), vc = vd[col];
+  C wf_c = wf(0);
+  R cp = cvt<R>(0.0f), dpu = cvt<R>(0.0f), dpv = cvt<R>(0.0f);
   for (int k = 0; k < nk; ++k) {
-    T a, b, c, du, dv;
-    hv_row(k > 0, k < nk - 1, wf_c, wf_p, dtr, um, uc, up, vm, vc, vp, a, b, c, du, dv);
-    const R m = k == 0 ? R(b) : R(b) - R(a) * cp;
-    const R inv = R(1) / m;
-    cp = R(c) * inv;
-    dpu = (R(du) - R(a) * dpu) * inv;
-    dpv = (R(dv) - R(a) * dpv) * inv;
-    R* s = scr + (int64_t)k * ncol + col;
+    const bool hi = k + 1 < nk;
+    const C up = hi ? ud[(int64_t)(k + 1) * ncol + col] : zero_<C>();
+    const C vp = hi ? vd[(int64_t)(k + 1) * ncol + col] : zero_<C>();
+    const C wf_p = hi ? wf(k + 1) : zero_<C>();
+    C a, b, c, du, dv;
+    hv_row(k > 0, hi, wf_c, wf_p, dtr, um, uc, up, vm, vc, vp, a, b, c, du, dv);
+    const R ra = cvt<R>(a);
+    const R m = k == 0 ? cvt<R>(b) : cvt<R>(b) - ra * cp;
+    const R inv = rcp_(m);
+    cp = cvt<R>(c) * inv;
+    dpu = (cvt<R>(du) - ra * dpu) * inv;
+    dpv = (cvt<R>(dv) - ra * dpv) * inv;
+    R* s = scr + ((int64_t)k * 3) * ncol + col;
     s[0] = cp;
-    s[plane] = dpu;
-    s[2 * plane] = dpv;
+    s[ncol] = dpu;
+    s[2 * ncol] = dpv;
     um = uc; uc = up; vm = vc; vc = vp;
     wf_c = wf_p;
-    if (k + 2 < nk) {
-      up = ldg(ud + (int64_t)(k + 2) * ncol + col);
-      vp = ldg(vd + (int64_t)(k + 2) * ncol + col);
-      wf_p = wf(k + 2);
-    }
   }
   R xu = dpu, xv = dpv;
-  int64_t o = (int64_t)(nk - 1) * p.sk + (int64_t)j * p.sj + i;
-  p.uo[o] = T(xu);
-  p.vo[o] = T(xv);
+  int64_t o = (int64_t)(nk - 1) * p.sk + cbase;
+  p.uo[o] = cvt<S>(xu);
+  p.vo[o] = cvt<S>(xv);
   for (int k = nk - 2; k >= 0; --k) {
-    const R* s = scr + (int64_t)k * ncol + col;
+    const R* s = scr + ((int64_t)k * 3) * ncol + col;
     const R ck = s[0];
-    xu = s[plane] - ck * xu;
-    xv = s[2 * plane] - ck * xv;
+    xu = s[ncol] - ck * xu;
+    xv = s[2 * ncol] - ck * xv;
     o -= p.sk;
-    p.uo[o] = T(xu);
-    p.vo[o] = T(xv);
+    p.uo[o] = cvt<S>(xu);
+    p.vo[o] = cvt<S>(xv);
   }
 }
 
-size_t elem(int dtype) { return dtype == OEC_F64 ? 8 : 4; }
+size_t csize(int dtype, int arith) { return dtype == OEC_F32 ? 4 : 8; }   // compute type bytes
+size_t rsize() { return 8; }                                                // double or df64
+
+template <class P, int TI, int TJ, int KC>
+cudaError_t launch_fused(const Dom& d, const HV<typename P::S>& p, double dtr, void* scratch, cudaStream_t st) {
+  typedef HVSmem<P, TI, TJ, KC> SM;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(hv_fused_kernel<P, TI, TJ, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(SM));
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  dim3 g(ceil_div(d.ni, TI), ceil_div(d.nj, TJ));
+  hv_fused_kernel<P, TI, TJ, KC><<<g, 2 * TI * TJ, sizeof(SM), st>>>(p, dtr, (typename P::R*)scratch);
+  return cudaGetLastError();
+}
+
+// the dynamic shared-memory attribute is set by batch_occupancy() at batch
+// creation, before any stream capture
+template <class P, int TI, int TJ, int KC>
+cudaError_t launch_batch(const HVBatchLaunch& b, cudaStream_t st) {
+  typedef HVSmem<P, TI, TJ, KC> SM;
+  hv_batch_kernel<P, TI, TJ, KC><<<b.grid, 2 * TI * TJ, sizeof(SM), st>>>(
+      b.members, b.n_members, b.total_items, b.counter, b.dtr, (typename P::R*)b.scratch, b.slot_elems);
+  return cudaGetLastError();
+}
+
+template <class P, int TI, int TJ, int KC>
+int batch_occupancy() {
+  typedef HVSmem<P, TI, TJ, KC> SM;
+  cudaFuncSetAttribute(hv_batch_kernel<P, TI, TJ, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SM));
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, hv_batch_kernel<P, TI, TJ, KC>, 2 * TI * TJ, sizeof(SM)) !=
+      cudaSuccess)
+    return 1;
+  return n > 0 ? n : 1;
+}
+
+// tiles (TI, TJ) and levels per chunk: KC keeps the shared memory of the
+// 8-byte compute types under ~64 KB
+#define OEC_HV_TILES(X) X(16, 4) X(32, 2) X(8, 8) X(32, 4)
+template <int TI, int TJ, int CB> struct KCOf { static constexpr int v = (TI * TJ >= 128) ? (CB == 4 ? 4 : 2) : (CB == 4 ? 8 : 4); };
+
+template <class P>
+cudaError_t dispatch_fused(const oec_schedule& s, const Dom& d, const HV<typename P::S>& p, double dtr, void* scratch,
+                           cudaStream_t st) {
+  constexpr int CB = sizeof(typename P::C);
+#define X(a, b) \
+  if (s.tile_i == a && s.tile_j == b) return launch_fused<P, a, b, KCOf<a, b, CB>::v>(d, p, dtr, scratch, st);
+  OEC_HV_TILES(X)
+#undef X
+  return cudaErrorInvalidValue;
+}
+
+template <class P>
+cudaError_t dispatch_batch(const oec_schedule& s, const HVBatchLaunch& b, cudaStream_t st) {
+  constexpr int CB = sizeof(typename P::C);
+#define X(a, c) \
+  if (s.tile_i == a && s.tile_j == c) return launch_batch<P, a, c, KCOf<a, c, CB>::v>(b, st);
+  OEC_HV_TILES(X)
+#undef X
+  return cudaErrorInvalidValue;
+}
+
+template <class P>
+int occupancy_of(const oec_schedule& s) {
+  constexpr int CB = sizeof(typename P::C);
+#define X(a, c) \
+  if (s.tile_i == a && s.tile_j == c) return batch_occupancy<P, a, c, KCOf<a, c, CB>::v>();
+  OEC_HV_TILES(X)
+#undef X
+  return 1;
+}
 
 struct Layout {
   size_t thomas, ud, vd, total;
@@ -215,63 +448,47 @@ Layout layout(const oec_schedule& s, int dtype, const Dom& d) {
   const size_t pts = size_t(d.ni) * d.nj * d.nk;
   Layout l;
   l.thomas = 0;
-  l.ud = align_up(3 * sizeof(double) * pts, 256);
   if (s.fusion == OEC_FUSE_NONE) {
-    l.vd = align_up(l.ud + elem(dtype) * pts, 256);
-    l.total = align_up(l.vd + elem(dtype) * pts, 256);
+    l.ud = align_up(3 * rsize() * pts, 256);
+    l.vd = align_up(l.ud + csize(dtype, s.arith) * pts, 256);
+    l.total = align_up(l.vd + csize(dtype, s.arith) * pts, 256);
   } else {
-    l.vd = l.ud;
-    l.total = l.ud;
+    // one slot of 3 x nk x (TI*TJ) recurrence values per tile
+    const size_t tiles = size_t(ceil_div(d.ni, s.tile_i)) * ceil_div(d.nj, s.tile_j);
+    l.ud = l.vd = l.total = align_up(3 * rsize() * tiles * d.nk * s.tile_i * s.tile_j, 256);
   }
   return l;
 }
 
-#define OEC_HV_TILES(X) X(32, 1) X(32, 2) X(32, 4) X(64, 1) X(64, 2) X(128, 1)
-
-template <typename T>
-cudaError_t dispatch(const oec_schedule& s, int dtype, const Dom& d, const HV<T>& p, double dtr, char* scratch,
-                     cudaStream_t st) {
+template <class P>
+cudaError_t run(const oec_schedule& s, int dtype, const Dom& d, const HV<typename P::S>& p, double dtr, char* scratch,
+                cudaStream_t st) {
   Layout l = layout(s, dtype, d);
-  double* scr = (double*)(scratch + l.thomas);
   if (s.fusion == OEC_FUSE_NONE) {
-    T* ud = (T*)(scratch + l.ud);
-    T* vd = (T*)(scratch + l.vd);
-    // hdiff(u) and hdiff(v) into domain-layout temporaries: the fused hdiff
-    // kernel with the temporaries' strides (pitch ni, plane ni*nj)
-    oec_schedule hs{};
-    hs.fusion = OEC_FUSE_INLINE;
-    hs.staging = OEC_STAGE_SMEM;
-    hs.tile_i = 64;
-    hs.tile_j = 4;
-    hs.unroll = 1;
-    cudaError_t e = hdiff_launch_strided(hs, dtype, d, p.u, p.coeff, ud, d.ni, (int64_t)d.ni * d.nj, st);
+    typedef typename P::C C;
+    C* ud = (C*)(scratch + l.ud);
+    C* vd = (C*)(scratch + l.vd);
+    cudaError_t e = hdiff_to_compute(s.arith, dtype, d, p.u, p.coeff, ud, st);
     if (e != cudaSuccess) return e;
-    e = hdiff_launch_strided(hs, dtype, d, p.v, p.coeff, vd, d.ni, (int64_t)d.ni * d.nj, st);
+    e = hdiff_to_compute(s.arith, dtype, d, p.v, p.coeff, vd, st);
     if (e != cudaSuccess) return e;
     const int64_t ncol = (int64_t)d.ni * d.nj;
-    vadvc_kernel<T, double><<<(unsigned)((ncol + 127) / 128), 128, 0, st>>>(p, ud, vd, T(dtr), scr);
+    vadvc_kernel<P><<<(unsigned)((ncol + 127) / 128), 128, 0, st>>>(p, ud, vd, dtr, (typename P::R*)(scratch + l.thomas));
     return cudaGetLastError();
   }
-#define X(a, b)                                                                                  \
-  if (s.tile_i == a && s.tile_j == b) {                                                          \
-    dim3 g(ceil_div(d.ni, a), ceil_div(d.nj, b));                                                \
-    hv_fused_kernel<T, double, a, b><<<g, a * b, 0, st>>>(p, T(dtr), scr);                       \
-    return cudaGetLastError();                                                                   \
-  }
-  OEC_HV_TILES(X)
-#undef X
-  return cudaErrorInvalidValue;
+  return dispatch_fused<P>(s, d, p, dtr, scratch + l.thomas, st);
 }
 
 }  // namespace
 
 bool hdiff_vadvc_schedule_ok(const oec_schedule& s, std::string& why) {
+  if (s.arith != 0 && s.arith != 1) { why = "arith must be 0 (native) or 1 (double-float)"; return false; }
   if (s.fusion == OEC_FUSE_NONE) return true;
   if (s.fusion != OEC_FUSE_INLINE) { why = "fusion must be OEC_FUSE_INLINE or OEC_FUSE_NONE"; return false; }
 #define X(a, b) if (s.tile_i == a && s.tile_j == b) return true;
   OEC_HV_TILES(X)
 #undef X
-  why = "hdiff+vadvc column tiles: 32x1, 32x2, 32x4, 64x1, 64x2, 128x1";
+  why = "hdiff+vadvc column tiles: 16x4, 32x2, 8x8, 32x4";
   return false;
 }
 
@@ -280,14 +497,31 @@ size_t hdiff_vadvc_scratch_bytes(const oec_schedule& s, int dtype, const Dom& d)
 cudaError_t hdiff_vadvc_launch(const oec_schedule& s, int dtype, const Dom& d, const void* u, const void* v,
                                const void* w, const void* coeff, void* u_out, void* v_out, double dtr, void* scratch,
                                cudaStream_t st) {
+  const bool df = s.arith == 1;
   if (dtype == OEC_F64) {
     HV<double> p{(const double*)u, (const double*)v, (const double*)w, (const double*)coeff,
                  (double*)u_out, (double*)v_out, d.ni, d.nj, d.nk, d.sj, d.sk};
-    return dispatch<double>(s, dtype, d, p, dtr, (char*)scratch, st);
+    return df ? run<P64D>(s, dtype, d, p, dtr, (char*)scratch, st) : run<P64>(s, dtype, d, p, dtr, (char*)scratch, st);
   }
   HV<float> p{(const float*)u, (const float*)v, (const float*)w, (const float*)coeff,
               (float*)u_out, (float*)v_out, d.ni, d.nj, d.nk, d.sj, d.sk};
-  return dispatch<float>(s, dtype, d, p, dtr, (char*)scratch, st);
+  return df ? run<P32D>(s, dtype, d, p, dtr, (char*)scratch, st) : run<P32>(s, dtype, d, p, dtr, (char*)scratch, st);
+}
+
+size_t hdiff_vadvc_batch_slot_elems(const oec_schedule& s, int nk_max) {
+  return size_t(3) * nk_max * s.tile_i * s.tile_j;
+}
+
+int hdiff_vadvc_batch_blocks_per_sm(const oec_schedule& s, int dtype) {
+  const bool df = s.arith == 1;
+  if (dtype == OEC_F64) return df ? occupancy_of<P64D>(s) : occupancy_of<P64>(s);
+  return df ? occupancy_of<P32D>(s) : occupancy_of<P32>(s);
+}
+
+cudaError_t hdiff_vadvc_batch_launch(const oec_schedule& s, int dtype, const HVBatchLaunch& b, cudaStream_t st) {
+  const bool df = s.arith == 1;
+  if (dtype == OEC_F64) return df ? dispatch_batch<P64D>(s, b, st) : dispatch_batch<P64>(s, b, st);
+  return df ? dispatch_batch<P32D>(s, b, st) : dispatch_batch<P32>(s, b, st);
 }
 
 }  // namespace oec

@@ -12,6 +12,7 @@
 #include <string>
 
 #include "../../include/oec.h"
+#include "k_vadvc.cuh"
 
 namespace oec {
 
@@ -25,9 +26,6 @@ bool hdiff_schedule_ok(const oec_schedule& s, std::string& why);
 size_t hdiff_scratch_bytes(const oec_schedule& s, int dtype, const Dom& d);
 cudaError_t hdiff_launch(const oec_schedule& s, int dtype, const Dom& d, const void* in, const void* coeff,
                          void* out, void* scratch, cudaStream_t st);
-// Fused schedules only: output written with its own strides (osj, osk).
-cudaError_t hdiff_launch_strided(const oec_schedule& s, int dtype, const Dom& d, const void* in, const void* coeff,
-                                 void* out, int64_t osj, int64_t osk, cudaStream_t st);
 
 // ---- horizontal diffusion of u, v + vertical advection (Thomas) -------------
 bool hdiff_vadvc_schedule_ok(const oec_schedule& s, std::string& why);
@@ -35,6 +33,14 @@ size_t hdiff_vadvc_scratch_bytes(const oec_schedule& s, int dtype, const Dom& d)
 cudaError_t hdiff_vadvc_launch(const oec_schedule& s, int dtype, const Dom& d, const void* u, const void* v,
                                const void* w, const void* coeff, void* u_out, void* v_out, double dtr,
                                void* scratch, cudaStream_t st);
+// batched persistent form (ensembles of domains)
+size_t hdiff_vadvc_batch_slot_elems(const oec_schedule& s, int nk_max);
+int hdiff_vadvc_batch_blocks_per_sm(const oec_schedule& s, int dtype);
+cudaError_t hdiff_vadvc_batch_launch(const oec_schedule& s, int dtype, const HVBatchLaunch& b, cudaStream_t st);
+// hdiff written in the compute type of (arith, dtype) over the domain layout
+// (pitch ni, plane ni*nj): the producer of the staged hdiff+vadvc form
+cudaError_t hdiff_to_compute(int arith, int dtype, const Dom& d, const void* in, const void* coeff, void* out,
+                             cudaStream_t st);
 
 // ---- fastwaves-like program -------------------------------------------------
 struct FastwavesPtrs {

@@ -1,0 +1,93 @@
+"""Batched ensembles: one persistent launch over members of different sizes
+must give, member by member, the same bits as applying the program to each
+member alone with the same schedule (both run the same tile sweep), and stay
+within the oracle tolerance. Graph replay and direct launch agree."""
+
+import numpy as np
+import pytest
+
+from conftest import TOL, rel_err
+from oracle import stencils as S
+from paper_2005_13014_gb300 import inputs, programs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+SHAPES = [(37, 23, 11), (64, 8, 3), (16, 40, 17), (5, 5, 1), (70, 33, 9), (24, 64, 2)]
+
+
+def _members(dtype, h=3, shapes=SHAPES, seed=100):
+    from paper_2005_13014_gb300.api import device_field
+    ms = []
+    for x, n in enumerate(shapes):
+        f = inputs.hdiff_vadvc_fields(*n, h, seed=seed + 10 * x)
+        if dtype == "f32":
+            f = {k: v.astype(np.float32).astype(np.float64) for k, v in f.items()}
+        d = [device_field(f[k], h, dtype) for k in ("u", "v", "w", "coeff")]
+        o = [device_field(np.full_like(f["u"], 3.0), h, dtype) for _ in range(2)]
+        ms.append((f, d, o, n))
+    return ms
+
+
+@pytest.mark.parametrize("dtype,arith", [("f64", 0), ("f64", 1), ("f32", 0), ("f32", 1)])
+@pytest.mark.parametrize("tile", [(16, 4), (32, 2), (8, 8), (32, 4)])
+def test_batch_equals_single_applies_and_oracle(dtype, arith, tile):
+    from paper_2005_13014_gb300.api import Batch, Program, device_field
+    h = 3
+    prog = Program(programs.HDIFF_VADVC, dtype)
+    prog.set_schedule(fusion=0, staging=1, tile_i=tile[0], tile_j=tile[1], arith=arith)
+    ms = _members(dtype, h)
+    batch = Batch(prog, [(d, o, (0, 0, 0), n, (h, h, h)) for (_, d, o, n) in ms], [2.0])
+    assert batch.n_items == sum(-(-n[0] // tile[0]) * -(-n[1] // tile[1]) for n in SHAPES)
+    for graph in (True, False):
+        for (_, _, o, _) in ms:
+            for t in o:
+                t.tensor.fill_(3.0)
+        batch.apply(graph=graph)
+        torch.cuda.synchronize()
+        for (f, d, o, n) in ms:
+            single = [device_field(np.zeros_like(f["u"]), h, dtype) for _ in range(2)]
+            prog.apply(d, single, (0, 0, 0), n, (h, h, h), [2.0])
+            torch.cuda.synchronize()
+            for a, b in zip(o, single):
+                assert torch.equal(a.tensor, b.tensor) or torch.equal(
+                    a.interior((0, 0, 0), n), b.interior((0, 0, 0), n))
+            G = {k: S.Grid.storage(v, h) for k, v in f.items()}
+            ru, rv = S.hdiff_vadvc(G["u"], G["v"], G["w"], G["coeff"], (0, 0, 0), n, 2.0)
+            gu = o[0].interior((0, 0, 0), n).cpu().numpy().astype(np.float64)
+            gv = o[1].interior((0, 0, 0), n).cpu().numpy().astype(np.float64)
+            assert max(rel_err(gu, ru), rel_err(gv, rv)) <= TOL[dtype]
+            # nothing written outside the member's domain
+            full = o[0].tensor.cpu().numpy()
+            oi, oj, ok = o[0].origin
+            mask = np.ones(full.shape, bool)
+            mask[ok:ok + n[2], oj:oj + n[1], oi:oi + n[0]] = False
+            assert np.all(full[mask] == 3.0)
+
+
+def test_batch_config_ensemble_32_members_f32():
+    """The 32-member ensemble of uneven domains (i, j in {64..512}, k in
+    {60, 80, 137}), FP32, checked on sampled columns against the oracle."""
+    from paper_2005_13014_gb300.api import Batch, Program, device_field
+    h = 3
+    shapes = inputs.ensemble_members(32)
+    prog = Program(programs.HDIFF_VADVC, "f32")
+    ms = []
+    for x, n in enumerate(shapes):
+        f = inputs.hdiff_vadvc_fields(*n, h, seed=inputs.SEED + x)
+        d = [device_field(f[k], h, "f32") for k in ("u", "v", "w", "coeff")]
+        o = [device_field(np.zeros_like(f["u"]), h, "f32") for _ in range(2)]
+        ms.append((f, d, o, n))
+    batch = Batch(prog, [(d, o, (0, 0, 0), n, (h, h, h)) for (_, d, o, n) in ms], [2.0])
+    batch.apply()
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(7)
+    for (f, d, o, n) in ms[::4]:
+        # oracle on a sub-block of columns (the column solve is local to a column)
+        i0, j0 = int(rng.integers(0, n[0] - 8)), int(rng.integers(0, n[1] - 8))
+        lb, ub = (i0, j0, 0), (i0 + 8, j0 + 8, n[2])
+        g = {k: S.Grid.storage(v.astype(np.float32).astype(np.float64), h) for k, v in f.items()}
+        ru, rv = S.hdiff_vadvc(g["u"], g["v"], g["w"], g["coeff"], lb, ub, 2.0)
+        gu = o[0].interior(lb, ub).cpu().numpy().astype(np.float64)
+        gv = o[1].interior(lb, ub).cpu().numpy().astype(np.float64)
+        assert max(rel_err(gu, ru), rel_err(gv, rv)) <= TOL["f32"]

@@ -76,21 +76,34 @@ def _hdiff_case(n, h, dtype, sched, align=0, lb=None, ub=None, poison=True):
     return rel_err(got, ref)
 
 
+# (dtype, arith): FP64 programs in native FP64 and in double-float; FP32 native
+PRECISIONS = [("f64", 0), ("f64", 1), ("f32", 0)]
+HV_PRECISIONS = [("f64", 0), ("f64", 1), ("f32", 0), ("f32", 1)]
+
+
+def _with(sched, arith):
+    s = dict(sched)
+    s["arith"] = arith
+    return s
+
+
 @pytest.mark.parametrize("sched", HDIFF_SCHEDS, ids=str)
-@pytest.mark.parametrize("dtype", ["f64", "f32"])
-def test_hdiff_ragged(sched, dtype):
-    assert _hdiff_case((37, 29, 5), 2, dtype, sched) <= TOL[dtype]
+@pytest.mark.parametrize("dtype,arith", PRECISIONS)
+def test_hdiff_ragged(sched, dtype, arith):
+    assert _hdiff_case((37, 29, 5), 2, dtype, _with(sched, arith)) <= TOL[dtype]
 
 
 @pytest.mark.parametrize("sched", [dict(fusion=1), dict(fusion=0, staging=1, tile_i=64, tile_j=4, k_chunk=2),
                                    dict(fusion=0, staging=0, tile_i=64, tile_j=4, unroll=2)], ids=str)
-def test_hdiff_config_64x64x60_f64(sched):
-    assert _hdiff_case((64, 64, 60), 2, "f64", sched) <= TOL["f64"]
+@pytest.mark.parametrize("arith", [0, 1])
+def test_hdiff_config_64x64x60_f64(sched, arith):
+    assert _hdiff_case((64, 64, 60), 2, "f64", _with(sched, arith)) <= TOL["f64"]
 
 
-@pytest.mark.parametrize("dtype", ["f32", "f64"])
-def test_hdiff_256x256x80_halo3(dtype):
-    assert _hdiff_case((256, 256, 80), 3, dtype, None, poison=False) <= TOL[dtype]
+@pytest.mark.parametrize("dtype,arith", PRECISIONS)
+def test_hdiff_256x256x80_halo3(dtype, arith):
+    sched = dict(fusion=0, staging=1, tile_i=64, tile_j=4, k_chunk=2, arith=arith)
+    assert _hdiff_case((256, 256, 80), 3, dtype, sched, poison=False) <= TOL[dtype]
 
 
 def test_hdiff_subdomain_and_aligned_rows():
@@ -107,7 +120,7 @@ def test_hdiff_single_point_and_line():
 # ---------------------------------------------------------------- hdiff+vadvc
 
 HV_SCHEDS = [dict(fusion=1)] + [dict(fusion=0, staging=1, tile_i=a, tile_j=b)
-                                for a, b in [(32, 1), (32, 2), (32, 4), (64, 1), (64, 2), (128, 1)]]
+                                for a, b in [(16, 4), (32, 2), (8, 8), (32, 4)]]
 
 
 def _hv_case(n, h, dtype, sched, dtr=2.0):
@@ -132,24 +145,27 @@ def _hv_case(n, h, dtype, sched, dtr=2.0):
 
 
 @pytest.mark.parametrize("sched", HV_SCHEDS, ids=str)
-@pytest.mark.parametrize("dtype", ["f64", "f32"])
-def test_hdiff_vadvc_ragged(sched, dtype):
-    assert _hv_case((37, 23, 11), 3, dtype, sched) <= TOL[dtype]
+@pytest.mark.parametrize("dtype,arith", HV_PRECISIONS)
+def test_hdiff_vadvc_ragged(sched, dtype, arith):
+    assert _hv_case((37, 23, 11), 3, dtype, _with(sched, arith)) <= TOL[dtype]
 
 
-@pytest.mark.parametrize("nk", [1, 2, 3])
-def test_hdiff_vadvc_short_columns(nk):
-    assert _hv_case((33, 5, nk), 3, "f64", None) <= TOL["f64"]
-    assert _hv_case((33, 5, nk), 3, "f64", dict(fusion=1)) <= TOL["f64"]
+@pytest.mark.parametrize("nk", [1, 2, 3, 4, 5, 9])
+@pytest.mark.parametrize("arith", [0, 1])
+def test_hdiff_vadvc_short_columns(nk, arith):
+    for sched in HV_SCHEDS:
+        assert _hv_case((33, 5, nk), 3, "f64", _with(sched, arith)) <= TOL["f64"]
 
 
-@pytest.mark.parametrize("sched", [None, dict(fusion=1)], ids=str)
-def test_hdiff_vadvc_config_128x128x80_f64(sched):
-    assert _hv_case((128, 128, 80), 3, "f64", sched) <= TOL["f64"]
+@pytest.mark.parametrize("sched", HV_SCHEDS[:3], ids=str)
+@pytest.mark.parametrize("arith", [0, 1])
+def test_hdiff_vadvc_config_128x128x80_f64(sched, arith):
+    assert _hv_case((128, 128, 80), 3, "f64", _with(sched, arith)) <= TOL["f64"]
 
 
-def test_hdiff_vadvc_config_128x128x137_f32():
-    assert _hv_case((128, 128, 137), 3, "f32", None) <= TOL["f32"]
+@pytest.mark.parametrize("arith", [0, 1])
+def test_hdiff_vadvc_config_128x128x137_f32(arith):
+    assert _hv_case((128, 128, 137), 3, "f32", dict(fusion=0, staging=1, tile_i=16, tile_j=4, arith=arith)) <= TOL["f32"]
 
 
 # ------------------------------------------------------------------ fastwaves
@@ -178,11 +194,12 @@ def _fw_case(n, h, dtype, sched, dt=0.5, alpha=0.0625):
 
 
 @pytest.mark.parametrize("sched", FW_SCHEDS, ids=str)
-@pytest.mark.parametrize("dtype", ["f64", "f32"])
-def test_fastwaves_ragged(sched, dtype):
-    assert _fw_case((37, 29, 7), 3, dtype, sched) <= TOL[dtype]
+@pytest.mark.parametrize("dtype,arith", PRECISIONS)
+def test_fastwaves_ragged(sched, dtype, arith):
+    assert _fw_case((37, 29, 7), 3, dtype, _with(sched, arith)) <= TOL[dtype]
 
 
-@pytest.mark.parametrize("dtype", ["f32", "f64"])
-def test_fastwaves_config_256x256x80(dtype):
-    assert _fw_case((256, 256, 80), 3, dtype, None) <= TOL[dtype]
+@pytest.mark.parametrize("dtype,arith", PRECISIONS)
+def test_fastwaves_config_256x256x80(dtype, arith):
+    sched = dict(fusion=0, staging=0, tile_i=64, tile_j=4, unroll=2, arith=arith)
+    assert _fw_case((256, 256, 80), 3, dtype, sched) <= TOL[dtype]
