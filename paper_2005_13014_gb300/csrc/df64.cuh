@@ -6,8 +6,8 @@
 // convert to/from IEEE binary64 storage with integer operations only.
 //
 // Range: finite values with 2^-74 <= |x| < 2^128 keep ~48 bits; below that
-// the low part is dropped (absolute error below 2^-98); |x| >= 2^128
-// overflows. Every operation is written with explicit-rounding intrinsics so
+// the low part is dropped (absolute error below 2^-98), below 2^-126 the
+// value flushes to zero; |x| >= 2^128 overflows. Every operation is written with explicit-rounding intrinsics so
 // that the compiler neither contracts nor reorders the error terms.
 #pragma once
 
@@ -88,40 +88,58 @@ __device__ __forceinline__ df64 df_rcp(df64 b) { return df64{1.0f, 0.0f} / b; }
 __device__ __forceinline__ bool df_gt0(df64 a) { return a.hi > 0.0f; }   // sign of a normalised pair
 __device__ __forceinline__ df64 df_abs(df64 a) { return a.hi < 0.0f ? -a : a; }
 
-// ---- conversion from IEEE binary64 -----------------------------------------
-// hi = x rounded to float; lo = (x - hi) rounded to float, where x - hi is
-// taken exactly as the difference of the two binary64 bit patterns (same sign,
-// same or adjacent binade, at most 2^28 units of x's ulp), so no FP64
-// arithmetic is issued. Conversion error below 2^-48 |x|.
-__device__ __forceinline__ df64 df_from_double(double x) {
-  const float hi = __double2float_rn(x);
-  const long long bx = __double_as_longlong(x);
-  const long long bh = __double_as_longlong((double)hi);
-  const int d = (int)(bx - bh);                          // (|x| - |hi|) in units of x's ulp
-  const unsigned ex = (unsigned)(bx >> 52) & 0x7FFu;     // biased exponent of x
-  const float scale = __uint_as_float((ex - 948u) << 23);  // 2^(e-52) as a float
-  float lo = __fmul_rn(__int2float_rn(d), scale);
-  lo = (ex >= 949u && ex <= 1150u) ? lo : 0.0f;          // tiny or huge x: lo dropped
-  lo = bx < 0 ? -lo : lo;
-  return df64{hi, lo};
+// float value of a non-negative integer below 2^30, without a conversion
+// instruction: the two halves are placed in float significands by bit
+// assembly (exact), then combined with one rounding.
+__device__ __forceinline__ float u30_to_float(unsigned r) {
+  const float fh = __fsub_rn(__uint_as_float(0x4B000000u | (r >> 12)), 8388608.0f);
+  const float fl = __fsub_rn(__uint_as_float(0x4B000000u | (r & 0xFFFu)), 8388608.0f);
+  return __fmaf_rn(fh, 4096.0f, fl);
 }
 
-// ---- conversion to IEEE binary64 -------------------------------------------
-// (double)hi plus lo expressed as an integer count of hi's binary64 ulp, added
-// to the bit pattern (sign-magnitude, so magnitudes add); when hi is a power of
-// two and lo lowers the magnitude, the result sits one binade down and the
-// count doubles. Error below one binary64 ulp; no FP64 arithmetic.
+// ---- conversion from IEEE binary64 (integer and FP32 operations only) ------
+// hi = x rounded (half up) to a 24-bit significand by bit assembly; lo =
+// (x - hi), an integer of at most 2^29 units of x's ulp, rounded to a float.
+// Conversion error below 2^-48 |x|. Conversion instructions between float and
+// double run on the FP64 pipe on this part, so none is used.
+__device__ __forceinline__ df64 df_from_double(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
+  const unsigned sign = hw & 0x80000000u;
+  const unsigned ex = (hw >> 20) & 0x7FFu;                // biased binary64 exponent
+  const unsigned rnd = (lw >> 28) & 1u;                   // first bit below the float significand
+  unsigned hib = __funnelshift_l(lw, (hw & 0x7FFFFFFFu) - 0x38000000u, 3) + rnd;  // exponent and fraction
+  hib = ex <= 896u ? 0u : hib;                            // below float range: zero
+  hib = ex >= 1151u ? 0x7F800000u : hib;                  // above float range: infinity
+  const int r = (int)(lw & 0x1FFFFFFFu) - (int)(rnd << 29);   // x - hi in units of x's ulp
+  const float scale = __uint_as_float((ex - 948u) << 23);    // 2^(e - 52) as a float
+  float lo = __fmul_rn(u30_to_float((unsigned)abs(r)), scale);
+  lo = (ex >= 949u && ex <= 1150u) ? lo : 0.0f;          // tiny or huge x: lo dropped
+  const unsigned lsign = sign ^ (r < 0 ? 0x80000000u : 0u);
+  return df64{__uint_as_float(sign | hib), __uint_as_float(__float_as_uint(lo) | lsign)};
+}
+
+// ---- conversion to IEEE binary64 (integer operations only) -----------------
+// hi's bits widened to binary64, plus lo expressed as an integer count of that
+// binary64's ulp, added to the bit pattern (sign-magnitude, so magnitudes
+// add); when hi is a power of two and lo lowers the magnitude the result sits
+// one binade down and the count doubles. lo bits below the binary64 ulp are
+// truncated (error below one ulp).
 __device__ __forceinline__ double df_to_double(df64 a) {
-  const unsigned hb = __float_as_uint(a.hi);
-  const unsigned eh = (hb >> 23) & 0xFFu;
-  const double hd = (double)a.hi;
-  if (eh < 52u || eh == 255u) return hd;                 // |hi| < 2^-75: lo dropped
-  const bool down = ((__float_as_uint(a.lo) ^ hb) & 0x80000000u) != 0u;
-  const bool pow2 = (hb & 0x7FFFFFu) == 0u;
-  float t = __fmul_rn(fabsf(a.lo), __uint_as_float((306u - eh) << 23));  // |lo| / ulp(hi as binary64)
-  t = (pow2 && down) ? __fmul_rn(t, 2.0f) : t;
-  const long long n = (long long)__float2int_rn(t);
-  return __longlong_as_double(__double_as_longlong(hd) + (down ? -n : n));
+  const unsigned hb = __float_as_uint(a.hi), lb = __float_as_uint(a.lo);
+  const unsigned eh = (hb >> 23) & 0xFFu, el = (lb >> 23) & 0xFFu;
+  if (eh == 0u) return 0.0;                               // zero (and float denormals)
+  unsigned long long bits = ((unsigned long long)(hb & 0x80000000u) << 32) |
+                            ((unsigned long long)(eh + 896u) << 52) | ((unsigned long long)(hb & 0x7FFFFFu) << 29);
+  if (el != 0u) {                                         // lo zero or denormal: nothing to add
+    const bool down = ((lb ^ hb) & 0x80000000u) != 0u;
+    const bool pow2 = (hb & 0x7FFFFFu) == 0u;
+    const int sh = 29 - (int)eh + (int)el + ((pow2 && down) ? 1 : 0);
+    const unsigned ml = (lb & 0x7FFFFFu) | 0x800000u;
+    const unsigned long long n = sh >= 0 ? ((unsigned long long)ml << min(sh, 31)) : (sh > -24 ? (ml >> -sh) : 0u);
+    bits = down ? bits - n : bits + n;
+  }
+  return __longlong_as_double((long long)bits);
 }
 
 __device__ __forceinline__ df64 df_from_float(float x) { return df64{x, 0.0f}; }

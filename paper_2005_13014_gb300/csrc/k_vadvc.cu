@@ -55,10 +55,8 @@ struct HVSmem {
   typedef typename P::S S;
   typedef typename P::C C;
   static constexpr int WI = TI + 4, WJ = TJ + 4, NC = TI * TJ, NT = 2 * NC, RING = KC + 2;
-  // raw storage values of one chunk: u, v windows, the w rows (TI+1 wide) and coeff
-  static constexpr int N_WIN = 2 * KC * WJ * WI, N_W = KC * TJ * (TI + 1), N_CF = KC * NC;
-  static constexpr int N_LOAD = N_WIN + N_W + N_CF;
-  static constexpr int PF = (N_LOAD + NT - 1) / NT;   // prefetch registers per thread
+  static constexpr int QW = (WJ * WI + NT - 1) / NT;        // window positions per thread
+  static constexpr int QR = (TJ * (TI + 1) + NT - 1) / NT;  // w-row positions per thread
   C win[2][KC][WJ][WI];
   C lap[2][KC][TJ + 2][TI + 2];
   C flx[2][KC][TJ][TI + 1];
@@ -70,57 +68,12 @@ struct HVSmem {
   int item;
 };
 
-// Global loads of chunk [k0, k0+nl): element e of the chunk's load list.
-template <class P, int TI, int TJ, int KC>
-__device__ __forceinline__ const typename P::S* hv_load_addr(const HV<typename P::S>& p, int i0, int j0, int k0, int nl,
-                                                             int e) {
-  typedef HVSmem<P, TI, TJ, KC> SM;
-  constexpr int WI = SM::WI, WJ = SM::WJ, NC = SM::NC;
-  if (e < 2 * nl * WJ * WI) {
-    const int c = e % WI, r = (e / WI) % WJ, l = (e / (WI * WJ)) % nl, f = e / (WI * WJ * nl);
-    return (f ? p.v : p.u) + (int64_t)(k0 + l) * p.sk + (int64_t)(j0 - 2 + r) * p.sj + (i0 - 2 + c);
-  }
-  e -= 2 * nl * WJ * WI;
-  if (e < nl * TJ * (TI + 1)) {
-    const int c = e % (TI + 1), r = (e / (TI + 1)) % TJ, l = e / ((TI + 1) * TJ);
-    return p.w + (int64_t)(k0 + l) * p.sk + (int64_t)(j0 + r) * p.sj + (i0 + c);
-  }
-  e -= nl * TJ * (TI + 1);
-  const int q = e % NC, l = e / NC;
-  return p.coeff + (int64_t)(k0 + l) * p.sk + (int64_t)(j0 + q / TI) * p.sj + (i0 + q % TI);
-}
-template <class P, int TI, int TJ, int KC>
-__device__ __forceinline__ bool hv_load_valid(int vi, int vj, int nl, int e) {
-  typedef HVSmem<P, TI, TJ, KC> SM;
-  constexpr int WI = SM::WI, WJ = SM::WJ, NC = SM::NC;
-  if (e < 2 * nl * WJ * WI) return e % WI < vi + 4 && (e / WI) % WJ < vj + 4;
-  e -= 2 * nl * WJ * WI;
-  if (e < nl * TJ * (TI + 1)) return e % (TI + 1) < vi + 1 && (e / (TI + 1)) % TJ < vj;
-  e -= nl * TJ * (TI + 1);
-  if (e >= nl * NC) return false;
-  const int q = e % NC;
-  return q % TI < vi && q / TI < vj;
-}
-template <class P, int TI, int TJ, int KC>
-__device__ __forceinline__ void hv_load_store(HVSmem<P, TI, TJ, KC>& sm, int nl, int e, typename P::S v) {
-  typedef HVSmem<P, TI, TJ, KC> SM;
-  typedef typename P::C C;
-  constexpr int WI = SM::WI, WJ = SM::WJ, NC = SM::NC;
-  if (e < 2 * nl * WJ * WI) {
-    const int c = e % WI, r = (e / WI) % WJ, l = (e / (WI * WJ)) % nl, f = e / (WI * WJ * nl);
-    sm.win[f][l][r][c] = cvt<C>(v);
-    return;
-  }
-  e -= 2 * nl * WJ * WI;
-  if (e < nl * TJ * (TI + 1)) {
-    sm.wrow[e / ((TI + 1) * TJ)][(e / (TI + 1)) % TJ][e % (TI + 1)] = v;
-    return;
-  }
-  e -= nl * TJ * (TI + 1);
-  sm.cf[e / NC][e % NC] = v;
-}
-
-// The fused sweep of one tile (all 2*TI*TJ threads of the CTA call it).
+// The fused sweep of one tile (all 2*TI*TJ threads of the CTA call it). Every
+// thread owns fixed positions of each plane (window, Laplacian, fluxes,
+// outputs) and loops over both fields and the chunk's levels there, so index
+// arithmetic is paid once per chunk. In the elimination phase thread t works
+// on column t % NC for field t / NC (u or v); both threads of a column carry
+// the shared c' recurrence.
 template <class P, int TI, int TJ, int KC>
 __device__ void hv_tile(const HV<typename P::S>& p, int i0, int j0, typename P::R* __restrict__ slot,
                         typename P::C dtr, HVSmem<P, TI, TJ, KC>& sm) {
@@ -128,35 +81,78 @@ __device__ void hv_tile(const HV<typename P::S>& p, int i0, int j0, typename P::
   typedef typename P::C C;
   typedef typename P::R R;
   typedef HVSmem<P, TI, TJ, KC> SM;
-  constexpr int NC = SM::NC, NT = SM::NT, RING = SM::RING, PF = SM::PF;
+  constexpr int NC = SM::NC, NT = SM::NT, RING = SM::RING, WI = SM::WI, WJ = SM::WJ;
+  constexpr int QW = SM::QW, QR = SM::QR;
   const int tid = threadIdx.x;
   const int vi = min(TI, p.ni - i0), vj = min(TJ, p.nj - j0);
   const int nk = p.nk;
-  // column state (threads tid < NC)
-  const int tx = tid % TI, ty = tid / TI;
-  const bool col = tid < NC && tx < vi && ty < vj;
+  // elimination-phase role: column q, field f
+  const int q = tid % NC, fld = tid / NC;
+  const int tx = q % TI, ty = q / TI;
+  const bool col = tx < vi && ty < vj;
   const int64_t cbase = (int64_t)(j0 + ty) * p.sj + (i0 + tx);
-  C um = zero_<C>(), uc = zero_<C>(), vm = zero_<C>(), vc = zero_<C>(), wf_c = zero_<C>();
-  R cp = cvt<R>(0.0f), dpu = cvt<R>(0.0f), dpv = cvt<R>(0.0f);
-  int knext = 0;   // next elimination step
+  const S* __restrict__ src = fld ? p.v : p.u;
+  S* __restrict__ dst = fld ? p.vo : p.uo;
 
-  // prefetch registers: the next chunk's raw values, loaded across phase B
-  S pf[PF];
+  // ---- per-thread load positions (computed once per tile) -----------------
+  int64_t woff[QW];
+  bool wok[QW];
+#pragma unroll
+  for (int x = 0; x < QW; ++x) {
+    const int e = tid + x * NT, r = e / WI, c = e % WI;
+    wok[x] = e < WJ * WI && c < vi + 4 && r < vj + 4;
+    woff[x] = (int64_t)(j0 - 2 + r) * p.sj + (i0 - 2 + c);
+  }
+  int64_t roff[QR];
+  bool rok[QR];
+#pragma unroll
+  for (int x = 0; x < QR; ++x) {
+    const int e = tid + x * NT, r = e / (TI + 1), c = e % (TI + 1);
+    rok[x] = e < TJ * (TI + 1) && c < vi + 1 && r < vj;
+    roff[x] = (int64_t)(j0 + r) * p.sj + (i0 + c);
+  }
+  const bool cfok = tid < NC && col;
+  S pw[QW][2][KC], pr[QR][KC], pc[KC];
   auto issue = [&](int k0, int nl) {
 #pragma unroll
-    for (int x = 0; x < PF; ++x) {
-      const int e = tid + x * NT;
-      if (e < SM::N_LOAD && hv_load_valid<P, TI, TJ, KC>(vi, vj, nl, e))
-        pf[x] = ldg(hv_load_addr<P, TI, TJ, KC>(p, i0, j0, k0, nl, e));
+    for (int l = 0; l < KC; ++l) {
+      if (l < nl) {
+        const int64_t ko = (int64_t)(k0 + l) * p.sk;
+#pragma unroll
+        for (int x = 0; x < QW; ++x)
+          if (wok[x]) {
+            pw[x][0][l] = ldg(p.u + ko + woff[x]);
+            pw[x][1][l] = ldg(p.v + ko + woff[x]);
+          }
+#pragma unroll
+        for (int x = 0; x < QR; ++x)
+          if (rok[x]) pr[x][l] = ldg(p.w + ko + roff[x]);
+        if (cfok) pc[l] = ldg(p.coeff + ko + cbase);
+      }
     }
   };
   auto land = [&](int nl) {
 #pragma unroll
-    for (int x = 0; x < PF; ++x) {
-      const int e = tid + x * NT;
-      if (e < SM::N_LOAD && hv_load_valid<P, TI, TJ, KC>(vi, vj, nl, e)) hv_load_store<P, TI, TJ, KC>(sm, nl, e, pf[x]);
+    for (int l = 0; l < KC; ++l) {
+      if (l < nl) {
+#pragma unroll
+        for (int x = 0; x < QW; ++x)
+          if (wok[x]) {
+            const int e = tid + x * NT;
+            (&sm.win[0][l][0][0])[e] = cvt<C>(pw[x][0][l]);
+            (&sm.win[1][l][0][0])[e] = cvt<C>(pw[x][1][l]);
+          }
+#pragma unroll
+        for (int x = 0; x < QR; ++x)
+          if (rok[x]) (&sm.wrow[l][0][0])[tid + x * NT] = pr[x][l];
+        if (cfok) sm.cf[l][q] = pc[l];
+      }
     }
   };
+
+  C um = zero_<C>(), uc = zero_<C>(), wf_c = zero_<C>();
+  R cp = cvt<R>(0.0f), dp = cvt<R>(0.0f);
+  int knext = 0;   // next elimination step
   issue(0, min(KC, nk));
   land(min(KC, nk));
   __syncthreads();
@@ -164,42 +160,62 @@ __device__ void hv_tile(const HV<typename P::S>& p, int i0, int j0, typename P::
   for (int k0 = 0; k0 < nk; k0 += KC) {
     const int nl = min(KC, nk - k0);
     // ---- phase A: hdiff of u and v (and wf) for levels [k0, k0+nl) ----------
-    for (int idx = tid; idx < 2 * nl * (TJ + 2) * (TI + 2); idx += NT) {
-      const int c = idx % (TI + 2), r = (idx / (TI + 2)) % (TJ + 2), l = (idx / ((TI + 2) * (TJ + 2))) % nl;
-      const int f = idx / ((TI + 2) * (TJ + 2) * nl);
+    for (int e = tid; e < (TJ + 2) * (TI + 2); e += NT) {
+      const int r = e / (TI + 2), c = e % (TI + 2);
       if (c < vi + 2 && r < vj + 2) {
-        const auto& W = sm.win[f][l];
-        sm.lap[f][l][r][c] = hlap(W[r + 1][c + 1], W[r + 1][c], W[r + 1][c + 2], W[r][c + 1], W[r + 2][c + 1]);
+#pragma unroll
+        for (int f = 0; f < 2; ++f)
+#pragma unroll
+          for (int l = 0; l < KC; ++l)
+            if (l < nl) {
+              const auto& W = sm.win[f][l];
+              sm.lap[f][l][r][c] = hlap(W[r + 1][c + 1], W[r + 1][c], W[r + 1][c + 2], W[r][c + 1], W[r + 2][c + 1]);
+            }
       }
     }
-    for (int idx = tid; idx < nl * NC; idx += NT) {
-      const int q = idx % NC, l = idx / NC, x = q % TI, y = q / TI;
-      if (x < vi && y < vj) sm.wf[l][q] = mul_p2(cvt<C>(sm.wrow[l][y][x]) + cvt<C>(sm.wrow[l][y][x + 1]), 0.5f);
+    if (tid < NC && col) {
+#pragma unroll
+      for (int l = 0; l < KC; ++l)
+        if (l < nl) sm.wf[l][q] = mul_p2(cvt<C>(sm.wrow[l][ty][tx]) + cvt<C>(sm.wrow[l][ty][tx + 1]), 0.5f);
     }
     __syncthreads();
-    for (int idx = tid; idx < 2 * nl * TJ * (TI + 1); idx += NT) {
-      const int c = idx % (TI + 1), r = (idx / (TI + 1)) % TJ, l = (idx / ((TI + 1) * TJ)) % nl, f = idx / ((TI + 1) * TJ * nl);
-      if (c < vi + 1 && r < vj) {
-        const auto& W = sm.win[f][l];
-        const auto& L = sm.lap[f][l];
-        sm.flx[f][l][r][c] = hflux(L[r + 1][c + 1], L[r + 1][c], W[r + 2][c + 2], W[r + 2][c + 1]);
-      }
-    }
-    for (int idx = tid; idx < 2 * nl * (TJ + 1) * TI; idx += NT) {
-      const int c = idx % TI, r = (idx / TI) % (TJ + 1), l = (idx / (TI * (TJ + 1))) % nl, f = idx / (TI * (TJ + 1) * nl);
-      if (c < vi && r < vj + 1) {
-        const auto& W = sm.win[f][l];
-        const auto& L = sm.lap[f][l];
-        sm.fly[f][l][r][c] = hflux(L[r + 1][c + 1], L[r][c + 1], W[r + 2][c + 2], W[r + 1][c + 2]);
+    for (int e = tid; e < TJ * (TI + 1) + (TJ + 1) * TI; e += NT) {
+      if (e < TJ * (TI + 1)) {
+        const int r = e / (TI + 1), c = e % (TI + 1);
+        if (c < vi + 1 && r < vj) {
+#pragma unroll
+          for (int f = 0; f < 2; ++f)
+#pragma unroll
+            for (int l = 0; l < KC; ++l)
+              if (l < nl) {
+                const auto& W = sm.win[f][l];
+                const auto& L = sm.lap[f][l];
+                sm.flx[f][l][r][c] = hflux(L[r + 1][c + 1], L[r + 1][c], W[r + 2][c + 2], W[r + 2][c + 1]);
+              }
+        }
+      } else {
+        const int g = e - TJ * (TI + 1), r = g / TI, c = g % TI;
+        if (c < vi && r < vj + 1) {
+#pragma unroll
+          for (int f = 0; f < 2; ++f)
+#pragma unroll
+            for (int l = 0; l < KC; ++l)
+              if (l < nl) {
+                const auto& W = sm.win[f][l];
+                const auto& L = sm.lap[f][l];
+                sm.fly[f][l][r][c] = hflux(L[r + 1][c + 1], L[r][c + 1], W[r + 2][c + 2], W[r + 1][c + 2]);
+              }
+        }
       }
     }
     __syncthreads();
-    for (int idx = tid; idx < 2 * nl * NC; idx += NT) {
-      const int q = idx % NC, l = (idx / NC) % nl, f = idx / (NC * nl);
-      const int x = q % TI, y = q / TI;
-      if (x < vi && y < vj)
-        sm.ring[f][(k0 + l) % RING][q] = hout(sm.win[f][l][y + 2][x + 2], cvt<C>(sm.cf[l][q]), sm.flx[f][l][y][x + 1],
-                                              sm.flx[f][l][y][x], sm.fly[f][l][y + 1][x], sm.fly[f][l][y][x]);
+    if (col) {   // thread (q, fld): hdiff output of field fld at column q
+#pragma unroll
+      for (int l = 0; l < KC; ++l)
+        if (l < nl)
+          sm.ring[fld][(k0 + l) % RING][q] =
+              hout(sm.win[fld][l][ty + 2][tx + 2], cvt<C>(sm.cf[l][q]), sm.flx[fld][l][ty][tx + 1], sm.flx[fld][l][ty][tx],
+                   sm.fly[fld][l][ty + 1][tx], sm.fly[fld][l][ty][tx]);
     }
     __syncthreads();
     // the next chunk's loads fly while this chunk's elimination steps run
@@ -209,29 +225,33 @@ __device__ void hv_tile(const HV<typename P::S>& p, int i0, int j0, typename P::
     const int last_avail = k0 + nl - 1;
     const int kend = last_avail == nk - 1 ? nk - 1 : last_avail - 1;
     if (col) {
-      if (knext == 0) wf_c = sm.wf[0][tid];
+      if (knext == 0) {
+        wf_c = sm.wf[0][q];
+        uc = sm.ring[fld][0][q];
+      }
       for (int k = knext; k <= kend; ++k) {
-        if (k == 0) {
-          uc = sm.ring[0][0][tid];
-          vc = sm.ring[1][0][tid];
-        }
-        const bool hi = k + 1 < nk;
-        const C up = hi ? sm.ring[0][(k + 1) % RING][tid] : zero_<C>();
-        const C vp = hi ? sm.ring[1][(k + 1) % RING][tid] : zero_<C>();
-        const C wf_p = hi ? sm.wf[k + 1 - k0][tid] : zero_<C>();
-        C a, b, c, du, dv;
-        hv_row(k > 0, hi, wf_c, wf_p, dtr, um, uc, up, vm, vc, vp, a, b, c, du, dv);
+        const bool lo = k > 0, hi = k + 1 < nk;
+        const C up = hi ? sm.ring[fld][(k + 1) % RING][q] : zero_<C>();
+        const C wf_p = hi ? sm.wf[k + 1 - k0][q] : zero_<C>();
+        const C a = lo ? -mul_p2(wf_c, 0.25f) : zero_<C>();
+        const C c = hi ? mul_p2(wf_p, 0.25f) : zero_<C>();
+        const C b = dtr + abs_(a) + abs_(c);
+        const C t = dtr * uc;
+        C d;
+        if (lo && hi) d = t - mul_p2(a * (um - uc) + c * (up - uc), 0.5f);
+        else if (hi) d = t - mul_p2(c * (up - uc), 0.5f);
+        else if (lo) d = t - mul_p2(a * (um - uc), 0.5f);
+        else d = t;
         const R ra = cvt<R>(a);
         const R m = k == 0 ? cvt<R>(b) : cvt<R>(b) - ra * cp;
         const R inv = rcp_(m);
         cp = cvt<R>(c) * inv;
-        dpu = (cvt<R>(du) - ra * dpu) * inv;
-        dpv = (cvt<R>(dv) - ra * dpv) * inv;
-        R* s = slot + (int64_t)k * 3 * NC + tid;
-        s[0] = cp;
-        s[NC] = dpu;
-        s[2 * NC] = dpv;
-        um = uc; uc = up; vm = vc; vc = vp;
+        dp = (cvt<R>(d) - ra * dp) * inv;
+        R* s = slot + (int64_t)k * 3 * NC + q;
+        if (fld == 0) s[0] = cp;
+        s[(1 + fld) * NC] = dp;
+        um = uc;
+        uc = up;
         wf_c = wf_p;
       }
     }
@@ -242,37 +262,34 @@ __device__ void hv_tile(const HV<typename P::S>& p, int i0, int j0, typename P::
       __syncthreads();
     }
   }
-  // ---- back substitution, loads batched BK levels at a time ---------------
+  // ---- back substitution (thread per column and field), loads batched ------
   if (col) {
     constexpr int BK = 8;
-    R xu = dpu, xv = dpv;
+    R x = dp;
     int64_t o = (int64_t)(nk - 1) * p.sk + cbase;
-    p.uo[o] = cvt<S>(xu);
-    p.vo[o] = cvt<S>(xv);
+    dst[o] = cvt<S>(x);
     for (int kt = nk - 2; kt >= 0; kt -= BK) {
-      R c_[BK], du_[BK], dv_[BK];
+      R c_[BK], d_[BK];
 #pragma unroll
-      for (int x = 0; x < BK; ++x) {
-        if (kt - x >= 0) {
-          const R* s = slot + (int64_t)(kt - x) * 3 * NC + tid;
-          c_[x] = s[0];
-          du_[x] = s[NC];
-          dv_[x] = s[2 * NC];
+      for (int y = 0; y < BK; ++y) {
+        if (kt - y >= 0) {
+          const R* s = slot + (int64_t)(kt - y) * 3 * NC + q;
+          c_[y] = s[0];
+          d_[y] = s[(1 + fld) * NC];
         }
       }
 #pragma unroll
-      for (int x = 0; x < BK; ++x) {
-        if (kt - x >= 0) {
-          xu = du_[x] - c_[x] * xu;
-          xv = dv_[x] - c_[x] * xv;
+      for (int y = 0; y < BK; ++y) {
+        if (kt - y >= 0) {
+          x = d_[y] - c_[y] * x;
           o -= p.sk;
-          p.uo[o] = cvt<S>(xu);
-          p.vo[o] = cvt<S>(xv);
+          dst[o] = cvt<S>(x);
         }
       }
     }
   }
   __syncthreads();
+  (void)src;
 }
 
 template <class P, int TI, int TJ, int KC>

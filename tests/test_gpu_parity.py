@@ -203,3 +203,28 @@ def test_fastwaves_ragged(sched, dtype, arith):
 def test_fastwaves_config_256x256x80(dtype, arith):
     sched = dict(fusion=0, staging=0, tile_i=64, tile_j=4, unroll=2, arith=arith)
     assert _fw_case((256, 256, 80), 3, dtype, sched) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("arith", [0, 1])
+def test_hdiff_f64_identity_on_edge_values(arith):
+    """coeff = 0 makes out = in: exercises the binary64 <-> double-float
+    conversions on powers of two, values next to binade boundaries, both signs
+    and magnitudes from 2^-70 to 2^110, inside the double-float range that
+    starts at 2^-74 (relative error within 2^-47)."""
+    from paper_2005_13014_gb300.api import Program, device_field
+    n, h = (40, 9, 3), 2
+    rng = np.random.default_rng(5)
+    base = np.array([1.0, -1.0, 2.0, 0.5, 1 - 2.0**-53, 1 + 2.0**-52, 2.0**-60, -(2.0**100), 3.0, 1 / 3,
+                     1 - 2.0**-25, 1 - 2.0**-24, 16777215.0, 16777217.0, 0.1, -7.25e-12, 123456.789])
+    inp = rng.choice(base, size=(n[2] + 2 * h, n[1] + 2 * h, n[0] + 2 * h)) * rng.choice([1.0, -1.0], size=1)
+    inp = inp * 10.0 ** rng.integers(-3, 4, size=inp.shape)
+    p = Program(programs.HDIFF, "f64")
+    p.set_schedule(fusion=0, staging=1, tile_i=32, tile_j=4, k_chunk=0, arith=arith)
+    din = device_field(inp, h, "f64")
+    dco = device_field(np.zeros_like(inp), h, "f64")
+    dout = device_field(np.zeros_like(inp), h, "f64")
+    p.apply([din, dco], [dout], (0, 0, 0), n, (h, h, h))
+    torch.cuda.synchronize()
+    got = dout.interior((0, 0, 0), n).cpu().numpy()
+    ref = inp[h:-h, h:-h, h:-h]
+    assert np.max(np.abs(got - ref) / np.abs(ref)) <= 2.0**-47
