@@ -74,7 +74,9 @@ typedef struct oec_field_desc {
 /* ---- schedules (paper §V-A: inlining and unrolling; §VI: grid mapping) --- */
 typedef enum {
   OEC_FUSE_INLINE = 0,   /* all producers inlined into one kernel (paper §V-A)          */
-  OEC_FUSE_NONE = 1      /* one kernel per stage, temporaries in device memory         */
+  OEC_FUSE_NONE = 1,     /* one kernel per stage, temporaries in device memory         */
+  OEC_FUSE_PARTIAL = 2   /* generated programs: stages read at more than two offsets are
+                            materialised, the rest inlined                              */
 } oec_fusion;
 
 typedef enum {
@@ -200,6 +202,67 @@ OEC_API int oec_program_apply(oec_program_t p, const oec_field_desc* in, int n_i
                       const double* params, int n_params, void* cuda_stream);
 
 /*
+ * Compile and load the generated kernels of a program without a hand-written
+ * kernel for a domain extent and field j/k strides (what the first apply at
+ * that shape would do), so that applies and stream capture that follow
+ * compile nothing. Safe to call for different programs from different host
+ * threads. No-op for programs with hand-written kernels.
+ * Errors: OEC_ERR_INVALID_ARG, OEC_ERR_SHAPE, OEC_ERR_UNSUPPORTED,
+ * OEC_ERR_COMPILE, OEC_ERR_CUDA.
+ */
+OEC_API int oec_program_prepare(oec_program_t p, const int64_t extent[3], int64_t sj, int64_t sk);
+
+/*
+ * The CUDA C++ that liboec generates for a program without a hand-written
+ * kernel (paper §V-C/§VI lowering: inlined stages, k-unrolled bodies,
+ * temporaries for materialised stages), for a domain extent and the fields' j/k
+ * strides: all fusion x unroll variants in one translation unit. The source is
+ * copied into buf (NUL-terminated, truncated to cap; buf may be NULL) and its
+ * full length stored in *len. With compile != 0 it is also compiled with NVRTC
+ * for sm_103a (no GPU needed; nothing is loaded). Errors: OEC_ERR_INVALID_ARG,
+ * OEC_ERR_SHAPE, OEC_ERR_UNSUPPORTED (column solves), OEC_ERR_COMPILE.
+ */
+OEC_API int oec_program_codegen(oec_program_t p, const int64_t extent[3], int64_t sj, int64_t sk, int compile, char* buf,
+                                int64_t cap, int64_t* len);
+
+/* ---- autotuning (paper §VII-C tunes unroll factors empirically; here every
+ * supported schedule is timed) -------------------------------------------- */
+
+/* The candidate schedules the autotuner tries for this program (every fusion,
+ * staging, tile, unroll, k-chunk and arithmetic choice its kernels support).
+ * Returns their number; copies up to cap of them into out (out may be NULL). */
+OEC_API int oec_program_candidates(oec_program_t p, oec_schedule* out, int cap);
+
+/*
+ * Time candidate schedules on the given fields and keep the fastest as the
+ * program's schedule. For each candidate (candidates = NULL: the program's own
+ * set from oec_program_candidates): one untimed apply (it compiles generated
+ * kernels and allocates scratch), then `reps` applies timed one by one with
+ * CUDA events on cuda_stream; times_ms[c] = the median in milliseconds, or -1
+ * for a candidate that cannot run. *best (may be NULL) receives the index of
+ * the fastest. Synchronises the stream; fields as for oec_program_apply
+ * (outputs are overwritten). Repeated applies reuse the same data, so domains
+ * that fit in L2 are timed cache-warm.
+ */
+OEC_API int oec_program_autotune(oec_program_t p, const oec_field_desc* in, int n_in, const oec_field_desc* out,
+                                 int n_out, const int64_t lb[3], const int64_t ub[3], const int64_t halo[3],
+                                 const double* params, int n_params, const oec_schedule* candidates, int n_candidates,
+                                 int reps, void* cuda_stream, double* times_ms, int* best);
+
+/*
+ * Features of (program, domain extent, field strides, schedule) for the learned
+ * cost model (no counterpart in the paper): 42 floats - program structure
+ * (stages, inputs, outputs, accesses, operations by kind, maximal offsets, DAG
+ * depth, inferred halos, read amplification), domain size, schedule (fusion
+ * one-hot, unroll, tile, threads), and the per-point loads, operations, stores
+ * and temporary bytes of the code generated for that schedule. Returns the
+ * number of features (out = NULL to query), or a negative error; programs with
+ * column solves are OEC_ERR_UNSUPPORTED. Host only.
+ */
+OEC_API int oec_program_features(oec_program_t p, const int64_t extent[3], int64_t sj, int64_t sk,
+                                 const oec_schedule* s, float* out, int cap);
+
+/*
  * Algorithmic device-memory bytes of one apply over [lb, ub): the sum over
  * inputs of the inferred range volume plus the sum over outputs of the domain
  * volume, times the element size. Temporaries are not counted (a fused
@@ -241,6 +304,39 @@ OEC_API int oec_batch_apply_direct(oec_batch_t b, void* cuda_stream);
 OEC_API int oec_batch_info(oec_batch_t b, int* n_items, int* n_ctas);
 /* Free the batch (NULL is a no-op); waits for its device work to finish. */
 OEC_API void oec_batch_destroy(oec_batch_t b);
+
+/* ---- learned cost model (no counterpart in the paper, which tunes
+ * empirically and always fuses, §VII-C) ----------------------------------- */
+typedef struct oec_costmodel* oec_costmodel_t;
+
+/*
+ * An FP32 MLP: features -> hidden -> hidden -> 1 with ReLU, predicting
+ * log(time per grid point) of a (program, domain, schedule). Parameters are
+ * one flat array W1 [H][F], b1 [H], W2 [H][H], b2 [H], W3 [1][H], b3 [1]
+ * (params_host may be NULL: all zero). Training uses mean squared error and
+ * Adam; all compute runs in liboec's kernels, and every reduction has a fixed
+ * order, so results are reproducible run to run. Device buffers for a batch
+ * grow on the first call with a larger n. All pointers other than the
+ * parameter copies are device memory; calls enqueue on cuda_stream.
+ */
+OEC_API int oec_costmodel_create(int n_features, int hidden, const float* params_host, oec_costmodel_t* out);
+OEC_API int oec_costmodel_param_count(oec_costmodel_t m);
+/* Copy the parameters to/from host memory (checkpoint and resume; setting
+ * them also resets Adam's moments and step count). Synchronous. */
+OEC_API int oec_costmodel_get_params(oec_costmodel_t m, float* params_host, int count);
+OEC_API int oec_costmodel_set_params(oec_costmodel_t m, const float* params_host, int count);
+/* Features are standardised as (x - mu[f]) / sigma[f] before the first layer
+ * (default mu = 0, sigma = 1; sigma <= 0 counts as 1). Host arrays of F floats. */
+OEC_API int oec_costmodel_set_normalization(oec_costmodel_t m, const float* mu, const float* sigma);
+/* y[n] = model(X[n][F]) */
+OEC_API int oec_costmodel_predict(oec_costmodel_t m, const float* X, int n, float* y, void* cuda_stream);
+/* grad[param_count] = d loss / d params and *loss = mean (y - t)^2 over n rows */
+OEC_API int oec_costmodel_gradient(oec_costmodel_t m, const float* X, const float* t, int n, float* grad, float* loss,
+                                   void* cuda_stream);
+/* One Adam step on the batch (X, t): *loss receives the batch loss before it. */
+OEC_API int oec_costmodel_train_step(oec_costmodel_t m, const float* X, const float* t, int n, float lr, float beta1,
+                                     float beta2, float eps, float* loss, void* cuda_stream);
+OEC_API void oec_costmodel_destroy(oec_costmodel_t m);
 
 /*
  * hdiff+vadvc without any device allocation. There is no counterpart in the

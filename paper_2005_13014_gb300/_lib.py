@@ -91,6 +91,24 @@ def lib():
         "oec_batch_apply_direct": (C.c_int, [P, P]),
         "oec_batch_info": (C.c_int, [P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "oec_batch_destroy": (None, [P]),
+        "oec_program_candidates": (C.c_int, [P, C.POINTER(Schedule), C.c_int]),
+        "oec_program_autotune": (C.c_int, [P, C.POINTER(FieldDesc), C.c_int, C.POINTER(FieldDesc), C.c_int, I64x3,
+                                           I64x3, I64x3, C.POINTER(C.c_double), C.c_int, C.POINTER(Schedule),
+                                           C.c_int, C.c_int, P, C.POINTER(C.c_double), C.POINTER(C.c_int)]),
+        "oec_program_features": (C.c_int, [P, I64x3, C.c_int64, C.c_int64, C.POINTER(Schedule),
+                                           C.POINTER(C.c_float), C.c_int]),
+        "oec_costmodel_create": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_float), C.POINTER(P)]),
+        "oec_costmodel_param_count": (C.c_int, [P]),
+        "oec_costmodel_get_params": (C.c_int, [P, C.POINTER(C.c_float), C.c_int]),
+        "oec_costmodel_set_params": (C.c_int, [P, C.POINTER(C.c_float), C.c_int]),
+        "oec_costmodel_set_normalization": (C.c_int, [P, C.POINTER(C.c_float), C.POINTER(C.c_float)]),
+        "oec_costmodel_predict": (C.c_int, [P, P, C.c_int, P, P]),
+        "oec_costmodel_gradient": (C.c_int, [P, P, P, C.c_int, P, P, P]),
+        "oec_costmodel_train_step": (C.c_int, [P, P, P, C.c_int, C.c_float, C.c_float, C.c_float, C.c_float, P, P]),
+        "oec_costmodel_destroy": (None, [P]),
+        "oec_program_prepare": (C.c_int, [P, I64x3, C.c_int64, C.c_int64]),
+        "oec_program_codegen": (C.c_int, [P, I64x3, C.c_int64, C.c_int64, C.c_int, C.c_char_p, C.c_int64,
+                                          C.POINTER(C.c_int64)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)

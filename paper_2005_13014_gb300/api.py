@@ -19,6 +19,20 @@ def _torch():
     return torch
 
 
+SCHEDULE_KEYS = ("fusion", "staging", "tile_i", "tile_j", "unroll", "k_chunk", "arith")
+
+
+def schedule_struct(d: dict) -> L.Schedule:
+    s = L.Schedule()
+    for k in SCHEDULE_KEYS:
+        setattr(s, k, int(d.get(k, 0)))
+    return s
+
+
+def schedule_dict(s: L.Schedule) -> dict:
+    return {k: int(getattr(s, k)) for k in SCHEDULE_KEYS}
+
+
 class Field:
     """A device field: a torch tensor indexed [k, j, i] plus the storage index
     (i, j, k) of the logical origin (paper §IV range notation)."""
@@ -131,6 +145,53 @@ class Program:
         b = C.c_int64()
         L.check(L.lib().oec_program_algorithmic_bytes(self._h, L.I64x3(*lb), L.I64x3(*ub), C.byref(b)))
         return b.value
+
+    def prepare(self, extent, sj, sk):
+        """Compile and load generated kernels for this shape ahead of time."""
+        L.check(L.lib().oec_program_prepare(self._h, L.I64x3(*extent), sj, sk))
+
+    def candidates(self):
+        """The schedules the autotuner tries for this program (list of dicts)."""
+        n = L.lib().oec_program_candidates(self._h, None, 0)
+        L.check(min(n, 0))
+        arr = (L.Schedule * n)()
+        L.lib().oec_program_candidates(self._h, arr, n)
+        return [schedule_dict(x) for x in arr]
+
+    def autotune(self, inputs, outputs, lb, ub, halo, params=(), candidates=None, reps=5, stream=None):
+        """Time candidate schedules (default: all) on these fields; the fastest
+        becomes the program's schedule. Returns (times_ms list, best index)."""
+        cands = candidates if candidates is not None else self.candidates()
+        arr = (L.Schedule * len(cands))(*[schedule_struct(c) for c in cands])
+        times = (C.c_double * len(cands))()
+        best = C.c_int(-1)
+        ins = (L.FieldDesc * max(1, len(inputs)))(*[f.desc() for f in inputs])
+        outs = (L.FieldDesc * max(1, len(outputs)))(*[f.desc() for f in outputs])
+        par = (C.c_double * max(1, len(params)))(*params)
+        L.check(L.lib().oec_program_autotune(self._h, ins, len(inputs), outs, len(outputs), L.I64x3(*lb),
+                                             L.I64x3(*ub), L.I64x3(*halo), par, len(params), arr, len(cands), reps,
+                                             C.c_void_p(_stream_handle(stream)), times, C.byref(best)))
+        return list(times), best.value
+
+    def features(self, extent, sj, sk, schedule: dict):
+        """Cost-model features of this program on a domain extent with the given
+        field strides and schedule (numpy float32 array)."""
+        n = L.lib().oec_program_features(self._h, L.I64x3(*extent), sj, sk, C.byref(schedule_struct(schedule)), None, 0)
+        L.check(min(n, 0))
+        out = (C.c_float * n)()
+        L.check(min(0, L.lib().oec_program_features(self._h, L.I64x3(*extent), sj, sk,
+                                                    C.byref(schedule_struct(schedule)), out, n)))
+        return np.frombuffer(out, dtype=np.float32).copy()
+
+    def generated_source(self, extent, sj, sk, compile=False) -> str:
+        """CUDA C++ generated for this program (all fusion x unroll variants);
+        with compile=True it is also compiled by NVRTC (no GPU needed)."""
+        n = C.c_int64()
+        L.check(L.lib().oec_program_codegen(self._h, L.I64x3(*extent), sj, sk, 0, None, 0, C.byref(n)))
+        buf = C.create_string_buffer(n.value + 1)
+        L.check(L.lib().oec_program_codegen(self._h, L.I64x3(*extent), sj, sk, 1 if compile else 0, buf,
+                                            n.value + 1, C.byref(n)))
+        return buf.value.decode()
 
     def apply(self, inputs, outputs, lb, ub, halo, params=(), stream=None):
         """Enqueue the program on ``stream`` (torch.cuda.Stream or raw handle;

@@ -1,0 +1,194 @@
+"""Learned cost model for schedule selection (no counterpart in the paper,
+which tunes unroll factors empirically and always fuses everything, §VII-C).
+
+An FP32 MLP (42 features -> 64 -> 64 -> 1, ReLU) predicts log(milliseconds per
+grid point) of a (stencil program, domain, schedule) triple. Features come from
+liboec (oec_program_features: program structure, domain, schedule, and the
+per-point loads/operations/stores of the code generated for that schedule);
+timings come from liboec's exhaustive autotuner (oec_program_autotune); the
+network is trained and evaluated by liboec's CUDA kernels (oec_costmodel_*).
+This module only moves arrays between those calls.
+
+Selection ("model top-k"): rank a program's candidate schedules by predicted
+time, measure the k best-ranked, keep the fastest; if that measured time is
+worse than the model predicted by more than a factor `fallback_ratio`, the
+program falls back to exhaustive autotuning.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import time
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+from . import _lib as L
+from .api import Program, device_field
+
+N_FEATURES = 42
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+class CostModel:
+    def __init__(self, n_features=N_FEATURES, hidden=64, params=None):
+        self._h = None
+        self.n_features, self.hidden = n_features, hidden
+        arr = None
+        if params is not None:
+            flat = np.ascontiguousarray(params, dtype=np.float32)
+            arr = flat.ctypes.data_as(C.POINTER(C.c_float))
+        h = C.c_void_p()
+        L.check(L.lib().oec_costmodel_create(n_features, hidden, arr, C.byref(h)))
+        self._h = h
+        self.param_count = L.lib().oec_costmodel_param_count(h)
+        self._loss = _torch().zeros(1, dtype=_torch().float32, device="cuda")
+
+    @staticmethod
+    def flatten(p: dict) -> np.ndarray:
+        """Flat parameter vector W1, b1, W2, b2, W3, b3 (float32)."""
+        return np.concatenate([np.asarray(p[k], np.float32).ravel() for k in ("W1", "b1", "W2", "b2", "W3", "b3")])
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.param_count, np.float32)
+        L.check(L.lib().oec_costmodel_get_params(self._h, out.ctypes.data_as(C.POINTER(C.c_float)), self.param_count))
+        return out
+
+    def set_params(self, flat):
+        flat = np.ascontiguousarray(flat, dtype=np.float32)
+        L.check(L.lib().oec_costmodel_set_params(self._h, flat.ctypes.data_as(C.POINTER(C.c_float)), self.param_count))
+
+    def set_normalization(self, mu, sigma):
+        mu = np.ascontiguousarray(mu, dtype=np.float32)
+        sigma = np.ascontiguousarray(sigma, dtype=np.float32)
+        self.mu, self.sigma = mu, sigma
+        L.check(L.lib().oec_costmodel_set_normalization(self._h, mu.ctypes.data_as(C.POINTER(C.c_float)),
+                                                         sigma.ctypes.data_as(C.POINTER(C.c_float))))
+
+    def save(self, path):
+        np.savez(path, params=self.get_params(), mu=self.mu, sigma=self.sigma,
+                 dims=np.array([self.n_features, self.hidden]))
+
+    @classmethod
+    def load(cls, path):
+        z = np.load(path)
+        m = cls(int(z["dims"][0]), int(z["dims"][1]), params=z["params"])
+        m.set_normalization(z["mu"], z["sigma"])
+        return m
+
+    def predict(self, X):
+        """X: device float32 tensor [n, F] -> device tensor [n]."""
+        torch = _torch()
+        y = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
+        L.check(L.lib().oec_costmodel_predict(self._h, _ptr(X), X.shape[0], _ptr(y),
+                                              C.c_void_p(torch.cuda.current_stream().cuda_stream)))
+        return y
+
+    def gradient(self, X, t):
+        torch = _torch()
+        g = torch.empty(self.param_count, dtype=torch.float32, device=X.device)
+        L.check(L.lib().oec_costmodel_gradient(self._h, _ptr(X), _ptr(t), X.shape[0], _ptr(g), _ptr(self._loss),
+                                               C.c_void_p(torch.cuda.current_stream().cuda_stream)))
+        return g, self._loss
+
+    def train_step(self, X, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        L.check(L.lib().oec_costmodel_train_step(self._h, _ptr(X), _ptr(t), X.shape[0], lr, beta1, beta2, eps,
+                                                 _ptr(self._loss),
+                                                 C.c_void_p(_torch().cuda.current_stream().cuda_stream)))
+        return self._loss
+
+    def fit(self, X, t, epochs=200, batch=512, lr=1e-3, seed=0):
+        """Mini-batch Adam over (X, t) (device tensors); returns per-epoch mean loss."""
+        torch = _torch()
+        n = X.shape[0]
+        rng = np.random.default_rng(seed)
+        losses = []
+        for _ in range(epochs):
+            perm = torch.from_numpy(rng.permutation(n)).to(X.device)
+            acc = torch.zeros(1, device=X.device)
+            nb = 0
+            for s in range(0, n, batch):
+                idx = perm[s:s + batch]
+                acc += self.train_step(X[idx].contiguous(), t[idx].contiguous(), lr=lr)
+                nb += 1
+            losses.append(float(acc.item()) / nb)
+        return losses
+
+    def __del__(self):
+        if getattr(self, "_h", None) is not None:
+            L.lib().oec_costmodel_destroy(self._h)
+            self._h = None
+
+
+# ---------------------------------------------------------------- measurement
+
+class DagCase:
+    """A generated program with device fields on a domain, ready to time."""
+
+    def __init__(self, src, shape, dtype="f32", halo=(8, 8, 4), seed=0):
+        from . import inputs
+        self.src, self.shape, self.dtype, self.halo = src, tuple(shape), dtype, tuple(halo)
+        self.program = Program(src, dtype, generic=True)
+        n, h = self.shape, self.halo
+        self.inputs = []
+        for x in range(self.program.n_inputs):
+            arr = inputs.field_uniform(n, h, -1.0, 1.0, seed * 16 + x)
+            self.inputs.append(device_field(arr, h, dtype))
+        self.outputs = [device_field(np.zeros_like(arr), h, dtype) for _ in range(self.program.n_outputs)]
+        t = self.inputs[0].tensor
+        self.sj, self.sk = t.stride(1), t.stride(0)
+
+    def prepare(self):
+        self.program.prepare(self.shape, self.sj, self.sk)
+
+    def features(self, candidates):
+        return np.stack([self.program.features(self.shape, self.sj, self.sk, c) for c in candidates])
+
+    def time(self, candidates, reps=3):
+        times, _ = self.program.autotune(self.inputs, self.outputs, (0, 0, 0), self.shape, self.halo,
+                                         candidates=candidates, reps=reps)
+        return np.array(times)
+
+
+def measure_dags(seeds, shape, dtype="f32", reps=3, threads=8, log=None):
+    """For each DAG seed: candidate features and exhaustive timings."""
+    from . import inputs
+    cases = [DagCase(inputs.random_dag(s), shape, dtype, seed=s) for s in seeds]
+    t0 = time.time()
+    with ThreadPoolExecutor(max_workers=threads) as ex:       # NVRTC compiles in parallel
+        list(ex.map(lambda c: c.prepare(), cases))
+    t_compile = time.time() - t0
+    cands = cases[0].program.candidates()
+    out = []
+    t0 = time.time()
+    for c in cases:
+        out.append((c.features(cands), c.time(cands, reps)))
+    if log is not None:
+        log["compile_s"] = t_compile
+        log["timing_s"] = time.time() - t0
+    return cands, out, cases
+
+
+def targets(times_ms, points):
+    """Training target: log of milliseconds per grid point."""
+    return np.log(np.maximum(times_ms, 1e-6) / points)
+
+
+def select(model, feats_dev, k=1):
+    """Indices of the k candidates with the lowest predicted time."""
+    pred = model.predict(feats_dev).cpu().numpy()
+    return np.argsort(pred, kind="stable")[:k], pred
+
+
+def regret_stats(r):
+    r = np.asarray(r)
+    return {"mean": float(np.mean(r)), "median": float(np.median(r)), "p90": float(np.percentile(r, 90)),
+            "max": float(np.max(r)), "frac_within_5pct": float(np.mean(r <= 0.05))}

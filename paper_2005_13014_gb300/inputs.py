@@ -58,6 +58,13 @@ def fastwaves_fields(ni, nj, nk, h, seed=SEED):
     return out
 
 
+def field_uniform(n, h, lo, hi, seed):
+    """One field U[lo, hi] over storage with halo h (int or (hi, hj, hk))."""
+    hh = (h, h, h) if np.isscalar(h) else tuple(h)
+    shape = (n[2] + 2 * hh[2], n[1] + 2 * hh[1], n[0] + 2 * hh[0])
+    return _uniform(shape, lo, hi, seed)
+
+
 def ensemble_members(n=32, seed=SEED):
     """Member interior extents (ni, nj, nk): i and j each from {64,128,256,512},
     k from {60,80,137}."""
