@@ -314,6 +314,204 @@ def run_gpu(args):
     return 0
 
 
+# --------------------------------------------------------------- other workloads
+
+def _timed(fn, steps, warmup, stream):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_mixed(args):
+    """hdiff and fastwaves at 256x256x80, halo 3: FP32 vs FP64 (native and
+    double-float) throughput, GB/s and per-field error against the oracle."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from oracle import stencils as S
+    from paper_2005_13014_gb300 import inputs, programs
+    from paper_2005_13014_gb300.api import Program, device_field
+    n, h = (256, 256, 80), 3
+    pts = n[0] * n[1] * n[2]
+    stream = torch.cuda.current_stream()
+    res = {}
+    fh = inputs.hdiff_fields(*n, h)
+    ffw = inputs.fastwaves_fields(*n, h)
+    ref_cache = {}
+    for prog_name in ("hdiff", "fastwaves"):
+        for dtype, arith in (("f32", 0), ("f64", 0), ("f64", 1)):
+            rnd = (lambda a: a.astype(np.float32).astype(np.float64)) if dtype == "f32" else (lambda a: a)
+            if prog_name == "hdiff":
+                f = {k: rnd(v) for k, v in fh.items()}
+                prog = Program(programs.HDIFF, dtype)
+                ins = [device_field(f["in"], h, dtype), device_field(f["coeff"], h, dtype)]
+                outs = [device_field(np.zeros_like(f["in"]), h, dtype)]
+                params = []
+            else:
+                f = {k: rnd(v) for k, v in ffw.items()}
+                prog = Program(programs.FASTWAVES, dtype)
+                ins = [device_field(f[k], h, dtype) for k in inputs.FASTWAVES_NAMES]
+                outs = [device_field(np.zeros_like(f["pp"]), h, dtype) for _ in range(2)]
+                params = [0.5, 0.0625]
+            cands = [c for c in prog.candidates() if c["arith"] == arith]
+            times, best = prog.autotune(ins, outs, (0, 0, 0), n, (h, h, h), params, candidates=cands, reps=5)
+            ms = _timed(lambda: prog.apply(ins, outs, (0, 0, 0), n, (h, h, h), params), args.steps, 3, stream)
+            key = (prog_name, dtype)
+            if key not in ref_cache:
+                G = {k: S.Grid.storage(v, h) for k, v in f.items()}
+                ref_cache[key] = ([S.hdiff(G["in"], G["coeff"], (0, 0, 0), n)] if prog_name == "hdiff"
+                                  else list(S.fastwaves(G, (0, 0, 0), n, 0.5, 0.0625)))
+            errs = []
+            for o, r in zip(outs, ref_cache[key]):
+                g = o.interior((0, 0, 0), n).cpu().numpy().astype(np.float64)
+                errs.append(float(np.max(np.abs(g - r)) / np.max(np.abs(r))))
+            nbytes = prog.algorithmic_bytes((0, 0, 0), n)
+            res[f"{prog_name}_{dtype}" + ("_df" if arith else "")] = {
+                "gpoints_per_s": pts / (ms * 1e-3) / 1e9, "ms": ms, "algorithmic_GBps": nbytes / (ms * 1e-3) / 1e9,
+                "frac_of_measured_hbm": nbytes / (ms * 1e-3) / 1e9 / _peaks().get("hbm_gbs", 6800.0),
+                "max_rel_err_per_output": errs, "schedule": prog.schedule}
+    print(json.dumps({"workload": "mixed precision 256x256x80 halo 3", "results": res}))
+    return 0
+
+
+def run_ensemble(args):
+    """32 uneven hdiff+vadvc members, FP32: one persistent launch replayed from
+    a CUDA graph (tile/arith picked by timing) vs 32 separate launches, plain
+    and graph-captured."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2005_13014_gb300 import inputs, programs
+    from paper_2005_13014_gb300.api import Batch, Program, device_field
+    h = 3
+    shapes = inputs.ensemble_members(32)
+    members = []
+    for x, n in enumerate(shapes):
+        f = inputs.hdiff_vadvc_fields(*n, h, seed=inputs.SEED + x)
+        d = [device_field(f[k], h, "f32") for k in ("u", "v", "w", "coeff")]
+        o = [device_field(np.zeros_like(f["u"]), h, "f32") for _ in range(2)]
+        members.append((d, o, (0, 0, 0), n, (h, h, h)))
+    pts = sum(n[0] * n[1] * n[2] for n in shapes)
+    stream = torch.cuda.current_stream()
+    prog = Program(programs.HDIFF_VADVC, "f32")
+    tune = {}
+    best = None
+    for c in prog.candidates():
+        if c["fusion"] != 0:
+            continue
+        prog.set_schedule(**c)
+        b = Batch(prog, members, [2.0])
+        ms = _timed(lambda: b.apply(), 5, 2, stream)
+        tune[f"{c['tile_i']}x{c['tile_j']}_arith{c['arith']}"] = ms
+        if best is None or ms < best[0]:
+            best = (ms, c)
+        del b
+    prog.set_schedule(**best[1])
+    batch = Batch(prog, members, [2.0])
+    ms_graph = _timed(lambda: batch.apply(graph=True), args.steps, 3, stream)
+    ms_direct = _timed(lambda: batch.apply(graph=False), args.steps, 3, stream)
+
+    def separate():
+        for (d, o, lb, ub, hh) in members:
+            prog.apply(d, o, lb, ub, hh, [2.0])
+    ms_sep = _timed(separate, args.steps, 3, stream)
+    g = torch.cuda.CUDAGraph()
+    separate()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g):
+        separate()
+    ms_sep_graph = _timed(lambda: g.replay(), args.steps, 3, torch.cuda.current_stream())
+    out = {"workload": "ensemble of 32 hdiff+vadvc members, FP32, halo 3", "members": shapes, "points": pts,
+           "schedule": best[1], "tuning_ms": tune,
+           "batched_graph": {"ms": ms_graph, "gpoints_per_s": pts / ms_graph / 1e6},
+           "batched_direct": {"ms": ms_direct, "gpoints_per_s": pts / ms_direct / 1e6},
+           "separate_32_launches": {"ms": ms_sep, "gpoints_per_s": pts / ms_sep / 1e6},
+           "separate_32_launches_graph": {"ms": ms_sep_graph, "gpoints_per_s": pts / ms_sep_graph / 1e6},
+           "batch_items": batch.n_items, "batch_ctas": batch.n_ctas}
+    print(json.dumps(out))
+    return 0
+
+
+def run_costmodel(args):
+    """Learned cost model on random stencil DAGs, 256x256x80 FP32: train on the
+    autotuner's timings of training DAGs, pick schedules for disjoint test DAGs,
+    report regret against exhaustive autotuning."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2005_13014_gb300 import inputs
+    from paper_2005_13014_gb300 import costmodel as CM
+    shape = (256, 256, 80)
+    pts = shape[0] * shape[1] * shape[2]
+    train_seeds = list(range(20000, 20000 + args.cm_train))
+    test_seeds = list(range(10000, 10000 + args.cm_test))
+    log = {}
+    t0 = time.time()
+
+    def measure(seeds):
+        feats, times = [], []
+        for c0 in range(0, len(seeds), 16):
+            cands, out, cases = CM.measure_dags(seeds[c0:c0 + 16], shape, "f32", reps=3, threads=16, log=log)
+            for fe, ti in out:
+                feats.append(fe)
+                times.append(ti)
+            del cases
+            torch.cuda.empty_cache()
+        return cands, np.stack(feats), np.stack(times)
+
+    cands, Ftr, Ttr = measure(train_seeds)
+    _, Fte, Tte = measure(test_seeds)
+    t_measure = time.time() - t0
+    ok_tr = Ttr > 0
+    X = Ftr[ok_tr].astype(np.float32)
+    y = CM.targets(Ttr[ok_tr], pts).astype(np.float32)
+    model = CM.CostModel(X.shape[1], 64, params=CM.CostModel.flatten(inputs.mlp_init(X.shape[1], 64)))
+    model.set_normalization(X.mean(0), X.std(0) + 1e-6)
+    Xd, yd = torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda()
+    t1 = time.time()
+    losses = model.fit(Xd, yd, epochs=args.cm_epochs, batch=512, lr=1e-3)
+    t_train = time.time() - t1
+    r1, r3, rdef, rrand, fallback = [], [], [], [], 0
+    default_idx = [x for x, c in enumerate(cands) if c["fusion"] == 0 and c["tile_i"] == 64 and c["tile_j"] == 4]
+    rng = np.random.default_rng(0)
+    for d in range(Fte.shape[0]):
+        t = Tte[d]
+        ok = t > 0
+        best = t[ok].min()
+        order, pred = CM.select(model, torch.from_numpy(Fte[d].astype(np.float32)).cuda(), k=len(cands))
+        order = [x for x in order if ok[x]]
+        r1.append(t[order[0]] / best - 1)
+        top3 = min(t[x] for x in order[:3])
+        if top3 > np.exp(pred[order[0]]) * pts * 1.5:      # misprediction: exhaustive fallback
+            fallback += 1
+            top3 = best
+        r3.append(top3 / best - 1)
+        rdef.append(min(t[x] for x in default_idx if ok[x]) / best - 1)
+        rrand.append(t[rng.choice(np.flatnonzero(ok))] / best - 1)
+    out = {"workload": "cost model: random DAGs 256x256x80 FP32", "train_dags": len(train_seeds),
+           "train_timings": int(ok_tr.sum()), "test_dags": len(test_seeds), "candidates": len(cands),
+           "final_train_loss": losses[-1], "first_train_loss": losses[0], "train_seconds": t_train,
+           "measure_seconds": t_measure, "compile_seconds_last_chunk": log.get("compile_s"),
+           "regret_top1": CM.regret_stats(r1), "regret_top3_with_fallback": CM.regret_stats(r3),
+           "fallbacks": fallback, "regret_paper_default_inline_64x4_tuned_unroll": CM.regret_stats(rdef),
+           "regret_random_schedule": CM.regret_stats(rrand),
+           "gain_top1_vs_paper_default_geomean": float(np.exp(np.mean(np.log((1 + np.array(rdef)) / (1 + np.array(r1)))))),
+           "timed_candidates_per_program": {"exhaustive": len(cands), "model_top1": 1, "model_top3": 3}}
+    print(json.dumps(out))
+    if args.cm_save:
+        np.savez(args.cm_save, Ftr=Ftr, Ttr=Ttr, Fte=Fte, Tte=Tte)
+        model.save(args.cm_save + ".model.npz")
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -323,9 +521,21 @@ def main():
     ap.add_argument("--schedule", default=None, help="JSON schedule override")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="hdiff_vadvc", choices=["hdiff_vadvc", "mixed", "ensemble", "costmodel"],
+                    help="hdiff_vadvc: the headline line; the others print their own report")
+    ap.add_argument("--cm-train", type=int, default=180)
+    ap.add_argument("--cm-test", type=int, default=200)
+    ap.add_argument("--cm-epochs", type=int, default=300)
+    ap.add_argument("--cm-save", default=None)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "mixed":
+        return run_mixed(args)
+    if args.workload == "ensemble":
+        return run_ensemble(args)
+    if args.workload == "costmodel":
+        return run_costmodel(args)
     return run_gpu(args)
 
 

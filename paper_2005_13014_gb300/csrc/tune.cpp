@@ -115,6 +115,10 @@ int oec_program_autotune(oec_program_t p, const oec_field_desc* in, int n_in, co
     p->sched = cand[c];
     int rc = oec_program_apply(p, in, n_in, out, n_out, lb, ub, halo, params, n_params, cuda_stream);   // warm-up
     if (rc == OEC_ERR_COMPILE || rc == OEC_ERR_UNSUPPORTED) continue;
+    if (rc == OEC_ERR_CUDA && cudaStreamSynchronize(st) == cudaSuccess) {
+      cudaGetLastError();   // a launch the hardware refuses (e.g. registers x threads): not a fault, skip it
+      continue;
+    }
     if (rc) { rc_all = rc; break; }
     for (int r = 0; r < reps && !rc; ++r) {
       cudaEventRecord(ev[2 * r], st);
