@@ -1,8 +1,10 @@
 """Learned cost model for schedule selection (no counterpart in the paper,
 which tunes unroll factors empirically and always fuses everything, §VII-C).
 
-An FP32 MLP (42 features -> 64 -> 64 -> 1, ReLU) predicts log(milliseconds per
-grid point) of a (stencil program, domain, schedule) triple. Features come from
+An FP32 MLP (42 features -> 64 -> 64 -> 1, ReLU) predicts, for a (stencil
+program, domain, schedule) triple, log(t / t_best): how much slower the
+schedule is than the program's fastest one (selection only ranks the schedules
+of one program, so the program's absolute cost level need not be learned). Features come from
 liboec (oec_program_features: program structure, domain, schedule, and the
 per-point loads/operations/stores of the code generated for that schedule);
 timings come from liboec's exhaustive autotuner (oec_program_autotune); the
@@ -10,9 +12,9 @@ network is trained and evaluated by liboec's CUDA kernels (oec_costmodel_*).
 This module only moves arrays between those calls.
 
 Selection ("model top-k"): rank a program's candidate schedules by predicted
-time, measure the k best-ranked, keep the fastest; if that measured time is
-worse than the model predicted by more than a factor `fallback_ratio`, the
-program falls back to exhaustive autotuning.
+time, measure the k best-ranked (k = 0: take the first unmeasured), keep the
+fastest. Exhaustive autotuning (every candidate timed) is the fallback and the
+ground truth against which the model's regret is reported.
 """
 
 from __future__ import annotations
@@ -178,8 +180,36 @@ def measure_dags(seeds, shape, dtype="f32", reps=3, threads=8, log=None):
 
 
 def targets(times_ms, points):
-    """Training target: log of milliseconds per grid point."""
+    """Absolute target: log of milliseconds per grid point."""
     return np.log(np.maximum(times_ms, 1e-6) / points)
+
+
+def relative_targets(times_ms):
+    """Per-program target: log(t / t_best) over the program's candidates
+    (selection only ranks schedules of one program, so the program's own cost
+    level need not be learned). Non-positive times (candidates that cannot
+    run) are dropped by the caller."""
+    t = np.asarray(times_ms, np.float64)
+    return np.log(t / t[t > 0].min())
+
+
+def training_set(features, times):
+    """Stack (features, relative target) over programs; features [P, C, F],
+    times [P, C]."""
+    X, y = [], []
+    for f, t in zip(features, times):
+        ok = t > 0
+        X.append(f[ok])
+        y.append(relative_targets(t)[ok])
+    return np.concatenate(X).astype(np.float32), np.concatenate(y).astype(np.float32)
+
+
+def best_fixed(times, ok_mask=None):
+    """Index of the single schedule with the lowest geometric-mean relative
+    time over the given programs (a data-driven fixed schedule)."""
+    t = np.where(times > 0, times, np.inf)
+    rel = np.log(t / t.min(axis=1, keepdims=True))
+    return int(np.argmin(np.mean(rel, axis=0)))
 
 
 def select(model, feats_dev, k=1):
