@@ -20,11 +20,13 @@
 namespace oec {
 namespace {
 
+// Two independent fields may share a launch: blocks with blockIdx.z >= nkz
+// work on (in1, out1) (nkz = number of k-chunks; in1 == nullptr: one field).
 template <class P, class OutT, int TI, int TJ>
 __global__ void __launch_bounds__(TI * TJ)
-hdiff_smem_kernel(const typename P::S* __restrict__ in, const typename P::S* __restrict__ coeff,
-                  OutT* __restrict__ out, int ni, int nj, int nk, int64_t sj, int64_t sk, int64_t osj, int64_t osk,
-                  int kchunk) {
+hdiff_smem_kernel(const typename P::S* __restrict__ in0, const typename P::S* __restrict__ in1,
+                  const typename P::S* __restrict__ coeff, OutT* __restrict__ out0, OutT* __restrict__ out1, int ni,
+                  int nj, int nk, int64_t sj, int64_t sk, int64_t osj, int64_t osk, int kchunk, int nkz) {
   typedef typename P::S S;
   typedef typename P::C C;
   constexpr int NT = TI * TJ, WI = TI + 4, WJ = TJ + 4;
@@ -34,7 +36,11 @@ hdiff_smem_kernel(const typename P::S* __restrict__ in, const typename P::S* __r
   __shared__ C s_fly[TJ + 1][TI];
   const int tid = threadIdx.x, tx = tid % TI, ty = tid / TI;
   const int i0 = blockIdx.x * TI, j0 = blockIdx.y * TJ;
-  const int k0 = blockIdx.z * kchunk, k1 = min(nk, k0 + kchunk);
+  const bool second = (int)blockIdx.z >= nkz;
+  const S* __restrict__ in = second ? in1 : in0;
+  OutT* __restrict__ out = second ? out1 : out0;
+  const int kz = second ? blockIdx.z - nkz : blockIdx.z;
+  const int k0 = kz * kchunk, k1 = min(nk, k0 + kchunk);
   const int vi = min(TI, ni - i0), vj = min(TJ, nj - j0);   // valid part of a ragged tile
   for (int k = k0; k < k1; ++k) {
     const S* pin = in + (int64_t)k * sk + (int64_t)(j0 - 2) * sj + (i0 - 2);
@@ -199,10 +205,13 @@ int kchunk_of(const oec_schedule& s, int nk) { return (s.k_chunk <= 0 || s.k_chu
 
 template <class P, class OutT, int TI, int TJ>
 cudaError_t run_smem(const oec_schedule& s, const Dom& d, int64_t osj, int64_t osk, const typename P::S* in,
-                     const typename P::S* coeff, OutT* out, cudaStream_t st) {
+                     const typename P::S* coeff, OutT* out, cudaStream_t st, const typename P::S* in1 = nullptr,
+                     OutT* out1 = nullptr) {
   const int kc = kchunk_of(s, d.nk);
-  dim3 g(ceil_div(d.ni, TI), ceil_div(d.nj, TJ), ceil_div(d.nk, kc));
-  hdiff_smem_kernel<P, OutT, TI, TJ><<<g, TI * TJ, 0, st>>>(in, coeff, out, d.ni, d.nj, d.nk, d.sj, d.sk, osj, osk, kc);
+  const int nkz = ceil_div(d.nk, kc);
+  dim3 g(ceil_div(d.ni, TI), ceil_div(d.nj, TJ), nkz * (in1 ? 2 : 1));
+  hdiff_smem_kernel<P, OutT, TI, TJ><<<g, TI * TJ, 0, st>>>(in, in1, coeff, out, out1, d.ni, d.nj, d.nk, d.sj, d.sk,
+                                                              osj, osk, kc, nkz);
   return cudaGetLastError();
 }
 
@@ -275,17 +284,20 @@ cudaError_t hdiff_launch(const oec_schedule& s, int dtype, const Dom& d, const v
   return dispatch<P32>(s, d, (const float*)in, (const float*)coeff, (float*)out, scratch, st);
 }
 
-cudaError_t hdiff_to_compute(int arith, int dtype, const Dom& d, const void* in, const void* coeff, void* out,
-                             cudaStream_t st) {
+cudaError_t hdiff_to_compute(int arith, int dtype, const Dom& d, const void* in0, const void* in1, const void* coeff,
+                             void* out0, void* out1, cudaStream_t st) {
   oec_schedule s{};
   s.k_chunk = 4;
   const int64_t osj = d.ni, osk = (int64_t)d.ni * d.nj;
   if (dtype == OEC_F64) {
     if (arith == 1)
-      return run_smem<P64D, df64, 64, 4>(s, d, osj, osk, (const double*)in, (const double*)coeff, (df64*)out, st);
-    return run_smem<P64, double, 64, 4>(s, d, osj, osk, (const double*)in, (const double*)coeff, (double*)out, st);
+      return run_smem<P64D, df64, 64, 4>(s, d, osj, osk, (const double*)in0, (const double*)coeff, (df64*)out0, st,
+                                         (const double*)in1, (df64*)out1);
+    return run_smem<P64, double, 64, 4>(s, d, osj, osk, (const double*)in0, (const double*)coeff, (double*)out0, st,
+                                        (const double*)in1, (double*)out1);
   }
-  return run_smem<P32, float, 64, 4>(s, d, osj, osk, (const float*)in, (const float*)coeff, (float*)out, st);
+  return run_smem<P32, float, 64, 4>(s, d, osj, osk, (const float*)in0, (const float*)coeff, (float*)out0, st,
+                                     (const float*)in1, (float*)out1);
 }
 
 }  // namespace oec

@@ -328,58 +328,103 @@ hv_batch_kernel(const HVMember* __restrict__ members, int n_members, int total_i
 
 // Staged form, second kernel: the column sweep over precomputed hdiff(u),
 // hdiff(v) held in the compute type (domain layout, pitch ni, plane ni*nj).
-template <class P>
-__global__ void vadvc_kernel(HV<typename P::S> p, const typename P::C* __restrict__ ud,
-                             const typename P::C* __restrict__ vd, double dtr_d, typename P::R* __restrict__ scr) {
+// Thread (column, field): 64 columns x 2 fields per CTA; both threads of a
+// column carry the shared c' recurrence, each its own field's d', and each
+// stores and later re-reads its own copy of c' (scratch [k][c'_u, d'_u, c'_v,
+// d'_v][column]), so the two threads never wait for each other. The values of
+// the next PD levels are loaded ahead into a register ring, so no load latency
+// sits on the recurrence.
+template <class P, int PD>
+__global__ void __launch_bounds__(128) vadvc_kernel(HV<typename P::S> p, const typename P::C* __restrict__ ud,
+                                                    const typename P::C* __restrict__ vd, double dtr_d,
+                                                    typename P::R* __restrict__ scr) {
   typedef typename P::S S;
   typedef typename P::C C;
   typedef typename P::R R;
+  constexpr int NCB = 64;   // columns per CTA
   const int64_t ncol = (int64_t)p.ni * p.nj;
-  const int64_t col = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int fld = threadIdx.x / NCB;
+  const int64_t col = (int64_t)blockIdx.x * NCB + threadIdx.x % NCB;
   if (col >= ncol) return;
   const int i = int(col % p.ni), j = int(col / p.ni);
   const int nk = p.nk;
   const C dtr = cvt<C>(dtr_d);
   const int64_t cbase = (int64_t)j * p.sj + i;
-  auto wf = [&](int k) -> C {
-    const S* q = p.w + (int64_t)k * p.sk + cbase;
-    return mul_p2(cvt<C>(ldg(q)) + cvt<C>(ldg(q + 1)), 0.5f);
-  };
-  C um = zero_<C>(), uc = ud[col], vm = zero_<C>(), vc = vd[col];
-  C wf_c = wf(0);
-  R cp = cvt<R>(0.0f), dpu = cvt<R>(0.0f), dpv = cvt<R>(0.0f);
-  for (int k = 0; k < nk; ++k) {
-    const bool hi = k + 1 < nk;
-    const C up = hi ? ud[(int64_t)(k + 1) * ncol + col] : zero_<C>();
-    const C vp = hi ? vd[(int64_t)(k + 1) * ncol + col] : zero_<C>();
-    const C wf_p = hi ? wf(k + 1) : zero_<C>();
-    C a, b, c, du, dv;
-    hv_row(k > 0, hi, wf_c, wf_p, dtr, um, uc, up, vm, vc, vp, a, b, c, du, dv);
-    const R ra = cvt<R>(a);
-    const R m = k == 0 ? cvt<R>(b) : cvt<R>(b) - ra * cp;
-    const R inv = rcp_(m);
-    cp = cvt<R>(c) * inv;
-    dpu = (cvt<R>(du) - ra * dpu) * inv;
-    dpv = (cvt<R>(dv) - ra * dpv) * inv;
-    R* s = scr + ((int64_t)k * 3) * ncol + col;
-    s[0] = cp;
-    s[ncol] = dpu;
-    s[2 * ncol] = dpv;
-    um = uc; uc = up; vm = vc; vc = vp;
-    wf_c = wf_p;
+  const C* __restrict__ phi = fld ? vd : ud;
+  S* __restrict__ dst = fld ? p.vo : p.uo;
+  // register ring of the next PD levels: phi, w(i), w(i+1)
+  C rphi[PD];
+  S rw0[PD], rw1[PD];
+#pragma unroll
+  for (int x = 0; x < PD; ++x) {
+    const int k = min(x, nk - 1);
+    rphi[x] = phi[(int64_t)k * ncol + col];
+    rw0[x] = ldg(p.w + (int64_t)k * p.sk + cbase);
+    rw1[x] = ldg(p.w + (int64_t)k * p.sk + cbase + 1);
   }
-  R xu = dpu, xv = dpv;
+  C um = zero_<C>(), uc = rphi[0];
+  C wf_c = mul_p2(cvt<C>(rw0[0]) + cvt<C>(rw1[0]), 0.5f);
+  R cp = cvt<R>(0.0f), dp = cvt<R>(0.0f);
+  for (int kb = 0; kb < nk; kb += PD) {
+#pragma unroll
+    for (int x = 0; x < PD; ++x) {
+      const int k = kb + x;
+      if (k < nk) {
+        // slot (x+1) % PD holds level k+1 (loaded PD-1 steps ago)
+        const int nx = (x + 1) % PD;
+        const bool lo = k > 0, hi = k + 1 < nk;
+        const C up = hi ? rphi[nx] : zero_<C>();
+        const C wf_p = hi ? mul_p2(cvt<C>(rw0[nx]) + cvt<C>(rw1[nx]), 0.5f) : zero_<C>();
+        // refill slot x with level k+PD
+        {
+          const int kf = min(k + PD, nk - 1);
+          rphi[x] = phi[(int64_t)kf * ncol + col];
+          rw0[x] = ldg(p.w + (int64_t)kf * p.sk + cbase);
+          rw1[x] = ldg(p.w + (int64_t)kf * p.sk + cbase + 1);
+        }
+        const C a = lo ? -mul_p2(wf_c, 0.25f) : zero_<C>();
+        const C c = hi ? mul_p2(wf_p, 0.25f) : zero_<C>();
+        const C b = dtr + abs_(a) + abs_(c);
+        const C t = dtr * uc;
+        C d;
+        if (lo && hi) d = t - mul_p2(a * (um - uc) + c * (up - uc), 0.5f);
+        else if (hi) d = t - mul_p2(c * (up - uc), 0.5f);
+        else if (lo) d = t - mul_p2(a * (um - uc), 0.5f);
+        else d = t;
+        const R ra = cvt<R>(a);
+        const R m = k == 0 ? cvt<R>(b) : cvt<R>(b) - ra * cp;
+        const R inv = rcp_(m);
+        cp = cvt<R>(c) * inv;
+        dp = (cvt<R>(d) - ra * dp) * inv;
+        R* s = scr + ((int64_t)k * 4 + 2 * fld) * ncol + col;
+        s[0] = cp;
+        s[ncol] = dp;
+        um = uc;
+        uc = up;
+        wf_c = wf_p;
+      }
+    }
+  }
+  constexpr int BK = 8;
+  R x = dp;
   int64_t o = (int64_t)(nk - 1) * p.sk + cbase;
-  p.uo[o] = cvt<S>(xu);
-  p.vo[o] = cvt<S>(xv);
-  for (int k = nk - 2; k >= 0; --k) {
-    const R* s = scr + ((int64_t)k * 3) * ncol + col;
-    const R ck = s[0];
-    xu = s[ncol] - ck * xu;
-    xv = s[2 * ncol] - ck * xv;
-    o -= p.sk;
-    p.uo[o] = cvt<S>(xu);
-    p.vo[o] = cvt<S>(xv);
+  dst[o] = cvt<S>(x);
+  for (int kt = nk - 2; kt >= 0; kt -= BK) {
+    R c_[BK], d_[BK];
+#pragma unroll
+    for (int y = 0; y < BK; ++y)
+      if (kt - y >= 0) {
+        const R* s = scr + ((int64_t)(kt - y) * 4 + 2 * fld) * ncol + col;
+        c_[y] = s[0];
+        d_[y] = s[ncol];
+      }
+#pragma unroll
+    for (int y = 0; y < BK; ++y)
+      if (kt - y >= 0) {
+        x = d_[y] - c_[y] * x;
+        o -= p.sk;
+        dst[o] = cvt<S>(x);
+      }
   }
 }
 
@@ -466,7 +511,7 @@ Layout layout(const oec_schedule& s, int dtype, const Dom& d) {
   Layout l;
   l.thomas = 0;
   if (s.fusion == OEC_FUSE_NONE) {
-    l.ud = align_up(3 * rsize() * pts, 256);
+    l.ud = align_up(4 * rsize() * pts, 256);
     l.vd = align_up(l.ud + csize(dtype, s.arith) * pts, 256);
     l.total = align_up(l.vd + csize(dtype, s.arith) * pts, 256);
   } else {
@@ -485,12 +530,10 @@ cudaError_t run(const oec_schedule& s, int dtype, const Dom& d, const HV<typenam
     typedef typename P::C C;
     C* ud = (C*)(scratch + l.ud);
     C* vd = (C*)(scratch + l.vd);
-    cudaError_t e = hdiff_to_compute(s.arith, dtype, d, p.u, p.coeff, ud, st);
-    if (e != cudaSuccess) return e;
-    e = hdiff_to_compute(s.arith, dtype, d, p.v, p.coeff, vd, st);
+    cudaError_t e = hdiff_to_compute(s.arith, dtype, d, p.u, p.v, p.coeff, ud, vd, st);
     if (e != cudaSuccess) return e;
     const int64_t ncol = (int64_t)d.ni * d.nj;
-    vadvc_kernel<P><<<(unsigned)((ncol + 127) / 128), 128, 0, st>>>(p, ud, vd, dtr, (typename P::R*)(scratch + l.thomas));
+    vadvc_kernel<P, 4><<<(unsigned)((ncol + 63) / 64), 128, 0, st>>>(p, ud, vd, dtr, (typename P::R*)(scratch + l.thomas));
     return cudaGetLastError();
   }
   return dispatch_fused<P>(s, d, p, dtr, scratch + l.thomas, st);
