@@ -65,6 +65,15 @@ __device__ __forceinline__ df64 rcp_(df64 a) { return df_rcp(a); }
 
 template <class T> __device__ __forceinline__ T zero_() { return kc<T>(0.0f); }
 
+// addition/subtraction for chains without catastrophic cancellation (the
+// column recurrence): the fast double-float add, plain IEEE otherwise
+__device__ __forceinline__ float addf(float a, float b) { return a + b; }
+__device__ __forceinline__ double addf(double a, double b) { return a + b; }
+__device__ __forceinline__ df64 addf(df64 a, df64 b) { return df_add_fast(a, b); }
+__device__ __forceinline__ float subf(float a, float b) { return a - b; }
+__device__ __forceinline__ double subf(double a, double b) { return a - b; }
+__device__ __forceinline__ df64 subf(df64 a, df64 b) { return df_sub_fast(a, b); }
+
 // a double-precision constant in the compute type
 template <class T> __device__ __forceinline__ T kd(double v) { return cvt<T>(v); }
 

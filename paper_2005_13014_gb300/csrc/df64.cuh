@@ -55,6 +55,17 @@ __device__ __forceinline__ df64 operator+(df64 a, df64 b) {
 }
 __device__ __forceinline__ df64 operator-(df64 a, df64 b) { return a + (-b); }
 
+// fast addition: the high parts summed error-free, the low parts added once
+// (error about 3 * 2^-48 (|a| + |b|), bounded by the operands rather than the
+// sum; for chains without catastrophic cancellation)
+__device__ __forceinline__ df64 df_add_fast(df64 a, df64 b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  return df_norm(s, e);
+}
+__device__ __forceinline__ df64 df_sub_fast(df64 a, df64 b) { return df_add_fast(a, -b); }
+
 __device__ __forceinline__ df64 operator*(df64 a, df64 b) {
   const float p = __fmul_rn(a.hi, b.hi);
   float e = __fmaf_rn(a.hi, b.hi, -p);
@@ -83,7 +94,13 @@ __device__ __forceinline__ df64 operator/(df64 a, df64 b) {
   df64 q = df_norm(q1, q2);
   return q + df64{q3, 0.0f};
 }
-__device__ __forceinline__ df64 df_rcp(df64 b) { return df64{1.0f, 0.0f} / b; }
+// 1 / b: correctly rounded float seed x0 (relative error 2^-24), one Newton
+// step x0 + x0 (1 - b x0) with the residual in double-float: error ~2^-47
+__device__ __forceinline__ df64 df_rcp(df64 b) {
+  const float x0 = __frcp_rn(b.hi);
+  const df64 r = df_sub_fast(df64{1.0f, 0.0f}, df_mulf(b, x0));
+  return df_norm(x0, __fmul_rn(r.hi, x0));
+}
 
 __device__ __forceinline__ bool df_gt0(df64 a) { return a.hi > 0.0f; }   // sign of a normalised pair
 __device__ __forceinline__ df64 df_abs(df64 a) { return a.hi < 0.0f ? -a : a; }

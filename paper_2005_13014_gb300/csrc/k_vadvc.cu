@@ -243,10 +243,10 @@ __device__ void hv_tile(const HV<typename P::S>& p, int i0, int j0, typename P::
         else if (lo) d = t - mul_p2(a * (um - uc), 0.5f);
         else d = t;
         const R ra = cvt<R>(a);
-        const R m = k == 0 ? cvt<R>(b) : cvt<R>(b) - ra * cp;
+        const R m = k == 0 ? cvt<R>(b) : subf(cvt<R>(b), ra * cp);
         const R inv = rcp_(m);
         cp = cvt<R>(c) * inv;
-        dp = (cvt<R>(d) - ra * dp) * inv;
+        dp = subf(cvt<R>(d), ra * dp) * inv;
         R* s = slot + (int64_t)k * 3 * NC + q;
         if (fld == 0) s[0] = cp;
         s[(1 + fld) * NC] = dp;
@@ -281,7 +281,7 @@ __device__ void hv_tile(const HV<typename P::S>& p, int i0, int j0, typename P::
 #pragma unroll
       for (int y = 0; y < BK; ++y) {
         if (kt - y >= 0) {
-          x = d_[y] - c_[y] * x;
+          x = subf(d_[y], c_[y] * x);
           o -= p.sk;
           dst[o] = cvt<S>(x);
         }
@@ -392,10 +392,10 @@ __global__ void __launch_bounds__(128) vadvc_kernel(HV<typename P::S> p, const t
         else if (lo) d = t - mul_p2(a * (um - uc), 0.5f);
         else d = t;
         const R ra = cvt<R>(a);
-        const R m = k == 0 ? cvt<R>(b) : cvt<R>(b) - ra * cp;
+        const R m = k == 0 ? cvt<R>(b) : subf(cvt<R>(b), ra * cp);
         const R inv = rcp_(m);
         cp = cvt<R>(c) * inv;
-        dp = (cvt<R>(d) - ra * dp) * inv;
+        dp = subf(cvt<R>(d), ra * dp) * inv;
         R* s = scr + ((int64_t)k * 4 + 2 * fld) * ncol + col;
         s[0] = cp;
         s[ncol] = dp;
@@ -421,7 +421,7 @@ __global__ void __launch_bounds__(128) vadvc_kernel(HV<typename P::S> p, const t
 #pragma unroll
     for (int y = 0; y < BK; ++y)
       if (kt - y >= 0) {
-        x = d_[y] - c_[y] * x;
+        x = subf(d_[y], c_[y] * x);
         o -= p.sk;
         dst[o] = cvt<S>(x);
       }
@@ -469,8 +469,10 @@ int batch_occupancy() {
 
 // tiles (TI, TJ) and levels per chunk: KC keeps the shared memory of the
 // 8-byte compute types under ~64 KB
-#define OEC_HV_TILES(X) X(16, 4) X(32, 2) X(8, 8) X(32, 4)
-template <int TI, int TJ, int CB> struct KCOf { static constexpr int v = (TI * TJ >= 128) ? (CB == 4 ? 4 : 2) : (CB == 4 ? 8 : 4); };
+#define OEC_HV_TILES(X) X(16, 4) X(32, 2) X(8, 8) X(32, 4) X(8, 4) X(16, 2)
+template <int TI, int TJ, int CB> struct KCOf {
+  static constexpr int v = (TI * TJ >= 128) ? (CB == 4 ? 4 : 2) : (TI * TJ >= 64) ? (CB == 4 ? 8 : 4) : (CB == 4 ? 16 : 8);
+};
 
 template <class P>
 cudaError_t dispatch_fused(const oec_schedule& s, const Dom& d, const HV<typename P::S>& p, double dtr, void* scratch,
@@ -548,7 +550,7 @@ bool hdiff_vadvc_schedule_ok(const oec_schedule& s, std::string& why) {
 #define X(a, b) if (s.tile_i == a && s.tile_j == b) return true;
   OEC_HV_TILES(X)
 #undef X
-  why = "hdiff+vadvc column tiles: 16x4, 32x2, 8x8, 32x4";
+  why = "hdiff+vadvc column tiles: 16x4, 32x2, 8x8, 32x4, 8x4, 16x2";
   return false;
 }
 

@@ -44,7 +44,7 @@ std::vector<oec_schedule> candidates(const oec_program* p) {
     case OEC_KIND_HDIFF_VADVC:
       for (int a : {0, 1}) {
         c.push_back(mk(OEC_FUSE_NONE, 0, 16, 4, 1, 0, a));
-        for (auto t : {std::pair<int, int>{16, 4}, {32, 2}, {8, 8}, {32, 4}})
+        for (auto t : {std::pair<int, int>{16, 4}, {32, 2}, {8, 8}, {32, 4}, {8, 4}, {16, 2}})
           c.push_back(mk(OEC_FUSE_INLINE, OEC_STAGE_SMEM, t.first, t.second, 1, 0, a));
       }
       break;

@@ -30,7 +30,7 @@ def _members(dtype, h=3, shapes=SHAPES, seed=100):
 
 
 @pytest.mark.parametrize("dtype,arith", [("f64", 0), ("f64", 1), ("f32", 0), ("f32", 1)])
-@pytest.mark.parametrize("tile", [(16, 4), (32, 2), (8, 8), (32, 4)])
+@pytest.mark.parametrize("tile", [(16, 4), (32, 2), (8, 8), (32, 4), (8, 4), (16, 2)])
 def test_batch_equals_single_applies_and_oracle(dtype, arith, tile):
     from paper_2005_13014_gb300.api import Batch, Program, device_field
     h = 3

@@ -120,7 +120,7 @@ def test_hdiff_single_point_and_line():
 # ---------------------------------------------------------------- hdiff+vadvc
 
 HV_SCHEDS = [dict(fusion=1)] + [dict(fusion=0, staging=1, tile_i=a, tile_j=b)
-                                for a, b in [(16, 4), (32, 2), (8, 8), (32, 4)]]
+                                for a, b in [(16, 4), (32, 2), (8, 8), (32, 4), (8, 4), (16, 2)]]
 
 
 def _hv_case(n, h, dtype, sched, dtr=2.0):
