@@ -104,6 +104,13 @@ typedef struct oec_schedule {
  * FP64 tolerance (normwise 1e-13) for values of magnitude 2^-74..2^128. */
 #define OEC_ARITH_NATIVE 0
 #define OEC_ARITH_DOUBLE_FLOAT 1
+/* OEC_ARITH_FIXED (FP64 horizontal diffusion only, fused SMEM schedules, and
+ * the stage-by-stage hdiff+vadvc form): the linear part of the stencil
+ * (Laplacian, fluxes, divergence) is evaluated exactly in 64-bit integers on a
+ * per-tile scale, the limiter's signs are taken exactly from the binary64
+ * inputs, and the output is one fused multiply-add in FP64. Inputs must be
+ * finite. */
+#define OEC_ARITH_FIXED 2
 
 /* ---- programs ----------------------------------------------------------- */
 typedef struct oec_program* oec_program_t;

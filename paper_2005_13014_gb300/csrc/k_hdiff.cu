@@ -117,6 +117,128 @@ __global__ void hdiff_regs_kernel(const typename P::S* __restrict__ in, const ty
   }
 }
 
+// ---- exact fixed-point FP64 hdiff (arith 2) --------------------------------
+// hdiff is linear in `in` apart from the limiter's sign tests and the final
+// product with coeff, so the Laplacian, fluxes and flux divergence of binary64
+// inputs are evaluated exactly in 64-bit integers. Per tile and level, E (the
+// largest biased exponent of the window's values) fixes the scale: value x =
+// m * 2^(e-1075) becomes X = m << (e - E + 3) (truncated toward zero when the
+// shift is negative), so |X| < 2^56 and |lap| < 2^59, |flux| < 2^60,
+// |divergence| < 2^62: no overflow. The limiter tests the sign of the flux
+// (exact) against the sign of in(i+1) - in(i) taken exactly from the raw
+// binary64 values (ordered integer keys). The output is one rounding of the
+// exact result: out = fma(-coeff, div * 2^(E - 1078), in). Only values more
+// than 2^53 times smaller than the tile's largest lose bits (absolute error
+// below 2^(E-1078) per value). Tiles whose values are all below 2^-923 are
+// treated as zero-diffusion (out = in). Inputs must be finite.
+__device__ __forceinline__ long long fx_of(double x, unsigned E) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FFu);
+  const long long m = (long long)((b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull);
+  const int sh = e - (int)E + 3;
+  long long X = sh >= 0 ? (m << sh) : (sh > -53 ? (m >> -sh) : 0ll);
+  X = e == 0 ? 0ll : X;
+  return (long long)(b >> 63) ? -X : X;
+}
+// total order of binary64 values as signed integers (-0 mapped to +0)
+__device__ __forceinline__ long long fx_key(double x) {
+  long long b = __double_as_longlong(x);
+  b = b == (long long)0x8000000000000000ull ? 0ll : b;
+  return b < 0 ? (b ^ 0x7FFFFFFFFFFFFFFFll) : b;
+}
+__device__ __forceinline__ long long fx_flux(long long lap_hi, long long lap_lo, double in_hi, double in_lo) {
+  const long long f = lap_hi - lap_lo;
+  const long long kh = fx_key(in_hi), kl = fx_key(in_lo);
+  const bool lim = (f > 0 && kh > kl) || (f < 0 && kh < kl);
+  return lim ? 0ll : f;
+}
+
+template <class OutT, int TI, int TJ>
+__global__ void __launch_bounds__(TI * TJ)
+hdiff_fixed_kernel(const double* __restrict__ in0, const double* __restrict__ in1, const double* __restrict__ coeff,
+                   OutT* __restrict__ out0, OutT* __restrict__ out1, int ni, int nj, int nk, int64_t sj, int64_t sk,
+                   int64_t osj, int64_t osk, int kchunk, int nkz) {
+  constexpr int NT = TI * TJ, WI = TI + 4, WJ = TJ + 4;
+  __shared__ double s_raw[WJ][WI];
+  __shared__ long long s_fix[WJ][WI];
+  __shared__ long long s_lap[TJ + 2][TI + 2];
+  __shared__ long long s_flx[TJ][TI + 1];
+  __shared__ long long s_fly[TJ + 1][TI];
+  __shared__ unsigned s_emax;
+  const int tid = threadIdx.x, tx = tid % TI, ty = tid / TI;
+  const int i0 = blockIdx.x * TI, j0 = blockIdx.y * TJ;
+  const bool second = (int)blockIdx.z >= nkz;
+  const double* __restrict__ in = second ? in1 : in0;
+  OutT* __restrict__ out = second ? out1 : out0;
+  const int kz = second ? blockIdx.z - nkz : blockIdx.z;
+  const int k0 = kz * kchunk, k1 = min(nk, k0 + kchunk);
+  const int vi = min(TI, ni - i0), vj = min(TJ, nj - j0);
+  if (tid == 0) s_emax = 0u;
+  __syncthreads();
+  for (int k = k0; k < k1; ++k) {
+    const double* pin = in + (int64_t)k * sk + (int64_t)(j0 - 2) * sj + (i0 - 2);
+    unsigned emax = 0u;
+    for (int idx = tid; idx < WI * WJ; idx += NT) {
+      const int r = idx / WI, c = idx - r * WI;
+      if (c < vi + 4 && r < vj + 4) {
+        const double x = ldg(pin + (int64_t)r * sj + c);
+        s_raw[r][c] = x;
+        emax = max(emax, (unsigned)(__double_as_longlong(x) >> 52) & 0x7FFu);
+      }
+    }
+    emax = __reduce_max_sync(0xFFFFFFFFu, emax);
+    if ((tid & 31) == 0) atomicMax(&s_emax, emax);
+    __syncthreads();
+    const unsigned E = max(s_emax, 100u);
+    for (int idx = tid; idx < WI * WJ; idx += NT) {
+      const int r = idx / WI, c = idx - r * WI;
+      if (c < vi + 4 && r < vj + 4) s_fix[r][c] = fx_of(s_raw[r][c], E);
+    }
+    __syncthreads();
+    for (int idx = tid; idx < (TI + 2) * (TJ + 2); idx += NT) {
+      const int r = idx / (TI + 2), c = idx - r * (TI + 2);
+      if (c < vi + 2 && r < vj + 2)
+        s_lap[r][c] = (s_fix[r + 1][c + 1] << 2) - s_fix[r + 1][c] - s_fix[r + 1][c + 2] - s_fix[r][c + 1] - s_fix[r + 2][c + 1];
+    }
+    __syncthreads();
+    for (int idx = tid; idx < (TI + 1) * TJ; idx += NT) {
+      const int r = idx / (TI + 1), c = idx - r * (TI + 1);
+      if (c < vi + 1 && r < vj)
+        s_flx[r][c] = fx_flux(s_lap[r + 1][c + 1], s_lap[r + 1][c], s_raw[r + 2][c + 2], s_raw[r + 2][c + 1]);
+    }
+    for (int idx = tid; idx < TI * (TJ + 1); idx += NT) {
+      const int r = idx / TI, c = idx - r * TI;
+      if (c < vi && r < vj + 1)
+        s_fly[r][c] = fx_flux(s_lap[r + 1][c + 1], s_lap[r][c + 1], s_raw[r + 2][c + 2], s_raw[r + 1][c + 2]);
+    }
+    __syncthreads();
+    if (tx < vi && ty < vj) {
+      const int64_t o = (int64_t)k * sk + (int64_t)(j0 + ty) * sj + (i0 + tx);
+      const long long div = (s_flx[ty][tx + 1] - s_flx[ty][tx]) + (s_fly[ty + 1][tx] - s_fly[ty][tx]);
+      double dv = __ll2double_rn(div);
+      // dv * 2^(E - 1078) by exponent arithmetic (dv is 0 or an integer >= 1 in magnitude)
+      dv = div == 0 ? 0.0 : __longlong_as_double(__double_as_longlong(dv) + ((long long)((int)E - 1078) << 52));
+      const double r = __fma_rn(-ldg(coeff + o), dv, s_raw[ty + 2][tx + 2]);
+      out[(int64_t)k * osk + (int64_t)(j0 + ty) * osj + (i0 + tx)] = cvt<OutT>(r);
+    }
+    __syncthreads();
+    if (tid == 0) s_emax = 0u;
+    __syncthreads();
+  }
+}
+
+template <class OutT, int TI, int TJ>
+cudaError_t run_fixed(const oec_schedule& s, const Dom& d, int64_t osj, int64_t osk, const double* in,
+                      const double* coeff, OutT* out, cudaStream_t st, const double* in1 = nullptr,
+                      OutT* out1 = nullptr) {
+  const int kc = (s.k_chunk <= 0 || s.k_chunk > d.nk) ? d.nk : s.k_chunk;
+  const int nkz = ceil_div(d.nk, kc);
+  dim3 g(ceil_div(d.ni, TI), ceil_div(d.nj, TJ), nkz * (in1 ? 2 : 1));
+  hdiff_fixed_kernel<OutT, TI, TJ><<<g, TI * TJ, 0, st>>>(in, in1, coeff, out, out1, d.ni, d.nj, d.nk, d.sj, d.sk, osj,
+                                                          osk, kc, nkz);
+  return cudaGetLastError();
+}
+
 // ---- unfused: one kernel per stage, temporaries (compute type) over their
 // inferred ranges ----------------------------------------------------------
 // lap over [-1, ni+1) x [-1, nj+1): element (i, j, k) at ((k*(nj+2) + j+1)*(ni+2) + i+1)
@@ -249,7 +371,11 @@ cudaError_t dispatch(const oec_schedule& s, const Dom& d, const typename P::S* i
 }  // namespace
 
 bool hdiff_schedule_ok(const oec_schedule& s, std::string& why) {
-  if (s.arith != 0 && s.arith != 1) { why = "arith must be 0 (native) or 1 (double-float)"; return false; }
+  if (s.arith < 0 || s.arith > 2) { why = "arith must be 0 (native), 1 (double-float) or 2 (fixed point)"; return false; }
+  if (s.arith == 2 && (s.fusion != OEC_FUSE_INLINE || s.staging != OEC_STAGE_SMEM)) {
+    why = "fixed-point arithmetic runs the fused SMEM-staged kernel";
+    return false;
+  }
   if (s.fusion == OEC_FUSE_NONE) return true;
   if (s.fusion != OEC_FUSE_INLINE) { why = "fusion must be OEC_FUSE_INLINE or OEC_FUSE_NONE"; return false; }
   if (s.k_chunk < 0) { why = "k_chunk must be >= 0"; return false; }
@@ -276,6 +402,14 @@ size_t hdiff_scratch_bytes(const oec_schedule& s, int dtype, const Dom& d) {
 
 cudaError_t hdiff_launch(const oec_schedule& s, int dtype, const Dom& d, const void* in, const void* coeff, void* out,
                          void* scratch, cudaStream_t st) {
+  if (dtype == OEC_F64 && s.arith == 2) {
+#define X(a, b)                                                                                               \
+  if (s.tile_i == a && s.tile_j == b)                                                                         \
+    return run_fixed<double, a, b>(s, d, d.sj, d.sk, (const double*)in, (const double*)coeff, (double*)out, st);
+    OEC_SMEM_TILES(X)
+#undef X
+    return cudaErrorInvalidValue;
+  }
   if (dtype == OEC_F64) {
     if (s.arith == 1)
       return dispatch<P64D>(s, d, (const double*)in, (const double*)coeff, (double*)out, scratch, st);
@@ -290,6 +424,9 @@ cudaError_t hdiff_to_compute(int arith, int dtype, const Dom& d, const void* in0
   s.k_chunk = 4;
   const int64_t osj = d.ni, osk = (int64_t)d.ni * d.nj;
   if (dtype == OEC_F64) {
+    if (arith == 2)
+      return run_fixed<df64, 64, 4>(s, d, osj, osk, (const double*)in0, (const double*)coeff, (df64*)out0, st,
+                                    (const double*)in1, (df64*)out1);
     if (arith == 1)
       return run_smem<P64D, df64, 64, 4>(s, d, osj, osk, (const double*)in0, (const double*)coeff, (df64*)out0, st,
                                          (const double*)in1, (df64*)out1);

@@ -544,7 +544,11 @@ cudaError_t run(const oec_schedule& s, int dtype, const Dom& d, const HV<typenam
 }  // namespace
 
 bool hdiff_vadvc_schedule_ok(const oec_schedule& s, std::string& why) {
-  if (s.arith != 0 && s.arith != 1) { why = "arith must be 0 (native) or 1 (double-float)"; return false; }
+  if (s.arith < 0 || s.arith > 2) { why = "arith must be 0 (native), 1 (double-float) or 2 (fixed point)"; return false; }
+  if (s.arith == 2 && s.fusion != OEC_FUSE_NONE) {
+    why = "fixed-point hdiff feeds the stage-by-stage (OEC_FUSE_NONE) form";
+    return false;
+  }
   if (s.fusion == OEC_FUSE_NONE) return true;
   if (s.fusion != OEC_FUSE_INLINE) { why = "fusion must be OEC_FUSE_INLINE or OEC_FUSE_NONE"; return false; }
 #define X(a, b) if (s.tile_i == a && s.tile_j == b) return true;
@@ -559,7 +563,7 @@ size_t hdiff_vadvc_scratch_bytes(const oec_schedule& s, int dtype, const Dom& d)
 cudaError_t hdiff_vadvc_launch(const oec_schedule& s, int dtype, const Dom& d, const void* u, const void* v,
                                const void* w, const void* coeff, void* u_out, void* v_out, double dtr, void* scratch,
                                cudaStream_t st) {
-  const bool df = s.arith == 1;
+  const bool df = s.arith >= 1;   // arith 2: fixed-point hdiff producer, double-float column
   if (dtype == OEC_F64) {
     HV<double> p{(const double*)u, (const double*)v, (const double*)w, (const double*)coeff,
                  (double*)u_out, (double*)v_out, d.ni, d.nj, d.nk, d.sj, d.sk};

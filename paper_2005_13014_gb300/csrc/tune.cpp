@@ -31,6 +31,9 @@ std::vector<oec_schedule> candidates(const oec_program* p) {
   const std::vector<int> ariths = p->dtype == OEC_F64 ? std::vector<int>{0, 1} : std::vector<int>{0};
   switch (p->kind) {
     case OEC_KIND_HDIFF:
+      if (p->dtype == OEC_F64)
+        for (auto t : {std::pair<int, int>{32, 4}, {32, 8}, {64, 2}, {64, 4}, {64, 8}, {128, 2}, {128, 4}})
+          for (int kc : {1, 2, 4, 8}) c.push_back(mk(OEC_FUSE_INLINE, OEC_STAGE_SMEM, t.first, t.second, 1, kc, 2));
       for (int a : ariths) {
         c.push_back(mk(OEC_FUSE_NONE, 0, 32, 8, 1, 0, a));
         for (auto t : {std::pair<int, int>{32, 4}, {32, 8}, {64, 2}, {64, 4}, {64, 8}, {128, 2}, {128, 4}})
@@ -42,6 +45,7 @@ std::vector<oec_schedule> candidates(const oec_program* p) {
       }
       break;
     case OEC_KIND_HDIFF_VADVC:
+      if (p->dtype == OEC_F64) c.push_back(mk(OEC_FUSE_NONE, 0, 16, 4, 1, 0, 2));
       for (int a : {0, 1}) {
         c.push_back(mk(OEC_FUSE_NONE, 0, 16, 4, 1, 0, a));
         for (auto t : {std::pair<int, int>{16, 4}, {32, 2}, {8, 8}, {32, 4}, {8, 4}, {16, 2}})

@@ -228,3 +228,60 @@ def test_hdiff_f64_identity_on_edge_values(arith):
     got = dout.interior((0, 0, 0), n).cpu().numpy()
     ref = inp[h:-h, h:-h, h:-h]
     assert np.max(np.abs(got - ref) / np.abs(ref)) <= 2.0**-47
+
+
+# ----------------------------------------------------- FP64 fixed-point hdiff
+
+FIXED_SCHEDS = [dict(fusion=0, staging=1, tile_i=a, tile_j=b, k_chunk=kc, arith=2)
+                for (a, b) in [(32, 4), (32, 8), (64, 2), (64, 4), (64, 8), (128, 2), (128, 4)] for kc in (0, 3)]
+
+
+@pytest.mark.parametrize("sched", FIXED_SCHEDS, ids=str)
+def test_hdiff_fixed_point_ragged(sched):
+    assert _hdiff_case((37, 29, 5), 2, "f64", sched) <= TOL["f64"]
+
+
+def test_hdiff_fixed_point_config_sizes():
+    assert _hdiff_case((64, 64, 60), 2, "f64", FIXED_SCHEDS[6]) <= TOL["f64"]
+    assert _hdiff_case((256, 256, 80), 3, "f64", FIXED_SCHEDS[7], poison=False) <= TOL["f64"]
+    assert _hdiff_case((40, 30, 6), 3, "f64", FIXED_SCHEDS[0], lb=(5, 3, 1), ub=(33, 27, 5)) <= TOL["f64"]
+
+
+def test_hdiff_fixed_point_identity_is_exact():
+    """coeff = 0: out = fma(-0, div, in) = in bit for bit, whatever the values."""
+    from paper_2005_13014_gb300.api import Program, device_field
+    n, h = (40, 9, 3), 2
+    rng = np.random.default_rng(9)
+    inp = rng.choice([1.0, -3.5, 2.0**-60, 2.0**100, 1 - 2.0**-53, 0.1], size=(n[2] + 4, n[1] + 4, n[0] + 4))
+    inp = inp * 10.0 ** rng.integers(-3, 4, size=inp.shape)
+    p = Program(programs.HDIFF, "f64")
+    p.set_schedule(**FIXED_SCHEDS[0])
+    out = device_field(np.zeros_like(inp), h, "f64")
+    p.apply([device_field(inp, h, "f64"), device_field(np.zeros_like(inp), h, "f64")], [out], (0, 0, 0), n, (h, h, h))
+    torch.cuda.synchronize()
+    assert np.array_equal(out.interior((0, 0, 0), n).cpu().numpy(), inp[h:-h, h:-h, h:-h])
+
+
+def test_hdiff_fixed_point_mixed_magnitudes():
+    """Tiles holding 1e10 next to tiny values with near-equal neighbours: the
+    limiter's sign decisions come from the exact inputs, so the result still
+    matches the oracle normwise."""
+    from paper_2005_13014_gb300.api import Program, device_field
+    n, h = (37, 21, 4), 2
+    rng = np.random.default_rng(10)
+    shape = (n[2] + 4, n[1] + 4, n[0] + 4)
+    inp = 1e-10 * (1.0 + 1e-12 * rng.integers(-3, 4, size=shape))
+    inp[:, ::7, ::5] = 1e10 * rng.uniform(-1, 1, size=inp[:, ::7, ::5].shape)
+    coeff = rng.uniform(0, 0.1, size=shape)
+    p = Program(programs.HDIFF, "f64")
+    p.set_schedule(**FIXED_SCHEDS[2])
+    out = device_field(np.zeros_like(inp), h, "f64")
+    p.apply([device_field(inp, h, "f64"), device_field(coeff, h, "f64")], [out], (0, 0, 0), n, (h, h, h))
+    torch.cuda.synchronize()
+    ref = S.hdiff(S.Grid.storage(inp, h), S.Grid.storage(coeff, h), (0, 0, 0), n)
+    assert rel_err(out.interior((0, 0, 0), n).cpu().numpy(), ref) <= TOL["f64"]
+
+
+@pytest.mark.parametrize("n", [(37, 23, 11), (33, 5, 1), (33, 5, 2), (128, 128, 80)], ids=str)
+def test_hdiff_vadvc_fixed_point_staged(n):
+    assert _hv_case(n, 3, "f64", dict(fusion=1, arith=2)) <= TOL["f64"]
