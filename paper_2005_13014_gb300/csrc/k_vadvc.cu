@@ -16,7 +16,8 @@
 // c'_k, d'_k go to a per-tile scratch slot ([k][3][column]) that the back
 // substitution reads on the way down.
 // Staged form: hdiff writes hdiff(u), hdiff(v) to scratch, then a column
-// kernel runs the sweep.
+// kernel runs the sweep from a shared-memory ring filled by asynchronous
+// copies.
 // Batched form: a persistent kernel pulls (member, tile) items of an ensemble
 // of domains from an atomic counter and runs the fused tile sweep on each.
 #include "arith.cuh"
@@ -326,106 +327,157 @@ hv_batch_kernel(const HVMember* __restrict__ members, int n_members, int total_i
   }
 }
 
-// Staged form, second kernel: the column sweep over precomputed hdiff(u),
-// hdiff(v) held in the compute type (domain layout, pitch ni, plane ni*nj).
-// Thread (column, field): 64 columns x 2 fields per CTA; both threads of a
-// column carry the shared c' recurrence, each its own field's d', and each
-// stores and later re-reads its own copy of c' (scratch [k][c'_u, d'_u, c'_v,
-// d'_v][column]), so the two threads never wait for each other. The values of
-// the next PD levels are loaded ahead into a register ring, so no load latency
-// sits on the recurrence.
-template <class P, int PD>
-__global__ void __launch_bounds__(128) vadvc_kernel(HV<typename P::S> p, const typename P::C* __restrict__ ud,
-                                                    const typename P::C* __restrict__ vd, double dtr_d,
-                                                    typename P::R* __restrict__ scr) {
+// Staged form, column sweep over hdiff(u), hdiff(v) held in the compute type
+// (domain layout, pitch ni, plane ni*nj). One thread per column solves both
+// fields with one elimination of the shared matrix. The CTA's NC columns are
+// consecutive in (j, i) order; every value a level needs (hdiff(u), hdiff(v),
+// w(i), w(i+1)) is copied asynchronously into a shared-memory ring DEPTH
+// levels ahead of the recurrence, so the sequential chain never waits on
+// DRAM. The rows are built in the sweep (they do not depend on the
+// recurrence, so they fill its latency). c', d'_u, d'_v go to scratch
+// ([k][c', d'_u, d'_v][column]) and come back through the same kind of ring,
+// in descending level order, for the back substitution. Each thread reads
+// only ring entries its own copies wrote; the one barrier separates the two
+// uses of the ring.
+template <class P, int NC, int DEPTH>
+__global__ void __launch_bounds__(NC) hv_thomas_kernel(HV<typename P::S> p, const typename P::C* __restrict__ ud,
+                                                       const typename P::C* __restrict__ vd, double dtr_d,
+                                                       typename P::R* __restrict__ scr) {
   typedef typename P::S S;
   typedef typename P::C C;
   typedef typename P::R R;
-  constexpr int NCB = 64;   // columns per CTA
+  constexpr size_t FB = size_t(DEPTH) * NC * (2 * sizeof(C) + 2 * sizeof(S));
+  constexpr size_t BB = size_t(DEPTH) * NC * 3 * sizeof(R);
+  __shared__ __align__(16) unsigned char ring[FB > BB ? FB : BB];
+  C(*su)[NC] = reinterpret_cast<C(*)[NC]>(ring);
+  C(*sv)[NC] = su + DEPTH;
+  S(*sw0)[NC] = reinterpret_cast<S(*)[NC]>(sv + DEPTH);
+  S(*sw1)[NC] = sw0 + DEPTH;
+  const int t = threadIdx.x;
   const int64_t ncol = (int64_t)p.ni * p.nj;
-  const int fld = threadIdx.x / NCB;
-  const int64_t col = (int64_t)blockIdx.x * NCB + threadIdx.x % NCB;
-  if (col >= ncol) return;
-  const int i = int(col % p.ni), j = int(col / p.ni);
+  const int64_t col = (int64_t)blockIdx.x * NC + t;
+  const bool active = col < ncol;   // inactive threads only join the barrier
+  const int i = active ? int(col % p.ni) : 0, j = active ? int(col / p.ni) : 0;
   const int nk = p.nk;
   const C dtr = cvt<C>(dtr_d);
   const int64_t cbase = (int64_t)j * p.sj + i;
-  const C* __restrict__ phi = fld ? vd : ud;
-  S* __restrict__ dst = fld ? p.vo : p.uo;
-  // register ring of the next PD levels: phi, w(i), w(i+1)
-  C rphi[PD];
-  S rw0[PD], rw1[PD];
-#pragma unroll
-  for (int x = 0; x < PD; ++x) {
-    const int k = min(x, nk - 1);
-    rphi[x] = phi[(int64_t)k * ncol + col];
-    rw0[x] = ldg(p.w + (int64_t)k * p.sk + cbase);
-    rw1[x] = ldg(p.w + (int64_t)k * p.sk + cbase + 1);
-  }
-  C um = zero_<C>(), uc = rphi[0];
-  C wf_c = mul_p2(cvt<C>(rw0[0]) + cvt<C>(rw1[0]), 0.5f);
-  R cp = cvt<R>(0.0f), dp = cvt<R>(0.0f);
-  for (int kb = 0; kb < nk; kb += PD) {
-#pragma unroll
-    for (int x = 0; x < PD; ++x) {
-      const int k = kb + x;
-      if (k < nk) {
-        // slot (x+1) % PD holds level k+1 (loaded PD-1 steps ago)
-        const int nx = (x + 1) % PD;
-        const bool lo = k > 0, hi = k + 1 < nk;
-        const C up = hi ? rphi[nx] : zero_<C>();
-        const C wf_p = hi ? mul_p2(cvt<C>(rw0[nx]) + cvt<C>(rw1[nx]), 0.5f) : zero_<C>();
-        // refill slot x with level k+PD
-        {
-          const int kf = min(k + PD, nk - 1);
-          rphi[x] = phi[(int64_t)kf * ncol + col];
-          rw0[x] = ldg(p.w + (int64_t)kf * p.sk + cbase);
-          rw1[x] = ldg(p.w + (int64_t)kf * p.sk + cbase + 1);
+  const S* __restrict__ wcol = p.w + cbase;
+  auto issue = [&](int k) {
+    if (active && k < nk) {
+      const int sl = k % DEPTH;
+      const int64_t o = (int64_t)k * ncol + col;
+      cp_async(&su[sl][t], ud + o);
+      cp_async(&sv[sl][t], vd + o);
+      cp_async(&sw0[sl][t], wcol + (int64_t)k * p.sk);
+      cp_async(&sw1[sl][t], wcol + (int64_t)k * p.sk + 1);
+    }
+    cp_async_commit();
+  };
+  R cp = cvt<R>(0.0f), dpu = cvt<R>(0.0f), dpv = cvt<R>(0.0f);
+#pragma unroll 1
+  for (int k = 0; k < DEPTH - 1; ++k) issue(k);
+  if (active) {
+    // Software pipeline: iteration k eliminates row k and builds row k+1 (the
+    // two are independent, so their latencies overlap). Carried: phi_{k+1},
+    // delta_k = phi_{k+1} - phi_k (row k+1 uses phi_k - phi_{k+1} = -delta_k,
+    // exactly), wf_{k+1}.
+    cp_async_wait<DEPTH - 3>();   // levels 0 and 1 have landed
+    const int n1 = nk > 1 ? 1 : 0;
+    C u1 = su[n1][t], v1 = sv[n1][t];
+    C wf1 = nk > 1 ? mul_p2(cvt<C>(sw0[1][t]) + cvt<C>(sw1[1][t]), 0.5f) : zero_<C>();
+    C du0 = nk > 1 ? u1 - su[0][t] : zero_<C>(), dv0 = nk > 1 ? v1 - sv[0][t] : zero_<C>();
+    // row 0
+    C a = zero_<C>(), c = nk > 1 ? mul_p2(wf1, 0.25f) : zero_<C>();
+    C b = addf(dtr, abs_(c));
+    C ru = dtr * su[0][t], rv = dtr * sv[0][t];
+    if (nk > 1) {
+      ru = ru - mul_p2(c * du0, 0.5f);
+      rv = rv - mul_p2(c * dv0, 0.5f);
+    }
+#pragma unroll 1
+    for (int k = 0; k < nk; ++k) {
+      issue(k + DEPTH - 1);
+      cp_async_wait<DEPTH - 3>();   // level k+2 has landed
+      // elimination of row k
+      const R ra = cvt<R>(a);
+      const R m = k == 0 ? cvt<R>(b) : subf(cvt<R>(b), ra * cp);
+      const R inv = rcp_(m);
+      cp = cvt<R>(c) * inv;
+      dpu = subf(cvt<R>(ru), ra * dpu) * inv;
+      dpv = subf(cvt<R>(rv), ra * dpv) * inv;
+      R* sp = scr + (int64_t)k * 3 * ncol + col;
+      sp[0] = cp;
+      sp[ncol] = dpu;
+      sp[2 * ncol] = dpv;
+      // row k+1 (k+1 >= 1, so it has the lower term)
+      if (k + 1 < nk) {
+        const bool hi = k + 2 < nk;
+        C u2 = zero_<C>(), v2 = zero_<C>(), wf2 = zero_<C>(), du1 = zero_<C>(), dv1 = zero_<C>();
+        if (hi) {
+          const int sl = (k + 2) % DEPTH;
+          u2 = su[sl][t];
+          v2 = sv[sl][t];
+          wf2 = mul_p2(cvt<C>(sw0[sl][t]) + cvt<C>(sw1[sl][t]), 0.5f);
+          du1 = u2 - u1;
+          dv1 = v2 - v1;
         }
-        const C a = lo ? -mul_p2(wf_c, 0.25f) : zero_<C>();
-        const C c = hi ? mul_p2(wf_p, 0.25f) : zero_<C>();
-        const C b = dtr + abs_(a) + abs_(c);
-        const C t = dtr * uc;
-        C d;
-        if (lo && hi) d = t - mul_p2(a * (um - uc) + c * (up - uc), 0.5f);
-        else if (hi) d = t - mul_p2(c * (up - uc), 0.5f);
-        else if (lo) d = t - mul_p2(a * (um - uc), 0.5f);
-        else d = t;
-        const R ra = cvt<R>(a);
-        const R m = k == 0 ? cvt<R>(b) : subf(cvt<R>(b), ra * cp);
-        const R inv = rcp_(m);
-        cp = cvt<R>(c) * inv;
-        dp = subf(cvt<R>(d), ra * dp) * inv;
-        R* s = scr + ((int64_t)k * 4 + 2 * fld) * ncol + col;
-        s[0] = cp;
-        s[ncol] = dp;
-        um = uc;
-        uc = up;
-        wf_c = wf_p;
+        a = -mul_p2(wf1, 0.25f);
+        c = hi ? mul_p2(wf2, 0.25f) : zero_<C>();
+        b = addf(addf(dtr, abs_(a)), abs_(c));
+        const C tu = dtr * u1, tv = dtr * v1;
+        if (hi) {
+          ru = tu - mul_p2(a * (-du0) + c * du1, 0.5f);
+          rv = tv - mul_p2(a * (-dv0) + c * dv1, 0.5f);
+        } else {
+          ru = tu - mul_p2(a * (-du0), 0.5f);
+          rv = tv - mul_p2(a * (-dv0), 0.5f);
+        }
+        u1 = u2;
+        v1 = v2;
+        du0 = du1;
+        dv0 = dv1;
+        wf1 = wf2;
       }
     }
+    cp_async_wait<0>();
   }
-  constexpr int BK = 8;
-  R x = dp;
+  __syncthreads();   // every thread is done with the forward ring
+  __threadfence_block();   // this thread's scratch stores precede its copies below
+  R(*sc)[NC] = reinterpret_cast<R(*)[NC]>(ring);
+  R(*sdu)[NC] = sc + DEPTH;
+  R(*sdv)[NC] = sdu + DEPTH;
+  // back substitution over levels nk-2 .. 0; step m handles level nk-2-m
+  auto issue_b = [&](int m) {
+    const int k = nk - 2 - m;
+    if (active && k >= 0) {
+      const int sl = m % DEPTH;
+      const R* s = scr + (int64_t)k * 3 * ncol + col;
+      cp_async(&sc[sl][t], s);
+      cp_async(&sdu[sl][t], s + ncol);
+      cp_async(&sdv[sl][t], s + 2 * ncol);
+    }
+    cp_async_commit();
+  };
+  if (!active) return;
+#pragma unroll 1
+  for (int m = 0; m < DEPTH - 1; ++m) issue_b(m);
+  R xu = dpu, xv = dpv;
   int64_t o = (int64_t)(nk - 1) * p.sk + cbase;
-  dst[o] = cvt<S>(x);
-  for (int kt = nk - 2; kt >= 0; kt -= BK) {
-    R c_[BK], d_[BK];
-#pragma unroll
-    for (int y = 0; y < BK; ++y)
-      if (kt - y >= 0) {
-        const R* s = scr + ((int64_t)(kt - y) * 4 + 2 * fld) * ncol + col;
-        c_[y] = s[0];
-        d_[y] = s[ncol];
-      }
-#pragma unroll
-    for (int y = 0; y < BK; ++y)
-      if (kt - y >= 0) {
-        x = subf(d_[y], c_[y] * x);
-        o -= p.sk;
-        dst[o] = cvt<S>(x);
-      }
+  p.uo[o] = cvt<S>(xu);
+  p.vo[o] = cvt<S>(xv);
+#pragma unroll 1
+  for (int m = 0; m < nk - 1; ++m) {
+    issue_b(m + DEPTH - 1);
+    cp_async_wait<DEPTH - 1>();   // step m's level has landed
+    const int sl = m % DEPTH;
+    const R c_ = sc[sl][t];
+    xu = subf(sdu[sl][t], c_ * xu);
+    xv = subf(sdv[sl][t], c_ * xv);
+    o -= p.sk;
+    p.uo[o] = cvt<S>(xu);
+    p.vo[o] = cvt<S>(xv);
   }
+  cp_async_wait<0>();
 }
 
 size_t csize(int dtype, int arith) { return dtype == OEC_F32 ? 4 : 8; }   // compute type bytes
@@ -513,7 +565,7 @@ Layout layout(const oec_schedule& s, int dtype, const Dom& d) {
   Layout l;
   l.thomas = 0;
   if (s.fusion == OEC_FUSE_NONE) {
-    l.ud = align_up(4 * rsize() * pts, 256);
+    l.ud = align_up(3 * rsize() * pts, 256);
     l.vd = align_up(l.ud + csize(dtype, s.arith) * pts, 256);
     l.total = align_up(l.vd + csize(dtype, s.arith) * pts, 256);
   } else {
@@ -534,8 +586,10 @@ cudaError_t run(const oec_schedule& s, int dtype, const Dom& d, const HV<typenam
     C* vd = (C*)(scratch + l.vd);
     cudaError_t e = hdiff_to_compute(s.arith, dtype, d, p.u, p.v, p.coeff, ud, vd, st);
     if (e != cudaSuccess) return e;
+    constexpr int NC = 64, DEPTH = 16;
     const int64_t ncol = (int64_t)d.ni * d.nj;
-    vadvc_kernel<P, 4><<<(unsigned)((ncol + 63) / 64), 128, 0, st>>>(p, ud, vd, dtr, (typename P::R*)(scratch + l.thomas));
+    hv_thomas_kernel<P, NC, DEPTH><<<(unsigned)((ncol + NC - 1) / NC), NC, 0, st>>>(p, ud, vd, dtr,
+                                                                                   (typename P::R*)(scratch + l.thomas));
     return cudaGetLastError();
   }
   return dispatch_fused<P>(s, d, p, dtr, scratch + l.thomas, st);

@@ -11,6 +11,20 @@ namespace oec {
 template <typename T>
 __device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
 
+// Asynchronous global -> shared copy of one element (4, 8 or 16 bytes) that
+// bypasses the registers; copies are grouped per commit and waited for by
+// group count, so a thread can keep many levels of a column in flight.
+template <typename T>
+__device__ __forceinline__ void cp_async(T* smem, const T* gmem) {
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8 || sizeof(T) == 16, "cp.async copies 4, 8 or 16 bytes");
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"((int)sizeof(T)) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// wait until at most N of this thread's committed groups are still pending
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 // Stage bodies of the horizontal-diffusion program, written once and used by
 // every kernel variant (fused, unfused, batched, and inside the column sweep).
 // Laplacian: 4*c - w - e - s - n, in that order.
