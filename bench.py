@@ -36,8 +36,11 @@ H = 3
 DTR = 2.0
 # algorithmic floating-point operations per interior point of hdiff(u), hdiff(v),
 # the tridiagonal build and the Thomas sweep (each add, sub, mul, div, compare
-# counted once; derivation in the design notes)
+# counted once; derivation in the design notes): hdiff of both fields 36, rows
+# and Thomas 35
 FLOPS_PER_POINT = 71
+FLOPS_HDIFF, FLOPS_COLUMN = 36, 35
+TIMING_EVERY = 8          # steps between per-kernel timing samples
 METRIC = "grid-points/s"
 
 
@@ -108,25 +111,41 @@ def _dist():
     return ws, rank, local
 
 
-def _kernel_source_hash():
+# the kernels one apply launches, per schedule form, with the source files
+# each is built from, the algorithmic FP64 operations per grid point it
+# performs, and the ncu summary that holds its DRAM traffic per launch
+def _kernels_of(sched):
+    common = ["kcommon.cuh", "arith.cuh", "df64.cuh"]
+    if sched["fusion"] == 0:
+        return [{"name": "hv_fused_kernel", "src": ["k_vadvc.cu"] + common, "flops": FLOPS_PER_POINT,
+                 "profile": None}]
+    hd = "hdiff_fixed_kernel" if sched.get("arith", 0) == 2 else "hdiff_smem_kernel"
+    return [{"name": hd, "src": ["k_hdiff.cu"] + common, "flops": FLOPS_HDIFF,
+             "profile": f"{hd}_f64_2fields_128x128x80.md"},
+            {"name": "hv_thomas_kernel", "src": ["k_vadvc.cu"] + common, "flops": FLOPS_COLUMN,
+             "profile": "hv_thomas_kernel_f64_128x128x80.md"}]
+
+
+def _kernel_source_hash(files):
     h = hashlib.sha256()
-    for name in ("k_vadvc.cu", "kcommon.cuh"):
+    for name in files:
         with open(os.path.join(ROOT, "paper_2005_13014_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def _ncu_traffic(kernel_hash):
-    """DRAM bytes per launch of the timed kernel from the committed ncu summary,
-    if it was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "hdiff_vadvc_fused_f64_128x128x80.md")
+def _ncu_traffic(kernel):
+    """DRAM bytes per launch of a kernel from its committed ncu summary, if
+    the summary was taken on the current source of that kernel."""
+    if not kernel["profile"]:
+        return None
     try:
-        text = open(path).read()
+        text = open(os.path.join(ROOT, "profiles", kernel["profile"])).read()
     except OSError:
         return None
     m = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
     t = re.search(r"dram_bytes_per_launch:\s*([0-9]+)", text)
-    if not m or not t or m.group(1) != kernel_hash:
+    if not m or not t or m.group(1) != _kernel_source_hash(kernel["src"]):
         return None
     return int(t.group(1))
 
@@ -225,7 +244,6 @@ def run_gpu(args):
         for w in range(max(args.warmup, 3)):
             step(w)
     torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     with ClockSampler(local) as clk:
         time.sleep(0.2)
         # keep the GPU busy while the sampler starts, then time exactly K steps
@@ -241,18 +259,26 @@ def run_gpu(args):
         with torch.cuda.stream(stream):
             t_start.record(stream)
             for s in range(args.steps):
-                ev[s][0].record(stream)
+                # every TIMING_EVERY-th step the library records an event
+                # before and after each of its kernels (per-kernel durations)
+                prog.set_timing(s % TIMING_EVERY == 0)
                 step(s)
-                ev[s][1].record(stream)
             t_end.record(stream)
         torch.cuda.synchronize()
+        prog.set_timing(False)
         if dist:
             dist.barrier()
         total_ms = t_start.elapsed_time(t_end)
         time.sleep(0.1)
         clocks = clk.summary(mark)
-    kern_ms = [a.elapsed_time(b) for a, b in ev]
-    kern_avg_ms = float(np.mean(kern_ms))
+    launches = prog.launch_count()
+    per_kernel = prog.kernel_times()          # [sampled steps, kernels of one apply], ms
+    kernels = _kernels_of(sched)
+    assert per_kernel.shape == ((args.steps + TIMING_EVERY - 1) // TIMING_EVERY, len(kernels)) \
+        and launches == len(kernels), (per_kernel.shape, launches, kernels)
+    step_ms = per_kernel.sum(axis=1)
+    k_avg = per_kernel.mean(axis=0)
+    dom = int(np.argmax(k_avg))
     tmax = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
     if dist:
         dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
@@ -285,11 +311,12 @@ def run_gpu(args):
     alg_bytes = prog.algorithmic_bytes(lb, ub)
     peaks = _peaks()
     fp64_peak = 1250.0        # GFLOP/s, GB300 nominal dense FP64
-    achieved_gflops = FLOPS_PER_POINT * points / (kern_avg_ms * 1e-3) / 1e9
-    achieved_gbs = alg_bytes / (kern_avg_ms * 1e-3) / 1e9
+    step_avg_ms = total_ms / args.steps
+    kd = kernels[dom]
+    achieved_gflops = kd["flops"] * points / (float(k_avg[dom]) * 1e-3) / 1e9
+    step_gflops = FLOPS_PER_POINT * points / (step_avg_ms * 1e-3) / 1e9
+    achieved_gbs = alg_bytes / (step_avg_ms * 1e-3) / 1e9
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    khash = _kernel_source_hash()
-    traffic = _ncu_traffic(khash)
     line = {
         "metric": METRIC, "value": value, "unit": "grid-points/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -300,15 +327,20 @@ def run_gpu(args):
                    "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU",
                    "autotune_ms": tuning},
         "roofline": {"bound": "alu", "achieved": achieved_gflops, "peak": fp64_peak, "unit": "GFLOP/s (FP64)",
-                     "frac": achieved_gflops / fp64_peak, "traffic": traffic,
-                     "kernel": "hv_fused_kernel", "flops_per_point": FLOPS_PER_POINT,
+                     "frac": achieved_gflops / fp64_peak, "traffic": _ncu_traffic(kd),
+                     "kernel": kd["name"], "kernel_ms": float(k_avg[dom]), "flops_per_point": kd["flops"],
                      "peak_source": "GB300 nominal dense FP64 1.25 TFLOP/s (profiling recipe table)"},
+        "roofline_step": {"achieved": step_gflops, "peak": fp64_peak, "unit": "GFLOP/s (FP64)",
+                          "frac": step_gflops / fp64_peak, "flops_per_point": FLOPS_PER_POINT},
         "roofline_hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": achieved_gbs / hbm_peak,
-                         "algorithmic_bytes_per_launch": alg_bytes, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"},
-        "kernel_ms": {"mean": kern_avg_ms, "median": float(np.median(kern_ms)),
-                      "q1": float(np.percentile(kern_ms, 25)), "q3": float(np.percentile(kern_ms, 75))},
+                         "algorithmic_bytes_per_step": alg_bytes, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"},
+        "kernels": [{"name": k["name"], "ms_mean": float(k_avg[x]), "share": float(k_avg[x] / k_avg.sum()),
+                     "traffic": _ncu_traffic(k)} for x, k in enumerate(kernels)],
+        "kernel_sum_ms": {"sampled_steps": int(len(step_ms)), "mean": float(np.mean(step_ms)),
+                          "median": float(np.median(step_ms)), "q1": float(np.percentile(step_ms, 25)),
+                          "q3": float(np.percentile(step_ms, 75))},
         "e2e": {"value": e2e_value, "unit": "grid-points/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": args.steps * (1 if sched["fusion"] == 0 else 3),
+        "gpu_launches": args.steps * launches,
         "clocks": clocks,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

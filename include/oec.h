@@ -277,6 +277,32 @@ OEC_API int oec_program_features(oec_program_t p, const int64_t extent[3], int64
  */
 OEC_API int oec_program_algorithmic_bytes(oec_program_t p, const int64_t lb[3], const int64_t ub[3], int64_t* bytes);
 
+/*
+ * Kernel launches and per-kernel timing of applies (measurement support; the
+ * paper times whole programs, §VII, and a staged schedule runs several kernels
+ * per apply).
+ *
+ * oec_program_launch_count: the number of kernels the program's most recent
+ * successful or failed oec_program_apply launched (0 before any apply, and for
+ * an empty domain).
+ *
+ * oec_program_set_timing(p, 1): from now on every oec_program_apply records a
+ * CUDA event on its stream before its first kernel and one after each kernel
+ * (events owned by the program, created on first use on the current device);
+ * an apply that fails records nothing. 0 stops recording; recorded applies
+ * are kept.
+ *
+ * oec_program_kernel_times: waits for the recorded events, writes the
+ * duration of kernel x of recorded apply a to ms[a * *n_kernels + x] (in
+ * milliseconds), sets *n_applies and *n_kernels, and forgets the recorded
+ * applies. Errors: OEC_ERR_INVALID_ARG (null argument, fewer than
+ * n_applies * n_kernels entries in cap - nothing is forgotten then -, or
+ * recorded applies with different kernel counts), OEC_ERR_CUDA.
+ */
+OEC_API int oec_program_launch_count(oec_program_t p);
+OEC_API int oec_program_set_timing(oec_program_t p, int enable);
+OEC_API int oec_program_kernel_times(oec_program_t p, float* ms, int cap, int* n_applies, int* n_kernels);
+
 /* ---- batched ensembles (no counterpart in the paper's compiler; the paper's
  * programs run one domain per launch) ------------------------------------- */
 typedef struct oec_batch* oec_batch_t;

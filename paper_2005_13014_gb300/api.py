@@ -146,6 +146,25 @@ class Program:
         L.check(L.lib().oec_program_algorithmic_bytes(self._h, L.I64x3(*lb), L.I64x3(*ub), C.byref(b)))
         return b.value
 
+    def launch_count(self) -> int:
+        """Kernels launched by the most recent apply."""
+        n = L.lib().oec_program_launch_count(self._h)
+        if n < 0:
+            L.check(n)
+        return n
+
+    def set_timing(self, enable: bool):
+        """Record an event before and after every kernel of the following applies."""
+        L.check(L.lib().oec_program_set_timing(self._h, 1 if enable else 0))
+
+    def kernel_times(self, cap=1 << 20):
+        """Durations (ms) of the recorded applies' kernels: numpy [n_applies, n_kernels]."""
+        ms = np.zeros(cap, np.float32)
+        na, nk = C.c_int(), C.c_int()
+        L.check(L.lib().oec_program_kernel_times(self._h, ms.ctypes.data_as(C.POINTER(C.c_float)), cap,
+                                                 C.byref(na), C.byref(nk)))
+        return ms[:na.value * nk.value].reshape(na.value, nk.value).copy()
+
     def prepare(self, extent, sj, sk):
         """Compile and load generated kernels for this shape ahead of time."""
         L.check(L.lib().oec_program_prepare(self._h, L.I64x3(*extent), sj, sk))

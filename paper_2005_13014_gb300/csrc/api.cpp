@@ -199,6 +199,34 @@ int ensure_scratch(oec_program* p, size_t bytes) {
 
 using namespace oec;
 
+namespace oec {
+namespace {
+// the program whose apply is running on this thread (launched() is a no-op
+// outside an apply, e.g. for batches and the no-allocation entry point)
+thread_local oec_program* t_applying = nullptr;
+
+int record_event(oec_program* p, cudaStream_t st) {
+  if (p->ev_used == (int)p->ev_pool.size()) {
+    cudaEvent_t e;
+    cudaError_t err = cudaEventCreate(&e);
+    if (err != cudaSuccess) return cuda_fail(err, "cudaEventCreate");
+    p->ev_pool.push_back(e);
+  }
+  cudaError_t err = cudaEventRecord(p->ev_pool[p->ev_used], st);
+  if (err != cudaSuccess) return cuda_fail(err, "cudaEventRecord");
+  ++p->ev_used;
+  return OEC_OK;
+}
+}  // namespace
+
+void launched(cudaStream_t st) {
+  oec_program* p = t_applying;
+  if (!p) return;
+  ++p->last_launches;
+  if (p->timing) record_event(p, st);
+}
+}  // namespace oec
+
 extern "C" {
 
 const char* oec_last_error(void) { return g_err.c_str(); }
@@ -238,6 +266,7 @@ void oec_program_destroy(oec_program_t p) {
     cudaSetDevice(cur);
   }
   generic_release(p);
+  for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
   delete p;
 }
 
@@ -313,6 +342,7 @@ int oec_program_apply(oec_program_t p, const oec_field_desc* in, int n_in, const
                       int n_params, void* cuda_stream) {
   clear_error();
   if (!p || !lb || !ub || !halo) return fail(OEC_ERR_INVALID_ARG, "null argument");
+  p->last_launches = 0;
   const Program& ir = p->ir;
   if (n_in != (int)ir.inputs.size() || (n_in && !in))
     return fail(OEC_ERR_INVALID_ARG, "program has %zu inputs, got %d", ir.inputs.size(), n_in);
@@ -329,7 +359,57 @@ int oec_program_apply(oec_program_t p, const oec_field_desc* in, int n_in, const
   std::vector<Box> ranges;
   int rc = validate_fields(p, in, n_in, out, n_out, lb, ub, halo, ranges);
   if (rc) return rc;
-  return dispatch_apply(p, in, out, lb, ub, params, (cudaStream_t)cuda_stream);
+  const cudaStream_t st = (cudaStream_t)cuda_stream;
+  const int first = p->ev_used;
+  if (p->timing && (rc = record_event(p, st))) return rc;
+  t_applying = p;
+  rc = dispatch_apply(p, in, out, lb, ub, params, st);
+  t_applying = nullptr;
+  if (p->timing) {
+    if (rc || p->ev_used != first + 1 + p->last_launches) {
+      p->ev_used = first;   // drop a partly recorded apply
+    } else {
+      p->ev_first.push_back(first);
+      p->ev_count.push_back(p->ev_used - first);
+    }
+  }
+  return rc;
+}
+
+int oec_program_set_timing(oec_program_t p, int enable) {
+  clear_error();
+  if (!p) return fail(OEC_ERR_INVALID_ARG, "null program");
+  p->timing = enable != 0;
+  return OEC_OK;
+}
+
+int oec_program_launch_count(oec_program_t p) {
+  clear_error();
+  if (!p) return fail(OEC_ERR_INVALID_ARG, "null program");
+  return p->last_launches;
+}
+
+int oec_program_kernel_times(oec_program_t p, float* ms, int cap, int* n_applies, int* n_kernels) {
+  clear_error();
+  if (!p || !n_applies || !n_kernels) return fail(OEC_ERR_INVALID_ARG, "null argument");
+  const int na = (int)p->ev_first.size();
+  const int nk = na ? p->ev_count[0] - 1 : 0;
+  for (int a = 1; a < na; ++a)
+    if (p->ev_count[a] - 1 != nk) return fail(OEC_ERR_INVALID_ARG, "recorded applies launched different kernel counts");
+  *n_applies = na;
+  *n_kernels = nk;
+  if ((int64_t)na * nk > cap || (na && !ms)) return fail(OEC_ERR_INVALID_ARG, "need room for %d times", na * nk);
+  for (int a = 0; a < na; ++a)
+    for (int x = 0; x < nk; ++x) {
+      cudaEvent_t e0 = p->ev_pool[p->ev_first[a] + x], e1 = p->ev_pool[p->ev_first[a] + x + 1];
+      cudaError_t err = cudaEventSynchronize(e1);
+      if (err == cudaSuccess) err = cudaEventElapsedTime(&ms[a * nk + x], e0, e1);
+      if (err != cudaSuccess) return cuda_fail(err, "kernel timing events");
+    }
+  p->ev_first.clear();
+  p->ev_count.clear();
+  p->ev_used = 0;
+  return OEC_OK;
 }
 
 }  // extern "C"

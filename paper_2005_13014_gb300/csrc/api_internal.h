@@ -20,6 +20,13 @@ struct oec_program {
   size_t scratch_bytes = 0;
   int scratch_dev = -1;
   oec_generic_state* gen = nullptr;
+  // kernel timing (oec_program_set_timing): events of the recorded applies,
+  // apply a's events at ev_first[a] .. ev_first[a] + ev_count[a]
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  int ev_used = 0;
+  std::vector<int> ev_first, ev_count;
+  int last_launches = 0;
 };
 
 namespace oec {

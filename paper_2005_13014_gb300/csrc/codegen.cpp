@@ -632,6 +632,7 @@ int generic_apply(oec_program* p, const oec_field_desc* in, const oec_field_desc
              (unsigned)((bnk + kp.unroll - 1) / kp.unroll));
     cudaError_t e = cudaLaunchKernel((const void*)v.fn[x], grd, blk, kargs, 0, st);
     if (e != cudaSuccess) return cuda_fail(e, "generated kernel launch");
+    launched(st);
   }
   return OEC_OK;
 }

@@ -228,12 +228,12 @@ cudaError_t dispatch(const oec_schedule& s, const Dom& d, const FW<typename P::S
     dim3 b(32, 8);
     dim3 g1(ceil_div(d.ni + 1, 32), ceil_div(d.nj + 1, 8), d.nk + 1), g(ceil_div(d.ni + 1, 32), ceil_div(d.nj + 1, 8), d.nk);
     dim3 gd(ceil_div(d.ni, 32), ceil_div(d.nj, 8), d.nk);
-    fw_s1<P><<<g1, b, 0, st>>>(p, pk);
-    fw_s2<P><<<g, b, 0, st>>>(p, pk, pc);
-    fw_s34<P, 0><<<gd, b, 0, st>>>(p, pc, pu);
-    fw_s34<P, 1><<<gd, b, 0, st>>>(p, pc, pv);
-    fw_s5<P><<<g, b, 0, st>>>(p, dv);
-    fw_s6<P><<<gd, b, 0, st>>>(p, pu, pv, dv, dt, alpha);
+    fw_s1<P><<<g1, b, 0, st>>>(p, pk); launched(st);
+    fw_s2<P><<<g, b, 0, st>>>(p, pk, pc); launched(st);
+    fw_s34<P, 0><<<gd, b, 0, st>>>(p, pc, pu); launched(st);
+    fw_s34<P, 1><<<gd, b, 0, st>>>(p, pc, pv); launched(st);
+    fw_s5<P><<<g, b, 0, st>>>(p, dv); launched(st);
+    fw_s6<P><<<gd, b, 0, st>>>(p, pu, pv, dv, dt, alpha); launched(st);
     return cudaGetLastError();
   }
   if (s.staging == OEC_STAGE_SMEM) {
@@ -241,7 +241,7 @@ cudaError_t dispatch(const oec_schedule& s, const Dom& d, const FW<typename P::S
 #define X(a, b)                                                                                 \
   if (s.tile_i == a && s.tile_j == b) {                                                         \
     dim3 g(ceil_div(d.ni, a), ceil_div(d.nj, b), ceil_div(d.nk, kc));                           \
-    fw_smem_kernel<P, a, b><<<g, a * b, 0, st>>>(p, dt, alpha, kc);                              \
+    fw_smem_kernel<P, a, b><<<g, a * b, 0, st>>>(p, dt, alpha, kc); launched(st);                              \
     return cudaGetLastError();                                                                  \
   }
     OEC_FW_TILES(X)
@@ -251,9 +251,9 @@ cudaError_t dispatch(const oec_schedule& s, const Dom& d, const FW<typename P::S
   dim3 b(s.tile_i, s.tile_j);
   dim3 g(ceil_div(d.ni, s.tile_i), ceil_div(d.nj, s.tile_j), ceil_div(d.nk, s.unroll));
   switch (s.unroll) {
-    case 1: fw_regs_kernel<P, 1><<<g, b, 0, st>>>(p, dt, alpha); break;
-    case 2: fw_regs_kernel<P, 2><<<g, b, 0, st>>>(p, dt, alpha); break;
-    case 4: fw_regs_kernel<P, 4><<<g, b, 0, st>>>(p, dt, alpha); break;
+    case 1: fw_regs_kernel<P, 1><<<g, b, 0, st>>>(p, dt, alpha); launched(st); break;
+    case 2: fw_regs_kernel<P, 2><<<g, b, 0, st>>>(p, dt, alpha); launched(st); break;
+    case 4: fw_regs_kernel<P, 4><<<g, b, 0, st>>>(p, dt, alpha); launched(st); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

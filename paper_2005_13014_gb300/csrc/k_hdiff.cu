@@ -235,7 +235,7 @@ cudaError_t run_fixed(const oec_schedule& s, const Dom& d, int64_t osj, int64_t 
   const int nkz = ceil_div(d.nk, kc);
   dim3 g(ceil_div(d.ni, TI), ceil_div(d.nj, TJ), nkz * (in1 ? 2 : 1));
   hdiff_fixed_kernel<OutT, TI, TJ><<<g, TI * TJ, 0, st>>>(in, in1, coeff, out, out1, d.ni, d.nj, d.nk, d.sj, d.sk, osj,
-                                                          osk, kc, nkz);
+                                                          osk, kc, nkz); launched(st);
   return cudaGetLastError();
 }
 
@@ -317,9 +317,13 @@ cudaError_t run_unfused(const Dom& d, const typename P::S* in, const typename P:
   C* fly = (C*)(scratch + t.fly);
   dim3 b(32, 8);
   hdiff_lap_kernel<P><<<dim3(ceil_div(d.ni + 2, 32), ceil_div(d.nj + 2, 8), d.nk), b, 0, st>>>(in, lap, d.ni, d.nj, d.nk, d.sj, d.sk);
+  launched(st);
   hdiff_flx_kernel<P><<<dim3(ceil_div(d.ni + 1, 32), ceil_div(d.nj, 8), d.nk), b, 0, st>>>(in, lap, flx, d.ni, d.nj, d.nk, d.sj, d.sk);
+  launched(st);
   hdiff_fly_kernel<P><<<dim3(ceil_div(d.ni, 32), ceil_div(d.nj + 1, 8), d.nk), b, 0, st>>>(in, lap, fly, d.ni, d.nj, d.nk, d.sj, d.sk);
+  launched(st);
   hdiff_out_kernel<P><<<dim3(ceil_div(d.ni, 32), ceil_div(d.nj, 8), d.nk), b, 0, st>>>(in, coeff, flx, fly, out, d.ni, d.nj, d.nk, d.sj, d.sk);
+  launched(st);
   return cudaGetLastError();
 }
 
@@ -333,7 +337,7 @@ cudaError_t run_smem(const oec_schedule& s, const Dom& d, int64_t osj, int64_t o
   const int nkz = ceil_div(d.nk, kc);
   dim3 g(ceil_div(d.ni, TI), ceil_div(d.nj, TJ), nkz * (in1 ? 2 : 1));
   hdiff_smem_kernel<P, OutT, TI, TJ><<<g, TI * TJ, 0, st>>>(in, in1, coeff, out, out1, d.ni, d.nj, d.nk, d.sj, d.sk,
-                                                              osj, osk, kc, nkz);
+                                                              osj, osk, kc, nkz); launched(st);
   return cudaGetLastError();
 }
 
@@ -343,7 +347,7 @@ cudaError_t run_regs(const oec_schedule& s, const Dom& d, const typename P::S* i
   const int kc = kchunk_of(s, d.nk);
   dim3 b(s.tile_i, s.tile_j / U);
   dim3 g(ceil_div(d.ni, s.tile_i), ceil_div(d.nj, s.tile_j), ceil_div(d.nk, kc));
-  hdiff_regs_kernel<P, U><<<g, b, 0, st>>>(in, coeff, out, d.ni, d.nj, d.nk, d.sj, d.sk, kc);
+  hdiff_regs_kernel<P, U><<<g, b, 0, st>>>(in, coeff, out, d.ni, d.nj, d.nk, d.sj, d.sk, kc); launched(st);
   return cudaGetLastError();
 }
 

@@ -494,7 +494,7 @@ cudaError_t launch_fused(const Dom& d, const HV<typename P::S>& p, double dtr, v
     configured = true;
   }
   dim3 g(ceil_div(d.ni, TI), ceil_div(d.nj, TJ));
-  hv_fused_kernel<P, TI, TJ, KC><<<g, 2 * TI * TJ, sizeof(SM), st>>>(p, dtr, (typename P::R*)scratch);
+  hv_fused_kernel<P, TI, TJ, KC><<<g, 2 * TI * TJ, sizeof(SM), st>>>(p, dtr, (typename P::R*)scratch); launched(st);
   return cudaGetLastError();
 }
 
@@ -504,7 +504,7 @@ template <class P, int TI, int TJ, int KC>
 cudaError_t launch_batch(const HVBatchLaunch& b, cudaStream_t st) {
   typedef HVSmem<P, TI, TJ, KC> SM;
   hv_batch_kernel<P, TI, TJ, KC><<<b.grid, 2 * TI * TJ, sizeof(SM), st>>>(
-      b.members, b.n_members, b.total_items, b.counter, b.dtr, (typename P::R*)b.scratch, b.slot_elems);
+      b.members, b.n_members, b.total_items, b.counter, b.dtr, (typename P::R*)b.scratch, b.slot_elems); launched(st);
   return cudaGetLastError();
 }
 
@@ -590,6 +590,7 @@ cudaError_t run(const oec_schedule& s, int dtype, const Dom& d, const HV<typenam
     const int64_t ncol = (int64_t)d.ni * d.nj;
     hv_thomas_kernel<P, NC, DEPTH><<<(unsigned)((ncol + NC - 1) / NC), NC, 0, st>>>(p, ud, vd, dtr,
                                                                                    (typename P::R*)(scratch + l.thomas));
+                                                                                   launched(st);
     return cudaGetLastError();
   }
   return dispatch_fused<P>(s, d, p, dtr, scratch + l.thomas, st);

@@ -16,6 +16,11 @@
 
 namespace oec {
 
+// Called after every kernel launch of an apply: counts the launches and, while
+// the program's kernel timing is on, records an event after the kernel.
+void launched(cudaStream_t st);
+
+
 struct Dom {
   int ni, nj, nk;        // domain extents
   int64_t sj, sk;        // element strides shared by all fields

@@ -121,3 +121,21 @@ def test_bad_schedule_rejected(liboec):
         p.set_schedule(fusion=0, staging=0, tile_i=64, tile_j=3, unroll=2)
     p.set_schedule(fusion=0, staging=0, tile_i=64, tile_j=4, unroll=2)
     assert p.schedule["unroll"] == 2
+
+
+def test_timing_calls_without_gpu(liboec):
+    """Launch counting and kernel timing need no GPU until an apply runs."""
+    import ctypes as C
+    from paper_2005_13014_gb300 import _lib as L
+    p = C.c_void_p()
+    L.check(liboec.oec_program_create(programs.HDIFF.encode(), None, C.byref(p)))
+    try:
+        assert liboec.oec_program_launch_count(p) == 0
+        assert liboec.oec_program_set_timing(p, 1) == 0
+        na, nk = C.c_int(-1), C.c_int(-1)
+        assert liboec.oec_program_kernel_times(p, None, 0, C.byref(na), C.byref(nk)) == 0
+        assert (na.value, nk.value) == (0, 0)
+        assert liboec.oec_program_kernel_times(p, None, 0, None, C.byref(nk)) == -1   # OEC_ERR_INVALID_ARG
+        assert liboec.oec_program_launch_count(None) == -1   # OEC_ERR_INVALID_ARG
+    finally:
+        liboec.oec_program_destroy(p)

@@ -1,0 +1,64 @@
+"""Launch counts and per-kernel timing of applies (oec_program_launch_count,
+oec_program_set_timing, oec_program_kernel_times): every schedule reports the
+kernels it launches, and the recorded per-kernel durations tile the apply."""
+
+import numpy as np
+import pytest
+
+from paper_2005_13014_gb300 import inputs, programs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _fields(names, n, h, dtype, seed=7):
+    from paper_2005_13014_gb300.api import device_field
+    return [device_field(inputs.field_uniform(n, h, -1.0, 1.0, seed + x), h, dtype) for x, _ in enumerate(names)]
+
+
+CASES = [
+    # (program, dtype, schedule, kernels per apply)
+    ("HDIFF", "f64", dict(fusion=0, staging=1, tile_i=64, tile_j=4), 1),
+    ("HDIFF", "f64", dict(fusion=0, staging=1, tile_i=64, tile_j=4, arith=2), 1),
+    ("HDIFF", "f32", dict(fusion=0, staging=0, tile_i=32, tile_j=4, unroll=2), 1),
+    ("HDIFF", "f32", dict(fusion=1), 4),
+    ("HDIFF_VADVC", "f64", dict(fusion=0, staging=1, tile_i=16, tile_j=4), 1),
+    ("HDIFF_VADVC", "f64", dict(fusion=1, arith=2), 2),
+    ("HDIFF_VADVC", "f32", dict(fusion=1), 2),
+    ("FASTWAVES", "f32", dict(fusion=1), 6),
+    ("FASTWAVES", "f64", dict(fusion=0, staging=0, tile_i=32, tile_j=4, unroll=2), 1),
+]
+
+
+@pytest.mark.parametrize("name,dtype,sched,nk", CASES)
+def test_launch_count_and_kernel_times(name, dtype, sched, nk):
+    from paper_2005_13014_gb300.api import Program
+    p = Program(getattr(programs, name), dtype)
+    p.set_schedule(**sched)
+    n, h = (70, 37, 9), 3
+    din = _fields(range(p.n_inputs), n, h, dtype)
+    dout = _fields(range(p.n_outputs), n, h, dtype, seed=100)
+    params = programs.PARAMS[name.lower()]
+    assert p.launch_count() == 0
+    p.apply(din, dout, (0, 0, 0), n, (h, h, h), params)
+    assert p.launch_count() == nk
+    # empty domain: nothing launched
+    p.apply(din, dout, (0, 0, 0), (0, n[1], n[2]), (h, h, h), params)
+    assert p.launch_count() == 0
+    stream = torch.cuda.Stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p.set_timing(True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(3):
+            p.apply(din, dout, (0, 0, 0), n, (h, h, h), params, stream=stream)
+        e1.record(stream)
+    p.set_timing(False)
+    p.apply(din, dout, (0, 0, 0), n, (h, h, h), params, stream=stream)   # not recorded
+    t = p.kernel_times()
+    torch.cuda.synchronize()
+    assert t.shape == (3, nk)
+    assert np.all(t > 0)
+    assert t.sum() <= e0.elapsed_time(e1) * 1.01 + 1e-3
+    assert p.kernel_times().shape == (0, 0)   # forgotten after reading
