@@ -74,7 +74,10 @@ typedef struct oec_field_desc {
 /* ---- schedules (paper §V-A: inlining and unrolling; §VI: grid mapping) --- */
 typedef enum {
   OEC_FUSE_INLINE = 0,   /* all producers inlined into one kernel (paper §V-A)          */
-  OEC_FUSE_NONE = 1,     /* one kernel per stage, temporaries in device memory         */
+  OEC_FUSE_NONE = 1,     /* one kernel per stage, temporaries in device memory; for
+                            hdiff+vadvc: hdiff of u and v in one kernel (tile_i x
+                            tile_j, k_chunk levels per CTA when they name an SMEM hdiff
+                            tile, else 64 x 4, 4 levels), then the column sweep      */
   OEC_FUSE_PARTIAL = 2   /* generated programs: stages read at more than two offsets are
                             materialised, the rest inlined                              */
 } oec_fusion;

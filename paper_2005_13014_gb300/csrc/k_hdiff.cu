@@ -146,25 +146,34 @@ __device__ __forceinline__ long long fx_key(double x) {
   b = b == (long long)0x8000000000000000ull ? 0ll : b;
   return b < 0 ? (b ^ 0x7FFFFFFFFFFFFFFFll) : b;
 }
-__device__ __forceinline__ long long fx_flux(long long lap_hi, long long lap_lo, double in_hi, double in_lo) {
+// flux with the limiter: zero where the flux and in_hi - in_lo (given by
+// their ordered keys) have the same strict sign
+__device__ __forceinline__ long long fx_flux(long long lap_hi, long long lap_lo, long long key_hi, long long key_lo) {
   const long long f = lap_hi - lap_lo;
-  const long long kh = fx_key(in_hi), kl = fx_key(in_lo);
-  const bool lim = (f > 0 && kh > kl) || (f < 0 && kh < kl);
+  const bool lim = (f > 0 && key_hi > key_lo) || (f < 0 && key_hi < key_lo);
   return lim ? 0ll : f;
 }
 
+// One CTA: a TI x TJ tile of one field over a chunk of levels. Per level:
+// (1) the (TI+4) x (TJ+4) window of raw values is loaded and its largest
+// exponent E reduced; (2) the window is converted to fixed point at scale E,
+// with the limiter keys; (3) the Laplacian over (TI+2) x (TJ+2); (4) every
+// output point forms its four limited fluxes from the Laplacian and keys
+// planes, the divergence, and one FP64 FMA. The raw window and the exponent
+// slot are double-buffered, so the next level's load overlaps this level's
+// step (4) and a level costs three barriers.
 template <class OutT, int TI, int TJ>
 __global__ void __launch_bounds__(TI * TJ)
 hdiff_fixed_kernel(const double* __restrict__ in0, const double* __restrict__ in1, const double* __restrict__ coeff,
                    OutT* __restrict__ out0, OutT* __restrict__ out1, int ni, int nj, int nk, int64_t sj, int64_t sk,
                    int64_t osj, int64_t osk, int kchunk, int nkz) {
-  constexpr int NT = TI * TJ, WI = TI + 4, WJ = TJ + 4;
-  __shared__ double s_raw[WJ][WI];
+  constexpr int NT = TI * TJ, WI = TI + 4, WJ = TJ + 4, NW = WI * WJ, LI = TI + 2, LJ = TJ + 2, NL = LI * LJ;
+  constexpr int QW = (NW + NT - 1) / NT, QL = (NL + NT - 1) / NT;
+  __shared__ double s_raw[2][WJ][WI];
   __shared__ long long s_fix[WJ][WI];
-  __shared__ long long s_lap[TJ + 2][TI + 2];
-  __shared__ long long s_flx[TJ][TI + 1];
-  __shared__ long long s_fly[TJ + 1][TI];
-  __shared__ unsigned s_emax;
+  __shared__ long long s_key[WJ][WI];
+  __shared__ long long s_lap[LJ][LI];
+  __shared__ unsigned s_emax[2];
   const int tid = threadIdx.x, tx = tid % TI, ty = tid / TI;
   const int i0 = blockIdx.x * TI, j0 = blockIdx.y * TJ;
   const bool second = (int)blockIdx.z >= nkz;
@@ -173,57 +182,65 @@ hdiff_fixed_kernel(const double* __restrict__ in0, const double* __restrict__ in
   const int kz = second ? blockIdx.z - nkz : blockIdx.z;
   const int k0 = kz * kchunk, k1 = min(nk, k0 + kchunk);
   const int vi = min(TI, ni - i0), vj = min(TJ, nj - j0);
-  if (tid == 0) s_emax = 0u;
+  if (tid < 2) s_emax[tid] = 0u;
   __syncthreads();
-  for (int k = k0; k < k1; ++k) {
+  int bf = 0;
+  for (int k = k0; k < k1; ++k, bf ^= 1) {
+    // (1) raw window and its largest exponent
     const double* pin = in + (int64_t)k * sk + (int64_t)(j0 - 2) * sj + (i0 - 2);
     unsigned emax = 0u;
-    for (int idx = tid; idx < WI * WJ; idx += NT) {
+#pragma unroll
+    for (int q = 0; q < QW; ++q) {
+      const int idx = tid + q * NT;
       const int r = idx / WI, c = idx - r * WI;
-      if (c < vi + 4 && r < vj + 4) {
+      if (idx < NW && c < vi + 4 && r < vj + 4) {
         const double x = ldg(pin + (int64_t)r * sj + c);
-        s_raw[r][c] = x;
+        s_raw[bf][r][c] = x;
         emax = max(emax, (unsigned)(__double_as_longlong(x) >> 52) & 0x7FFu);
       }
     }
     emax = __reduce_max_sync(0xFFFFFFFFu, emax);
-    if ((tid & 31) == 0) atomicMax(&s_emax, emax);
+    if ((tid & 31) == 0) atomicMax(&s_emax[bf], emax);
     __syncthreads();
-    const unsigned E = max(s_emax, 100u);
-    for (int idx = tid; idx < WI * WJ; idx += NT) {
+    // (2) fixed point at scale E, and the limiter keys
+    const unsigned E = max(s_emax[bf], 100u);
+#pragma unroll
+    for (int q = 0; q < QW; ++q) {
+      const int idx = tid + q * NT;
       const int r = idx / WI, c = idx - r * WI;
-      if (c < vi + 4 && r < vj + 4) s_fix[r][c] = fx_of(s_raw[r][c], E);
+      if (idx < NW && c < vi + 4 && r < vj + 4) {
+        const double x = s_raw[bf][r][c];
+        s_fix[r][c] = fx_of(x, E);
+        s_key[r][c] = fx_key(x);
+      }
     }
     __syncthreads();
-    for (int idx = tid; idx < (TI + 2) * (TJ + 2); idx += NT) {
-      const int r = idx / (TI + 2), c = idx - r * (TI + 2);
-      if (c < vi + 2 && r < vj + 2)
+    if (tid == 0) s_emax[bf] = 0u;   // read by everyone before the barrier; next written two levels on
+    // (3) Laplacian
+#pragma unroll
+    for (int q = 0; q < QL; ++q) {
+      const int idx = tid + q * NT;
+      const int r = idx / LI, c = idx - r * LI;
+      if (idx < NL && c < vi + 2 && r < vj + 2)
         s_lap[r][c] = (s_fix[r + 1][c + 1] << 2) - s_fix[r + 1][c] - s_fix[r + 1][c + 2] - s_fix[r][c + 1] - s_fix[r + 2][c + 1];
     }
     __syncthreads();
-    for (int idx = tid; idx < (TI + 1) * TJ; idx += NT) {
-      const int r = idx / (TI + 1), c = idx - r * (TI + 1);
-      if (c < vi + 1 && r < vj)
-        s_flx[r][c] = fx_flux(s_lap[r + 1][c + 1], s_lap[r + 1][c], s_raw[r + 2][c + 2], s_raw[r + 2][c + 1]);
-    }
-    for (int idx = tid; idx < TI * (TJ + 1); idx += NT) {
-      const int r = idx / TI, c = idx - r * TI;
-      if (c < vi && r < vj + 1)
-        s_fly[r][c] = fx_flux(s_lap[r + 1][c + 1], s_lap[r][c + 1], s_raw[r + 2][c + 2], s_raw[r + 1][c + 2]);
-    }
-    __syncthreads();
+    // (4) limited fluxes, divergence, output
     if (tx < vi && ty < vj) {
+      const long long lc = s_lap[ty + 1][tx + 1];
+      const long long kc = s_key[ty + 2][tx + 2];
+      const long long fxp = fx_flux(s_lap[ty + 1][tx + 2], lc, s_key[ty + 2][tx + 3], kc);
+      const long long fxm = fx_flux(lc, s_lap[ty + 1][tx], kc, s_key[ty + 2][tx + 1]);
+      const long long fyp = fx_flux(s_lap[ty + 2][tx + 1], lc, s_key[ty + 3][tx + 2], kc);
+      const long long fym = fx_flux(lc, s_lap[ty][tx + 1], kc, s_key[ty + 1][tx + 2]);
+      const long long div = (fxp - fxm) + (fyp - fym);
       const int64_t o = (int64_t)k * sk + (int64_t)(j0 + ty) * sj + (i0 + tx);
-      const long long div = (s_flx[ty][tx + 1] - s_flx[ty][tx]) + (s_fly[ty + 1][tx] - s_fly[ty][tx]);
       double dv = __ll2double_rn(div);
       // dv * 2^(E - 1078) by exponent arithmetic (dv is 0 or an integer >= 1 in magnitude)
       dv = div == 0 ? 0.0 : __longlong_as_double(__double_as_longlong(dv) + ((long long)((int)E - 1078) << 52));
-      const double r = __fma_rn(-ldg(coeff + o), dv, s_raw[ty + 2][tx + 2]);
+      const double r = __fma_rn(-ldg(coeff + o), dv, s_raw[bf][ty + 2][tx + 2]);
       out[(int64_t)k * osk + (int64_t)(j0 + ty) * osj + (i0 + tx)] = cvt<OutT>(r);
     }
-    __syncthreads();
-    if (tid == 0) s_emax = 0u;
-    __syncthreads();
   }
 }
 
@@ -422,23 +439,39 @@ cudaError_t hdiff_launch(const oec_schedule& s, int dtype, const Dom& d, const v
   return dispatch<P32>(s, d, (const float*)in, (const float*)coeff, (float*)out, scratch, st);
 }
 
-cudaError_t hdiff_to_compute(int arith, int dtype, const Dom& d, const void* in0, const void* in1, const void* coeff,
-                             void* out0, void* out1, cudaStream_t st) {
-  oec_schedule s{};
-  s.k_chunk = 4;
-  const int64_t osj = d.ni, osk = (int64_t)d.ni * d.nj;
-  if (dtype == OEC_F64) {
-    if (arith == 2)
-      return run_fixed<df64, 64, 4>(s, d, osj, osk, (const double*)in0, (const double*)coeff, (df64*)out0, st,
-                                    (const double*)in1, (df64*)out1);
-    if (arith == 1)
-      return run_smem<P64D, df64, 64, 4>(s, d, osj, osk, (const double*)in0, (const double*)coeff, (df64*)out0, st,
-                                         (const double*)in1, (df64*)out1);
-    return run_smem<P64, double, 64, 4>(s, d, osj, osk, (const double*)in0, (const double*)coeff, (double*)out0, st,
-                                        (const double*)in1, (double*)out1);
+cudaError_t hdiff_to_compute(const oec_schedule& sched, int dtype, const Dom& d, const void* in0, const void* in1,
+                             const void* coeff, void* out0, void* out1, cudaStream_t st) {
+  // the schedule's tile and k_chunk pick the producer's tile when they name
+  // one of its tiles; otherwise 64 x 4, 4 levels per CTA
+  oec_schedule s = sched;
+  bool known = false;
+#define X(a, b) known = known || (s.tile_i == a && s.tile_j == b);
+  OEC_SMEM_TILES(X)
+#undef X
+  if (!known) {
+    s.tile_i = 64;
+    s.tile_j = 4;
   }
-  return run_smem<P32, float, 64, 4>(s, d, osj, osk, (const float*)in0, (const float*)coeff, (float*)out0, st,
-                                     (const float*)in1, (float*)out1);
+  if (s.k_chunk <= 0) s.k_chunk = 4;
+  const int64_t osj = d.ni, osk = (int64_t)d.ni * d.nj;
+#define X(a, b)                                                                                                  \
+  if (s.tile_i == a && s.tile_j == b) {                                                                          \
+    if (dtype == OEC_F64) {                                                                                      \
+      if (s.arith == 2)                                                                                          \
+        return run_fixed<df64, a, b>(s, d, osj, osk, (const double*)in0, (const double*)coeff, (df64*)out0, st,  \
+                                     (const double*)in1, (df64*)out1);                                           \
+      if (s.arith == 1)                                                                                          \
+        return run_smem<P64D, df64, a, b>(s, d, osj, osk, (const double*)in0, (const double*)coeff, (df64*)out0, \
+                                          st, (const double*)in1, (df64*)out1);                                  \
+      return run_smem<P64, double, a, b>(s, d, osj, osk, (const double*)in0, (const double*)coeff,               \
+                                         (double*)out0, st, (const double*)in1, (double*)out1);                  \
+    }                                                                                                            \
+    return run_smem<P32, float, a, b>(s, d, osj, osk, (const float*)in0, (const float*)coeff, (float*)out0, st,  \
+                                      (const float*)in1, (float*)out1);                                          \
+  }
+  OEC_SMEM_TILES(X)
+#undef X
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace oec

@@ -584,7 +584,7 @@ cudaError_t run(const oec_schedule& s, int dtype, const Dom& d, const HV<typenam
     typedef typename P::C C;
     C* ud = (C*)(scratch + l.ud);
     C* vd = (C*)(scratch + l.vd);
-    cudaError_t e = hdiff_to_compute(s.arith, dtype, d, p.u, p.v, p.coeff, ud, vd, st);
+    cudaError_t e = hdiff_to_compute(s, dtype, d, p.u, p.v, p.coeff, ud, vd, st);
     if (e != cudaSuccess) return e;
     constexpr int NC = 64, DEPTH = 16;
     const int64_t ncol = (int64_t)d.ni * d.nj;

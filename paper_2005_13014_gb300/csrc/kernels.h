@@ -42,11 +42,12 @@ cudaError_t hdiff_vadvc_launch(const oec_schedule& s, int dtype, const Dom& d, c
 size_t hdiff_vadvc_batch_slot_elems(const oec_schedule& s, int nk_max);
 int hdiff_vadvc_batch_blocks_per_sm(const oec_schedule& s, int dtype);
 cudaError_t hdiff_vadvc_batch_launch(const oec_schedule& s, int dtype, const HVBatchLaunch& b, cudaStream_t st);
-// hdiff of two fields (one launch) written in the compute type of (arith,
+// hdiff of two fields (one launch) written in the compute type of (s.arith,
 // dtype) over the domain layout (pitch ni, plane ni*nj): the producer of the
-// staged hdiff+vadvc form
-cudaError_t hdiff_to_compute(int arith, int dtype, const Dom& d, const void* in0, const void* in1, const void* coeff,
-                             void* out0, void* out1, cudaStream_t st);
+// staged hdiff+vadvc form. s.tile_i x s.tile_j and s.k_chunk pick its tile
+// when they name an SMEM hdiff tile, else 64 x 4 with 4 levels per CTA.
+cudaError_t hdiff_to_compute(const oec_schedule& s, int dtype, const Dom& d, const void* in0, const void* in1,
+                             const void* coeff, void* out0, void* out1, cudaStream_t st);
 
 // ---- fastwaves-like program -------------------------------------------------
 struct FastwavesPtrs {

@@ -45,12 +45,13 @@ std::vector<oec_schedule> candidates(const oec_program* p) {
       }
       break;
     case OEC_KIND_HDIFF_VADVC:
-      if (p->dtype == OEC_F64) c.push_back(mk(OEC_FUSE_NONE, 0, 16, 4, 1, 0, 2));
-      for (int a : {0, 1}) {
-        c.push_back(mk(OEC_FUSE_NONE, 0, 16, 4, 1, 0, a));
+      // staged: the tile is the hdiff producer's
+      for (int a : p->dtype == OEC_F64 ? std::vector<int>{2, 1, 0} : std::vector<int>{1, 0})
+        for (auto t : {std::pair<int, int>{32, 4}, {32, 8}, {64, 4}, {64, 8}, {128, 4}})
+          for (int kc : {4, 8}) c.push_back(mk(OEC_FUSE_NONE, 0, t.first, t.second, 1, kc, a));
+      for (int a : {0, 1})
         for (auto t : {std::pair<int, int>{16, 4}, {32, 2}, {8, 8}, {32, 4}, {8, 4}, {16, 2}})
           c.push_back(mk(OEC_FUSE_INLINE, OEC_STAGE_SMEM, t.first, t.second, 1, 0, a));
-      }
       break;
     case OEC_KIND_FASTWAVES:
       for (int a : ariths) {
