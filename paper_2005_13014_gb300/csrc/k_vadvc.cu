@@ -394,13 +394,11 @@ __global__ void __launch_bounds__(NC) hv_thomas_kernel(HV<typename P::S> p, cons
       ru = ru - mul_p2(c * du0, 0.5f);
       rv = rv - mul_p2(c * dv0, 0.5f);
     }
-#pragma unroll 1
-    for (int k = 0; k < nk; ++k) {
-      issue(k + DEPTH - 1);
-      cp_async_wait<DEPTH - 3>();   // level k+2 has landed
-      // elimination of row k
+    // elimination of row k (row 0 needs no special case: a_0 = 0 and c' = 0
+    // make m = b exactly)
+    auto eliminate = [&](int k) {
       const R ra = cvt<R>(a);
-      const R m = k == 0 ? cvt<R>(b) : subf(cvt<R>(b), ra * cp);
+      const R m = subf(cvt<R>(b), ra * cp);
       const R inv = rcp_(m);
       cp = cvt<R>(c) * inv;
       dpu = subf(cvt<R>(ru), ra * dpu) * inv;
@@ -409,35 +407,50 @@ __global__ void __launch_bounds__(NC) hv_thomas_kernel(HV<typename P::S> p, cons
       sp[0] = cp;
       sp[ncol] = dpu;
       sp[2 * ncol] = dpv;
-      // row k+1 (k+1 >= 1, so it has the lower term)
-      if (k + 1 < nk) {
-        const bool hi = k + 2 < nk;
-        C u2 = zero_<C>(), v2 = zero_<C>(), wf2 = zero_<C>(), du1 = zero_<C>(), dv1 = zero_<C>();
-        if (hi) {
-          const int sl = (k + 2) % DEPTH;
-          u2 = su[sl][t];
-          v2 = sv[sl][t];
-          wf2 = mul_p2(cvt<C>(sw0[sl][t]) + cvt<C>(sw1[sl][t]), 0.5f);
-          du1 = u2 - u1;
-          dv1 = v2 - v1;
-        }
-        a = -mul_p2(wf1, 0.25f);
-        c = hi ? mul_p2(wf2, 0.25f) : zero_<C>();
-        b = addf(addf(dtr, abs_(a)), abs_(c));
-        const C tu = dtr * u1, tv = dtr * v1;
-        if (hi) {
-          ru = tu - mul_p2(a * (-du0) + c * du1, 0.5f);
-          rv = tv - mul_p2(a * (-dv0) + c * dv1, 0.5f);
-        } else {
-          ru = tu - mul_p2(a * (-du0), 0.5f);
-          rv = tv - mul_p2(a * (-dv0), 0.5f);
-        }
-        u1 = u2;
-        v1 = v2;
-        du0 = du1;
-        dv0 = dv1;
-        wf1 = wf2;
+    };
+    // row k+1 (k+1 >= 1, so it has the lower term; hi: it has the upper one)
+    auto build_next = [&](int k, bool hi) {
+      C u2 = zero_<C>(), v2 = zero_<C>(), wf2 = zero_<C>(), du1 = zero_<C>(), dv1 = zero_<C>();
+      if (hi) {
+        const int sl = (k + 2) % DEPTH;
+        u2 = su[sl][t];
+        v2 = sv[sl][t];
+        wf2 = mul_p2(cvt<C>(sw0[sl][t]) + cvt<C>(sw1[sl][t]), 0.5f);
+        du1 = u2 - u1;
+        dv1 = v2 - v1;
       }
+      a = -mul_p2(wf1, 0.25f);
+      c = hi ? mul_p2(wf2, 0.25f) : zero_<C>();
+      b = addf(addf(dtr, abs_(a)), abs_(c));
+      const C tu = dtr * u1, tv = dtr * v1;
+      if (hi) {
+        ru = tu - mul_p2(a * (-du0) + c * du1, 0.5f);
+        rv = tv - mul_p2(a * (-dv0) + c * dv1, 0.5f);
+      } else {
+        ru = tu - mul_p2(a * (-du0), 0.5f);
+        rv = tv - mul_p2(a * (-dv0), 0.5f);
+      }
+      u1 = u2;
+      v1 = v2;
+      du0 = du1;
+      dv0 = dv1;
+      wf1 = wf2;
+    };
+    int k = 0;
+    // main part, branch-free: row k+1 always has both neighbours
+#pragma unroll 2
+    for (; k + 2 < nk; ++k) {
+      issue(k + DEPTH - 1);
+      cp_async_wait<DEPTH - 3>();   // level k+2 has landed
+      eliminate(k);
+      build_next(k, true);
+    }
+    // the last two levels
+    for (; k < nk; ++k) {
+      issue(k + DEPTH - 1);
+      cp_async_wait<DEPTH - 3>();
+      eliminate(k);
+      if (k + 1 < nk) build_next(k, false);
     }
     cp_async_wait<0>();
   }
@@ -465,7 +478,7 @@ __global__ void __launch_bounds__(NC) hv_thomas_kernel(HV<typename P::S> p, cons
   int64_t o = (int64_t)(nk - 1) * p.sk + cbase;
   p.uo[o] = cvt<S>(xu);
   p.vo[o] = cvt<S>(xv);
-#pragma unroll 1
+#pragma unroll 4
   for (int m = 0; m < nk - 1; ++m) {
     issue_b(m + DEPTH - 1);
     cp_async_wait<DEPTH - 1>();   // step m's level has landed
