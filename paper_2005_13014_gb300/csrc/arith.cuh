@@ -65,6 +65,13 @@ __device__ __forceinline__ df64 rcp_(df64 a) { return df_rcp(a); }
 
 template <class T> __device__ __forceinline__ T zero_() { return kc<T>(0.0f); }
 
+// exchange with the lane whose index differs in the bits of m (full warp)
+__device__ __forceinline__ float shfl_xor_(float a, int m) { return __shfl_xor_sync(0xFFFFFFFFu, a, m); }
+__device__ __forceinline__ double shfl_xor_(double a, int m) { return __shfl_xor_sync(0xFFFFFFFFu, a, m); }
+__device__ __forceinline__ df64 shfl_xor_(df64 a, int m) {
+  return df64{__shfl_xor_sync(0xFFFFFFFFu, a.hi, m), __shfl_xor_sync(0xFFFFFFFFu, a.lo, m)};
+}
+
 // addition/subtraction for chains without catastrophic cancellation (the
 // column recurrence): the fast double-float add, plain IEEE otherwise
 __device__ __forceinline__ float addf(float a, float b) { return a + b; }

@@ -328,165 +328,205 @@ hv_batch_kernel(const HVMember* __restrict__ members, int n_members, int total_i
 }
 
 // Staged form, column sweep over hdiff(u), hdiff(v) held in the compute type
-// (domain layout, pitch ni, plane ni*nj). One thread per column solves both
-// fields with one elimination of the shared matrix. The CTA's NC columns are
-// consecutive in (j, i) order; every value a level needs (hdiff(u), hdiff(v),
-// w(i), w(i+1)) is copied asynchronously into a shared-memory ring DEPTH
-// levels ahead of the recurrence, so the sequential chain never waits on
-// DRAM. The rows are built in the sweep (they do not depend on the
-// recurrence, so they fill its latency). c', d'_u, d'_v go to scratch
-// ([k][c', d'_u, d'_v][column]) and come back through the same kind of ring,
-// in descending level order, for the back substitution. Each thread reads
-// only ring entries its own copies wrote; the one barrier separates the two
-// uses of the ring.
+// (domain layout, pitch ni, plane ni*nj), by twisted factorisation: the
+// column's rows [0, m) are eliminated upwards from level 0 and its rows
+// [m, nk) downwards from the top level at the same time (m = ceil(nk/2)),
+// the two halves meet in a 2 x 2 system for x_{m-1}, x_m, and each half
+// substitutes back outwards. The operation count is that of the Thomas
+// algorithm; each thread's sequential chain is half a column long. Both
+// halves run one instruction stream: a half walks its levels in direction
+// dir (+1 up, -1 down), and for a row the coupling to the level behind it is
+// beta (a_k going up, c_k going down) and to the level ahead gamma:
+//   m_k = b_k - beta_k g_prev,  g_k = gamma_k / m_k,
+//   e_k = (d_k - beta_k e_prev) / m_k,   x_k = e_k - g_k x_ahead.
+// Warp layout: lanes 0..15 eliminate 16 columns upwards, lanes 16..31 the same
+// columns downwards (partner = lane ^ 16); NC columns per CTA, consecutive in
+// (j, i) order. A thread solves both fields (one shared g recurrence). The
+// values a level needs (hdiff(u), hdiff(v) there, w for the edge behind it)
+// are copied asynchronously into a shared-memory ring DEPTH levels ahead, and
+// row s+1 is built while row s is eliminated. g, e_u, e_v go to scratch
+// ([k][g, e_u, e_v][column]) and come back through the same kind of ring for
+// the back substitution. Each thread reads only ring entries its own copies
+// wrote; the one barrier separates the two uses of the ring.
 template <class P, int NC, int DEPTH>
-__global__ void __launch_bounds__(NC) hv_thomas_kernel(HV<typename P::S> p, const typename P::C* __restrict__ ud,
-                                                       const typename P::C* __restrict__ vd, double dtr_d,
-                                                       typename P::R* __restrict__ scr) {
+__global__ void __launch_bounds__(2 * NC) hv_thomas_kernel(HV<typename P::S> p, const typename P::C* __restrict__ ud,
+                                                           const typename P::C* __restrict__ vd, double dtr_d,
+                                                           typename P::R* __restrict__ scr) {
   typedef typename P::S S;
   typedef typename P::C C;
   typedef typename P::R R;
-  constexpr size_t FB = size_t(DEPTH) * NC * (2 * sizeof(C) + 2 * sizeof(S));
-  constexpr size_t BB = size_t(DEPTH) * NC * 3 * sizeof(R);
+  constexpr int NT = 2 * NC;
+  constexpr size_t FB = size_t(DEPTH) * NT * (2 * sizeof(C) + 2 * sizeof(S));
+  constexpr size_t BB = size_t(DEPTH) * NT * 3 * sizeof(R);
   __shared__ __align__(16) unsigned char ring[FB > BB ? FB : BB];
-  C(*su)[NC] = reinterpret_cast<C(*)[NC]>(ring);
-  C(*sv)[NC] = su + DEPTH;
-  S(*sw0)[NC] = reinterpret_cast<S(*)[NC]>(sv + DEPTH);
-  S(*sw1)[NC] = sw0 + DEPTH;
-  const int t = threadIdx.x;
+  C(*su)[NT] = reinterpret_cast<C(*)[NT]>(ring);
+  C(*sv)[NT] = su + DEPTH;
+  S(*sw0)[NT] = reinterpret_cast<S(*)[NT]>(sv + DEPTH);
+  S(*sw1)[NT] = sw0 + DEPTH;
+  const int t = threadIdx.x, lane = t & 31;
+  const bool down = lane >= 16;
   const int64_t ncol = (int64_t)p.ni * p.nj;
-  const int64_t col = (int64_t)blockIdx.x * NC + t;
-  const bool active = col < ncol;   // inactive threads only join the barrier
+  const int64_t col = (int64_t)blockIdx.x * NC + (t >> 5) * 16 + (lane & 15);
+  const bool active = col < ncol;   // inactive threads only join the barrier and the exchange
   const int i = active ? int(col % p.ni) : 0, j = active ? int(col / p.ni) : 0;
-  const int nk = p.nk;
+  const int nk = p.nk, mid = (nk + 1) / 2;
+  const int nsteps = active ? (down ? nk - mid : mid) : 0;
   const C dtr = cvt<C>(dtr_d);
   const int64_t cbase = (int64_t)j * p.sj + i;
   const S* __restrict__ wcol = p.w + cbase;
-  auto issue = [&](int k) {
-    if (active && k < nk) {
-      const int sl = k % DEPTH;
-      const int64_t o = (int64_t)k * ncol + col;
-      cp_async(&su[sl][t], ud + o);
-      cp_async(&sv[sl][t], vd + o);
-      cp_async(&sw0[sl][t], wcol + (int64_t)k * p.sk);
-      cp_async(&sw1[sl][t], wcol + (int64_t)k * p.sk + 1);
+  // level of step s, and the level whose w gives the edge behind step s
+  // (the edge between levels k-1 and k belongs to w at level k)
+  auto lev = [&](int st) { return down ? nk - 1 - st : st; };
+  auto wlev = [&](int st) { return down ? nk - st : st; };
+  auto issue = [&](int st) {
+    if (st <= nsteps) {
+      const int sl = st % DEPTH, k = lev(st), kw = wlev(st);
+      if (k >= 0 && k < nk) {
+        const int64_t o = (int64_t)k * ncol + col;
+        cp_async(&su[sl][t], ud + o);
+        cp_async(&sv[sl][t], vd + o);
+      }
+      if (kw < nk) {
+        cp_async(&sw0[sl][t], wcol + (int64_t)kw * p.sk);
+        cp_async(&sw1[sl][t], wcol + (int64_t)kw * p.sk + 1);
+      }
     }
     cp_async_commit();
   };
-  R cp = cvt<R>(0.0f), dpu = cvt<R>(0.0f), dpv = cvt<R>(0.0f);
+  // wf of the edge held in slot st (zero where there is none)
+  auto wf_of = [&](int st) {
+    const int sl = st % DEPTH;
+    return wlev(st) < nk ? mul_p2(cvt<C>(sw0[sl][t]) + cvt<C>(sw1[sl][t]), 0.5f) : zero_<C>();
+  };
+  const float sgn = down ? -1.0f : 1.0f;   // beta = -sgn wf_behind / 4, gamma = sgn wf_ahead / 4
+  R g = cvt<R>(0.0f), eu = cvt<R>(0.0f), ev = cvt<R>(0.0f);
 #pragma unroll 1
-  for (int k = 0; k < DEPTH - 1; ++k) issue(k);
-  if (active) {
-    // Software pipeline: iteration k eliminates row k and builds row k+1 (the
-    // two are independent, so their latencies overlap). Carried: phi_{k+1},
-    // delta_k = phi_{k+1} - phi_k (row k+1 uses phi_k - phi_{k+1} = -delta_k,
-    // exactly), wf_{k+1}.
-    cp_async_wait<DEPTH - 3>();   // levels 0 and 1 have landed
-    const int n1 = nk > 1 ? 1 : 0;
-    C u1 = su[n1][t], v1 = sv[n1][t];
-    C wf1 = nk > 1 ? mul_p2(cvt<C>(sw0[1][t]) + cvt<C>(sw1[1][t]), 0.5f) : zero_<C>();
-    C du0 = nk > 1 ? u1 - su[0][t] : zero_<C>(), dv0 = nk > 1 ? v1 - sv[0][t] : zero_<C>();
-    // row 0
-    C a = zero_<C>(), c = nk > 1 ? mul_p2(wf1, 0.25f) : zero_<C>();
-    C b = addf(dtr, abs_(c));
-    C ru = dtr * su[0][t], rv = dtr * sv[0][t];
-    if (nk > 1) {
-      ru = ru - mul_p2(c * du0, 0.5f);
-      rv = rv - mul_p2(c * dv0, 0.5f);
+  for (int st = 0; st < DEPTH - 1; ++st) issue(st);
+  cp_async_wait<DEPTH - 3>();   // slots 0 and 1 have landed
+  // row of step 0: no level behind; ahead: slot 1 (absent only when nk == 1)
+  const bool ahead0 = nsteps > 0 && lev(1) >= 0 && lev(1) < nk;
+  C u1 = zero_<C>(), v1 = zero_<C>(), wfa = zero_<C>(), du0 = zero_<C>(), dv0 = zero_<C>();
+  C beta = zero_<C>(), gamma = zero_<C>(), b = dtr, ru = zero_<C>(), rv = zero_<C>();
+  if (nsteps > 0) {
+    const C u0 = su[0][t], v0 = sv[0][t];
+    if (ahead0) {
+      u1 = su[1][t];
+      v1 = sv[1][t];
+      wfa = wf_of(1);
+      du0 = u1 - u0;
+      dv0 = v1 - v0;
+      gamma = mul_p2(wfa, 0.25f * sgn);
     }
-    // elimination of row k (row 0 needs no special case: a_0 = 0 and c' = 0
-    // make m = b exactly)
-    auto eliminate = [&](int k) {
-      const R ra = cvt<R>(a);
-      const R m = subf(cvt<R>(b), ra * cp);
-      const R inv = rcp_(m);
-      cp = cvt<R>(c) * inv;
-      dpu = subf(cvt<R>(ru), ra * dpu) * inv;
-      dpv = subf(cvt<R>(rv), ra * dpv) * inv;
-      R* sp = scr + (int64_t)k * 3 * ncol + col;
-      sp[0] = cp;
-      sp[ncol] = dpu;
-      sp[2 * ncol] = dpv;
-    };
-    // row k+1 (k+1 >= 1, so it has the lower term; hi: it has the upper one)
-    auto build_next = [&](int k, bool hi) {
-      C u2 = zero_<C>(), v2 = zero_<C>(), wf2 = zero_<C>(), du1 = zero_<C>(), dv1 = zero_<C>();
-      if (hi) {
-        const int sl = (k + 2) % DEPTH;
-        u2 = su[sl][t];
-        v2 = sv[sl][t];
-        wf2 = mul_p2(cvt<C>(sw0[sl][t]) + cvt<C>(sw1[sl][t]), 0.5f);
-        du1 = u2 - u1;
-        dv1 = v2 - v1;
-      }
-      a = -mul_p2(wf1, 0.25f);
-      c = hi ? mul_p2(wf2, 0.25f) : zero_<C>();
-      b = addf(addf(dtr, abs_(a)), abs_(c));
-      const C tu = dtr * u1, tv = dtr * v1;
-      if (hi) {
-        ru = tu - mul_p2(a * (-du0) + c * du1, 0.5f);
-        rv = tv - mul_p2(a * (-dv0) + c * dv1, 0.5f);
-      } else {
-        ru = tu - mul_p2(a * (-du0), 0.5f);
-        rv = tv - mul_p2(a * (-dv0), 0.5f);
-      }
-      u1 = u2;
-      v1 = v2;
-      du0 = du1;
-      dv0 = dv1;
-      wf1 = wf2;
-    };
-    int k = 0;
-    // main part, branch-free: row k+1 always has both neighbours
+    b = addf(dtr, abs_(gamma));
+    ru = dtr * u0;
+    rv = dtr * v0;
+    if (ahead0) {
+      ru = ru - mul_p2(gamma * du0, 0.5f);
+      rv = rv - mul_p2(gamma * dv0, 0.5f);
+    }
+  }
+  // elimination of the row of step st (step 0 needs no special case:
+  // beta = 0 and g = 0 make m = b exactly)
+  auto eliminate = [&](int st) {
+    const R rb = cvt<R>(beta);
+    const R m = subf(cvt<R>(b), rb * g);
+    const R inv = rcp_(m);
+    g = cvt<R>(gamma) * inv;
+    eu = subf(cvt<R>(ru), rb * eu) * inv;
+    ev = subf(cvt<R>(rv), rb * ev) * inv;
+    R* sp = scr + (int64_t)lev(st) * 3 * ncol + col;
+    sp[0] = g;
+    sp[ncol] = eu;
+    sp[2 * ncol] = ev;
+  };
+  // row of step st+1 (it has a level behind; hi: it has one ahead)
+  auto build_next = [&](int st, bool hi) {
+    C u2 = zero_<C>(), v2 = zero_<C>(), wf2 = zero_<C>(), du1 = zero_<C>(), dv1 = zero_<C>();
+    if (hi) {
+      const int sl = (st + 2) % DEPTH;
+      u2 = su[sl][t];
+      v2 = sv[sl][t];
+      wf2 = wf_of(st + 2);
+      du1 = u2 - u1;
+      dv1 = v2 - v1;
+    }
+    beta = mul_p2(wfa, -0.25f * sgn);
+    gamma = hi ? mul_p2(wf2, 0.25f * sgn) : zero_<C>();
+    b = addf(addf(dtr, abs_(beta)), abs_(gamma));
+    const C tu = dtr * u1, tv = dtr * v1;
+    if (hi) {
+      ru = tu - mul_p2(beta * (-du0) + gamma * du1, 0.5f);
+      rv = tv - mul_p2(beta * (-dv0) + gamma * dv1, 0.5f);
+    } else {
+      ru = tu - mul_p2(beta * (-du0), 0.5f);
+      rv = tv - mul_p2(beta * (-dv0), 0.5f);
+    }
+    u1 = u2;
+    v1 = v2;
+    du0 = du1;
+    dv0 = dv1;
+    wfa = wf2;
+  };
+  // every row a half builds has a level ahead (the other half's first row is
+  // there), except the single row of a one-level column
+  int st = 0;
 #pragma unroll 2
-    for (; k + 2 < nk; ++k) {
-      issue(k + DEPTH - 1);
-      cp_async_wait<DEPTH - 3>();   // level k+2 has landed
-      eliminate(k);
-      build_next(k, true);
-    }
-    // the last two levels
-    for (; k < nk; ++k) {
-      issue(k + DEPTH - 1);
-      cp_async_wait<DEPTH - 3>();
-      eliminate(k);
-      if (k + 1 < nk) build_next(k, false);
-    }
-    cp_async_wait<0>();
+  for (; st + 1 < nsteps; ++st) {
+    issue(st + DEPTH - 1);
+    cp_async_wait<DEPTH - 3>();   // slot st+2 has landed
+    eliminate(st);
+    build_next(st, true);
+  }
+  if (st < nsteps) {
+    issue(st + DEPTH - 1);
+    eliminate(st);
+  }
+  cp_async_wait<0>();
+  // the halves meet: x_lo = x_{mid-1} (upward half's last row), x_hi = x_mid
+  const R g_o = shfl_xor_(g, 16), eu_o = shfl_xor_(eu, 16), ev_o = shfl_xor_(ev, 16);
+  const R g_lo = down ? g_o : g, g_hi = down ? g : g_o;
+  const R inv = rcp_(subf(cvt<R>(1.0f), g_lo * g_hi));
+  R xu, xv;
+  {
+    const R eu_lo = down ? eu_o : eu, eu_hi = down ? eu : eu_o;
+    const R ev_lo = down ? ev_o : ev, ev_hi = down ? ev : ev_o;
+    const R xu_lo = subf(eu_lo, g_lo * eu_hi) * inv, xv_lo = subf(ev_lo, g_lo * ev_hi) * inv;
+    xu = down ? subf(eu_hi, g_hi * xu_lo) : xu_lo;
+    xv = down ? subf(ev_hi, g_hi * xv_lo) : xv_lo;
   }
   __syncthreads();   // every thread is done with the forward ring
   __threadfence_block();   // this thread's scratch stores precede its copies below
-  R(*sc)[NC] = reinterpret_cast<R(*)[NC]>(ring);
-  R(*sdu)[NC] = sc + DEPTH;
-  R(*sdv)[NC] = sdu + DEPTH;
-  // back substitution over levels nk-2 .. 0; step m handles level nk-2-m
-  auto issue_b = [&](int m) {
-    const int k = nk - 2 - m;
-    if (active && k >= 0) {
-      const int sl = m % DEPTH;
-      const R* s = scr + (int64_t)k * 3 * ncol + col;
-      cp_async(&sc[sl][t], s);
-      cp_async(&sdu[sl][t], s + ncol);
-      cp_async(&sdv[sl][t], s + 2 * ncol);
+  R(*sg)[NT] = reinterpret_cast<R(*)[NT]>(ring);
+  R(*seu)[NT] = sg + DEPTH;
+  R(*sev)[NT] = seu + DEPTH;
+  // back substitution outwards: back step mm handles step nsteps-2-mm
+  auto issue_b = [&](int mm) {
+    const int sb = nsteps - 2 - mm;
+    if (sb >= 0) {
+      const int sl = mm % DEPTH;
+      const R* sp = scr + (int64_t)lev(sb) * 3 * ncol + col;
+      cp_async(&sg[sl][t], sp);
+      cp_async(&seu[sl][t], sp + ncol);
+      cp_async(&sev[sl][t], sp + 2 * ncol);
     }
     cp_async_commit();
   };
-  if (!active) return;
+  if (nsteps == 0) return;
 #pragma unroll 1
-  for (int m = 0; m < DEPTH - 1; ++m) issue_b(m);
-  R xu = dpu, xv = dpv;
-  int64_t o = (int64_t)(nk - 1) * p.sk + cbase;
+  for (int mm = 0; mm < DEPTH - 1; ++mm) issue_b(mm);
+  int64_t o = (int64_t)lev(nsteps - 1) * p.sk + cbase;
+  const int64_t ostep = down ? p.sk : -p.sk;   // outwards
   p.uo[o] = cvt<S>(xu);
   p.vo[o] = cvt<S>(xv);
 #pragma unroll 4
-  for (int m = 0; m < nk - 1; ++m) {
-    issue_b(m + DEPTH - 1);
-    cp_async_wait<DEPTH - 1>();   // step m's level has landed
-    const int sl = m % DEPTH;
-    const R c_ = sc[sl][t];
-    xu = subf(sdu[sl][t], c_ * xu);
-    xv = subf(sdv[sl][t], c_ * xv);
-    o -= p.sk;
+  for (int mm = 0; mm < nsteps - 1; ++mm) {
+    issue_b(mm + DEPTH - 1);
+    cp_async_wait<DEPTH - 1>();   // back step mm's values have landed
+    const int sl = mm % DEPTH;
+    const R gk = sg[sl][t];
+    xu = subf(seu[sl][t], gk * xu);
+    xv = subf(sev[sl][t], gk * xv);
+    o += ostep;
     p.uo[o] = cvt<S>(xu);
     p.vo[o] = cvt<S>(xv);
   }
@@ -599,9 +639,9 @@ cudaError_t run(const oec_schedule& s, int dtype, const Dom& d, const HV<typenam
     C* vd = (C*)(scratch + l.vd);
     cudaError_t e = hdiff_to_compute(s, dtype, d, p.u, p.v, p.coeff, ud, vd, st);
     if (e != cudaSuccess) return e;
-    constexpr int NC = 64, DEPTH = 16;
+    constexpr int NC = 32, DEPTH = 16;   // 64 threads: two warps of 16 columns
     const int64_t ncol = (int64_t)d.ni * d.nj;
-    hv_thomas_kernel<P, NC, DEPTH><<<(unsigned)((ncol + NC - 1) / NC), NC, 0, st>>>(p, ud, vd, dtr,
+    hv_thomas_kernel<P, NC, DEPTH><<<(unsigned)((ncol + NC - 1) / NC), 2 * NC, 0, st>>>(p, ud, vd, dtr,
                                                                                    (typename P::R*)(scratch + l.thomas));
                                                                                    launched(st);
     return cudaGetLastError();
