@@ -285,3 +285,13 @@ def test_hdiff_fixed_point_mixed_magnitudes():
 @pytest.mark.parametrize("n", [(37, 23, 11), (33, 5, 1), (33, 5, 2), (128, 128, 80)], ids=str)
 def test_hdiff_vadvc_fixed_point_staged(n):
     assert _hv_case(n, 3, "f64", dict(fusion=1, arith=2)) <= TOL["f64"]
+
+
+@pytest.mark.parametrize("kc", [4, 8])
+@pytest.mark.parametrize("tile", [(32, 4), (32, 8), (64, 4), (64, 8), (128, 4)], ids=str)
+@pytest.mark.parametrize("dtype,arith", [("f64", 0), ("f64", 1), ("f64", 2), ("f32", 0), ("f32", 1)])
+def test_hdiff_vadvc_staged_producer_tiles(dtype, arith, tile, kc):
+    """The staged form's hdiff producer on each tile the tuner may pick, with
+    the twisted column sweep behind it (ragged tiles, odd column count)."""
+    sched = dict(fusion=1, tile_i=tile[0], tile_j=tile[1], k_chunk=kc, arith=arith)
+    assert _hv_case((37, 23, 11), 3, dtype, sched) <= TOL[dtype]
