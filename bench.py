@@ -357,68 +357,113 @@ def run_gpu(args):
 # --------------------------------------------------------------- other workloads
 
 def _timed(fn, steps, warmup, stream):
+    """Mean ms per call of fn(step) over `steps` calls after `warmup` calls."""
     import torch
-    for _ in range(warmup):
-        fn()
+    for w in range(warmup):
+        fn(w)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(steps):
-        fn()
+    for s in range(steps):
+        fn(s)
     e1.record(stream)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / steps
 
 
-def run_mixed(args):
-    """hdiff and fastwaves at 256x256x80, halo 3: FP32 vs FP64 (native and
-    double-float) throughput, GB/s and per-field error against the oracle."""
+def _l2_bytes():
     import torch
-    import __graft_entry__
-    __graft_entry__.build()
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    return getattr(props, "L2_cache_size", 128 << 20)
+
+
+def _run_program(prog_name, dtype, arith, steps, schedule=None, cache=None):
+    """One stencil program at 256x256x80, halo 3: autotuned (or the given
+    schedule) and timed over rotating resident copies of its fields (> 3 x L2,
+    so every apply reads HBM); error per output against the FP64 oracle."""
+    import torch
     from oracle import stencils as S
     from paper_2005_13014_gb300 import inputs, programs
     from paper_2005_13014_gb300.api import Program, device_field
-    n, h = (256, 256, 80), 3
+    n, h = MIXED_N, 3
     pts = n[0] * n[1] * n[2]
     stream = torch.cuda.current_stream()
-    res = {}
-    fh = inputs.hdiff_fields(*n, h)
-    ffw = inputs.fastwaves_fields(*n, h)
-    ref_cache = {}
+    cache = {} if cache is None else cache
+    rnd = (lambda a: a.astype(np.float32).astype(np.float64)) if dtype == "f32" else (lambda a: a)
+    if prog_name == "hdiff":
+        if "hdiff_fields" not in cache:
+            cache["hdiff_fields"] = inputs.hdiff_fields(*n, h)
+        f0 = cache["hdiff_fields"]
+        f = {k: rnd(v) for k, v in f0.items()}
+        prog = Program(programs.HDIFF, dtype)
+        names, n_out, params = ["in", "coeff"], 1, []
+    else:
+        if "fw_fields" not in cache:
+            cache["fw_fields"] = inputs.fastwaves_fields(*n, h)
+        f0 = cache["fw_fields"]
+        f = {k: rnd(v) for k, v in f0.items()}
+        prog = Program(programs.FASTWAVES, dtype)
+        names, n_out, params = list(inputs.FASTWAVES_NAMES), 2, [0.5, 0.0625]
+    set_bytes = (len(names) + n_out) * f[names[0]].size * (4 if dtype == "f32" else 8)
+    n_sets = max(1, int(np.ceil(3 * _l2_bytes() / set_bytes)))
+    # rows padded so that every row's first interior point is 16-byte aligned
+    # (the vectorised schedules need it; the others do not care)
+    sets = [([device_field(f[k], h, dtype, align_bytes=16) for k in names],
+             [device_field(np.zeros_like(f[names[0]]), h, dtype, align_bytes=16) for _ in range(n_out)])
+            for _ in range(n_sets)]
+    ins, outs = sets[0]
+    if schedule:
+        prog.set_schedule(**schedule)
+    else:
+        cands = [c for c in prog.candidates() if c["arith"] == arith]
+        prog.autotune(ins, outs, (0, 0, 0), n, (h, h, h), params, candidates=cands, reps=5)
+    ms = _timed(lambda x: prog.apply(*sets[x % n_sets], (0, 0, 0), n, (h, h, h), params), steps, 3, stream)
+    key = (prog_name, dtype)
+    if key not in cache:
+        G = {k: S.Grid.storage(v, h) for k, v in f.items()}
+        cache[key] = ([S.hdiff(G["in"], G["coeff"], (0, 0, 0), n)] if prog_name == "hdiff"
+                      else list(S.fastwaves(G, (0, 0, 0), n, 0.5, 0.0625)))
+    prog.apply(ins, outs, (0, 0, 0), n, (h, h, h), params)
+    torch.cuda.synchronize()
+    errs = []
+    for o, r in zip(outs, cache[key]):
+        g = o.interior((0, 0, 0), n).cpu().numpy().astype(np.float64)
+        errs.append(float(np.max(np.abs(g - r)) / np.max(np.abs(r))))
+    nbytes = prog.algorithmic_bytes((0, 0, 0), n)
+    return {"gpoints_per_s": pts / (ms * 1e-3) / 1e9, "ms": ms, "algorithmic_GBps": nbytes / (ms * 1e-3) / 1e9,
+            "frac_of_measured_hbm": nbytes / (ms * 1e-3) / 1e9 / _peaks().get("hbm_gbs", 6800.0),
+            "max_rel_err_per_output": errs, "schedule": prog.schedule, "launches_per_apply": prog.launch_count(),
+            "rotating_sets": n_sets}
+
+
+MIXED_N = (256, 256, 80)
+
+
+def run_mixed(args):
+    """hdiff and fastwaves at 256x256x80, halo 3: FP32 vs FP64 (native,
+    double-float and, for hdiff, fixed point) throughput, GB/s and per-field
+    error against the oracle."""
+    import __graft_entry__
+    __graft_entry__.build()
+    res, cache = {}, {}
     for prog_name in ("hdiff", "fastwaves"):
         for dtype, arith in (("f32", 0), ("f64", 0), ("f64", 1)) + ((("f64", 2),) if prog_name == "hdiff" else ()):
-            rnd = (lambda a: a.astype(np.float32).astype(np.float64)) if dtype == "f32" else (lambda a: a)
-            if prog_name == "hdiff":
-                f = {k: rnd(v) for k, v in fh.items()}
-                prog = Program(programs.HDIFF, dtype)
-                ins = [device_field(f["in"], h, dtype), device_field(f["coeff"], h, dtype)]
-                outs = [device_field(np.zeros_like(f["in"]), h, dtype)]
-                params = []
-            else:
-                f = {k: rnd(v) for k, v in ffw.items()}
-                prog = Program(programs.FASTWAVES, dtype)
-                ins = [device_field(f[k], h, dtype) for k in inputs.FASTWAVES_NAMES]
-                outs = [device_field(np.zeros_like(f["pp"]), h, dtype) for _ in range(2)]
-                params = [0.5, 0.0625]
-            cands = [c for c in prog.candidates() if c["arith"] == arith]
-            times, best = prog.autotune(ins, outs, (0, 0, 0), n, (h, h, h), params, candidates=cands, reps=5)
-            ms = _timed(lambda: prog.apply(ins, outs, (0, 0, 0), n, (h, h, h), params), args.steps, 3, stream)
-            key = (prog_name, dtype)
-            if key not in ref_cache:
-                G = {k: S.Grid.storage(v, h) for k, v in f.items()}
-                ref_cache[key] = ([S.hdiff(G["in"], G["coeff"], (0, 0, 0), n)] if prog_name == "hdiff"
-                                  else list(S.fastwaves(G, (0, 0, 0), n, 0.5, 0.0625)))
-            errs = []
-            for o, r in zip(outs, ref_cache[key]):
-                g = o.interior((0, 0, 0), n).cpu().numpy().astype(np.float64)
-                errs.append(float(np.max(np.abs(g - r)) / np.max(np.abs(r))))
-            nbytes = prog.algorithmic_bytes((0, 0, 0), n)
-            res[f"{prog_name}_{dtype}" + {0: "", 1: "_df", 2: "_fixed"}[arith]] = {
-                "gpoints_per_s": pts / (ms * 1e-3) / 1e9, "ms": ms, "algorithmic_GBps": nbytes / (ms * 1e-3) / 1e9,
-                "frac_of_measured_hbm": nbytes / (ms * 1e-3) / 1e9 / _peaks().get("hbm_gbs", 6800.0),
-                "max_rel_err_per_output": errs, "schedule": prog.schedule}
-    print(json.dumps({"workload": "mixed precision 256x256x80 halo 3", "results": res}))
+            key = f"{prog_name}_{dtype}" + {0: "", 1: "_df", 2: "_fixed"}[arith]
+            res[key] = _run_program(prog_name, dtype, arith, args.steps, cache=cache)
+    print(json.dumps({"workload": "mixed precision 256x256x80 halo 3", "l2": "inputs rotated over > 3 x L2",
+                      "results": res}))
+    return 0
+
+
+def run_single(args):
+    """One program (--workload hdiff|fastwaves) at 256x256x80 with --dtype,
+    --arith and an optional --schedule."""
+    import __graft_entry__
+    __graft_entry__.build()
+    r = _run_program(args.workload, args.dtype, args.arith, args.steps,
+                     schedule=json.loads(args.schedule) if args.schedule else None)
+    print(json.dumps({"workload": f"{args.workload} {args.dtype} arith {args.arith} 256x256x80 halo 3",
+                      "l2": "inputs rotated over > 3 x L2", "result": r}))
     return 0
 
 
@@ -449,26 +494,26 @@ def run_ensemble(args):
             continue
         prog.set_schedule(**c)
         b = Batch(prog, members, [2.0])
-        ms = _timed(lambda: b.apply(), 5, 2, stream)
+        ms = _timed(lambda _: b.apply(), 5, 2, stream)
         tune[f"{c['tile_i']}x{c['tile_j']}_arith{c['arith']}"] = ms
         if best is None or ms < best[0]:
             best = (ms, c)
         del b
     prog.set_schedule(**best[1])
     batch = Batch(prog, members, [2.0])
-    ms_graph = _timed(lambda: batch.apply(graph=True), args.steps, 3, stream)
-    ms_direct = _timed(lambda: batch.apply(graph=False), args.steps, 3, stream)
+    ms_graph = _timed(lambda _: batch.apply(graph=True), args.steps, 3, stream)
+    ms_direct = _timed(lambda _: batch.apply(graph=False), args.steps, 3, stream)
 
     def separate():
         for (d, o, lb, ub, hh) in members:
             prog.apply(d, o, lb, ub, hh, [2.0])
-    ms_sep = _timed(separate, args.steps, 3, stream)
+    ms_sep = _timed(lambda _: separate(), args.steps, 3, stream)
     g = torch.cuda.CUDAGraph()
     separate()
     torch.cuda.synchronize()
     with torch.cuda.graph(g):
         separate()
-    ms_sep_graph = _timed(lambda: g.replay(), args.steps, 3, torch.cuda.current_stream())
+    ms_sep_graph = _timed(lambda _: g.replay(), args.steps, 3, torch.cuda.current_stream())
     out = {"workload": "ensemble of 32 hdiff+vadvc members, FP32, halo 3", "members": shapes, "points": pts,
            "schedule": best[1], "tuning_ms": tune,
            "batched_graph": {"ms": ms_graph, "gpoints_per_s": pts / ms_graph / 1e6},
@@ -564,12 +609,15 @@ def main():
     ap.add_argument("--schedule", default=None, help="JSON schedule override")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="hdiff_vadvc", choices=["hdiff_vadvc", "mixed", "ensemble", "costmodel"],
+    ap.add_argument("--workload", default="hdiff_vadvc",
+                    choices=["hdiff_vadvc", "mixed", "ensemble", "costmodel", "hdiff", "fastwaves"],
                     help="hdiff_vadvc: the headline line; the others print their own report")
     ap.add_argument("--cm-train", type=int, default=180)
     ap.add_argument("--cm-test", type=int, default=200)
     ap.add_argument("--cm-epochs", type=int, default=300)
     ap.add_argument("--cm-save", default=None)
+    ap.add_argument("--dtype", default="f32", choices=["f32", "f64"], help="--workload hdiff|fastwaves")
+    ap.add_argument("--arith", type=int, default=0, help="--workload hdiff|fastwaves: autotune within this arith")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -579,6 +627,8 @@ def main():
         return run_ensemble(args)
     if args.workload == "costmodel":
         return run_costmodel(args)
+    if args.workload in ("hdiff", "fastwaves"):
+        return run_single(args)
     return run_gpu(args)
 
 

@@ -84,7 +84,15 @@ typedef enum {
 
 typedef enum {
   OEC_STAGE_REGS = 0,    /* every thread recomputes what it reads (paper's model)      */
-  OEC_STAGE_SMEM = 1     /* overlapped tile in shared memory, no redundant compute     */
+  OEC_STAGE_SMEM = 1,    /* overlapped tile in shared memory, no redundant compute     */
+  OEC_STAGE_STREAM = 2,  /* horizontal diffusion: overlapped tile walked up k, the next
+                            levels' windows copied asynchronously into a shared-memory
+                            ring while the current level is computed                   */
+  OEC_STAGE_WARP = 3     /* horizontal diffusion: a warp owns `unroll` (1, 2, 4) rows of
+                            32 x 16-byte vectors of columns; neighbours across vectors by
+                            warp shuffles; the next level loaded ahead. Needs 16-byte
+                            aligned rows (base at the domain corner and j/k strides),
+                            else OEC_ERR_UNSUPPORTED; tile_i/tile_j unused             */
 } oec_staging;
 
 typedef struct oec_schedule {

@@ -65,6 +65,17 @@ __device__ __forceinline__ df64 rcp_(df64 a) { return df_rcp(a); }
 
 template <class T> __device__ __forceinline__ T zero_() { return kc<T>(0.0f); }
 
+// value of the lane d below / above (full warp; lanes at the edge get their own)
+__device__ __forceinline__ float shfl_up_(float a, int d) { return __shfl_up_sync(0xFFFFFFFFu, a, d); }
+__device__ __forceinline__ double shfl_up_(double a, int d) { return __shfl_up_sync(0xFFFFFFFFu, a, d); }
+__device__ __forceinline__ df64 shfl_up_(df64 a, int d) {
+  return df64{__shfl_up_sync(0xFFFFFFFFu, a.hi, d), __shfl_up_sync(0xFFFFFFFFu, a.lo, d)};
+}
+__device__ __forceinline__ float shfl_down_(float a, int d) { return __shfl_down_sync(0xFFFFFFFFu, a, d); }
+__device__ __forceinline__ double shfl_down_(double a, int d) { return __shfl_down_sync(0xFFFFFFFFu, a, d); }
+__device__ __forceinline__ df64 shfl_down_(df64 a, int d) {
+  return df64{__shfl_down_sync(0xFFFFFFFFu, a.hi, d), __shfl_down_sync(0xFFFFFFFFu, a.lo, d)};
+}
 // exchange with the lane whose index differs in the bits of m (full warp)
 __device__ __forceinline__ float shfl_xor_(float a, int m) { return __shfl_xor_sync(0xFFFFFFFFu, a, m); }
 __device__ __forceinline__ double shfl_xor_(double a, int m) { return __shfl_xor_sync(0xFFFFFFFFu, a, m); }

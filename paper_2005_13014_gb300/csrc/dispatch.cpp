@@ -2,6 +2,8 @@
 // kernels: base pointers at the domain's lower corner, shared strides, scratch.
 #include <cuda_runtime.h>
 
+#include <cstdint>
+
 #include "../../include/oec.h"
 #include "api_internal.h"
 #include "kernels.h"
@@ -36,6 +38,11 @@ int dispatch_apply(oec_program* p, const oec_field_desc* in, const oec_field_des
   int rc = OEC_OK;
   switch (p->kind) {
     case OEC_KIND_HDIFF:
+      if (p->sched.fusion == OEC_FUSE_INLINE && p->sched.staging == OEC_STAGE_WARP &&
+          (((uintptr_t)I[0] | (uintptr_t)I[1] | (uintptr_t)O[0]) % 16 != 0 || (sj * (int64_t)es) % 16 != 0 ||
+           (sk * (int64_t)es) % 16 != 0))
+        return fail(OEC_ERR_UNSUPPORTED,
+                    "OEC_STAGE_WARP needs 16-byte aligned rows: domain corner of every field and j/k strides");
       rc = ensure_scratch(p, hdiff_scratch_bytes(p->sched, p->dtype, d));
       if (rc) return rc;
       e = hdiff_launch(p->sched, p->dtype, d, I[0], I[1], O[0], p->scratch, st);

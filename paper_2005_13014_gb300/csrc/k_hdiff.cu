@@ -77,7 +77,20 @@ hdiff_smem_kernel(const typename P::S* __restrict__ in0, const typename P::S* __
   }
 }
 
-template <class P, int U>
+// REGS form (the paper's model: every thread recomputes what it reads): a
+// thread owns U consecutive rows of one column and walks its k-chunk. The
+// values one level needs (the cross of offsets -2..2 around the U rows, and
+// coeff) are loaded into registers one level ahead, so the next level's loads
+// are in flight while the current level is computed.
+template <class S, int U>
+struct RegsWin {
+  S c0[U + 4];           // (i,   jb-2 .. jb+U+1)
+  S m1[U + 2], p1[U + 2];  // (i-1 / i+1, jb-1 .. jb+U)
+  S m2[U], p2[U];          // (i-2 / i+2, jb .. jb+U-1)
+  S cf[U];               // coeff (i, jb .. jb+U-1)
+};
+
+template <class P, int U, class Off, int NB>
 __global__ void hdiff_regs_kernel(const typename P::S* __restrict__ in, const typename P::S* __restrict__ coeff,
                                   typename P::S* __restrict__ out, int ni, int nj, int nk, int64_t sj, int64_t sk,
                                   int kchunk) {
@@ -88,33 +101,350 @@ __global__ void hdiff_regs_kernel(const typename P::S* __restrict__ in, const ty
   if (i >= ni || jb >= nj) return;
   const int jmax = nj + 1 - jb;          // last row offset inside the halo-2 window
   const int k0 = blockIdx.z * kchunk, k1 = min(nk, k0 + kchunk);
-  for (int k = k0; k < k1; ++k) {
-    const S* p = in + (int64_t)k * sk + (int64_t)jb * sj + i;
-    auto at = [&](int di, int dj) { return cvt<C>(ldg(p + (int64_t)min(dj, jmax) * sj + di)); };
-    C lc[U + 2], lw[U], le[U];   // lap(i, jb-1+r); lap(i-1, jb+r); lap(i+1, jb+r)
+  // element offsets from the level's (i, jb): rows jb-2 .. jb+U+1 (clamped to
+  // the window), computed once; the level offset advances by sk
+  Off roff[U + 4];
 #pragma unroll
-    for (int r = 0; r < U + 2; ++r) {
-      const int dj = r - 1;
-      lc[r] = hlap(at(0, dj), at(-1, dj), at(1, dj), at(0, dj - 1), at(0, dj + 1));
+  for (int x = 0; x < U + 4; ++x) roff[x] = (Off)min(x - 2, jmax) * (Off)sj;
+  const Off ksk = (Off)sk;
+  Off lev = (Off)k0 * ksk + (Off)jb * (Off)sj + i;
+  auto load = [&](RegsWin<S, U>& w, Off l) {
+#pragma unroll
+    for (int x = 0; x < U + 4; ++x) w.c0[x] = ldg(in + (l + roff[x]));
+#pragma unroll
+    for (int x = 0; x < U + 2; ++x) {
+      w.m1[x] = ldg(in + (l + roff[x + 1] - 1));
+      w.p1[x] = ldg(in + (l + roff[x + 1] + 1));
     }
 #pragma unroll
-    for (int r = 0; r < U; ++r) {
-      lw[r] = hlap(at(-1, r), at(-2, r), at(0, r), at(-1, r - 1), at(-1, r + 1));
-      le[r] = hlap(at(1, r), at(0, r), at(2, r), at(1, r - 1), at(1, r + 1));
+    for (int x = 0; x < U; ++x) {
+      w.m2[x] = ldg(in + (l + roff[x + 2] - 2));
+      w.p2[x] = ldg(in + (l + roff[x + 2] + 2));
+      if (jb + x < nj) w.cf[x] = ldg(coeff + (l + roff[x + 2]));
     }
+  };
+  // NB register windows, used in rotation with the level loop unrolled by
+  // NB: window x holds level k+x; after computing it, it is refilled with
+  // level k+x+NB, so NB-1 levels of compute cover every load's latency
+  RegsWin<S, U> win[NB];
 #pragma unroll
-    for (int r = 0; r < U; ++r) {
-      if (jb + r < nj) {
-        const C c = at(0, r);
-        const C flx = hflux(le[r], lc[r + 1], at(1, r), c);
-        const C flx_m = hflux(lc[r + 1], lw[r], c, at(-1, r));
-        const C fly = hflux(lc[r + 2], lc[r + 1], at(0, r + 1), c);
-        const C fly_m = hflux(lc[r + 1], lc[r], c, at(0, r - 1));
-        const int64_t o = (int64_t)k * sk + (int64_t)(jb + r) * sj + i;
-        out[o] = cvt<S>(hout(c, cvt<C>(ldg(coeff + o)), flx, flx_m, fly, fly_m));
+  for (int x = 0; x < NB; ++x)
+    if (k0 + x < k1) load(win[x], lev + (Off)x * ksk);
+  for (int k = k0; k < k1; k += NB, lev += (Off)NB * ksk) {
+#pragma unroll
+    for (int x = 0; x < NB; ++x) {
+      if (k + x >= k1) break;
+      const RegsWin<S, U>& cur = win[x];
+      const Off lx = lev + (Off)x * ksk;
+      // at(di, dj): the value at (i + di, jb + dj)
+      auto at = [&](int di, int dj) {
+        return cvt<C>(di == 0 ? cur.c0[dj + 2] : di == -1 ? cur.m1[dj + 1] : di == 1 ? cur.p1[dj + 1]
+                      : di == -2 ? cur.m2[dj] : cur.p2[dj]);
+      };
+      C lc[U + 2], lw[U], le[U];   // lap(i, jb-1+r); lap(i-1, jb+r); lap(i+1, jb+r)
+#pragma unroll
+      for (int r = 0; r < U + 2; ++r) {
+        const int dj = r - 1;
+        lc[r] = hlap(at(0, dj), at(-1, dj), at(1, dj), at(0, dj - 1), at(0, dj + 1));
       }
+#pragma unroll
+      for (int r = 0; r < U; ++r) {
+        lw[r] = hlap(at(-1, r), at(-2, r), at(0, r), at(-1, r - 1), at(-1, r + 1));
+        le[r] = hlap(at(1, r), at(0, r), at(2, r), at(1, r - 1), at(1, r + 1));
+      }
+#pragma unroll
+      for (int r = 0; r < U; ++r) {
+        if (jb + r < nj) {
+          const C c = at(0, r);
+          const C flx = hflux(le[r], lc[r + 1], at(1, r), c);
+          const C flx_m = hflux(lc[r + 1], lw[r], c, at(-1, r));
+          const C fly = hflux(lc[r + 2], lc[r + 1], at(0, r + 1), c);
+          const C fly_m = hflux(lc[r + 1], lc[r], c, at(0, r - 1));
+          out[lx + roff[r + 2]] = cvt<S>(hout(c, cvt<C>(cur.cf[r]), flx, flx_m, fly, fly_m));
+        }
+      }
+      if (k + x + NB < k1) load(win[x], lx + (Off)NB * ksk);
     }
   }
+}
+
+// true when every element offset a kernel forms from the domain's base
+// pointers (halo 2 around the domain) fits in a 32-bit int
+bool offsets_fit_int32(const Dom& d) {
+  const int64_t hi = (int64_t)(d.nk + 1) * d.sk + (int64_t)(d.nj + 2) * d.sj + d.ni + 2;
+  const int64_t lo = -(2 * d.sj + 2);
+  return hi < INT32_MAX && lo > INT32_MIN;
+}
+
+// ---- vectorised warp-row hdiff (OEC_STAGE_WARP) ------------------------------
+// A warp owns U rows of W = 32 V consecutive columns, V = 16 bytes / element
+// (4 floats or 2 doubles): lane l loads columns i0 + V l .. + V-1 of each row
+// as one 16-byte vector and computes those V points. Each Laplacian and each
+// flux is evaluated once per column; the values across a vector boundary
+// come from the adjacent lane by warp shuffles, and lane 0 / lane 31 load the
+// two columns outside the warp (i0-1, i0-2 / i0+W, i0+W+1) and evaluate the
+// Laplacian there. j-neighbours are the lane's other rows. The level loop
+// keeps NB register windows in rotation (the next levels' loads in flight
+// while this one is computed). Needs 16-byte aligned rows (checked by the
+// caller); a vector that would cross the input range's end is read element
+// by element.
+template <class S> struct Vec16;
+template <> struct Vec16<float> { typedef float4 T; static constexpr int V = 4; };
+template <> struct Vec16<double> { typedef double2 T; static constexpr int V = 2; };
+template <class S, int V> __device__ __forceinline__ void vsplit(const typename Vec16<S>::T& t, S (&d)[V]);
+template <> __device__ __forceinline__ void vsplit<float, 4>(const float4& t, float (&d)[4]) {
+  d[0] = t.x; d[1] = t.y; d[2] = t.z; d[3] = t.w;
+}
+template <> __device__ __forceinline__ void vsplit<double, 2>(const double2& t, double (&d)[2]) {
+  d[0] = t.x; d[1] = t.y;
+}
+template <class S, int V> __device__ __forceinline__ typename Vec16<S>::T vjoin(const S (&d)[V]);
+template <> __device__ __forceinline__ float4 vjoin<float, 4>(const float (&d)[4]) { return make_float4(d[0], d[1], d[2], d[3]); }
+template <> __device__ __forceinline__ double2 vjoin<double, 2>(const double (&d)[2]) { return make_double2(d[0], d[1]); }
+
+template <class S, int U, int V>
+struct VecWin {
+  S v[U + 4][V];   // rows jb-2 .. jb+U+1, this lane's columns
+  S ea[U + 2];     // lane 0: column i0-1, lane 31: column i0+W; rows jb-1 .. jb+U
+  S eb[U];         // lane 0: column i0-2, lane 31: column i0+W+1; rows jb .. jb+U-1
+  S cf[U][V];      // coeff, rows jb .. jb+U-1
+};
+
+template <class P, int U, class Off, int NB>
+__global__ void __launch_bounds__(128)
+hdiff_vec_kernel(const typename P::S* __restrict__ in, const typename P::S* __restrict__ coeff,
+                 typename P::S* __restrict__ out, int ni, int nj, int nk, int64_t sj, int64_t sk, int kchunk) {
+  typedef typename P::S S;
+  typedef typename P::C C;
+  typedef typename Vec16<S>::T VT;
+  constexpr int V = Vec16<S>::V, W = 32 * V;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int i0 = blockIdx.x * W, c0 = i0 + V * lane;
+  const int jb = (blockIdx.y * 4 + wid) * U;
+  if (jb >= nj) return;                                  // whole warp
+  const int jmax = nj + 1 - jb;                          // last row offset inside the halo-2 window
+  const int k0 = blockIdx.z * kchunk, k1 = min(nk, k0 + kchunk);
+  const bool vin_full = c0 + V - 1 <= ni + 1;            // whole vector inside the input range [-2, ni+2)
+  const bool vout_full = c0 + V - 1 < ni;                // whole vector inside the domain
+  const bool edge = lane == 0 || lane == 31;
+  const int ca = lane == 0 ? i0 - 1 : i0 + W, cb = lane == 0 ? i0 - 2 : i0 + W + 1;
+  const bool ea_ok = edge && ca <= ni + 1, eb_ok = edge && cb <= ni + 1;
+  Off roff[U + 4];
+#pragma unroll
+  for (int x = 0; x < U + 4; ++x) roff[x] = (Off)min(x - 2, jmax) * (Off)sj;
+  const Off ksk = (Off)sk;
+  Off lev = (Off)k0 * ksk + (Off)jb * (Off)sj;
+  auto load = [&](VecWin<S, U, V>& w, Off l) {
+#pragma unroll
+    for (int r = 0; r < U + 4; ++r) {
+      const S* q = in + (l + roff[r] + c0);
+      if (vin_full) {
+        vsplit<S, V>(__ldg(reinterpret_cast<const VT*>(q)), w.v[r]);
+      } else {
+#pragma unroll
+        for (int x = 0; x < V; ++x) w.v[r][x] = c0 + x <= ni + 1 ? ldg(q + x) : S(0);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < U + 2; ++r) w.ea[r] = ea_ok ? ldg(in + (l + roff[r + 1] + ca)) : S(0);
+#pragma unroll
+    for (int r = 0; r < U; ++r) {
+      w.eb[r] = eb_ok ? ldg(in + (l + roff[r + 2] + cb)) : S(0);
+      if (jb + r < nj) {
+        const S* q = coeff + (l + roff[r + 2] + c0);
+        if (vout_full) {
+          vsplit<S, V>(__ldg(reinterpret_cast<const VT*>(q)), w.cf[r]);
+        } else {
+#pragma unroll
+          for (int x = 0; x < V; ++x) w.cf[r][x] = c0 + x < ni ? ldg(q + x) : S(0);
+        }
+      }
+    }
+  };
+  VecWin<S, U, V> win[NB];
+#pragma unroll
+  for (int x = 0; x < NB; ++x)
+    if (k0 + x < k1) load(win[x], lev + (Off)x * ksk);
+  for (int k = k0; k < k1; k += NB, lev += (Off)NB * ksk) {
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      if (k + b >= k1) break;
+      const VecWin<S, U, V>& w = win[b];
+      const Off lx = lev + (Off)b * ksk;
+      auto at = [&](int r, int x) { return cvt<C>(w.v[r][x]); };
+      // Laplacians of rows jb-1 .. jb+U (index q = row - jb + 1) at this lane's
+      // columns; the input value right of this lane's last column
+      C lap[U + 2][V], inr[U + 2];
+#pragma unroll
+      for (int q = 0; q < U + 2; ++q) {
+        const int r = q + 1;
+        C left = shfl_up_(at(r, V - 1), 1), right = shfl_down_(at(r, 0), 1);
+        if (lane == 0) left = cvt<C>(w.ea[q]);
+        if (lane == 31) right = cvt<C>(w.ea[q]);
+        inr[q] = right;
+#pragma unroll
+        for (int x = 0; x < V; ++x)
+          lap[q][x] = hlap(at(r, x), x > 0 ? at(r, x - 1) : left, x < V - 1 ? at(r, x + 1) : right, at(r - 1, x),
+                           at(r + 1, x));
+      }
+      // fly between rows jb-1+q and jb+q
+      C fly[U + 1][V];
+#pragma unroll
+      for (int q = 0; q < U + 1; ++q)
+#pragma unroll
+        for (int x = 0; x < V; ++x) fly[q][x] = hflux(lap[q + 1][x], lap[q][x], at(q + 2, x), at(q + 1, x));
+#pragma unroll
+      for (int o = 0; o < U; ++o) {
+        const int q = o + 1, r = o + 2;
+        // the Laplacian just outside the warp (lanes 0 and 31 only)
+        const C le = lane == 0 ? hlap(cvt<C>(w.ea[q]), cvt<C>(w.eb[o]), at(r, 0), cvt<C>(w.ea[q - 1]), cvt<C>(w.ea[q + 1]))
+                               : hlap(cvt<C>(w.ea[q]), at(r, V - 1), cvt<C>(w.eb[o]), cvt<C>(w.ea[q - 1]), cvt<C>(w.ea[q + 1]));
+        C lapr = shfl_down_(lap[q][0], 1);
+        if (lane == 31) lapr = le;
+        C flx[V];
+#pragma unroll
+        for (int x = 0; x < V; ++x)
+          flx[x] = x < V - 1 ? hflux(lap[q][x + 1], lap[q][x], at(r, x + 1), at(r, x))
+                             : hflux(lapr, lap[q][x], inr[q], at(r, x));
+        C flxl = shfl_up_(flx[V - 1], 1);
+        if (lane == 0) flxl = hflux(lap[q][0], le, at(r, 0), cvt<C>(w.ea[q]));
+        if (jb + o < nj) {
+          S res[V];
+#pragma unroll
+          for (int x = 0; x < V; ++x)
+            res[x] = cvt<S>(hout(at(r, x), cvt<C>(w.cf[o][x]), flx[x], x > 0 ? flx[x - 1] : flxl, fly[o + 1][x], fly[o][x]));
+          S* q2 = out + (lx + roff[r] + c0);
+          if (vout_full) {
+            *reinterpret_cast<VT*>(q2) = vjoin<S, V>(res);
+          } else {
+#pragma unroll
+            for (int x = 0; x < V; ++x)
+              if (c0 + x < ni) q2[x] = res[x];
+          }
+        }
+      }
+      if (k + b + NB < k1) load(win[b], lx + (Off)NB * ksk);
+    }
+  }
+}
+
+template <class P, int U>
+cudaError_t run_vec(const oec_schedule& s, const Dom& d, const typename P::S* in, const typename P::S* coeff,
+                    typename P::S* out, cudaStream_t st) {
+  constexpr int W = 32 * Vec16<typename P::S>::V;
+  const int kc = (s.k_chunk <= 0 || s.k_chunk > d.nk) ? d.nk : s.k_chunk;
+  dim3 g(ceil_div(d.ni, W), ceil_div(d.nj, 4 * U), ceil_div(d.nk, kc));
+  if (offsets_fit_int32(d))
+    hdiff_vec_kernel<P, U, int, 2><<<g, 128, 0, st>>>(in, coeff, out, d.ni, d.nj, d.nk, d.sj, d.sk, kc);
+  else
+    hdiff_vec_kernel<P, U, int64_t, 2><<<g, 128, 0, st>>>(in, coeff, out, d.ni, d.nj, d.nk, d.sj, d.sk, kc);
+  launched(st);
+  return cudaGetLastError();
+}
+
+// ---- k-streaming hdiff (OEC_STAGE_STREAM) ----------------------------------
+// A CTA owns a TI x TJ tile and walks a chunk of levels. The raw window of
+// level k+D-1 ((TI+4) x (TJ+4) values) and its coeff tile are copied
+// asynchronously into a D-slot shared-memory ring while level k is computed,
+// so each SM keeps D-1 levels of loads in flight: a bandwidth-bound kernel
+// needs bytes in flight, not more threads. Per level: a barrier that makes
+// level k's copies visible and frees level k-1's slot for the next copy; the
+// Laplacian plane of the tile plus one ring, once per point; a barrier; then
+// every point forms its four limited fluxes from that plane and its window
+// values, and the divergence (overlapped tiling, paper §VII-D).
+template <class P, int TI, int TJ>
+struct StreamDepth {
+  static constexpr int v = sizeof(typename P::S) == 4 ? 4 : 3;   // ring slots (<= 48 KB static)
+};
+
+template <class P, int TI, int TJ>
+__global__ void __launch_bounds__(TI * TJ)
+hdiff_stream_kernel(const typename P::S* __restrict__ in, const typename P::S* __restrict__ coeff,
+                    typename P::S* __restrict__ out, int ni, int nj, int nk, int64_t sj, int64_t sk, int kchunk) {
+  typedef typename P::S S;
+  typedef typename P::C C;
+  constexpr int D = StreamDepth<P, TI, TJ>::v;
+  constexpr int NT = TI * TJ, WI = TI + 4, WJ = TJ + 4, NW = WI * WJ, QW = (NW + NT - 1) / NT;
+  constexpr int LI = TI + 2, LJ = TJ + 2, NL = LI * LJ, QL = (NL + NT - 1) / NT;
+  constexpr int SLOT = NW + NT;   // one level: window, then the coeff tile
+  __shared__ __align__(16) S s_ring[D * SLOT];
+  __shared__ C s_lap[NL];
+  const int tid = threadIdx.x, tx = tid % TI, ty = tid / TI;
+  const int i0 = blockIdx.x * TI, j0 = blockIdx.y * TJ;
+  const int k0 = blockIdx.z * kchunk, k1 = min(nk, k0 + kchunk);
+  const int vi = min(TI, ni - i0), vj = min(TJ, nj - j0);   // valid part of a ragged tile
+  const bool own = tx < vi && ty < vj;
+  // every offset this thread uses, computed once: window copies (global
+  // offset from the level's window corner, ring offset), Laplacian positions
+  // (window centre, plane slot), and its own output point
+  int64_t wg[QW];
+  int ws[QW];
+  bool wok[QW];
+#pragma unroll
+  for (int q = 0; q < QW; ++q) {
+    const int idx = tid + q * NT, r = idx / WI, c = idx - r * WI;
+    wok[q] = idx < NW && c < vi + 4 && r < vj + 4;
+    wg[q] = (int64_t)r * sj + c;
+    ws[q] = idx;
+  }
+  int lw[QL], ll[QL];
+  bool lok[QL];
+#pragma unroll
+  for (int q = 0; q < QL; ++q) {
+    const int idx = tid + q * NT, r = idx / LI, c = idx - r * LI;
+    lok[q] = idx < NL && c < vi + 2 && r < vj + 2;
+    lw[q] = (r + 1) * WI + c + 1;
+    ll[q] = idx;
+  }
+  const int ow = (ty + 2) * WI + tx + 2, ol = (ty + 1) * LI + tx + 1;
+  const S* __restrict__ wcorner = in + (int64_t)(j0 - 2) * sj + (i0 - 2);
+  const int64_t oc = (int64_t)(j0 + ty) * sj + (i0 + tx);
+  auto issue = [&](int k, S* slot) {
+    if (k < k1) {
+      const S* pin = wcorner + (int64_t)k * sk;
+#pragma unroll
+      for (int q = 0; q < QW; ++q)
+        if (wok[q]) cp_async(slot + ws[q], pin + wg[q]);
+      if (own) cp_async(slot + NW + tid, coeff + (int64_t)k * sk + oc);
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int x = 0; x < D - 1; ++x) issue(k0 + x, s_ring + x * SLOT);
+  int sl = 0;   // ring slot of level k
+  for (int k = k0; k < k1; ++k) {
+    cp_async_wait<D - 2>();   // this thread's copies of level k have landed
+    __syncthreads();          // everyone's have; everyone is done with level k-1
+    issue(k + D - 1, s_ring + (sl == 0 ? D - 1 : sl - 1) * SLOT);   // into level k-1's slot
+    const S* W = s_ring + sl * SLOT;
+#pragma unroll
+    for (int q = 0; q < QL; ++q)
+      if (lok[q]) {
+        const S* p = W + lw[q];
+        s_lap[ll[q]] = hlap(cvt<C>(p[0]), cvt<C>(p[-1]), cvt<C>(p[1]), cvt<C>(p[-WI]), cvt<C>(p[WI]));
+      }
+    __syncthreads();
+    if (own) {
+      const S* p = W + ow;
+      const C* L = s_lap + ol;
+      const C c0 = cvt<C>(p[0]), lc = L[0];
+      const C fxp = hflux(L[1], lc, cvt<C>(p[1]), c0), fxm = hflux(lc, L[-1], c0, cvt<C>(p[-1]));
+      const C fyp = hflux(L[LI], lc, cvt<C>(p[WI]), c0), fym = hflux(lc, L[-LI], c0, cvt<C>(p[-WI]));
+      out[(int64_t)k * sk + oc] = cvt<S>(hout(c0, cvt<C>(W[NW + tid]), fxp, fxm, fyp, fym));
+    }
+    sl = sl == D - 1 ? 0 : sl + 1;
+  }
+  cp_async_wait<0>();
+}
+
+template <class P, int TI, int TJ>
+cudaError_t run_stream(const oec_schedule& s, const Dom& d, const typename P::S* in, const typename P::S* coeff,
+                       typename P::S* out, cudaStream_t st) {
+  const int kc = (s.k_chunk <= 0 || s.k_chunk > d.nk) ? d.nk : s.k_chunk;
+  dim3 g(ceil_div(d.ni, TI), ceil_div(d.nj, TJ), ceil_div(d.nk, kc));
+  hdiff_stream_kernel<P, TI, TJ><<<g, TI * TJ, 0, st>>>(in, coeff, out, d.ni, d.nj, d.nk, d.sj, d.sk, kc);
+  launched(st);
+  return cudaGetLastError();
 }
 
 // ---- exact fixed-point FP64 hdiff (arith 2) --------------------------------
@@ -358,23 +688,45 @@ cudaError_t run_smem(const oec_schedule& s, const Dom& d, int64_t osj, int64_t o
   return cudaGetLastError();
 }
 
+#ifndef REGS_NB
+#define REGS_NB 2   // register windows in rotation (prefetch distance REGS_NB - 1 levels)
+#endif
 template <class P, int U>
 cudaError_t run_regs(const oec_schedule& s, const Dom& d, const typename P::S* in, const typename P::S* coeff,
                      typename P::S* out, cudaStream_t st) {
   const int kc = kchunk_of(s, d.nk);
   dim3 b(s.tile_i, s.tile_j / U);
   dim3 g(ceil_div(d.ni, s.tile_i), ceil_div(d.nj, s.tile_j), ceil_div(d.nk, kc));
-  hdiff_regs_kernel<P, U><<<g, b, 0, st>>>(in, coeff, out, d.ni, d.nj, d.nk, d.sj, d.sk, kc); launched(st);
+  if (offsets_fit_int32(d))
+    hdiff_regs_kernel<P, U, int, REGS_NB><<<g, b, 0, st>>>(in, coeff, out, d.ni, d.nj, d.nk, d.sj, d.sk, kc);
+  else
+    hdiff_regs_kernel<P, U, int64_t, REGS_NB><<<g, b, 0, st>>>(in, coeff, out, d.ni, d.nj, d.nk, d.sj, d.sk, kc);
+  launched(st);
   return cudaGetLastError();
 }
 
 #define OEC_SMEM_TILES(X) X(32, 4) X(32, 8) X(64, 2) X(64, 4) X(64, 8) X(128, 2) X(128, 4)
+#define OEC_STREAM_TILES(X) X(32, 4) X(32, 8) X(64, 4) X(64, 8) X(128, 2) X(128, 4)
 
 template <class P>
 cudaError_t dispatch(const oec_schedule& s, const Dom& d, const typename P::S* in, const typename P::S* coeff,
                      typename P::S* out, void* scratch, cudaStream_t st) {
   typedef typename P::S S;
   if (s.fusion == OEC_FUSE_NONE) return run_unfused<P>(d, in, coeff, out, (char*)scratch, st);
+  if (s.staging == OEC_STAGE_WARP) {
+    switch (s.unroll) {
+      case 1: return run_vec<P, 1>(s, d, in, coeff, out, st);
+      case 2: return run_vec<P, 2>(s, d, in, coeff, out, st);
+      case 4: return run_vec<P, 4>(s, d, in, coeff, out, st);
+    }
+    return cudaErrorInvalidValue;
+  }
+  if (s.staging == OEC_STAGE_STREAM) {
+#define X(a, b) if (s.tile_i == a && s.tile_j == b) return run_stream<P, a, b>(s, d, in, coeff, out, st);
+    OEC_STREAM_TILES(X)
+#undef X
+    return cudaErrorInvalidValue;
+  }
   if (s.staging == OEC_STAGE_SMEM) {
 #define X(a, b) if (s.tile_i == a && s.tile_j == b) return run_smem<P, S, a, b>(s, d, d.sj, d.sk, in, coeff, out, st);
     OEC_SMEM_TILES(X)
@@ -400,6 +752,17 @@ bool hdiff_schedule_ok(const oec_schedule& s, std::string& why) {
   if (s.fusion == OEC_FUSE_NONE) return true;
   if (s.fusion != OEC_FUSE_INLINE) { why = "fusion must be OEC_FUSE_INLINE or OEC_FUSE_NONE"; return false; }
   if (s.k_chunk < 0) { why = "k_chunk must be >= 0"; return false; }
+  if (s.staging == OEC_STAGE_WARP) {
+    if (s.unroll != 1 && s.unroll != 2 && s.unroll != 4) { why = "WARP staging: unroll (rows per warp) 1, 2 or 4"; return false; }
+    return true;
+  }
+  if (s.staging == OEC_STAGE_STREAM) {
+#define X(a, b) if (s.tile_i == a && s.tile_j == b && s.unroll == 1) return true;
+    OEC_STREAM_TILES(X)
+#undef X
+    why = "STREAM staging supports tiles 32x4, 32x8, 64x4, 64x8, 128x2, 128x4 with unroll 1";
+    return false;
+  }
   if (s.staging == OEC_STAGE_SMEM) {
 #define X(a, b) if (s.tile_i == a && s.tile_j == b && s.unroll == 1) return true;
     OEC_SMEM_TILES(X)

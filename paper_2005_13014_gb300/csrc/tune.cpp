@@ -42,6 +42,10 @@ std::vector<oec_schedule> candidates(const oec_program* p) {
           for (int tj : {4, 8})
             for (int u : {1, 2, 4})
               for (int kc : {1, 4}) c.push_back(mk(OEC_FUSE_INLINE, OEC_STAGE_REGS, ti, tj, u, kc, a));
+        for (auto t : {std::pair<int, int>{32, 4}, {32, 8}, {64, 4}, {64, 8}, {128, 2}, {128, 4}})
+          for (int kc : {8, 16, 40}) c.push_back(mk(OEC_FUSE_INLINE, OEC_STAGE_STREAM, t.first, t.second, 1, kc, a));
+        for (int u : {1, 2, 4})
+          for (int kc : {4, 8, 16}) c.push_back(mk(OEC_FUSE_INLINE, OEC_STAGE_WARP, 32, 4 * u, u, kc, a));
       }
       break;
     case OEC_KIND_HDIFF_VADVC:

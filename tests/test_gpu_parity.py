@@ -40,7 +40,13 @@ HDIFF_SCHEDS = (
        for (a, b) in [(32, 4), (32, 8), (64, 2), (64, 4), (64, 8), (128, 2), (128, 4)] for kc in (0, 3)]
     + [dict(fusion=0, staging=0, tile_i=a, tile_j=b, unroll=u, k_chunk=kc)
        for (a, b, u) in [(32, 4, 1), (64, 4, 2), (32, 8, 4), (128, 4, 4), (64, 1, 1)] for kc in (0, 2)]
+    + [dict(fusion=0, staging=2, tile_i=a, tile_j=b, k_chunk=kc)
+       for (a, b) in [(32, 4), (32, 8), (64, 4), (64, 8), (128, 2), (128, 4)] for kc in (0, 3)]
 )
+
+# vectorised warp rows: need 16-byte aligned rows
+WARP_SCHEDS = [dict(fusion=0, staging=3, tile_i=32, tile_j=4 * u, unroll=u, k_chunk=kc) for u in (1, 2, 4)
+               for kc in (0, 3)]
 
 
 def _hdiff_case(n, h, dtype, sched, align=0, lb=None, ub=None, poison=True):
@@ -91,6 +97,21 @@ def _with(sched, arith):
 @pytest.mark.parametrize("dtype,arith", PRECISIONS)
 def test_hdiff_ragged(sched, dtype, arith):
     assert _hdiff_case((37, 29, 5), 2, dtype, _with(sched, arith)) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("n", [(37, 29, 5), (130, 9, 3), (257, 6, 2), (3, 40, 2)], ids=str)
+@pytest.mark.parametrize("sched", WARP_SCHEDS, ids=str)
+@pytest.mark.parametrize("dtype,arith", PRECISIONS)
+def test_hdiff_vector_rows(sched, dtype, arith, n):
+    """Ragged warps (partial vectors at the end of the input range and of the
+    domain), edge lanes inside and outside the range, poisoned halos."""
+    assert _hdiff_case(n, 2, dtype, _with(sched, arith), align=16) <= TOL[dtype]
+
+
+def test_hdiff_vector_rows_need_alignment():
+    from paper_2005_13014_gb300._lib import OecError
+    with pytest.raises(OecError, match="16-byte aligned"):
+        _hdiff_case((37, 29, 5), 3, "f32", WARP_SCHEDS[0], align=0)
 
 
 @pytest.mark.parametrize("sched", [dict(fusion=1), dict(fusion=0, staging=1, tile_i=64, tile_j=4, k_chunk=2),
