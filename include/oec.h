@@ -88,11 +88,17 @@ typedef enum {
   OEC_STAGE_STREAM = 2,  /* horizontal diffusion: overlapped tile walked up k, the next
                             levels' windows copied asynchronously into a shared-memory
                             ring while the current level is computed                   */
-  OEC_STAGE_WARP = 3     /* horizontal diffusion: a warp owns `unroll` (1, 2, 4) rows of
+  OEC_STAGE_WARP = 3,    /* horizontal diffusion: a warp owns `unroll` (1, 2, 4) rows of
                             32 x 16-byte vectors of columns; neighbours across vectors by
                             warp shuffles; the next level loaded ahead. Needs 16-byte
                             aligned rows (base at the domain corner and j/k strides),
                             else OEC_ERR_UNSUPPORTED; tile_i/tile_j unused             */
+  OEC_STAGE_TMA = 4      /* horizontal diffusion: as OEC_STAGE_WARP, computed by a
+                            persistent grid whose CTAs stream (tile, level) units; the
+                            windows of the next 4 units are copied by the tensor memory
+                            accelerator (cp.async.bulk.tensor) into a shared-memory ring.
+                            Same alignment needs, and 16-byte aligned storage; k_chunk
+                            unused                                                     */
 } oec_staging;
 
 typedef struct oec_schedule {
@@ -310,6 +316,14 @@ OEC_API int oec_program_algorithmic_bytes(oec_program_t p, const int64_t lb[3], 
  * n_applies * n_kernels entries in cap - nothing is forgotten then -, or
  * recorded applies with different kernel counts), OEC_ERR_CUDA.
  */
+/*
+ * Status of the library's bounded device-side waits (the TMA-staged kernels
+ * wait on mbarriers for their own copies, for about a second at most).
+ * Synchronises cuda_stream, then returns OEC_ERR_TIMEOUT if any wait gave up
+ * since the previous call (the affected outputs are incomplete), OEC_OK
+ * otherwise, and clears the record. Errors: OEC_ERR_CUDA.
+ */
+OEC_API int oec_device_status(void* cuda_stream);
 OEC_API int oec_program_launch_count(oec_program_t p);
 OEC_API int oec_program_set_timing(oec_program_t p, int enable);
 OEC_API int oec_program_kernel_times(oec_program_t p, float* ms, int cap, int* n_applies, int* n_kernels);

@@ -376,6 +376,15 @@ int oec_program_apply(oec_program_t p, const oec_field_desc* in, int n_in, const
   return rc;
 }
 
+int oec_device_status(void* cuda_stream) {
+  clear_error();
+  unsigned n = 0;
+  const int e = device_wait_timeouts((cudaStream_t)cuda_stream, &n);
+  if (e) return cuda_fail((cudaError_t)e, "oec_device_status");
+  if (n) return fail(OEC_ERR_TIMEOUT, "%u bounded device waits gave up", n);
+  return OEC_OK;
+}
+
 int oec_program_set_timing(oec_program_t p, int enable) {
   clear_error();
   if (!p) return fail(OEC_ERR_INVALID_ARG, "null program");

@@ -37,16 +37,32 @@ int dispatch_apply(oec_program* p, const oec_field_desc* in, const oec_field_des
   cudaError_t e = cudaSuccess;
   int rc = OEC_OK;
   switch (p->kind) {
-    case OEC_KIND_HDIFF:
-      if (p->sched.fusion == OEC_FUSE_INLINE && p->sched.staging == OEC_STAGE_WARP &&
-          (((uintptr_t)I[0] | (uintptr_t)I[1] | (uintptr_t)O[0]) % 16 != 0 || (sj * (int64_t)es) % 16 != 0 ||
-           (sk * (int64_t)es) % 16 != 0))
+    case OEC_KIND_HDIFF: {
+      const bool vec = p->sched.fusion == OEC_FUSE_INLINE &&
+                       (p->sched.staging == OEC_STAGE_WARP || p->sched.staging == OEC_STAGE_TMA);
+      if (vec && ((((uintptr_t)I[0] | (uintptr_t)I[1] | (uintptr_t)O[0]) % 16 != 0) || (sj * (int64_t)es) % 16 != 0 ||
+                  (sk * (int64_t)es) % 16 != 0))
         return fail(OEC_ERR_UNSUPPORTED,
-                    "OEC_STAGE_WARP needs 16-byte aligned rows: domain corner of every field and j/k strides");
+                    "OEC_STAGE_WARP/TMA need 16-byte aligned rows: domain corner of every field and j/k strides");
+      if (vec && p->sched.staging == OEC_STAGE_TMA) {
+        TmaField t[2];
+        for (int x = 0; x < 2; ++x) {
+          if ((uintptr_t)in[x].data % 16 != 0) return fail(OEC_ERR_UNSUPPORTED, "TMA staging: storage not 16-byte aligned");
+          t[x].base = in[x].data;
+          for (int a = 0; a < 3; ++a) {
+            t[x].size[a] = in[x].size[a];
+            t[x].corner[a] = in[x].origin[a] + lb[a];
+          }
+        }
+        e = hdiff_tma_launch(p->sched, p->dtype, d, t[0], t[1], O[0], st);
+        if (e == cudaErrorNotSupported) return fail(OEC_ERR_UNSUPPORTED, "TMA staging: tensor maps unavailable");
+        break;
+      }
       rc = ensure_scratch(p, hdiff_scratch_bytes(p->sched, p->dtype, d));
       if (rc) return rc;
       e = hdiff_launch(p->sched, p->dtype, d, I[0], I[1], O[0], p->scratch, st);
       break;
+    }
     case OEC_KIND_HDIFF_VADVC:
       rc = ensure_scratch(p, hdiff_vadvc_scratch_bytes(p->sched, p->dtype, d));
       if (rc) return rc;

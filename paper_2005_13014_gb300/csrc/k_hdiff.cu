@@ -168,180 +168,6 @@ __global__ void hdiff_regs_kernel(const typename P::S* __restrict__ in, const ty
   }
 }
 
-// true when every element offset a kernel forms from the domain's base
-// pointers (halo 2 around the domain) fits in a 32-bit int
-bool offsets_fit_int32(const Dom& d) {
-  const int64_t hi = (int64_t)(d.nk + 1) * d.sk + (int64_t)(d.nj + 2) * d.sj + d.ni + 2;
-  const int64_t lo = -(2 * d.sj + 2);
-  return hi < INT32_MAX && lo > INT32_MIN;
-}
-
-// ---- vectorised warp-row hdiff (OEC_STAGE_WARP) ------------------------------
-// A warp owns U rows of W = 32 V consecutive columns, V = 16 bytes / element
-// (4 floats or 2 doubles): lane l loads columns i0 + V l .. + V-1 of each row
-// as one 16-byte vector and computes those V points. Each Laplacian and each
-// flux is evaluated once per column; the values across a vector boundary
-// come from the adjacent lane by warp shuffles, and lane 0 / lane 31 load the
-// two columns outside the warp (i0-1, i0-2 / i0+W, i0+W+1) and evaluate the
-// Laplacian there. j-neighbours are the lane's other rows. The level loop
-// keeps NB register windows in rotation (the next levels' loads in flight
-// while this one is computed). Needs 16-byte aligned rows (checked by the
-// caller); a vector that would cross the input range's end is read element
-// by element.
-template <class S> struct Vec16;
-template <> struct Vec16<float> { typedef float4 T; static constexpr int V = 4; };
-template <> struct Vec16<double> { typedef double2 T; static constexpr int V = 2; };
-template <class S, int V> __device__ __forceinline__ void vsplit(const typename Vec16<S>::T& t, S (&d)[V]);
-template <> __device__ __forceinline__ void vsplit<float, 4>(const float4& t, float (&d)[4]) {
-  d[0] = t.x; d[1] = t.y; d[2] = t.z; d[3] = t.w;
-}
-template <> __device__ __forceinline__ void vsplit<double, 2>(const double2& t, double (&d)[2]) {
-  d[0] = t.x; d[1] = t.y;
-}
-template <class S, int V> __device__ __forceinline__ typename Vec16<S>::T vjoin(const S (&d)[V]);
-template <> __device__ __forceinline__ float4 vjoin<float, 4>(const float (&d)[4]) { return make_float4(d[0], d[1], d[2], d[3]); }
-template <> __device__ __forceinline__ double2 vjoin<double, 2>(const double (&d)[2]) { return make_double2(d[0], d[1]); }
-
-template <class S, int U, int V>
-struct VecWin {
-  S v[U + 4][V];   // rows jb-2 .. jb+U+1, this lane's columns
-  S ea[U + 2];     // lane 0: column i0-1, lane 31: column i0+W; rows jb-1 .. jb+U
-  S eb[U];         // lane 0: column i0-2, lane 31: column i0+W+1; rows jb .. jb+U-1
-  S cf[U][V];      // coeff, rows jb .. jb+U-1
-};
-
-template <class P, int U, class Off, int NB>
-__global__ void __launch_bounds__(128)
-hdiff_vec_kernel(const typename P::S* __restrict__ in, const typename P::S* __restrict__ coeff,
-                 typename P::S* __restrict__ out, int ni, int nj, int nk, int64_t sj, int64_t sk, int kchunk) {
-  typedef typename P::S S;
-  typedef typename P::C C;
-  typedef typename Vec16<S>::T VT;
-  constexpr int V = Vec16<S>::V, W = 32 * V;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int i0 = blockIdx.x * W, c0 = i0 + V * lane;
-  const int jb = (blockIdx.y * 4 + wid) * U;
-  if (jb >= nj) return;                                  // whole warp
-  const int jmax = nj + 1 - jb;                          // last row offset inside the halo-2 window
-  const int k0 = blockIdx.z * kchunk, k1 = min(nk, k0 + kchunk);
-  const bool vin_full = c0 + V - 1 <= ni + 1;            // whole vector inside the input range [-2, ni+2)
-  const bool vout_full = c0 + V - 1 < ni;                // whole vector inside the domain
-  const bool edge = lane == 0 || lane == 31;
-  const int ca = lane == 0 ? i0 - 1 : i0 + W, cb = lane == 0 ? i0 - 2 : i0 + W + 1;
-  const bool ea_ok = edge && ca <= ni + 1, eb_ok = edge && cb <= ni + 1;
-  Off roff[U + 4];
-#pragma unroll
-  for (int x = 0; x < U + 4; ++x) roff[x] = (Off)min(x - 2, jmax) * (Off)sj;
-  const Off ksk = (Off)sk;
-  Off lev = (Off)k0 * ksk + (Off)jb * (Off)sj;
-  auto load = [&](VecWin<S, U, V>& w, Off l) {
-#pragma unroll
-    for (int r = 0; r < U + 4; ++r) {
-      const S* q = in + (l + roff[r] + c0);
-      if (vin_full) {
-        vsplit<S, V>(__ldg(reinterpret_cast<const VT*>(q)), w.v[r]);
-      } else {
-#pragma unroll
-        for (int x = 0; x < V; ++x) w.v[r][x] = c0 + x <= ni + 1 ? ldg(q + x) : S(0);
-      }
-    }
-#pragma unroll
-    for (int r = 0; r < U + 2; ++r) w.ea[r] = ea_ok ? ldg(in + (l + roff[r + 1] + ca)) : S(0);
-#pragma unroll
-    for (int r = 0; r < U; ++r) {
-      w.eb[r] = eb_ok ? ldg(in + (l + roff[r + 2] + cb)) : S(0);
-      if (jb + r < nj) {
-        const S* q = coeff + (l + roff[r + 2] + c0);
-        if (vout_full) {
-          vsplit<S, V>(__ldg(reinterpret_cast<const VT*>(q)), w.cf[r]);
-        } else {
-#pragma unroll
-          for (int x = 0; x < V; ++x) w.cf[r][x] = c0 + x < ni ? ldg(q + x) : S(0);
-        }
-      }
-    }
-  };
-  VecWin<S, U, V> win[NB];
-#pragma unroll
-  for (int x = 0; x < NB; ++x)
-    if (k0 + x < k1) load(win[x], lev + (Off)x * ksk);
-  for (int k = k0; k < k1; k += NB, lev += (Off)NB * ksk) {
-#pragma unroll
-    for (int b = 0; b < NB; ++b) {
-      if (k + b >= k1) break;
-      const VecWin<S, U, V>& w = win[b];
-      const Off lx = lev + (Off)b * ksk;
-      auto at = [&](int r, int x) { return cvt<C>(w.v[r][x]); };
-      // Laplacians of rows jb-1 .. jb+U (index q = row - jb + 1) at this lane's
-      // columns; the input value right of this lane's last column
-      C lap[U + 2][V], inr[U + 2];
-#pragma unroll
-      for (int q = 0; q < U + 2; ++q) {
-        const int r = q + 1;
-        C left = shfl_up_(at(r, V - 1), 1), right = shfl_down_(at(r, 0), 1);
-        if (lane == 0) left = cvt<C>(w.ea[q]);
-        if (lane == 31) right = cvt<C>(w.ea[q]);
-        inr[q] = right;
-#pragma unroll
-        for (int x = 0; x < V; ++x)
-          lap[q][x] = hlap(at(r, x), x > 0 ? at(r, x - 1) : left, x < V - 1 ? at(r, x + 1) : right, at(r - 1, x),
-                           at(r + 1, x));
-      }
-      // fly between rows jb-1+q and jb+q
-      C fly[U + 1][V];
-#pragma unroll
-      for (int q = 0; q < U + 1; ++q)
-#pragma unroll
-        for (int x = 0; x < V; ++x) fly[q][x] = hflux(lap[q + 1][x], lap[q][x], at(q + 2, x), at(q + 1, x));
-#pragma unroll
-      for (int o = 0; o < U; ++o) {
-        const int q = o + 1, r = o + 2;
-        // the Laplacian just outside the warp (lanes 0 and 31 only)
-        const C le = lane == 0 ? hlap(cvt<C>(w.ea[q]), cvt<C>(w.eb[o]), at(r, 0), cvt<C>(w.ea[q - 1]), cvt<C>(w.ea[q + 1]))
-                               : hlap(cvt<C>(w.ea[q]), at(r, V - 1), cvt<C>(w.eb[o]), cvt<C>(w.ea[q - 1]), cvt<C>(w.ea[q + 1]));
-        C lapr = shfl_down_(lap[q][0], 1);
-        if (lane == 31) lapr = le;
-        C flx[V];
-#pragma unroll
-        for (int x = 0; x < V; ++x)
-          flx[x] = x < V - 1 ? hflux(lap[q][x + 1], lap[q][x], at(r, x + 1), at(r, x))
-                             : hflux(lapr, lap[q][x], inr[q], at(r, x));
-        C flxl = shfl_up_(flx[V - 1], 1);
-        if (lane == 0) flxl = hflux(lap[q][0], le, at(r, 0), cvt<C>(w.ea[q]));
-        if (jb + o < nj) {
-          S res[V];
-#pragma unroll
-          for (int x = 0; x < V; ++x)
-            res[x] = cvt<S>(hout(at(r, x), cvt<C>(w.cf[o][x]), flx[x], x > 0 ? flx[x - 1] : flxl, fly[o + 1][x], fly[o][x]));
-          S* q2 = out + (lx + roff[r] + c0);
-          if (vout_full) {
-            *reinterpret_cast<VT*>(q2) = vjoin<S, V>(res);
-          } else {
-#pragma unroll
-            for (int x = 0; x < V; ++x)
-              if (c0 + x < ni) q2[x] = res[x];
-          }
-        }
-      }
-      if (k + b + NB < k1) load(win[b], lx + (Off)NB * ksk);
-    }
-  }
-}
-
-template <class P, int U>
-cudaError_t run_vec(const oec_schedule& s, const Dom& d, const typename P::S* in, const typename P::S* coeff,
-                    typename P::S* out, cudaStream_t st) {
-  constexpr int W = 32 * Vec16<typename P::S>::V;
-  const int kc = (s.k_chunk <= 0 || s.k_chunk > d.nk) ? d.nk : s.k_chunk;
-  dim3 g(ceil_div(d.ni, W), ceil_div(d.nj, 4 * U), ceil_div(d.nk, kc));
-  if (offsets_fit_int32(d))
-    hdiff_vec_kernel<P, U, int, 2><<<g, 128, 0, st>>>(in, coeff, out, d.ni, d.nj, d.nk, d.sj, d.sk, kc);
-  else
-    hdiff_vec_kernel<P, U, int64_t, 2><<<g, 128, 0, st>>>(in, coeff, out, d.ni, d.nj, d.nk, d.sj, d.sk, kc);
-  launched(st);
-  return cudaGetLastError();
-}
-
 // ---- k-streaming hdiff (OEC_STAGE_STREAM) ----------------------------------
 // A CTA owns a TI x TJ tile and walks a chunk of levels. The raw window of
 // level k+D-1 ((TI+4) x (TJ+4) values) and its coeff tile are copied
@@ -713,14 +539,6 @@ cudaError_t dispatch(const oec_schedule& s, const Dom& d, const typename P::S* i
                      typename P::S* out, void* scratch, cudaStream_t st) {
   typedef typename P::S S;
   if (s.fusion == OEC_FUSE_NONE) return run_unfused<P>(d, in, coeff, out, (char*)scratch, st);
-  if (s.staging == OEC_STAGE_WARP) {
-    switch (s.unroll) {
-      case 1: return run_vec<P, 1>(s, d, in, coeff, out, st);
-      case 2: return run_vec<P, 2>(s, d, in, coeff, out, st);
-      case 4: return run_vec<P, 4>(s, d, in, coeff, out, st);
-    }
-    return cudaErrorInvalidValue;
-  }
   if (s.staging == OEC_STAGE_STREAM) {
 #define X(a, b) if (s.tile_i == a && s.tile_j == b) return run_stream<P, a, b>(s, d, in, coeff, out, st);
     OEC_STREAM_TILES(X)
@@ -752,8 +570,8 @@ bool hdiff_schedule_ok(const oec_schedule& s, std::string& why) {
   if (s.fusion == OEC_FUSE_NONE) return true;
   if (s.fusion != OEC_FUSE_INLINE) { why = "fusion must be OEC_FUSE_INLINE or OEC_FUSE_NONE"; return false; }
   if (s.k_chunk < 0) { why = "k_chunk must be >= 0"; return false; }
-  if (s.staging == OEC_STAGE_WARP) {
-    if (s.unroll != 1 && s.unroll != 2 && s.unroll != 4) { why = "WARP staging: unroll (rows per warp) 1, 2 or 4"; return false; }
+  if (s.staging == OEC_STAGE_WARP || s.staging == OEC_STAGE_TMA) {
+    if (s.unroll != 1 && s.unroll != 2 && s.unroll != 4) { why = "WARP/TMA staging: unroll (rows per warp) 1, 2 or 4"; return false; }
     return true;
   }
   if (s.staging == OEC_STAGE_STREAM) {
@@ -786,6 +604,7 @@ size_t hdiff_scratch_bytes(const oec_schedule& s, int dtype, const Dom& d) {
 
 cudaError_t hdiff_launch(const oec_schedule& s, int dtype, const Dom& d, const void* in, const void* coeff, void* out,
                          void* scratch, cudaStream_t st) {
+  if (s.fusion == OEC_FUSE_INLINE && s.staging == OEC_STAGE_WARP) return hdiff_warp_launch(s, dtype, d, in, coeff, out, st);
   if (dtype == OEC_F64 && s.arith == 2) {
 #define X(a, b)                                                                                               \
   if (s.tile_i == a && s.tile_j == b)                                                                         \

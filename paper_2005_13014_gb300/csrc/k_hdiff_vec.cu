@@ -1,0 +1,435 @@
+// k_hdiff_vec.cu - horizontal diffusion on vectorised warp rows, for fields
+// whose rows are 16-byte aligned: OEC_STAGE_WARP (each warp loads its rows
+// with 16-byte vector loads, the next levels held in registers) and
+// OEC_STAGE_TMA (a CTA's window of every level copied by the tensor memory
+// accelerator into a shared-memory ring, one cp.async.bulk.tensor per level,
+// completion tracked on an mbarrier). Both evaluate the same per-warp row
+// arithmetic (vec_rows): lap -> limited fluxes -> out, paper Table II hdiffsa,
+// each Laplacian and flux once per column (stencil inlining, §V-A).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "arith.cuh"
+#include "kcommon.cuh"
+#include "kernels.h"
+
+namespace oec {
+namespace {
+
+// bounded-wait give-ups (see device_wait_timeouts)
+__device__ unsigned g_wait_timeouts;
+
+template <class S> struct Vec16;
+template <> struct Vec16<float> { typedef float4 T; static constexpr int V = 4; };
+template <> struct Vec16<double> { typedef double2 T; static constexpr int V = 2; };
+template <class S, int V> __device__ __forceinline__ void vsplit(const typename Vec16<S>::T& t, S (&d)[V]);
+template <> __device__ __forceinline__ void vsplit<float, 4>(const float4& t, float (&d)[4]) {
+  d[0] = t.x; d[1] = t.y; d[2] = t.z; d[3] = t.w;
+}
+template <> __device__ __forceinline__ void vsplit<double, 2>(const double2& t, double (&d)[2]) {
+  d[0] = t.x; d[1] = t.y;
+}
+template <class S, int V> __device__ __forceinline__ typename Vec16<S>::T vjoin(const S (&d)[V]);
+template <> __device__ __forceinline__ float4 vjoin<float, 4>(const float (&d)[4]) {
+  return make_float4(d[0], d[1], d[2], d[3]);
+}
+template <> __device__ __forceinline__ double2 vjoin<double, 2>(const double (&d)[2]) { return make_double2(d[0], d[1]); }
+
+// The values one warp row-strip of one level needs: U output rows of W = 32 V
+// columns (lane l: columns c0 = i0 + V l .. c0 + V - 1).
+template <class S, int U, int V>
+struct VecWin {
+  S v[U + 4][V];   // rows jb-2 .. jb+U+1, this lane's columns
+  S ea[U + 2];     // lane 0: column i0-1, lane 31: column i0+W; rows jb-1 .. jb+U
+  S eb[U];         // lane 0: column i0-2, lane 31: column i0+W+1; rows jb .. jb+U-1
+  S cf[U][V];      // coeff, rows jb .. jb+U-1
+};
+
+// The arithmetic of one warp row-strip: Laplacians of rows jb-1 .. jb+U at
+// the lane's columns (neighbours across the vector boundary from the adjacent
+// lanes; lanes 0 and 31 use their outer columns and evaluate the Laplacian
+// outside the warp), fluxes once per column, outputs written to q0 + o sj
+// (row jb+o) where the point lies in the domain.
+template <class P, int U>
+__device__ __forceinline__ void vec_rows(const VecWin<typename P::S, U, Vec16<typename P::S>::V>& w, int lane, int c0,
+                                         int jb, int ni, int nj, typename P::S* q0, int64_t sj) {
+  typedef typename P::S S;
+  typedef typename P::C C;
+  typedef typename Vec16<S>::T VT;
+  constexpr int V = Vec16<S>::V;
+  auto at = [&](int r, int x) { return cvt<C>(w.v[r][x]); };
+  C lap[U + 2][V], inr[U + 2];
+#pragma unroll
+  for (int q = 0; q < U + 2; ++q) {
+    const int r = q + 1;
+    C left = shfl_up_(at(r, V - 1), 1), right = shfl_down_(at(r, 0), 1);
+    if (lane == 0) left = cvt<C>(w.ea[q]);
+    if (lane == 31) right = cvt<C>(w.ea[q]);
+    inr[q] = right;
+#pragma unroll
+    for (int x = 0; x < V; ++x)
+      lap[q][x] = hlap(at(r, x), x > 0 ? at(r, x - 1) : left, x < V - 1 ? at(r, x + 1) : right, at(r - 1, x),
+                       at(r + 1, x));
+  }
+  C fly[U + 1][V];   // between rows jb-1+q and jb+q
+#pragma unroll
+  for (int q = 0; q < U + 1; ++q)
+#pragma unroll
+    for (int x = 0; x < V; ++x) fly[q][x] = hflux(lap[q + 1][x], lap[q][x], at(q + 2, x), at(q + 1, x));
+  const bool vout_full = c0 + V - 1 < ni;
+#pragma unroll
+  for (int o = 0; o < U; ++o) {
+    const int q = o + 1, r = o + 2;
+    const C le = lane == 0 ? hlap(cvt<C>(w.ea[q]), cvt<C>(w.eb[o]), at(r, 0), cvt<C>(w.ea[q - 1]), cvt<C>(w.ea[q + 1]))
+                           : hlap(cvt<C>(w.ea[q]), at(r, V - 1), cvt<C>(w.eb[o]), cvt<C>(w.ea[q - 1]), cvt<C>(w.ea[q + 1]));
+    C lapr = shfl_down_(lap[q][0], 1);
+    if (lane == 31) lapr = le;
+    C flx[V];
+#pragma unroll
+    for (int x = 0; x < V; ++x)
+      flx[x] = x < V - 1 ? hflux(lap[q][x + 1], lap[q][x], at(r, x + 1), at(r, x))
+                         : hflux(lapr, lap[q][x], inr[q], at(r, x));
+    C flxl = shfl_up_(flx[V - 1], 1);
+    if (lane == 0) flxl = hflux(lap[q][0], le, at(r, 0), cvt<C>(w.ea[q]));
+    if (jb + o < nj) {
+      S res[V];
+#pragma unroll
+      for (int x = 0; x < V; ++x)
+        res[x] = cvt<S>(hout(at(r, x), cvt<C>(w.cf[o][x]), flx[x], x > 0 ? flx[x - 1] : flxl, fly[o + 1][x], fly[o][x]));
+      S* q2 = q0 + (int64_t)o * sj;
+      if (vout_full) {
+        *reinterpret_cast<VT*>(q2) = vjoin<S, V>(res);
+      } else {
+#pragma unroll
+        for (int x = 0; x < V; ++x)
+          if (c0 + x < ni) q2[x] = res[x];
+      }
+    }
+  }
+}
+
+// ---- OEC_STAGE_WARP: vector loads from global memory ------------------------
+// The level loop keeps NB register windows in rotation (unrolled by NB, no
+// copies): a window is refilled with level k+NB right after level k is
+// computed, so the loads of NB-1 levels are in flight during each level.
+template <class P, int U, class Off, int NB>
+__global__ void __launch_bounds__(128)
+hdiff_vec_kernel(const typename P::S* __restrict__ in, const typename P::S* __restrict__ coeff,
+                 typename P::S* __restrict__ out, int ni, int nj, int nk, int64_t sj, int64_t sk, int kchunk) {
+  typedef typename P::S S;
+  typedef typename Vec16<S>::T VT;
+  constexpr int V = Vec16<S>::V, W = 32 * V;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int i0 = blockIdx.x * W, c0 = i0 + V * lane;
+  const int jb = (blockIdx.y * 4 + wid) * U;
+  if (jb >= nj) return;                                  // whole warp
+  const int jmax = nj + 1 - jb;                          // last row offset inside the halo-2 window
+  const int k0 = blockIdx.z * kchunk, k1 = min(nk, k0 + kchunk);
+  const bool vin_full = c0 + V - 1 <= ni + 1;            // whole vector inside the input range [-2, ni+2)
+  const bool vout_full = c0 + V - 1 < ni;                // whole vector inside the domain
+  const bool edge = lane == 0 || lane == 31;
+  const int ca = lane == 0 ? i0 - 1 : i0 + W, cb = lane == 0 ? i0 - 2 : i0 + W + 1;
+  const bool ea_ok = edge && ca <= ni + 1, eb_ok = edge && cb <= ni + 1;
+  Off roff[U + 4];
+#pragma unroll
+  for (int x = 0; x < U + 4; ++x) roff[x] = (Off)min(x - 2, jmax) * (Off)sj;
+  const Off ksk = (Off)sk;
+  Off lev = (Off)k0 * ksk + (Off)jb * (Off)sj;
+  auto load = [&](VecWin<S, U, V>& w, Off l) {
+#pragma unroll
+    for (int r = 0; r < U + 4; ++r) {
+      const S* q = in + (l + roff[r] + c0);
+      if (vin_full) {
+        vsplit<S, V>(__ldg(reinterpret_cast<const VT*>(q)), w.v[r]);
+      } else {
+#pragma unroll
+        for (int x = 0; x < V; ++x) w.v[r][x] = c0 + x <= ni + 1 ? ldg(q + x) : S(0);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < U + 2; ++r) w.ea[r] = ea_ok ? ldg(in + (l + roff[r + 1] + ca)) : S(0);
+#pragma unroll
+    for (int r = 0; r < U; ++r) {
+      w.eb[r] = eb_ok ? ldg(in + (l + roff[r + 2] + cb)) : S(0);
+      if (jb + r < nj) {
+        const S* q = coeff + (l + roff[r + 2] + c0);
+        if (vout_full) {
+          vsplit<S, V>(__ldg(reinterpret_cast<const VT*>(q)), w.cf[r]);
+        } else {
+#pragma unroll
+          for (int x = 0; x < V; ++x) w.cf[r][x] = c0 + x < ni ? ldg(q + x) : S(0);
+        }
+      }
+    }
+  };
+  VecWin<S, U, V> win[NB];
+#pragma unroll
+  for (int x = 0; x < NB; ++x)
+    if (k0 + x < k1) load(win[x], lev + (Off)x * ksk);
+  for (int k = k0; k < k1; k += NB, lev += (Off)NB * ksk) {
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      if (k + b >= k1) break;
+      const Off lx = lev + (Off)b * ksk;
+      vec_rows<P, U>(win[b], lane, c0, jb, ni, nj, out + (lx + c0), sj);
+      if (k + b + NB < k1) load(win[b], lx + (Off)NB * ksk);
+    }
+  }
+}
+
+template <class P, int U>
+cudaError_t run_vec(const oec_schedule& s, const Dom& d, const typename P::S* in, const typename P::S* coeff,
+                    typename P::S* out, cudaStream_t st) {
+  constexpr int W = 32 * Vec16<typename P::S>::V;
+  const int kc = (s.k_chunk <= 0 || s.k_chunk > d.nk) ? d.nk : s.k_chunk;
+  dim3 g(ceil_div(d.ni, W), ceil_div(d.nj, 4 * U), ceil_div(d.nk, kc));
+  if (offsets_fit_int32(d))
+    hdiff_vec_kernel<P, U, int, 2><<<g, 128, 0, st>>>(in, coeff, out, d.ni, d.nj, d.nk, d.sj, d.sk, kc);
+  else
+    hdiff_vec_kernel<P, U, int64_t, 2><<<g, 128, 0, st>>>(in, coeff, out, d.ni, d.nj, d.nk, d.sj, d.sk, kc);
+  launched(st);
+  return cudaGetLastError();
+}
+
+// ---- OEC_STAGE_TMA: tensor-memory-accelerator ring ---------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+// bounded wait for the phase with the given parity to complete; false when
+// it gave up (about a second of polling)
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+  for (int it = 0; it < (1 << 20); ++it) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+// 3-D tile load global -> shared, completion counted on bar; x must be a
+// multiple of 16 bytes / element size (the caller guarantees it)
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, unsigned bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n"
+      ::"r"(smem_u32(dst)), "l"(map), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+
+template <class S, int U>
+struct TmaGeom {
+  static constexpr int V = Vec16<S>::V, W = 32 * V, TJ = 4 * U;
+  static constexpr int BX = W + 2 * V, BY = TJ + 4;                  // window box: columns i0-V .., rows j0-2 ..
+  static constexpr int WIN = BX * BY, COE = W * TJ;                  // elements per stage
+  static constexpr int STAGE = WIN + COE;
+  static constexpr int D = 4;                                        // ring stages
+  static constexpr size_t SMEM = size_t(D) * STAGE * sizeof(S) + D * sizeof(unsigned long long);
+};
+
+// Persistent: grid = SMs x resident CTAs. The work units are (tile, level)
+// pairs, level fastest (a tile is W columns x 4U rows); CTA b streams the
+// contiguous range [b N / G, (b+1) N / G). Thread 0 keeps D units of window +
+// coeff in flight across tile boundaries: after every warp is done with unit
+// u (barrier) it refills that stage with unit u+D. Each warp copies its row
+// strip out of the stage into registers and runs vec_rows. A wait that gives
+// up counts a timeout, and the CTA stops after waiting (bounded) for the
+// copies it still has in flight.
+template <class P, int U>
+__global__ void __launch_bounds__(128)
+hdiff_tma_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tco, int cxi, int cyi,
+                 int czi, int cxc, int cyc, int czc, typename P::S* __restrict__ out, int ni, int nj, int nk,
+                 int64_t sj, int64_t sk, int ntx, long long nunits) {
+  typedef typename P::S S;
+  typedef TmaGeom<S, U> G;
+  constexpr int V = G::V, W = G::W, D = G::D;
+  extern __shared__ __align__(128) unsigned char smem[];
+  S* ring = reinterpret_cast<S*>(smem);
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem + size_t(D) * G::STAGE * sizeof(S));
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const long long u0 = (long long)blockIdx.x * nunits / gridDim.x;
+  const long long u1 = (long long)(blockIdx.x + 1) * nunits / gridDim.x;
+  auto unit = [&](long long u, int& i0, int& j0, int& k) {
+    k = (int)(u % nk);
+    const long long t = u / nk;
+    i0 = (int)(t % ntx) * W;
+    j0 = (int)(t / ntx) * G::TJ;
+  };
+  if (tid == 0) {
+    for (int x = 0; x < D; ++x) mbar_init(smem_u32(&bars[x]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  auto issue = [&](long long u) {   // thread 0 only
+    int i0, j0, k;
+    unit(u, i0, j0, k);
+    const int sl = (int)((u - u0) % D);
+    S* st_ = ring + (size_t)sl * G::STAGE;
+    const unsigned bar = smem_u32(&bars[sl]);
+    mbar_expect_tx(bar, G::STAGE * sizeof(S));
+    tma_load_3d(st_, &tin, cxi + i0 - V, cyi + j0 - 2, czi + k, bar);
+    tma_load_3d(st_ + G::WIN, &tco, cxc + i0, cyc + j0, czc + k, bar);
+  };
+  if (tid == 0)
+    for (long long u = u0; u < min(u1, u0 + D); ++u) issue(u);
+  long long issued_to = min(u1, u0 + D);   // units [u0, issued_to) have been issued (thread 0's view)
+  long long failed_at = -1;
+  for (long long u = u0; u < u1; ++u) {
+    const int sl = (int)((u - u0) % D);
+    const bool ok = mbar_wait(smem_u32(&bars[sl]), (unsigned)(((u - u0) / D) & 1));
+    if (__syncthreads_or(!ok)) {
+      failed_at = u;
+      if (tid == 0) atomicAdd(&g_wait_timeouts, 1u);
+      break;
+    }
+    int i0, j0, k;
+    unit(u, i0, j0, k);
+    const int c0 = i0 + V * lane, jb = j0 + wid * U;
+    const S* stg = ring + (size_t)sl * G::STAGE;
+    if (jb < nj) {
+      // this warp's strip: window rows wid*U .. wid*U+U+3, columns V + V lane ..
+      VecWin<S, U, V> w;
+      const S* wrow = stg + (size_t)(wid * U) * G::BX;
+#pragma unroll
+      for (int r = 0; r < U + 4; ++r)
+        vsplit<S, V>(*reinterpret_cast<const typename Vec16<S>::T*>(wrow + r * G::BX + V + V * lane), w.v[r]);
+      const int ea_col = lane == 0 ? V - 1 : V + W, eb_col = lane == 0 ? V - 2 : V + W + 1;
+#pragma unroll
+      for (int r = 0; r < U + 2; ++r) w.ea[r] = wrow[(r + 1) * G::BX + ea_col];
+#pragma unroll
+      for (int r = 0; r < U; ++r) {
+        w.eb[r] = wrow[(r + 2) * G::BX + eb_col];
+        vsplit<S, V>(*reinterpret_cast<const typename Vec16<S>::T*>(stg + G::WIN + (size_t)(wid * U + r) * W + V * lane),
+                     w.cf[r]);
+      }
+      vec_rows<P, U>(w, lane, c0, jb, ni, nj, out + ((int64_t)k * sk + (int64_t)jb * sj + c0), sj);
+    }
+    __syncthreads();   // every warp is done with this stage
+    if (tid == 0 && u + D < u1) {
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      issue(u + D);
+      issued_to = u + D + 1;
+    }
+  }
+  if (failed_at >= 0 && tid == 0) {
+    // wait (bounded) for the copies still in flight before the CTA exits
+    for (long long u = failed_at; u < issued_to; ++u)
+      mbar_wait(smem_u32(&bars[(u - u0) % D]), (unsigned)(((u - u0) / D) & 1));
+  }
+}
+
+// cuTensorMapEncodeTiled from the driver, looked up once
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  });
+  return fn;
+}
+
+template <class S>
+bool encode_map(CUtensorMap* m, const TmaField& f, int64_t sj, int64_t sk, int bx, int by) {
+  auto enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)f.size[0], (cuuint64_t)f.size[1], (cuuint64_t)f.size[2]};
+  const cuuint64_t strides[2] = {(cuuint64_t)(sj * sizeof(S)), (cuuint64_t)(sk * sizeof(S))};
+  const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  return enc(m, sizeof(S) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3,
+             const_cast<void*>(f.base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <class P, int U>
+cudaError_t run_tma(const oec_schedule& s, const Dom& d, const TmaField& fin, const TmaField& fco,
+                    typename P::S* out, cudaStream_t st) {
+  typedef typename P::S S;
+  typedef TmaGeom<S, U> G;
+  if (fin.corner[0] % G::V != 0 || fco.corner[0] % G::V != 0) return cudaErrorMisalignedAddress;
+  CUtensorMap tin, tco;
+  if (!encode_map<S>(&tin, fin, d.sj, d.sk, G::BX, G::BY) || !encode_map<S>(&tco, fco, d.sj, d.sk, G::W, G::TJ))
+    return cudaErrorNotSupported;
+  static std::once_flag attr;
+  static int per_sm = 1;
+  std::call_once(attr, [] {
+    cudaFuncSetAttribute(hdiff_tma_kernel<P, U>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, hdiff_tma_kernel<P, U>, 128, G::SMEM) == cudaSuccess && n > 0)
+      per_sm = n;
+  });
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int ntx = ceil_div(d.ni, G::W), nty = ceil_div(d.nj, G::TJ);
+  const long long nunits = (long long)ntx * nty * d.nk;
+  const long long grid = std::min<long long>(nunits, (long long)sms * per_sm);
+  hdiff_tma_kernel<P, U><<<(unsigned)grid, 128, G::SMEM, st>>>(tin, tco, (int)fin.corner[0], (int)fin.corner[1],
+                                                               (int)fin.corner[2], (int)fco.corner[0],
+                                                               (int)fco.corner[1], (int)fco.corner[2], out, d.ni,
+                                                               d.nj, d.nk, d.sj, d.sk, ntx, nunits);
+  launched(st);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t hdiff_warp_launch(const oec_schedule& s, int dtype, const Dom& d, const void* in, const void* coeff,
+                              void* out, cudaStream_t st) {
+#define OEC_VEC_U(P, T)                                                                       \
+  switch (s.unroll) {                                                                         \
+    case 1: return run_vec<P, 1>(s, d, (const T*)in, (const T*)coeff, (T*)out, st);          \
+    case 2: return run_vec<P, 2>(s, d, (const T*)in, (const T*)coeff, (T*)out, st);          \
+    case 4: return run_vec<P, 4>(s, d, (const T*)in, (const T*)coeff, (T*)out, st);          \
+  }                                                                                           \
+  return cudaErrorInvalidValue;
+  if (dtype == OEC_F64) {
+    if (s.arith == 1) { OEC_VEC_U(P64D, double) }
+    OEC_VEC_U(P64, double)
+  }
+  OEC_VEC_U(P32, float)
+#undef OEC_VEC_U
+}
+
+cudaError_t hdiff_tma_launch(const oec_schedule& s, int dtype, const Dom& d, const TmaField& in, const TmaField& coeff,
+                             void* out, cudaStream_t st) {
+#define OEC_TMA_U(P, T)                                                     \
+  switch (s.unroll) {                                                       \
+    case 1: return run_tma<P, 1>(s, d, in, coeff, (T*)out, st);             \
+    case 2: return run_tma<P, 2>(s, d, in, coeff, (T*)out, st);             \
+    case 4: return run_tma<P, 4>(s, d, in, coeff, (T*)out, st);             \
+  }                                                                         \
+  return cudaErrorInvalidValue;
+  if (dtype == OEC_F64) {
+    if (s.arith == 1) { OEC_TMA_U(P64D, double) }
+    OEC_TMA_U(P64, double)
+  }
+  OEC_TMA_U(P32, float)
+#undef OEC_TMA_U
+}
+
+int device_wait_timeouts(cudaStream_t st, unsigned* count) {
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return (int)e;
+  unsigned v = 0, zero = 0;
+  e = cudaMemcpyFromSymbol(&v, g_wait_timeouts, sizeof(v));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_wait_timeouts, &zero, sizeof(zero));
+  *count = v;
+  return (int)e;
+}
+
+}  // namespace oec

@@ -26,9 +26,33 @@ struct Dom {
   int64_t sj, sk;        // element strides shared by all fields
 };
 
+// true when every element offset a kernel forms from the domain's base
+// pointers (halo 2 around the domain) fits in a 32-bit int
+inline bool offsets_fit_int32(const Dom& d) {
+  const int64_t hi = (int64_t)(d.nk + 1) * d.sk + (int64_t)(d.nj + 2) * d.sj + d.ni + 2;
+  const int64_t lo = -(2 * d.sj + 2);
+  return hi < INT32_MAX && lo > INT32_MIN;
+}
+
 // ---- horizontal diffusion: in, coeff -> out --------------------------------
 bool hdiff_schedule_ok(const oec_schedule& s, std::string& why);
 size_t hdiff_scratch_bytes(const oec_schedule& s, int dtype, const Dom& d);
+// vectorised warp rows (OEC_STAGE_WARP, k_hdiff_vec.cu); pointers and
+// strides 16-byte aligned (checked by the caller)
+cudaError_t hdiff_warp_launch(const oec_schedule& s, int dtype, const Dom& d, const void* in, const void* coeff,
+                              void* out, cudaStream_t st);
+// TMA-staged vectorised warp rows (OEC_STAGE_TMA): a field's storage (element
+// 0, extents) and the storage coordinates of the domain's lower corner
+struct TmaField {
+  const void* base;
+  int64_t size[3];
+  int64_t corner[3];
+};
+cudaError_t hdiff_tma_launch(const oec_schedule& s, int dtype, const Dom& d, const TmaField& in,
+                             const TmaField& coeff, void* out, cudaStream_t st);
+// number of bounded device-side waits that gave up since the last call (the
+// stream is synchronised first); clears the count
+int device_wait_timeouts(cudaStream_t st, unsigned* count);
 cudaError_t hdiff_launch(const oec_schedule& s, int dtype, const Dom& d, const void* in, const void* coeff,
                          void* out, void* scratch, cudaStream_t st);
 

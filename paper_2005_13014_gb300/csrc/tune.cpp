@@ -46,6 +46,7 @@ std::vector<oec_schedule> candidates(const oec_program* p) {
           for (int kc : {8, 16, 40}) c.push_back(mk(OEC_FUSE_INLINE, OEC_STAGE_STREAM, t.first, t.second, 1, kc, a));
         for (int u : {1, 2, 4})
           for (int kc : {4, 8, 16}) c.push_back(mk(OEC_FUSE_INLINE, OEC_STAGE_WARP, 32, 4 * u, u, kc, a));
+        for (int u : {1, 2, 4}) c.push_back(mk(OEC_FUSE_INLINE, OEC_STAGE_TMA, 32, 4 * u, u, 0, a));
       }
       break;
     case OEC_KIND_HDIFF_VADVC:

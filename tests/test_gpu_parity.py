@@ -45,8 +45,8 @@ HDIFF_SCHEDS = (
 )
 
 # vectorised warp rows: need 16-byte aligned rows
-WARP_SCHEDS = [dict(fusion=0, staging=3, tile_i=32, tile_j=4 * u, unroll=u, k_chunk=kc) for u in (1, 2, 4)
-               for kc in (0, 3)]
+WARP_SCHEDS = [dict(fusion=0, staging=st, tile_i=32, tile_j=4 * u, unroll=u, k_chunk=kc) for st in (3, 4)
+               for u in (1, 2, 4) for kc in (0, 3)]
 
 
 def _hdiff_case(n, h, dtype, sched, align=0, lb=None, ub=None, poison=True):
@@ -103,9 +103,13 @@ def test_hdiff_ragged(sched, dtype, arith):
 @pytest.mark.parametrize("sched", WARP_SCHEDS, ids=str)
 @pytest.mark.parametrize("dtype,arith", PRECISIONS)
 def test_hdiff_vector_rows(sched, dtype, arith, n):
-    """Ragged warps (partial vectors at the end of the input range and of the
-    domain), edge lanes inside and outside the range, poisoned halos."""
+    """Vectorised warp rows, loaded directly (staging 3) or by TMA into a
+    shared-memory ring (staging 4): ragged warps (partial vectors at the end
+    of the input range and of the domain), edge lanes inside and outside the
+    range, poisoned halos; no bounded wait gives up."""
+    from paper_2005_13014_gb300 import _lib as L
     assert _hdiff_case(n, 2, dtype, _with(sched, arith), align=16) <= TOL[dtype]
+    assert L.lib().oec_device_status(None) == 0
 
 
 def test_hdiff_vector_rows_need_alignment():
