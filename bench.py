@@ -385,12 +385,18 @@ def _run_program(prog_name, dtype, arith, steps, schedule=None, cache=None):
     from oracle import stencils as S
     from paper_2005_13014_gb300 import inputs, programs
     from paper_2005_13014_gb300.api import Program, device_field
-    n, h = MIXED_N, 3
+    n, h = (N if prog_name == "hdiff_vadvc" else MIXED_N), 3
     pts = n[0] * n[1] * n[2]
     stream = torch.cuda.current_stream()
     cache = {} if cache is None else cache
     rnd = (lambda a: a.astype(np.float32).astype(np.float64)) if dtype == "f32" else (lambda a: a)
-    if prog_name == "hdiff":
+    if prog_name == "hdiff_vadvc":
+        if "hv_fields" not in cache:
+            cache["hv_fields"] = inputs.hdiff_vadvc_fields(*n, h)
+        f = {k: rnd(v) for k, v in cache["hv_fields"].items()}
+        prog = Program(programs.HDIFF_VADVC, dtype)
+        names, n_out, params = ["u", "v", "w", "coeff"], 2, [DTR]
+    elif prog_name == "hdiff":
         if "hdiff_fields" not in cache:
             cache["hdiff_fields"] = inputs.hdiff_fields(*n, h)
         f0 = cache["hdiff_fields"]
@@ -417,8 +423,11 @@ def _run_program(prog_name, dtype, arith, steps, schedule=None, cache=None):
     else:
         cands = [c for c in prog.candidates() if c["arith"] == arith]
         prog.autotune(ins, outs, (0, 0, 0), n, (h, h, h), params, candidates=cands, reps=5)
-    # direct: one C-ABI call per apply from Python (host overhead included)
+    # direct: one C-ABI call per apply from Python (host overhead included),
+    # arguments marshalled per call (apply) and once (bind)
     ms_direct = _timed(lambda x: prog.apply(*sets[x % n_sets], (0, 0, 0), n, (h, h, h), params), steps, 3, stream)
+    bound = [prog.bind(*sets[x], (0, 0, 0), n, (h, h, h), params, stream=stream) for x in range(n_sets)]
+    ms_bound = _timed(lambda x: bound[x % n_sets](), steps, 3, stream)
     # device throughput: the same applies captured once into a CUDA graph (one
     # per resident set) and replayed, so host launch overhead is excluded
     gstream = torch.cuda.Stream()
@@ -436,8 +445,12 @@ def _run_program(prog_name, dtype, arith, steps, schedule=None, cache=None):
     key = (prog_name, dtype)
     if key not in cache:
         G = {k: S.Grid.storage(v, h) for k, v in f.items()}
-        cache[key] = ([S.hdiff(G["in"], G["coeff"], (0, 0, 0), n)] if prog_name == "hdiff"
-                      else list(S.fastwaves(G, (0, 0, 0), n, 0.5, 0.0625)))
+        if prog_name == "hdiff":
+            cache[key] = [S.hdiff(G["in"], G["coeff"], (0, 0, 0), n)]
+        elif prog_name == "hdiff_vadvc":
+            cache[key] = list(S.hdiff_vadvc(G["u"], G["v"], G["w"], G["coeff"], (0, 0, 0), n, DTR))
+        else:
+            cache[key] = list(S.fastwaves(G, (0, 0, 0), n, 0.5, 0.0625))
     prog.apply(ins, outs, (0, 0, 0), n, (h, h, h), params)
     torch.cuda.synchronize()
     errs = []
@@ -446,7 +459,9 @@ def _run_program(prog_name, dtype, arith, steps, schedule=None, cache=None):
         errs.append(float(np.max(np.abs(g - r)) / np.max(np.abs(r))))
     nbytes = prog.algorithmic_bytes((0, 0, 0), n)
     return {"gpoints_per_s": pts / (ms * 1e-3) / 1e9, "ms": ms, "ms_direct_launch": ms_direct,
-            "timing": "CUDA-graph replay of one apply per resident set (ms_direct_launch: one Python call each)",
+            "ms_bound_launch": ms_bound,
+            "timing": "CUDA-graph replay of one apply per resident set (ms_direct_launch: one Program.apply call "
+                      "each; ms_bound_launch: one Program.bind call each)",
             "algorithmic_GBps": nbytes / (ms * 1e-3) / 1e9,
             "frac_of_measured_hbm": nbytes / (ms * 1e-3) / 1e9 / _peaks().get("hbm_gbs", 6800.0),
             "max_rel_err_per_output": errs, "schedule": prog.schedule, "launches_per_apply": prog.launch_count(),
@@ -459,16 +474,22 @@ MIXED_N = (256, 256, 80)
 def run_mixed(args):
     """hdiff and fastwaves at 256x256x80, halo 3: FP32 vs FP64 (native,
     double-float and, for hdiff, fixed point) throughput, GB/s and per-field
-    error against the oracle."""
+    error against the oracle; hdiff+vadvc at 128x128x80 with FP32 fields (FP64
+    or double-float recurrence) next to its best FP64 form."""
     import __graft_entry__
     __graft_entry__.build()
     res, cache = {}, {}
-    for prog_name in ("hdiff", "fastwaves"):
-        for dtype, arith in (("f32", 0), ("f64", 0), ("f64", 1)) + ((("f64", 2),) if prog_name == "hdiff" else ()):
+    for prog_name in ("hdiff", "fastwaves", "hdiff_vadvc"):
+        variants = (("f32", 0), ("f64", 0), ("f64", 1))
+        if prog_name == "hdiff":
+            variants += (("f64", 2),)
+        if prog_name == "hdiff_vadvc":   # FP32 fields with an FP64 or double-float recurrence vs FP64 fields
+            variants = (("f32", 0), ("f32", 1), ("f64", 2))
+        for dtype, arith in variants:
             key = f"{prog_name}_{dtype}" + {0: "", 1: "_df", 2: "_fixed"}[arith]
             res[key] = _run_program(prog_name, dtype, arith, args.steps, cache=cache)
-    print(json.dumps({"workload": "mixed precision 256x256x80 halo 3", "l2": "inputs rotated over > 3 x L2",
-                      "results": res}))
+    print(json.dumps({"workload": "mixed precision: hdiff, fastwaves 256x256x80, hdiff+vadvc 128x128x80, halo 3",
+                      "l2": "inputs rotated over > 3 x L2", "results": res}))
     return 0
 
 

@@ -92,6 +92,28 @@ def device_field(arr: np.ndarray, h, dtype="f64", device="cuda", align_bytes=0, 
     return Field(t, (front + hi, hj, hk))
 
 
+class BoundApply:
+    """One program apply with its arguments marshalled once (Program.bind)."""
+
+    def __init__(self, prog, inputs, outputs, lb, ub, halo, params, stream):
+        if stream is None:
+            stream = _torch().cuda.current_stream().cuda_stream
+        elif hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        self._keep = (prog, list(inputs), list(outputs))   # the fields must outlive the binding
+        ins = (L.FieldDesc * max(1, len(inputs)))(*[f.desc() for f in inputs])
+        outs = (L.FieldDesc * max(1, len(outputs)))(*[f.desc() for f in outputs])
+        par = (C.c_double * max(1, len(params)))(*params)
+        self._args = (prog._h, ins, len(inputs), outs, len(outputs), L.I64x3(*lb), L.I64x3(*ub), L.I64x3(*halo),
+                      par, len(params), C.c_void_p(stream))
+        self._fn = L.lib().oec_program_apply
+
+    def __call__(self):
+        rc = self._fn(*self._args)
+        if rc:
+            L.check(rc)
+
+
 class Program:
     """A compiled stencil program (liboec handle)."""
 
@@ -145,6 +167,13 @@ class Program:
         b = C.c_int64()
         L.check(L.lib().oec_program_algorithmic_bytes(self._h, L.I64x3(*lb), L.I64x3(*ub), C.byref(b)))
         return b.value
+
+    def bind(self, inputs, outputs, lb, ub, halo, params=(), stream=None):
+        """Prepare repeated applies of the same fields: the ctypes arguments
+        are built once, and calling the result enqueues one apply (a single
+        foreign call, for loops where the per-call marshalling of ``apply``
+        would cost more than a short kernel)."""
+        return BoundApply(self, inputs, outputs, lb, ub, halo, params, stream)
 
     def launch_count(self) -> int:
         """Kernels launched by the most recent apply."""

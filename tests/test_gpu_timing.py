@@ -62,3 +62,19 @@ def test_launch_count_and_kernel_times(name, dtype, sched, nk):
     assert np.all(t > 0)
     assert t.sum() <= e0.elapsed_time(e1) * 1.01 + 1e-3
     assert p.kernel_times().shape == (0, 0)   # forgotten after reading
+
+
+def test_bound_apply_matches_apply():
+    """Program.bind marshals once; its call enqueues the same apply."""
+    from paper_2005_13014_gb300.api import Program
+    p = Program(programs.HDIFF, "f32")
+    n, h = (70, 37, 9), 3
+    din = _fields(range(2), n, h, "f32")
+    a, b = _fields(range(1), n, h, "f32", seed=100), _fields(range(1), n, h, "f32", seed=200)
+    p.apply(din, a, (0, 0, 0), n, (h, h, h))
+    call = p.bind(din, b, (0, 0, 0), n, (h, h, h))
+    call()
+    call()
+    torch.cuda.synchronize()
+    assert torch.equal(a[0].interior((0, 0, 0), n), b[0].interior((0, 0, 0), n))
+    assert p.launch_count() == 1
