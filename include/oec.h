@@ -85,9 +85,11 @@ typedef enum {
 typedef enum {
   OEC_STAGE_REGS = 0,    /* every thread recomputes what it reads (paper's model)      */
   OEC_STAGE_SMEM = 1,    /* overlapped tile in shared memory, no redundant compute     */
-  OEC_STAGE_STREAM = 2,  /* horizontal diffusion: overlapped tile walked up k, the next
+  OEC_STAGE_STREAM = 2,  /* k-streaming. hdiff: overlapped tile walked up k, the next
                             levels' windows copied asynchronously into a shared-memory
-                            ring while the current level is computed                   */
+                            ring while the current level is computed. fastwaves: a
+                            thread walks its column, carrying the k-shared values from
+                            level to level, next level's loads in flight            */
   OEC_STAGE_WARP = 3,    /* horizontal diffusion: a warp owns `unroll` (1, 2, 4) rows of
                             32 x 16-byte vectors of columns; neighbours across vectors by
                             warp shuffles; the next level loaded ahead. Needs 16-byte

@@ -95,9 +95,17 @@ __device__ __forceinline__ df64 subf(df64 a, df64 b) { return df_sub_fast(a, b);
 // a double-precision constant in the compute type
 template <class T> __device__ __forceinline__ T kd(double v) { return cvt<T>(v); }
 
-// x / 12 (division for the IEEE types, multiplication by the double-float
-// reciprocal for df64)
-__device__ __forceinline__ float div12(float x) { return x / 12.0f; }
+// a / b for the stencil bodies: FP32 by the hardware reciprocal and one
+// multiply (within 2 ulp for |b| in [2^-126, 2^126]); FP64 IEEE division;
+// df64 its estimate-and-correct quotient
+__device__ __forceinline__ float fdiv_(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double fdiv_(double a, double b) { return a / b; }
+__device__ __forceinline__ df64 fdiv_(df64 a, df64 b) { return a / b; }
+
+// x / 12: FP32 multiplies by the rounded reciprocal (within 1 ulp of the
+// quotient, far inside FP32's tolerance), FP64 divides (IEEE), df64
+// multiplies by the double-float reciprocal
+__device__ __forceinline__ float div12(float x) { return x * (1.0f / 12.0f); }
 __device__ __forceinline__ double div12(double x) { return x / 12.0; }
 __device__ __forceinline__ df64 div12(df64 x) { return x * df_from_double(1.0 / 12.0); }
 

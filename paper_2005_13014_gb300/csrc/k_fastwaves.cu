@@ -39,7 +39,7 @@ template <class C>
 __device__ __forceinline__ C fw_ppgk(C wg, C pp, C pp_km1) { return wg * pp + (kc<C>(1.0f) - wg) * pp_km1; }
 template <class C>
 __device__ __forceinline__ C fw_pgrad(C pp_n, C pp, C pc_n, C pc, C h_k1, C h, C hn_k1, C hn) {
-  return (pp_n - pp) + mul_p2(pc_n + pc, 0.25f) * ((h_k1 + h) - (hn_k1 + hn)) / ((h_k1 - h) + (hn_k1 - hn));
+  return (pp_n - pp) + fdiv_(mul_p2(pc_n + pc, 0.25f) * ((h_k1 + h) - (hn_k1 + hn)), (h_k1 - h) + (hn_k1 - hn));
 }
 template <class C>
 __device__ __forceinline__ C fw_d4(C m2, C m1, C p1, C p2) {
@@ -47,7 +47,7 @@ __device__ __forceinline__ C fw_d4(C m2, C m1, C p1, C p2) {
 }
 template <class C>
 __device__ __forceinline__ C fw_out(C uin, C dt, C tens, C pg, C fx, C rho_n, C rho, C alpha, C div_n, C div) {
-  return uin + dt * ((tens - mul_p2(pg, 2.0f) * fx / (rho_n + rho)) + alpha * (div_n - div));
+  return uin + dt * ((tens - fdiv_(mul_p2(pg, 2.0f) * fx, rho_n + rho)) + alpha * (div_n - div));
 }
 
 template <class P>
@@ -103,6 +103,115 @@ __global__ void fw_regs_kernel(FW<typename P::S> p, double dt_d, double alpha_d)
       const int64_t o = (int64_t)(kb + r) * p.sk + col;
       fw_point<P>(p, o, pk[r + 1] - pk[r], pk_e[r + 1] - pk_e[r], pk_n[r + 1] - pk_n[r], div_at<P>(p, o),
                   div_at<P>(p, o + 1), div_at<P>(p, o + p.sj), dt, alpha);
+    }
+  }
+}
+
+// k-streaming form (OEC_STAGE_STREAM): a thread walks its column up a chunk
+// of levels and carries, from level k to k+1, ppgk, pp and hhl of the three
+// columns it needs ((i,j), (i+1,j), (i,j+1)): per level it loads only level
+// k+1 of pp, wgtfac, hhl there, the stencil of u and v for the divergence at
+// the three points, and the point's own inputs (35 loads; the REGS form makes
+// 59). Element offsets are 32-bit where the fields allow it, and the next
+// level's loads are issued before the current level is computed (two
+// register windows in rotation).
+template <class S>
+struct FwWin {
+  S pp1[3], wg1[3], hh1[3];   // level k+1 at (i,j), (i+1,j), (i,j+1)
+  S ur0[6];                   // u_in(i-2 .. i+3, j)
+  S ur1[4];                   // u_in(i-2, i-1, i+1, i+2; j+1)
+  S vc0[6];                   // v_in(i, j-2 .. j+3)
+  S vc1[4];                   // v_in(i+1; j-2, j-1, j+1, j+2)
+  S fx, rho, rho_e, rho_n, ut, vt;
+};
+
+template <class P, class Off>
+__global__ void fw_stream_kernel(FW<typename P::S> p, double dt_d, double alpha_d, int kchunk) {
+  typedef typename P::C T;
+  typedef typename P::S S;
+  const T dt = kd<T>(dt_d), alpha = kd<T>(alpha_d);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= p.ni || j >= p.nj) return;
+  const int k0 = blockIdx.z * kchunk, k1 = min(p.nk, k0 + kchunk);
+  const Off sj = (Off)p.sj, sk = (Off)p.sk;
+  const Off col = (Off)j * sj + i;
+  const Off cn[3] = {0, 1, sj};   // the three columns, relative to (i,j)
+  auto ld = [&](const S* f, Off o) { return ldg(f + o); };
+  auto load = [&](FwWin<S>& w, int k) {   // level k's window (pp, wgtfac, hhl of level k+1)
+    const Off o = (Off)k * sk + col, o1 = o + sk;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      w.pp1[c] = ld(p.pp, o1 + cn[c]);
+      w.wg1[c] = ld(p.wgtfac, o1 + cn[c]);
+      w.hh1[c] = ld(p.hhl, o1 + cn[c]);
+    }
+#pragma unroll
+    for (int x = 0; x < 6; ++x) w.ur0[x] = ld(p.u_in, o + (x - 2));
+    w.ur1[0] = ld(p.u_in, o + sj - 2);
+    w.ur1[1] = ld(p.u_in, o + sj - 1);
+    w.ur1[2] = ld(p.u_in, o + sj + 1);
+    w.ur1[3] = ld(p.u_in, o + sj + 2);
+#pragma unroll
+    for (int x = 0; x < 6; ++x) w.vc0[x] = ld(p.v_in, o + (Off)(x - 2) * sj);
+    w.vc1[0] = ld(p.v_in, o + 1 - 2 * sj);
+    w.vc1[1] = ld(p.v_in, o + 1 - sj);
+    w.vc1[2] = ld(p.v_in, o + 1 + sj);
+    w.vc1[3] = ld(p.v_in, o + 1 + 2 * sj);
+    w.fx = ld(p.fx, o);
+    w.rho = ld(p.rho, o);
+    w.rho_e = ld(p.rho, o + 1);
+    w.rho_n = ld(p.rho, o + sj);
+    w.ut = ld(p.utens, o);
+    w.vt = ld(p.vtens, o);
+  };
+  // carried state at level k: ppgk(k), pp(k), hhl(k) of the three columns
+  T pk[3], ppv[3], hh[3];
+  {
+    const Off o = (Off)k0 * sk + col;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      ppv[c] = cvt<T>(ld(p.pp, o + cn[c]));
+      pk[c] = fw_ppgk(cvt<T>(ld(p.wgtfac, o + cn[c])), ppv[c], cvt<T>(ld(p.pp, o + cn[c] - sk)));
+      hh[c] = cvt<T>(ld(p.hhl, o + cn[c]));
+    }
+  }
+  FwWin<S> win[2];
+  load(win[0], k0);
+  if (k0 + 1 < k1) load(win[1], k0 + 1);
+  for (int k = k0; k < k1; k += 2) {
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      if (k + b >= k1) break;
+      const FwWin<S>& w = win[b];
+      const Off o = (Off)(k + b) * sk + col;
+      T pk1[3], pc[3], h1[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        pk1[c] = fw_ppgk(cvt<T>(w.wg1[c]), cvt<T>(w.pp1[c]), ppv[c]);
+        pc[c] = pk1[c] - pk[c];
+        h1[c] = cvt<T>(w.hh1[c]);
+      }
+      const T ppgu = fw_pgrad(ppv[1], ppv[0], pc[1], pc[0], h1[0], hh[0], h1[1], hh[1]);
+      const T ppgv = fw_pgrad(ppv[2], ppv[0], pc[2], pc[0], h1[0], hh[0], h1[2], hh[2]);
+      auto U0 = [&](int x) { return cvt<T>(w.ur0[x + 2]); };   // u_in(i+x, j)
+      auto V0 = [&](int y) { return cvt<T>(w.vc0[y + 2]); };   // v_in(i, j+y)
+      // divergence at (i,j), (i+1,j), (i,j+1)
+      const T dv = fw_d4(U0(-2), U0(-1), U0(1), U0(2)) + fw_d4(V0(-2), V0(-1), V0(1), V0(2));
+      const T dv_e = fw_d4(U0(-1), U0(0), U0(2), U0(3)) +
+                     fw_d4(cvt<T>(w.vc1[0]), cvt<T>(w.vc1[1]), cvt<T>(w.vc1[2]), cvt<T>(w.vc1[3]));
+      const T dv_n = fw_d4(cvt<T>(w.ur1[0]), cvt<T>(w.ur1[1]), cvt<T>(w.ur1[2]), cvt<T>(w.ur1[3])) +
+                     fw_d4(V0(-1), V0(0), V0(2), V0(3));
+      const T fx = cvt<T>(w.fx), rho = cvt<T>(w.rho);
+      p.u_out[o] = cvt<S>(fw_out(U0(0), dt, cvt<T>(w.ut), ppgu, fx, cvt<T>(w.rho_e), rho, alpha, dv_e, dv));
+      p.v_out[o] = cvt<S>(fw_out(V0(0), dt, cvt<T>(w.vt), ppgv, fx, cvt<T>(w.rho_n), rho, alpha, dv_n, dv));
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        pk[c] = pk1[c];
+        ppv[c] = cvt<T>(w.pp1[c]);
+        hh[c] = h1[c];
+      }
+      if (k + b + 2 < k1) load(win[b], k + b + 2);
     }
   }
 }
@@ -215,6 +324,14 @@ Tmp tmp_layout(size_t e, const Dom& d) {
 
 int kchunk_of(const oec_schedule& s, int nk) { return (s.k_chunk <= 0 || s.k_chunk > nk) ? nk : s.k_chunk; }
 
+// every element offset the k-streaming kernel forms (halo 3 in i/j, 1 in k)
+// fits in a 32-bit int
+bool offsets_fit_fw(const Dom& d) {
+  const int64_t hi = (int64_t)(d.nk + 1) * d.sk + (int64_t)(d.nj + 3) * d.sj + d.ni + 3;
+  const int64_t lo = -(d.sk + 3 * d.sj + 3);
+  return hi < INT32_MAX && lo > INT32_MIN;
+}
+
 #define OEC_FW_TILES(X) X(32, 4) X(32, 8) X(64, 2) X(64, 4) X(128, 2)
 
 template <class P>
@@ -234,6 +351,17 @@ cudaError_t dispatch(const oec_schedule& s, const Dom& d, const FW<typename P::S
     fw_s34<P, 1><<<gd, b, 0, st>>>(p, pc, pv); launched(st);
     fw_s5<P><<<g, b, 0, st>>>(p, dv); launched(st);
     fw_s6<P><<<gd, b, 0, st>>>(p, pu, pv, dv, dt, alpha); launched(st);
+    return cudaGetLastError();
+  }
+  if (s.staging == OEC_STAGE_STREAM) {
+    const int kc = kchunk_of(s, d.nk);
+    dim3 b(s.tile_i, s.tile_j);
+    dim3 g(ceil_div(d.ni, s.tile_i), ceil_div(d.nj, s.tile_j), ceil_div(d.nk, kc));
+    if (offsets_fit_fw(d))
+      fw_stream_kernel<P, int><<<g, b, 0, st>>>(p, dt, alpha, kc);
+    else
+      fw_stream_kernel<P, int64_t><<<g, b, 0, st>>>(p, dt, alpha, kc);
+    launched(st);
     return cudaGetLastError();
   }
   if (s.staging == OEC_STAGE_SMEM) {
@@ -273,8 +401,11 @@ bool fastwaves_schedule_ok(const oec_schedule& s, std::string& why) {
     why = "fastwaves SMEM tiles: 32x4, 32x8, 64x2, 64x4, 128x2";
     return false;
   }
-  if (s.staging != OEC_STAGE_REGS) { why = "unknown staging"; return false; }
-  if (s.unroll != 1 && s.unroll != 2 && s.unroll != 4) { why = "unroll (along k) must be 1, 2 or 4"; return false; }
+  if (s.staging != OEC_STAGE_REGS && s.staging != OEC_STAGE_STREAM) { why = "unknown staging"; return false; }
+  if (s.staging == OEC_STAGE_REGS && s.unroll != 1 && s.unroll != 2 && s.unroll != 4) {
+    why = "unroll (along k) must be 1, 2 or 4";
+    return false;
+  }
   if (s.tile_i < 16 || s.tile_i > 256 || s.tile_i % 16 || s.tile_j < 1 || s.tile_j > 16 || s.tile_i * s.tile_j > 1024) {
     why = "tile_i a multiple of 16 in [16,256], tile_j in [1,16], at most 1024 threads";
     return false;

@@ -199,7 +199,9 @@ FW_SCHEDS = ([dict(fusion=1)]
              + [dict(fusion=0, staging=1, tile_i=a, tile_j=b, k_chunk=kc)
                 for (a, b) in [(32, 4), (32, 8), (64, 2), (64, 4), (128, 2)] for kc in (0, 3)]
              + [dict(fusion=0, staging=0, tile_i=a, tile_j=b, unroll=u)
-                for (a, b, u) in [(32, 4, 1), (64, 4, 2), (32, 8, 4), (128, 2, 4)]])
+                for (a, b, u) in [(32, 4, 1), (64, 4, 2), (32, 8, 4), (128, 2, 4)]]
+             + [dict(fusion=0, staging=2, tile_i=a, tile_j=b, k_chunk=kc)
+                for (a, b) in [(32, 4), (64, 4), (128, 2)] for kc in (0, 3, 4)])
 
 
 def _fw_case(n, h, dtype, sched, dt=0.5, alpha=0.0625):
