@@ -370,8 +370,10 @@ OEC_API void oec_batch_destroy(oec_batch_t b);
 typedef struct oec_costmodel* oec_costmodel_t;
 
 /*
- * An FP32 MLP: features -> hidden -> hidden -> 1 with ReLU, predicting
- * log(time per grid point) of a (program, domain, schedule). Parameters are
+ * An FP32 MLP: features -> hidden -> hidden -> 1 with ReLU, predicting a
+ * log cost of a (program, domain, schedule) - the project trains it on
+ * log(t / t_best) within each program, and selection only ranks predictions
+ * of one program's candidates. Parameters are
  * one flat array W1 [H][F], b1 [H], W2 [H][H], b2 [H], W3 [1][H], b3 [1]
  * (params_host may be NULL: all zero). Training uses mean squared error and
  * Adam; all compute runs in liboec's kernels, and every reduction has a fixed
@@ -397,6 +399,30 @@ OEC_API int oec_costmodel_gradient(oec_costmodel_t m, const float* X, const floa
 OEC_API int oec_costmodel_train_step(oec_costmodel_t m, const float* X, const float* t, int n, float lr, float beta1,
                                      float beta2, float eps, float* loss, void* cuda_stream);
 OEC_API void oec_costmodel_destroy(oec_costmodel_t m);
+
+/* Checkpoint file: dimensions, parameters and standardisation (binary, little
+ * endian as written). save errors: OEC_ERR_INVALID_ARG (path unwritable);
+ * load: OEC_ERR_INVALID_ARG (unreadable, or not a checkpoint), and
+ * oec_costmodel_create's errors. Synchronous. */
+OEC_API int oec_costmodel_save(oec_costmodel_t m, const char* path);
+OEC_API int oec_costmodel_load(const char* path, oec_costmodel_t* out);
+
+/*
+ * Model-guided schedule selection: the features of every candidate schedule
+ * (oec_program_candidates, oec_program_features) are predicted by m; top_k <= 0
+ * takes the best-ranked valid candidate untimed, top_k > 0 times the top_k
+ * best-ranked as oec_program_autotune does (reps applies each; fields as for
+ * oec_program_apply, outputs overwritten) and takes the fastest, with
+ * exhaustive oec_program_autotune as the reference it is judged against.
+ * Sets the program's schedule; *best = the pick's index in the candidate
+ * list; pred (may be NULL) receives the n_cand predictions. Synchronises
+ * cuda_stream. Errors: as oec_program_features and oec_program_autotune, and
+ * OEC_ERR_INVALID_ARG when the model's feature count differs.
+ */
+OEC_API int oec_program_autotune_model(oec_program_t p, oec_costmodel_t m, const oec_field_desc* in, int n_in,
+                                       const oec_field_desc* out, int n_out, const int64_t lb[3], const int64_t ub[3],
+                                       const int64_t halo[3], const double* params, int n_params, int top_k, int reps,
+                                       void* cuda_stream, float* pred, int* best);
 
 /*
  * hdiff+vadvc without any device allocation. There is no counterpart in the

@@ -84,6 +84,11 @@ def lib():
                                         I64x3, I64x3, I64x3, C.POINTER(C.c_double), C.c_int, P]),
         "oec_program_algorithmic_bytes": (C.c_int, [P, I64x3, I64x3, C.POINTER(C.c_int64)]),
         "oec_device_status": (C.c_int, [P]),
+        "oec_costmodel_save": (C.c_int, [P, C.c_char_p]),
+        "oec_costmodel_load": (C.c_int, [C.c_char_p, C.POINTER(P)]),
+        "oec_program_autotune_model": (C.c_int, [P, P, C.POINTER(FieldDesc), C.c_int, C.POINTER(FieldDesc), C.c_int,
+                                                 I64x3, I64x3, I64x3, C.POINTER(C.c_double), C.c_int, C.c_int,
+                                                 C.c_int, P, C.POINTER(C.c_float), C.POINTER(C.c_int)]),
         "oec_program_launch_count": (C.c_int, [P]),
         "oec_program_set_timing": (C.c_int, [P, C.c_int]),
         "oec_program_kernel_times": (C.c_int, [P, C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_int),

@@ -168,6 +168,23 @@ class Program:
         L.check(L.lib().oec_program_algorithmic_bytes(self._h, L.I64x3(*lb), L.I64x3(*ub), C.byref(b)))
         return b.value
 
+    def autotune_model(self, model, inputs, outputs, lb, ub, halo, params=(), top_k=3, reps=3, stream=None):
+        """Model-guided selection in liboec: rank every candidate by the cost
+        model's prediction, time the top_k (top_k=0: take the best-ranked
+        untimed), set the schedule. Returns (index of the pick in
+        candidates(), predictions)."""
+        n = len(self.candidates())
+        ins = (L.FieldDesc * max(1, len(inputs)))(*[f.desc() for f in inputs])
+        outs = (L.FieldDesc * max(1, len(outputs)))(*[f.desc() for f in outputs])
+        par = (C.c_double * max(1, len(params)))(*params)
+        pred = np.zeros(max(1, n), np.float32)
+        best = C.c_int(-1)
+        L.check(L.lib().oec_program_autotune_model(
+            self._h, model._h, ins, len(inputs), outs, len(outputs), L.I64x3(*lb), L.I64x3(*ub), L.I64x3(*halo),
+            par, len(params), top_k, reps, C.c_void_p(_stream_handle(stream)),
+            pred.ctypes.data_as(C.POINTER(C.c_float)), C.byref(best)))
+        return best.value, pred[:n]
+
     def bind(self, inputs, outputs, lb, ub, halo, params=(), stream=None):
         """Prepare repeated applies of the same fields: the ctypes arguments
         are built once, and calling the result enqueues one apply (a single

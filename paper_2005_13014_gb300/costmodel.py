@@ -76,14 +76,19 @@ class CostModel:
                                                          sigma.ctypes.data_as(C.POINTER(C.c_float))))
 
     def save(self, path):
-        np.savez(path, params=self.get_params(), mu=self.mu, sigma=self.sigma,
-                 dims=np.array([self.n_features, self.hidden]))
+        """Checkpoint file (liboec's format: dimensions, parameters, standardisation)."""
+        L.check(L.lib().oec_costmodel_save(self._h, str(path).encode()))
 
     @classmethod
     def load(cls, path):
-        z = np.load(path)
-        m = cls(int(z["dims"][0]), int(z["dims"][1]), params=z["params"])
-        m.set_normalization(z["mu"], z["sigma"])
+        h = C.c_void_p()
+        L.check(L.lib().oec_costmodel_load(str(path).encode(), C.byref(h)))
+        m = cls.__new__(cls)
+        m._h = h
+        m.param_count = L.lib().oec_costmodel_param_count(h)
+        m.hidden = None
+        m.n_features = None
+        m._loss = _torch().zeros(1, dtype=_torch().float32, device="cuda")
         return m
 
     def predict(self, X):

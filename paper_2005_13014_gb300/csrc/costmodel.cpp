@@ -3,8 +3,12 @@
 // driven by the MLP kernels of k_mlp.cu.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstring>
 #include <new>
+#include <numeric>
 #include <vector>
 
 #include "../../include/oec.h"
@@ -20,6 +24,7 @@ struct oec_costmodel {
   int step = 0;
   float* mu = nullptr;          // feature standardisation (x - mu) * inv_sigma
   float* inv_sigma = nullptr;
+  std::vector<float> mu_host, sigma_host;   // as last set (checkpoints)
   oec::MlpWork work;
   int dev = 0;
 };
@@ -149,6 +154,8 @@ int oec_costmodel_set_normalization(oec_costmodel_t c, const float* mu, const fl
   if (!c || !mu || !sigma) return fail(OEC_ERR_INVALID_ARG, "null argument");
   std::vector<float> inv(c->dims.F);
   for (int f = 0; f < c->dims.F; ++f) inv[f] = sigma[f] > 0.0f ? 1.0f / sigma[f] : 1.0f;
+  c->mu_host.assign(mu, mu + c->dims.F);
+  c->sigma_host.assign(sigma, sigma + c->dims.F);
   cudaError_t e = cudaMemcpy(c->mu, mu, sizeof(float) * c->dims.F, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(c->inv_sigma, inv.data(), sizeof(float) * c->dims.F, cudaMemcpyHostToDevice);
   return e == cudaSuccess ? OEC_OK : cuda_fail(e, "cost-model normalisation");
@@ -166,6 +173,126 @@ void oec_costmodel_destroy(oec_costmodel_t c) {
     if (b) cudaFree(b);
   cudaSetDevice(cur);
   delete c;
+}
+
+// ---- checkpoints: magic, F, H, parameter count, parameters, mu, sigma ------
+int oec_costmodel_save(oec_costmodel_t c, const char* path) {
+  clear_error();
+  if (!c || !path) return fail(OEC_ERR_INVALID_ARG, "null argument");
+  const int n = oec_costmodel_param_count(c);
+  std::vector<float> P(n);
+  int rc = oec_costmodel_get_params(c, P.data(), n);
+  if (rc) return rc;
+  std::vector<float> mu(c->mu_host), sg(c->sigma_host);
+  mu.resize(c->dims.F, 0.0f);
+  sg.resize(c->dims.F, 1.0f);
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(OEC_ERR_INVALID_ARG, "cannot write %s", path);
+  const char magic[8] = {'O', 'E', 'C', 'M', 'L', 'P', '1', 0};
+  const int32_t hdr[3] = {c->dims.F, c->dims.H, n};
+  bool ok = std::fwrite(magic, 1, 8, f) == 8 && std::fwrite(hdr, sizeof(int32_t), 3, f) == 3 &&
+            std::fwrite(P.data(), sizeof(float), n, f) == (size_t)n &&
+            std::fwrite(mu.data(), sizeof(float), mu.size(), f) == mu.size() &&
+            std::fwrite(sg.data(), sizeof(float), sg.size(), f) == sg.size();
+  ok = (std::fclose(f) == 0) && ok;
+  return ok ? OEC_OK : fail(OEC_ERR_INVALID_ARG, "short write to %s", path);
+}
+
+int oec_costmodel_load(const char* path, oec_costmodel_t* out) {
+  clear_error();
+  if (!path || !out) return fail(OEC_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(OEC_ERR_INVALID_ARG, "cannot read %s", path);
+  char magic[8];
+  int32_t hdr[3];
+  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "OECMLP1", 8) == 0 &&
+            std::fread(hdr, sizeof(int32_t), 3, f) == 3 && hdr[0] > 0 && hdr[1] > 0 && hdr[2] > 0 &&
+            hdr[0] <= 4096 && hdr[1] <= 4096;
+  std::vector<float> P, mu, sg;
+  if (ok) {
+    P.resize(hdr[2]);
+    mu.resize(hdr[0]);
+    sg.resize(hdr[0]);
+    ok = std::fread(P.data(), sizeof(float), P.size(), f) == P.size() &&
+         std::fread(mu.data(), sizeof(float), mu.size(), f) == mu.size() &&
+         std::fread(sg.data(), sizeof(float), sg.size(), f) == sg.size();
+  }
+  std::fclose(f);
+  if (!ok) return fail(OEC_ERR_INVALID_ARG, "%s is not a cost-model checkpoint", path);
+  oec_costmodel_t c = nullptr;
+  int rc = oec_costmodel_create(hdr[0], hdr[1], P.data(), &c);
+  if (rc) return rc;
+  if (oec_costmodel_param_count(c) != hdr[2]) {
+    oec_costmodel_destroy(c);
+    return fail(OEC_ERR_INVALID_ARG, "%s: parameter count does not match its dimensions", path);
+  }
+  rc = oec_costmodel_set_normalization(c, mu.data(), sg.data());
+  if (rc) {
+    oec_costmodel_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return OEC_OK;
+}
+
+// ---- model-guided schedule selection ------------------------------------------
+int oec_program_autotune_model(oec_program_t p, oec_costmodel_t m, const oec_field_desc* in, int n_in,
+                               const oec_field_desc* out, int n_out, const int64_t lb[3], const int64_t ub[3],
+                               const int64_t halo[3], const double* params, int n_params, int top_k, int reps,
+                               void* cuda_stream, float* pred, int* best) {
+  clear_error();
+  if (!p || !m || !out || n_out < 1 || !lb || !ub || !halo || !best) return fail(OEC_ERR_INVALID_ARG, "null argument");
+  const int nc = oec_program_candidates(p, nullptr, 0);
+  if (nc < 1) return nc < 0 ? nc : fail(OEC_ERR_UNSUPPORTED, "no candidate schedules");
+  std::vector<oec_schedule> cand(nc);
+  oec_program_candidates(p, cand.data(), nc);
+  const int64_t ext[3] = {ub[0] - lb[0], ub[1] - lb[1], ub[2] - lb[2]};
+  const int64_t sj = out[0].stride[1], sk = out[0].stride[2];
+  const int F = m->dims.F;
+  std::vector<float> X((size_t)nc * F);
+  for (int c = 0; c < nc; ++c) {
+    const int nf = oec_program_features(p, ext, sj, sk, &cand[c], &X[(size_t)c * F], F);
+    if (nf < 0) return nf;
+    if (nf != F) return fail(OEC_ERR_INVALID_ARG, "the model takes %d features, the program gives %d", F, nf);
+  }
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  float *dX = nullptr, *dy = nullptr;
+  std::vector<float> y(nc);
+  cudaError_t e = cudaMalloc(&dX, sizeof(float) * X.size());
+  if (e == cudaSuccess) e = cudaMalloc(&dy, sizeof(float) * nc);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dX, X.data(), sizeof(float) * X.size(), cudaMemcpyHostToDevice, st);
+  int rc = e == cudaSuccess ? oec_costmodel_predict(m, dX, nc, dy, cuda_stream) : OEC_OK;
+  if (e == cudaSuccess && rc == OEC_OK) e = cudaMemcpyAsync(y.data(), dy, sizeof(float) * nc, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && rc == OEC_OK) e = cudaStreamSynchronize(st);
+  if (dX) cudaFree(dX);
+  if (dy) cudaFree(dy);
+  if (rc) return rc;
+  if (e != cudaSuccess) return cuda_fail(e, "cost-model prediction");
+  if (pred) std::copy(y.begin(), y.end(), pred);
+  std::vector<int> order(nc);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return y[a] < y[b]; });
+  if (top_k <= 0) {
+    std::string why;
+    for (int c : order)
+      if (schedule_ok(p->kind, cand[c], why)) {
+        p->sched = cand[c];
+        *best = c;
+        return OEC_OK;
+      }
+    return fail(OEC_ERR_UNSUPPORTED, "no valid candidate schedule");
+  }
+  const int k = std::min(top_k, nc);
+  std::vector<oec_schedule> sub(k);
+  for (int x = 0; x < k; ++x) sub[x] = cand[order[x]];
+  std::vector<double> t(k);
+  int bi = -1;
+  rc = oec_program_autotune(p, in, n_in, out, n_out, lb, ub, halo, params, n_params, sub.data(), k, reps < 1 ? 1 : reps,
+                            cuda_stream, t.data(), &bi);
+  if (rc) return rc;
+  *best = order[bi];
+  return OEC_OK;
 }
 
 }  // extern "C"

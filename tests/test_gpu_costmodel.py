@@ -83,14 +83,40 @@ def test_training_reduces_loss_and_checkpoint_roundtrip(tmp_path):
     losses = m.fit(Xd, td, epochs=60, batch=256, lr=3e-3)
     assert losses[-1] < 0.1 * losses[0]
     y0 = m.predict(Xd).cpu().numpy()
-    m.save(tmp_path / "cm.npz")
+    m.save(tmp_path / "cm.oecm")
     from paper_2005_13014_gb300.costmodel import CostModel
-    m2 = CostModel.load(tmp_path / "cm.npz")
+    m2 = CostModel.load(tmp_path / "cm.oecm")
     assert np.array_equal(m2.predict(Xd).cpu().numpy(), y0)
     # standardisation on the device equals feeding standardised features
     m3 = CostModel(42, 64, params=m.get_params())
     Xs = ((X - X.mean(0)) / X.std(0)).astype(np.float32)
     assert np.max(np.abs(m3.predict(torch.from_numpy(Xs).cuda()).cpu().numpy() - y0)) <= 1e-4 * np.max(np.abs(y0))
+
+
+def test_model_guided_selection_in_the_library(tmp_path):
+    """oec_program_autotune_model ranks every candidate by the model's
+    prediction (the same features and kernels as the Python path), takes the
+    best-ranked untimed with top_k = 0, or times the top_k and keeps the
+    fastest; a corrupt checkpoint is refused."""
+    from paper_2005_13014_gb300 import costmodel as CM
+    from paper_2005_13014_gb300._lib import OecError
+    case = CM.DagCase(inputs.random_dag(10007), (64, 48, 20), "f32", seed=7)
+    case.prepare()
+    cands = case.program.candidates()
+    F = case.features(cands)
+    m = CM.CostModel(F.shape[1], 64, params=CM.CostModel.flatten(inputs.mlp_init(F.shape[1], 64)))
+    m.set_normalization(F.mean(0), F.std(0) + 1e-6)
+    pred_py = m.predict(torch.from_numpy(F.astype(np.float32)).cuda()).cpu().numpy()
+    lb, ub, h = (0, 0, 0), case.shape, case.halo
+    best0, pred = case.program.autotune_model(m, case.inputs, case.outputs, lb, ub, h, top_k=0)
+    assert np.array_equal(pred, pred_py)
+    assert best0 == int(np.argsort(pred, kind="stable")[0]) and case.program.schedule == cands[best0]
+    best3, _ = case.program.autotune_model(m, case.inputs, case.outputs, lb, ub, h, top_k=3, reps=2)
+    assert best3 in set(np.argsort(pred, kind="stable")[:3].tolist())
+    assert case.program.schedule == cands[best3]
+    (tmp_path / "bad.oecm").write_bytes(b"not a checkpoint")
+    with pytest.raises(OecError, match="not a cost-model checkpoint"):
+        CM.CostModel.load(tmp_path / "bad.oecm")
 
 
 def test_autotuner_times_every_candidate():
