@@ -327,6 +327,13 @@ hv_batch_kernel(const HVMember* __restrict__ members, int n_members, int total_i
   }
 }
 
+// w(i) + w(i+1) in the compute type: for FP64 fields with double-float
+// compute, the binary64 sum rounded once by one FP64 add and then split into a
+// pair (one conversion instead of two and a pair addition); otherwise the
+// compute type's own sum.
+template <class C, class S> __device__ __forceinline__ C wsum(S a, S b) { return cvt<C>(a) + cvt<C>(b); }
+template <> __device__ __forceinline__ df64 wsum<df64, double>(double a, double b) { return df_from_double(a + b); }
+
 // Staged form, column sweep over hdiff(u), hdiff(v) held in the compute type
 // (domain layout, pitch ni, plane ni*nj), by twisted factorisation: the
 // column's rows [0, m) are eliminated upwards from level 0 and its rows
@@ -396,7 +403,7 @@ __global__ void __launch_bounds__(2 * NC) hv_thomas_kernel(HV<typename P::S> p, 
   // wf of the edge held in slot st (zero where there is none)
   auto wf_of = [&](int st) {
     const int sl = st % DEPTH;
-    return wlev(st) < nk ? mul_p2(cvt<C>(sw0[sl][t]) + cvt<C>(sw1[sl][t]), 0.5f) : zero_<C>();
+    return wlev(st) < nk ? mul_p2(wsum<C>(sw0[sl][t], sw1[sl][t]), 0.5f) : zero_<C>();
   };
   const float sgn = down ? -1.0f : 1.0f;   // beta = -sgn wf_behind / 4, gamma = sgn wf_ahead / 4
   R g = cvt<R>(0.0f), eu = cvt<R>(0.0f), ev = cvt<R>(0.0f);
@@ -413,16 +420,16 @@ __global__ void __launch_bounds__(2 * NC) hv_thomas_kernel(HV<typename P::S> p, 
       u1 = su[1][t];
       v1 = sv[1][t];
       wfa = wf_of(1);
-      du0 = u1 - u0;
-      dv0 = v1 - v0;
+      du0 = subf(u1, u0);
+      dv0 = subf(v1, v0);
       gamma = mul_p2(wfa, 0.25f * sgn);
     }
     b = addf(dtr, abs_(gamma));
     ru = dtr * u0;
     rv = dtr * v0;
     if (ahead0) {
-      ru = ru - mul_p2(gamma * du0, 0.5f);
-      rv = rv - mul_p2(gamma * dv0, 0.5f);
+      ru = subf(ru, mul_p2(gamma * du0, 0.5f));
+      rv = subf(rv, mul_p2(gamma * dv0, 0.5f));
     }
   }
   // elimination of the row of step st (step 0 needs no special case:
@@ -447,19 +454,19 @@ __global__ void __launch_bounds__(2 * NC) hv_thomas_kernel(HV<typename P::S> p, 
       u2 = su[sl][t];
       v2 = sv[sl][t];
       wf2 = wf_of(st + 2);
-      du1 = u2 - u1;
-      dv1 = v2 - v1;
+      du1 = subf(u2, u1);
+      dv1 = subf(v2, v1);
     }
     beta = mul_p2(wfa, -0.25f * sgn);
     gamma = hi ? mul_p2(wf2, 0.25f * sgn) : zero_<C>();
     b = addf(addf(dtr, abs_(beta)), abs_(gamma));
     const C tu = dtr * u1, tv = dtr * v1;
     if (hi) {
-      ru = tu - mul_p2(beta * (-du0) + gamma * du1, 0.5f);
-      rv = tv - mul_p2(beta * (-dv0) + gamma * dv1, 0.5f);
+      ru = subf(tu, mul_p2(addf(beta * (-du0), gamma * du1), 0.5f));
+      rv = subf(tv, mul_p2(addf(beta * (-dv0), gamma * dv1), 0.5f));
     } else {
-      ru = tu - mul_p2(beta * (-du0), 0.5f);
-      rv = tv - mul_p2(beta * (-dv0), 0.5f);
+      ru = subf(tu, mul_p2(beta * (-du0), 0.5f));
+      rv = subf(tv, mul_p2(beta * (-dv0), 0.5f));
     }
     u1 = u2;
     v1 = v2;
