@@ -318,17 +318,17 @@ __device__ __forceinline__ long long fx_flux(long long lap_hi, long long lap_lo,
 // planes, the divergence, and one FP64 FMA. The raw window and the exponent
 // slot are double-buffered, so the next level's load overlaps this level's
 // step (4) and a level costs three barriers.
-template <class OutT, int TI, int TJ>
+template <class OutT, int TI, int TJ, class Off>
 __global__ void __launch_bounds__(TI * TJ)
 hdiff_fixed_kernel(const double* __restrict__ in0, const double* __restrict__ in1, const double* __restrict__ coeff,
                    OutT* __restrict__ out0, OutT* __restrict__ out1, int ni, int nj, int nk, int64_t sj, int64_t sk,
                    int64_t osj, int64_t osk, int kchunk, int nkz) {
   constexpr int NT = TI * TJ, WI = TI + 4, WJ = TJ + 4, NW = WI * WJ, LI = TI + 2, LJ = TJ + 2, NL = LI * LJ;
   constexpr int QW = (NW + NT - 1) / NT, QL = (NL + NT - 1) / NT;
-  __shared__ double s_raw[2][WJ][WI];
-  __shared__ long long s_fix[WJ][WI];
-  __shared__ long long s_key[WJ][WI];
-  __shared__ long long s_lap[LJ][LI];
+  __shared__ double s_raw[2][NW];
+  __shared__ long long s_fix[NW];
+  __shared__ long long s_key[NW];
+  __shared__ long long s_lap[NL];
   __shared__ unsigned s_emax[2];
   const int tid = threadIdx.x, tx = tid % TI, ty = tid / TI;
   const int i0 = blockIdx.x * TI, j0 = blockIdx.y * TJ;
@@ -338,64 +338,80 @@ hdiff_fixed_kernel(const double* __restrict__ in0, const double* __restrict__ in
   const int kz = second ? blockIdx.z - nkz : blockIdx.z;
   const int k0 = kz * kchunk, k1 = min(nk, k0 + kchunk);
   const int vi = min(TI, ni - i0), vj = min(TJ, nj - j0);
+  // this thread's positions, fixed for every level: window copies (offset
+  // from the window corner), Laplacian positions (window centre), its output
+  Off wg[QW];
+  bool wok[QW];
+#pragma unroll
+  for (int q = 0; q < QW; ++q) {
+    const int idx = tid + q * NT, r = idx / WI, c = idx - r * WI;
+    wok[q] = idx < NW && c < vi + 4 && r < vj + 4;
+    wg[q] = (Off)r * (Off)sj + c;
+  }
+  int lw[QL];
+  bool lok[QL];
+#pragma unroll
+  for (int q = 0; q < QL; ++q) {
+    const int idx = tid + q * NT, r = idx / LI, c = idx - r * LI;
+    lok[q] = idx < NL && c < vi + 2 && r < vj + 2;
+    lw[q] = (r + 1) * WI + c + 1;
+  }
+  const bool own = tx < vi && ty < vj;
+  const int ow = (ty + 2) * WI + tx + 2, ol = (ty + 1) * LI + tx + 1;
+  const double* __restrict__ wcorner = in + ((Off)(j0 - 2) * (Off)sj + (i0 - 2));
+  const Off oin = (Off)(j0 + ty) * (Off)sj + (i0 + tx), oout = (Off)(j0 + ty) * (Off)osj + (i0 + tx);
   if (tid < 2) s_emax[tid] = 0u;
   __syncthreads();
   int bf = 0;
   for (int k = k0; k < k1; ++k, bf ^= 1) {
     // (1) raw window and its largest exponent
-    const double* pin = in + (int64_t)k * sk + (int64_t)(j0 - 2) * sj + (i0 - 2);
+    const double* pin = wcorner + (Off)k * (Off)sk;
     unsigned emax = 0u;
 #pragma unroll
-    for (int q = 0; q < QW; ++q) {
-      const int idx = tid + q * NT;
-      const int r = idx / WI, c = idx - r * WI;
-      if (idx < NW && c < vi + 4 && r < vj + 4) {
-        const double x = ldg(pin + (int64_t)r * sj + c);
-        s_raw[bf][r][c] = x;
+    for (int q = 0; q < QW; ++q)
+      if (wok[q]) {
+        const double x = ldg(pin + wg[q]);
+        s_raw[bf][tid + q * NT] = x;
         emax = max(emax, (unsigned)(__double_as_longlong(x) >> 52) & 0x7FFu);
       }
-    }
     emax = __reduce_max_sync(0xFFFFFFFFu, emax);
     if ((tid & 31) == 0) atomicMax(&s_emax[bf], emax);
     __syncthreads();
     // (2) fixed point at scale E, and the limiter keys
     const unsigned E = max(s_emax[bf], 100u);
 #pragma unroll
-    for (int q = 0; q < QW; ++q) {
-      const int idx = tid + q * NT;
-      const int r = idx / WI, c = idx - r * WI;
-      if (idx < NW && c < vi + 4 && r < vj + 4) {
-        const double x = s_raw[bf][r][c];
-        s_fix[r][c] = fx_of(x, E);
-        s_key[r][c] = fx_key(x);
+    for (int q = 0; q < QW; ++q)
+      if (wok[q]) {
+        const int idx = tid + q * NT;
+        const double x = s_raw[bf][idx];
+        s_fix[idx] = fx_of(x, E);
+        s_key[idx] = fx_key(x);
       }
-    }
     __syncthreads();
     if (tid == 0) s_emax[bf] = 0u;   // read by everyone before the barrier; next written two levels on
     // (3) Laplacian
 #pragma unroll
-    for (int q = 0; q < QL; ++q) {
-      const int idx = tid + q * NT;
-      const int r = idx / LI, c = idx - r * LI;
-      if (idx < NL && c < vi + 2 && r < vj + 2)
-        s_lap[r][c] = (s_fix[r + 1][c + 1] << 2) - s_fix[r + 1][c] - s_fix[r + 1][c + 2] - s_fix[r][c + 1] - s_fix[r + 2][c + 1];
-    }
+    for (int q = 0; q < QL; ++q)
+      if (lok[q]) {
+        const long long* f = s_fix + lw[q];
+        s_lap[tid + q * NT] = (f[0] << 2) - f[-1] - f[1] - f[-WI] - f[WI];
+      }
     __syncthreads();
     // (4) limited fluxes, divergence, output
-    if (tx < vi && ty < vj) {
-      const long long lc = s_lap[ty + 1][tx + 1];
-      const long long kc = s_key[ty + 2][tx + 2];
-      const long long fxp = fx_flux(s_lap[ty + 1][tx + 2], lc, s_key[ty + 2][tx + 3], kc);
-      const long long fxm = fx_flux(lc, s_lap[ty + 1][tx], kc, s_key[ty + 2][tx + 1]);
-      const long long fyp = fx_flux(s_lap[ty + 2][tx + 1], lc, s_key[ty + 3][tx + 2], kc);
-      const long long fym = fx_flux(lc, s_lap[ty][tx + 1], kc, s_key[ty + 1][tx + 2]);
+    if (own) {
+      const long long* L = s_lap + ol;
+      const long long* K = s_key + ow;
+      const long long lc = L[0], kc = K[0];
+      const long long fxp = fx_flux(L[1], lc, K[1], kc);
+      const long long fxm = fx_flux(lc, L[-1], kc, K[-1]);
+      const long long fyp = fx_flux(L[LI], lc, K[WI], kc);
+      const long long fym = fx_flux(lc, L[-LI], kc, K[-WI]);
       const long long div = (fxp - fxm) + (fyp - fym);
-      const int64_t o = (int64_t)k * sk + (int64_t)(j0 + ty) * sj + (i0 + tx);
       double dv = __ll2double_rn(div);
       // dv * 2^(E - 1078) by exponent arithmetic (dv is 0 or an integer >= 1 in magnitude)
       dv = div == 0 ? 0.0 : __longlong_as_double(__double_as_longlong(dv) + ((long long)((int)E - 1078) << 52));
-      const double r = __fma_rn(-ldg(coeff + o), dv, s_raw[bf][ty + 2][tx + 2]);
-      out[(int64_t)k * osk + (int64_t)(j0 + ty) * osj + (i0 + tx)] = cvt<OutT>(r);
+      const double r = __fma_rn(-ldg(coeff + ((Off)k * (Off)sk + oin)), dv, s_raw[bf][ow]);
+      out[(Off)k * (Off)osk + oout] = cvt<OutT>(r);
     }
   }
 }
@@ -407,8 +423,13 @@ cudaError_t run_fixed(const oec_schedule& s, const Dom& d, int64_t osj, int64_t 
   const int kc = (s.k_chunk <= 0 || s.k_chunk > d.nk) ? d.nk : s.k_chunk;
   const int nkz = ceil_div(d.nk, kc);
   dim3 g(ceil_div(d.ni, TI), ceil_div(d.nj, TJ), nkz * (in1 ? 2 : 1));
-  hdiff_fixed_kernel<OutT, TI, TJ><<<g, TI * TJ, 0, st>>>(in, in1, coeff, out, out1, d.ni, d.nj, d.nk, d.sj, d.sk, osj,
-                                                          osk, kc, nkz); launched(st);
+  if (offsets_fit_int32(d))
+    hdiff_fixed_kernel<OutT, TI, TJ, int><<<g, TI * TJ, 0, st>>>(in, in1, coeff, out, out1, d.ni, d.nj, d.nk, d.sj,
+                                                                 d.sk, osj, osk, kc, nkz);
+  else
+    hdiff_fixed_kernel<OutT, TI, TJ, int64_t><<<g, TI * TJ, 0, st>>>(in, in1, coeff, out, out1, d.ni, d.nj, d.nk, d.sj,
+                                                                     d.sk, osj, osk, kc, nkz);
+  launched(st);
   return cudaGetLastError();
 }
 
