@@ -362,18 +362,28 @@ hdiff_fixed_kernel(const double* __restrict__ in0, const double* __restrict__ in
   const Off oin = (Off)(j0 + ty) * (Off)sj + (i0 + tx), oout = (Off)(j0 + ty) * (Off)osj + (i0 + tx);
   if (tid < 2) s_emax[tid] = 0u;
   __syncthreads();
+  // the window values of the next level are loaded into registers while the
+  // current level is computed
+  double nx[QW];
+  auto fetch = [&](int k) {
+    const double* pin = wcorner + (Off)k * (Off)sk;
+#pragma unroll
+    for (int q = 0; q < QW; ++q)
+      if (wok[q]) nx[q] = ldg(pin + wg[q]);
+  };
+  if (k0 < k1) fetch(k0);
   int bf = 0;
   for (int k = k0; k < k1; ++k, bf ^= 1) {
     // (1) raw window and its largest exponent
-    const double* pin = wcorner + (Off)k * (Off)sk;
     unsigned emax = 0u;
 #pragma unroll
     for (int q = 0; q < QW; ++q)
       if (wok[q]) {
-        const double x = ldg(pin + wg[q]);
+        const double x = nx[q];
         s_raw[bf][tid + q * NT] = x;
         emax = max(emax, (unsigned)(__double_as_longlong(x) >> 52) & 0x7FFu);
       }
+    if (k + 1 < k1) fetch(k + 1);
     emax = __reduce_max_sync(0xFFFFFFFFu, emax);
     if ((tid & 31) == 0) atomicMax(&s_emax[bf], emax);
     __syncthreads();
