@@ -155,3 +155,30 @@ def mlp_init(n_features, hidden=64, seed=SEED):
     return {"W1": he(hidden, n_features), "b1": np.zeros(hidden),
             "W2": he(hidden, hidden), "b2": np.zeros(hidden),
             "W3": he(1, hidden), "b3": np.zeros(1)}
+
+
+# input distributions of the Table II stand-ins (programs.TESTSET): uniform
+# ranges, or "kup"/"kdown" for fields that increase/decrease with k like
+# pressure and geopotential on a k-staggered grid (100 per level + U[0,10])
+TESTSET_INPUTS = {
+    "uvbke": {"uc": (-1, 1), "vc": (-1, 1), "cosa": (-0.3, 0.3), "rsina": (1.0, 1.1)},
+    "p_grad_c": {"uc": (-1, 1), "vc": (-1, 1), "delpc": (1.0, 2.0), "pkc": "kup", "gz": "kdown",
+                 "rdxc": (0.5, 1.5), "rdyc": (0.5, 1.5)},
+    "hadvuv": {n: (-1, 1) for n in ("uin", "vin", "uatupos", "vatupos", "uatvpos", "vatvpos")},
+    "fvtp2d_flux": {n: (-1, 1) for n in ("q", "crx", "cry", "xfx", "yfx", "al", "bl")},
+}
+
+
+def testset_fields(name, ni, nj, nk, h, seed=SEED):
+    """Storage arrays [k, j, i] (halo h) of one stand-in program's inputs."""
+    out = {}
+    for x, (fname, dist) in enumerate(TESTSET_INPUTS[name].items()):
+        rng = np.random.default_rng(seed + x)
+        shape = (nk + 2 * h, nj + 2 * h, ni + 2 * h)
+        if isinstance(dist, str):
+            k = np.arange(shape[0], dtype=np.float64)[:, None, None]
+            ramp = 100.0 * (k if dist == "kup" else (shape[0] - k))
+            out[fname] = ramp + rng.uniform(0.0, 10.0, shape)
+        else:
+            out[fname] = rng.uniform(dist[0], dist[1], shape)
+    return out

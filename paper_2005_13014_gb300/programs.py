@@ -69,5 +69,66 @@ output u_out, v_out
 
 BUILTIN = {"hdiff": HDIFF, "hdiff_vadvc": HDIFF_VADVC, "fastwaves": FASTWAVES}
 
+# ---- shape-matched stand-ins for more of the paper's test set (Table II) ----
+# The paper gives only the shape of its COSMO/FV3 benchmarks (applies,
+# inputs/outputs, control flow), not their formulas; these programs have the
+# listed shapes with stencils of the same kind (averaging, pressure gradients
+# over a k-staggered grid, third-order upwind advection with an `if` written
+# as select, and upwind flux selection), and run through the generic code
+# generator. They are stand-ins, not the COSMO/FV3 kernels.
+
+# uvbke (FV3): 2 applies, 4 inputs / 2 outputs
+UVBKE = """
+input uc, vc, cosa, rsina
+param dt5
+stage ub = dt5*(uc[0,-1,0] + uc - (vc[-1,0,0] + vc)*cosa)*rsina
+stage vb = dt5*(vc[-1,0,0] + vc - (uc[0,-1,0] + uc)*cosa)*rsina
+output ub, vb
+"""
+
+# p_grad_c (FV3): 3 applies, 7 inputs / 2 outputs, 3-D (k-staggered pressure)
+P_GRAD_C = """
+input uc, vc, delpc, pkc, gz, rdxc, rdyc
+param dt2
+stage wk = delpc + pkc[0,0,1] - pkc
+stage uc_out = uc + dt2*rdxc/(wk[-1,0,0] + wk)*((gz[-1,0,1] - gz)*(pkc[0,0,1] - pkc[-1,0,0]) + (gz[-1,0,0] - gz[0,0,1])*(pkc[-1,0,1] - pkc))
+stage vc_out = vc + dt2*rdyc/(wk[0,-1,0] + wk)*((gz[0,-1,1] - gz)*(pkc[0,0,1] - pkc[0,-1,0]) + (gz[0,-1,0] - gz[0,0,1])*(pkc[0,-1,1] - pkc))
+output uc_out, vc_out
+"""
+
+# hadvuv (COSMO): 8 applies, 6 inputs / 2 outputs, `if` (upwind direction)
+HADVUV = """
+input uin, vin, uatupos, vatupos, uatvpos, vatvpos
+param eddlat, eddlon
+stage axu = select(uatupos > 0.0, uatupos*(2.0*uin[1,0,0] + 3.0*uin - 6.0*uin[-1,0,0] + uin[-2,0,0]), uatupos*(-uin[2,0,0] + 6.0*uin[1,0,0] - 3.0*uin - 2.0*uin[-1,0,0]))
+stage ayu = select(vatupos > 0.0, vatupos*(2.0*uin[0,1,0] + 3.0*uin - 6.0*uin[0,-1,0] + uin[0,-2,0]), vatupos*(-uin[0,2,0] + 6.0*uin[0,1,0] - 3.0*uin - 2.0*uin[0,-1,0]))
+stage axv = select(uatvpos > 0.0, uatvpos*(2.0*vin[1,0,0] + 3.0*vin - 6.0*vin[-1,0,0] + vin[-2,0,0]), uatvpos*(-vin[2,0,0] + 6.0*vin[1,0,0] - 3.0*vin - 2.0*vin[-1,0,0]))
+stage ayv = select(vatvpos > 0.0, vatvpos*(2.0*vin[0,1,0] + 3.0*vin - 6.0*vin[0,-1,0] + vin[0,-2,0]), vatvpos*(-vin[0,2,0] + 6.0*vin[0,1,0] - 3.0*vin - 2.0*vin[0,-1,0]))
+stage advu = (eddlon*axu + eddlat*ayu)/6.0
+stage advv = (eddlon*axv + eddlat*ayv)/6.0
+stage uout = uin - advu
+stage vout = vin - advv
+output uout, vout
+"""
+
+# fvtp2d_flux (FV3): 5 applies, 7 inputs / 2 outputs, `if` (upwind side)
+FVTP2D_FLUX = """
+input q, crx, cry, xfx, yfx, al, bl
+stage qm = 0.5*(q[1,0,0] + q[-1,0,0])
+stage fx1 = select(crx > 0.0, q[-1,0,0] + (1.0 - crx)*(al - q[-1,0,0]), q + (1.0 + crx)*(al - qm))
+stage fy1 = select(cry > 0.0, q[0,-1,0] + (1.0 - cry)*(bl - q[0,-1,0]), q + (1.0 + cry)*(bl - q))
+stage fx = xfx*fx1
+stage fy = yfx*fy1
+output fx, fy
+"""
+
+# name: (text, scalar parameters, (applies, inputs, outputs) as Table II lists them)
+TESTSET = {
+    "uvbke": (UVBKE, [0.5], (2, 4, 2)),
+    "p_grad_c": (P_GRAD_C, [0.01], (3, 7, 2)),
+    "hadvuv": (HADVUV, [0.1, 0.1], (8, 6, 2)),
+    "fvtp2d_flux": (FVTP2D_FLUX, [], (5, 7, 2)),
+}
+
 # default scalar parameters of the synthetic workloads
 PARAMS = {"hdiff": [], "hdiff_vadvc": [2.0], "fastwaves": [0.5, 0.0625]}

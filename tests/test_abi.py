@@ -59,6 +59,7 @@ def _oracle_ranges(src, lb, ub):
 
 
 @pytest.mark.parametrize("src", [programs.HDIFF, programs.HDIFF_VADVC, programs.FASTWAVES]
+                         + [t[0] for t in programs.TESTSET.values()]
                          + [inputs.random_dag(s) for s in range(10000, 10030)])
 def test_input_ranges_match_oracle_shape_inference(liboec, src):
     p = _prog(src)
