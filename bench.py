@@ -523,7 +523,7 @@ def run_testset(args):
     for name, (src, params, shape) in programs.TESTSET.items():
         prog = OP.parse(src)
         f0 = inputs.testset_fields(name, *n, h)
-        for dtype in ("f32", "f64"):
+        for dtype, arith in (("f32", 0), ("f64", 0), ("f64", 1)):
             f = {k: v.astype(np.float32).astype(np.float64) for k, v in f0.items()} if dtype == "f32" else f0
             p = Program(src, dtype, generic=True)
             set_bytes = (len(prog.inputs) + len(prog.outputs)) * f[prog.inputs[0]].size * (4 if dtype == "f32" else 8)
@@ -531,9 +531,10 @@ def run_testset(args):
             sets = [([device_field(f[k], h, dtype) for k in prog.inputs],
                      [device_field(np.zeros_like(f[prog.inputs[0]]), h, dtype) for _ in prog.outputs])
                     for _ in range(n_sets)]
+            p.set_schedule(arith=arith)
             p.prepare(n, sets[0][0][0].tensor.stride(1), sets[0][0][0].tensor.stride(0))
-            times, best = p.autotune(*sets[0], (0, 0, 0), n, (h, h, h), params, reps=3)
-            cands = p.candidates()
+            cands = [dict(c, arith=arith) for c in p.candidates()]   # double-float only when asked
+            times, best = p.autotune(*sets[0], (0, 0, 0), n, (h, h, h), params, candidates=cands, reps=3)
             unfused = min(t for c, t in zip(cands, times) if c["fusion"] == 1 and t > 0)
             gstream = torch.cuda.Stream()
             graph = torch.cuda.CUDAGraph()
@@ -551,7 +552,7 @@ def run_testset(args):
             errs = [float(np.max(np.abs(o.interior((0, 0, 0), n).cpu().numpy().astype(np.float64) - ref[nm]))
                           / np.max(np.abs(ref[nm]))) for o, nm in zip(sets[n_sets - 1][1], prog.outputs)]
             nbytes = p.algorithmic_bytes((0, 0, 0), n)
-            res[f"{name}_{dtype}"] = {
+            res[f"{name}_{dtype}" + ("_df" if arith else "")] = {
                 "table_ii_shape": shape, "gpoints_per_s": pts / (ms * 1e-3) / 1e9, "ms": ms,
                 "algorithmic_GBps": nbytes / (ms * 1e-3) / 1e9,
                 "frac_of_measured_hbm": nbytes / (ms * 1e-3) / 1e9 / _peaks().get("hbm_gbs", 6800.0),

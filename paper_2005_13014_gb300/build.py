@@ -20,8 +20,24 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liboec.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc")
+GEN = os.path.join(BUILD, "gen")
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
-         "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
+         "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include"), "-I", GEN]
+
+
+def _generate():
+    """Generated includes: the double-float arithmetic (csrc/df64.cuh) as a
+    string literal, prepended by the code generator to NVRTC sources that
+    evaluate FP64 programs in double-float (NVRTC has no host headers, so the
+    #include and #pragma lines are dropped)."""
+    os.makedirs(GEN, exist_ok=True)
+    with open(os.path.join(CSRC, "df64.cuh")) as f:
+        body = "".join(l for l in f if not l.startswith("#include") and not l.startswith("#pragma once"))
+    out = os.path.join(GEN, "df64_nvrtc.inc")
+    text = 'R"OECDF(' + body + ')OECDF"\n'
+    if not os.path.exists(out) or open(out).read() != text:
+        with open(out, "w") as f:
+            f.write(text)
 
 
 def _sources():
@@ -56,6 +72,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and up_to_date():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
+    _generate()
     srcs = _sources()
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), max(2, os.cpu_count() or 2))) as ex:
         objs = list(ex.map(_compile, srcs))

@@ -311,6 +311,8 @@ int oec_program_set_schedule(oec_program_t p, const oec_schedule* s) {
   if (!p || !s) return fail(OEC_ERR_INVALID_ARG, "null argument");
   std::string why;
   if (!schedule_ok(p->kind, *s, why)) return fail(OEC_ERR_UNSUPPORTED, "schedule: %s", why.c_str());
+  if (p->kind == OEC_KIND_GENERIC && s->arith == 1 && p->dtype != OEC_F64)
+    return fail(OEC_ERR_UNSUPPORTED, "schedule: double-float generated kernels are for FP64 programs");
   p->sched = *s;
   return OEC_OK;
 }

@@ -114,10 +114,16 @@ struct Variant {
 
 struct ShapeKey {
   int64_t ni, nj, nk, sj, sk;
+  int arith = 0;   // 1: FP64 programs evaluated in double-float
   bool operator<(const ShapeKey& o) const {
-    return std::tie(ni, nj, nk, sj, sk) < std::tie(o.ni, o.nj, o.nk, o.sj, o.sk);
+    return std::tie(ni, nj, nk, sj, sk, arith) < std::tie(o.ni, o.nj, o.nk, o.sj, o.sk, o.arith);
   }
 };
+
+// the double-float arithmetic (csrc/df64.cuh without its includes), for NVRTC
+const char* const kDf64Source =
+#include "df64_nvrtc.inc"
+    ;
 
 struct Module {
   cudaLibrary_t lib = nullptr;
@@ -188,7 +194,13 @@ struct Emitter {
 
   std::string tmpname() { return fmt("t%d", next++); }
 
+  bool df = false;   // compute type is df64 (storage binary64)
+
   std::string literal(double v) {
+    if (df) {
+      const float hi = (float)v, lo = (float)(v - (double)hi);
+      return fmt("df64{%af, %af}", hi, lo);
+    }
     return fmt("((%s)%a)", T, v);
   }
 
@@ -200,7 +212,7 @@ struct Emitter {
       if (it != load_memo.end()) return it->second;
       std::string n = tmpname();
       if (val.kind == ValueKind::Input) {
-        body += fmt("  const %s %s = __ldg(in%d + (%lldLL));\n", T, n.c_str(), val.index,
+        body += fmt("  const %s %s = cvt_in(__ldg(in%d + (%lldLL)));\n", T, n.c_str(), val.index,
                     (long long)di + (long long)dj * sh.sj + (long long)dk * sh.sk);
       } else {
         const Box& b = lay.tmp.at(v).second;
@@ -233,15 +245,15 @@ struct Emitter {
       case Op::Num: return literal(e.num);
       case Op::Acc: return value(e.ref, di + e.off[0], dj + e.off[1], dk + e.off[2]);
       case Op::Let: return lets.at(e.ref);
-      case Op::Param: return fmt("((%s)prm%d)", T, e.ref);
-      case Op::KPos: return fmt("((%s)(k + %d))", T, dk);
+      case Op::Param: return fmt("P%d", e.ref);
+      case Op::KPos: return df ? fmt("df64{(float)(k + %d), 0.0f}", dk) : fmt("((%s)(k + %d))", T, dk);
       case Op::KSize: return literal((double)sh.nk);
       default: break;
     }
     n = tmpname();
     switch (e.op) {
       case Op::Neg: body += fmt("  const %s %s = -%s;\n", T, n.c_str(), sub(e.a).c_str()); break;
-      case Op::Abs: body += fmt("  const %s %s = fabs(%s);\n", T, n.c_str(), sub(e.a).c_str()); break;
+      case Op::Abs: body += fmt("  const %s %s = cabs_(%s);\n", T, n.c_str(), sub(e.a).c_str()); break;
       case Op::Add:
       case Op::Sub:
       case Op::Mul:
@@ -254,7 +266,7 @@ struct Emitter {
       case Op::Min:
       case Op::Max: {
         std::string a = sub(e.a), b = sub(e.b);
-        body += fmt("  const %s %s = %s(%s, %s);\n", T, n.c_str(), e.op == Op::Min ? "fmin" : "fmax", a.c_str(), b.c_str());
+        body += fmt("  const %s %s = %s(%s, %s);\n", T, n.c_str(), e.op == Op::Min ? "cmin_" : "cmax_", a.c_str(), b.c_str());
         break;
       }
       case Op::Sel: {
@@ -322,6 +334,7 @@ std::string kernel_source(const Program& p, const std::vector<Box>& ranges, cons
   std::set<int> mat_except_self = v.materialised;
   for (int si : kp.stmts) mat_except_self.erase(si);
   Emitter e{p, ranges, mat_except_self, v.layout, sh, T};
+  e.df = sh.arith == 1;
   const Box& b = kp.box;
   const int64_t bni = b.hi[0] - b.lo[0], bnj = b.hi[1] - b.lo[1], bnk = b.hi[2] - b.lo[2];
   std::string src;
@@ -335,7 +348,8 @@ std::string kernel_source(const Program& p, const std::vector<Box>& ranges, cons
   src += "  const long long fo = (long long)k * " + fmt("%lldLL", (long long)sh.sk) + " + (long long)j * " +
          fmt("%lldLL", (long long)sh.sj) + " + i;\n";
   for (size_t x = 0; x < p.inputs.size(); ++x)
-    src += fmt("  const %s* __restrict__ in%zu = a.in[%zu] + fo;\n", T, x, x);
+    src += fmt("  const S_* __restrict__ in%zu = a.in[%zu] + fo;\n", x, x);
+  for (size_t x = 0; x < p.params.size(); ++x) src += fmt("  const %s P%zu = cvt_in(prm%zu);\n", T, x, x);
   for (auto& t : v.layout.tmp) {
     const Box& tb = t.second.second;
     const long long tj = tb.hi[0] - tb.lo[0], tk = tj * (tb.hi[1] - tb.lo[1]);
@@ -358,7 +372,7 @@ std::string kernel_source(const Program& p, const std::vector<Box>& ranges, cons
           if (p.outputs[o] == val) {
             e.body += fmt("  if (i >= 0 && i < %lld && j >= 0 && j < %lld && k + %d >= 0 && k + %d < %lld)\n",
                           (long long)sh.ni, (long long)sh.nj, u, u, (long long)sh.nk);
-            e.body += fmt("    a.out[%zu][fo + %lldLL] = %s;\n", o, (long long)u * sh.sk, res[r].c_str());
+            e.body += fmt("    a.out[%zu][fo + %lldLL] = cvt_out(%s);\n", o, (long long)u * sh.sk, res[r].c_str());
           }
       }
     }
@@ -370,10 +384,32 @@ std::string kernel_source(const Program& p, const std::vector<Box>& ranges, cons
 
 std::string module_source(oec_program* prog, const ShapeKey& sh, const std::vector<Box>& ranges, Module& m) {
   const Program& p = prog->ir;
-  const char* T = prog->dtype == OEC_F64 ? "double" : "float";
-  const size_t es = elem_size(prog->dtype);
-  std::string src = fmt("typedef %s T_;\n", T);
-  src += "struct Args { const T_* in[16]; T_* out[8]; char* scratch; };\n";   // layout shared with the host
+  const char* S = prog->dtype == OEC_F64 ? "double" : "float";
+  const bool df = sh.arith == 1;
+  const char* T = df ? "df64" : S;   // compute type
+  const size_t es = elem_size(prog->dtype);   // df64 pairs are 8 bytes, as binary64
+  std::string src;
+  if (df) {
+    src += kDf64Source;
+    src += "using namespace oec;\n"
+           "__device__ __forceinline__ df64 cvt_in(double x) { return df_from_double(x); }\n"
+           "__device__ __forceinline__ double cvt_out(df64 x) { return df_to_double(x); }\n"
+           "__device__ __forceinline__ bool operator<(df64 a, df64 b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }\n"
+           "__device__ __forceinline__ bool operator>(df64 a, df64 b) { return b < a; }\n"
+           "__device__ __forceinline__ bool operator<=(df64 a, df64 b) { return !(b < a); }\n"
+           "__device__ __forceinline__ bool operator>=(df64 a, df64 b) { return !(a < b); }\n"
+           "__device__ __forceinline__ df64 cabs_(df64 a) { return df_abs(a); }\n"
+           "__device__ __forceinline__ df64 cmin_(df64 a, df64 b) { return b < a ? b : a; }\n"
+           "__device__ __forceinline__ df64 cmax_(df64 a, df64 b) { return a < b ? b : a; }\n";
+  } else {
+    src += fmt("__device__ __forceinline__ %s cvt_in(%s x) { return x; }\n", S, S);
+    src += fmt("__device__ __forceinline__ %s cvt_out(%s x) { return x; }\n", S, S);
+    src += fmt("__device__ __forceinline__ %s cabs_(%s a) { return fabs(a); }\n", S, S);
+    src += fmt("__device__ __forceinline__ %s cmin_(%s a, %s b) { return fmin(a, b); }\n", S, S, S);
+    src += fmt("__device__ __forceinline__ %s cmax_(%s a, %s b) { return fmax(a, b); }\n", S, S, S);
+  }
+  src += fmt("typedef %s S_;\n", S);
+  src += "struct Args { const S_* in[16]; S_* out[8]; char* scratch; };\n";   // layout shared with the host
   for (size_t x = 0; x < p.params.size(); ++x) src += fmt("__constant__ double prm%zu;\n", x);
   for (int fusion : {OEC_FUSE_INLINE, OEC_FUSE_NONE, OEC_FUSE_PARTIAL})
     for (int unroll : {1, 2, 4}) {
@@ -568,7 +604,10 @@ bool generic_schedule_ok(const oec_schedule& s, std::string& why) {
     why = "tile_i * tile_j must be in [1, 1024]";
     return false;
   }
-  if (s.arith != 0) { why = "generated kernels use the dtype's own arithmetic (arith 0)"; return false; }
+  if (s.arith != 0 && s.arith != 1) {
+    why = "generated kernels: arith 0 (the dtype's own) or 1 (double-float, FP64 programs)";
+    return false;
+  }
   return true;
 }
 
@@ -591,7 +630,9 @@ int generic_apply(oec_program* p, const oec_field_desc* in, const oec_field_desc
       return fail(OEC_ERR_UNSUPPORTED, "generated kernels need 3-D fields with equal j/k strides (field %d differs)", x);
   }
   if (n_in > 16 || n_out > 8) return fail(OEC_ERR_UNSUPPORTED, "at most 16 inputs and 8 outputs");
-  const ShapeKey key{ub[0] - lb[0], ub[1] - lb[1], ub[2] - lb[2], sj, sk};
+  if (p->sched.arith == 1 && p->dtype != OEC_F64)
+    return fail(OEC_ERR_UNSUPPORTED, "double-float generated kernels are for FP64 programs");
+  const ShapeKey key{ub[0] - lb[0], ub[1] - lb[1], ub[2] - lb[2], sj, sk, p->sched.arith};
   Module* m = nullptr;
   int rc = get_module(p, key, &m);
   if (rc) return rc;
@@ -666,7 +707,8 @@ extern "C" int oec_program_prepare(oec_program_t p, const int64_t extent[3], int
   if (extent[0] < 1 || extent[1] < 1 || extent[2] < 1 || sj < extent[0] || sk < sj)
     return fail(OEC_ERR_INVALID_ARG, "bad extent or strides");
   Module* m = nullptr;
-  return get_module(p, ShapeKey{extent[0], extent[1], extent[2], sj, sk}, &m);
+  const int arith = p->dtype == OEC_F64 && p->sched.arith == 1 ? 1 : 0;
+  return get_module(p, ShapeKey{extent[0], extent[1], extent[2], sj, sk, arith}, &m);
 }
 
 extern "C" int oec_program_codegen(oec_program_t p, const int64_t extent[3], int64_t sj, int64_t sk, int compile,
@@ -677,7 +719,7 @@ extern "C" int oec_program_codegen(oec_program_t p, const int64_t extent[3], int
     if (s.kind == StmtKind::Column) return fail(OEC_ERR_UNSUPPORTED, "generated kernels do not solve columns");
   if (extent[0] < 1 || extent[1] < 1 || extent[2] < 1 || sj < extent[0] || sk < sj)
     return fail(OEC_ERR_INVALID_ARG, "bad extent or strides");
-  const ShapeKey key{extent[0], extent[1], extent[2], sj, sk};
+  const ShapeKey key{extent[0], extent[1], extent[2], sj, sk, p->dtype == OEC_F64 && p->sched.arith == 1 ? 1 : 0};
   const int64_t zlb[3] = {0, 0, 0}, zub[3] = {extent[0], extent[1], extent[2]};
   std::vector<Box> ranges;
   std::string err;

@@ -72,10 +72,14 @@ std::vector<oec_schedule> candidates(const oec_program* p) {
       }
       break;
     default:
+      // generated kernels in the dtype's own arithmetic: double-float code
+      // (arith 1) keeps ~48 bits, which a program that differences large,
+      // nearly equal values can need, so it is the caller's choice (set the
+      // schedule, or pass such candidates) and never an automatic pick
       for (int f : {OEC_FUSE_INLINE, OEC_FUSE_NONE, OEC_FUSE_PARTIAL})
         for (int u : {1, 2, 4})
-          for (auto t : {std::pair<int, int>{32, 2}, {32, 4}, {32, 8}, {64, 1}, {64, 2}, {64, 4}, {128, 1}, {128, 2},
-                         {128, 4}, {256, 1}, {256, 2}, {16, 8}})
+          for (auto t : {std::pair<int, int>{32, 2}, {32, 4}, {32, 8}, {64, 1}, {64, 2}, {64, 4}, {128, 1},
+                         {128, 2}, {128, 4}, {256, 1}, {256, 2}, {16, 8}})
             c.push_back(mk(f, OEC_STAGE_REGS, t.first, t.second, u, 0, 0));
       break;
   }

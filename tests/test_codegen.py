@@ -35,6 +35,20 @@ def test_builtin_texts_compile_generically(liboec):
     assert e.value.name == "UNSUPPORTED"
 
 
+def test_double_float_generated_source_compiles(liboec):
+    """FP64 programs with arith 1: the generated module carries the
+    double-float arithmetic and compiles with NVRTC for sm_103a."""
+    for src in (programs.TESTSET["hadvuv"][0], programs.TESTSET["p_grad_c"][0], inputs.random_dag(10001)):
+        p = _prog(src, "f64")
+        p.set_schedule(fusion=0, arith=1)
+        gen = p.generated_source((33, 17, 5), 41, 41 * 25, compile=True)
+        assert "struct df64" in gen and "cvt_in(__ldg(" in gen and "df_to_double" in gen
+    from paper_2005_13014_gb300 import _lib as L
+    with pytest.raises(L.OecError) as e:
+        _prog(inputs.random_dag(10001), "f32").set_schedule(fusion=0, arith=1)
+    assert e.value.name == "UNSUPPORTED"
+
+
 def test_injected_compile_failure(liboec, monkeypatch):
     from paper_2005_13014_gb300 import _lib as L
     monkeypatch.setenv("OEC_FAULT", "compile")

@@ -18,7 +18,7 @@ VARIANTS = [dict(fusion=f, unroll=u, tile_i=ti, tile_j=tj)
             for f in (0, 1, 2) for u in (1, 2, 4) for (ti, tj) in ((32, 4), (64, 2))]
 
 
-def _case(name, n, dtype, h=3):
+def _case(name, n, dtype, h=3, arith=0):
     from paper_2005_13014_gb300.api import Program, device_field
     src, params, _ = programs.TESTSET[name]
     prog = OP.parse(src)
@@ -39,7 +39,7 @@ def _case(name, n, dtype, h=3):
     din = [device_field(poisoned[nm], h, dtype) for nm in prog.inputs]
     errs = []
     for sched in VARIANTS:
-        p.set_schedule(**sched)
+        p.set_schedule(**sched, arith=arith)
         outs = [device_field(np.full_like(f[prog.inputs[0]], 7.0), h, dtype) for _ in prog.outputs]
         p.apply(din, outs, (0, 0, 0), n, (h, h, h), params)
         torch.cuda.synchronize()
@@ -55,10 +55,11 @@ def _case(name, n, dtype, h=3):
     return max(errs)
 
 
-@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("dtype,arith", [("f32", 0), ("f64", 0), ("f64", 1)])
 @pytest.mark.parametrize("name", list(programs.TESTSET))
-def test_testset_ragged(name, dtype):
-    assert _case(name, (37, 29, 7), dtype) <= TOL[dtype]
+def test_testset_ragged(name, dtype, arith):
+    """arith 1: the FP64 program evaluated in generated double-float code."""
+    assert _case(name, (37, 29, 7), dtype, arith=arith) <= TOL[dtype]
 
 
 @pytest.mark.parametrize("name", list(programs.TESTSET))
