@@ -46,7 +46,7 @@ extern "C" {
 #define OEC_ERR_HALO (-4)          /* inferred input range exceeds the caller's halo      */
 #define OEC_ERR_ALIAS (-5)         /* an output range overlaps an input or other output   */
 #define OEC_ERR_DTYPE (-6)         /* field element type differs from the program's       */
-#define OEC_ERR_UNSUPPORTED (-7)   /* valid request this build cannot run                 */
+#define OEC_ERR_UNSUPPORTED (-7)   /* valid request the library cannot run                */
 #define OEC_ERR_COMPILE (-8)       /* run-time compilation of a generated kernel failed    */
 #define OEC_ERR_CUDA (-9)          /* a CUDA runtime call failed                          */
 #define OEC_ERR_TIMEOUT (-10)      /* a bounded device-side wait gave up                  */

@@ -349,7 +349,7 @@ std::string kernel_source(const Program& p, const std::vector<Box>& ranges, cons
          fmt("%lldLL", (long long)sh.sj) + " + i;\n";
   for (size_t x = 0; x < p.inputs.size(); ++x)
     src += fmt("  const S_* __restrict__ in%zu = a.in[%zu] + fo;\n", x, x);
-  for (size_t x = 0; x < p.params.size(); ++x) src += fmt("  const %s P%zu = cvt_in(prm%zu);\n", T, x, x);
+  for (size_t x = 0; x < p.params.size(); ++x) src += fmt("  const %s P%zu = cvt_in(a.prm[%zu]);\n", T, x, x);
   for (auto& t : v.layout.tmp) {
     const Box& tb = t.second.second;
     const long long tj = tb.hi[0] - tb.lo[0], tk = tj * (tb.hi[1] - tb.lo[1]);
@@ -409,8 +409,9 @@ std::string module_source(oec_program* prog, const ShapeKey& sh, const std::vect
     src += fmt("__device__ __forceinline__ %s cmax_(%s a, %s b) { return fmax(a, b); }\n", S, S, S);
   }
   src += fmt("typedef %s S_;\n", S);
-  src += "struct Args { const S_* in[16]; S_* out[8]; char* scratch; };\n";   // layout shared with the host
-  for (size_t x = 0; x < p.params.size(); ++x) src += fmt("__constant__ double prm%zu;\n", x);
+  // layout shared with the host; the scalar parameters travel by value with
+  // every launch (a launch captured into a CUDA graph keeps its own values)
+  src += "struct Args { const S_* in[16]; S_* out[8]; char* scratch; double prm[16]; };\n";
   for (int fusion : {OEC_FUSE_INLINE, OEC_FUSE_NONE, OEC_FUSE_PARTIAL})
     for (int unroll : {1, 2, 4}) {
       Variant v = plan_variant(p, ranges, sh, fusion, unroll, es);
@@ -639,22 +640,14 @@ int generic_apply(oec_program* p, const oec_field_desc* in, const oec_field_desc
   const Variant& v = m->variants.at({p->sched.fusion, p->sched.unroll});
   rc = ensure_scratch(p, v.layout.bytes);
   if (rc) return rc;
-  // parameters live in __constant__ memory of the module
-  for (size_t x = 0; x < ir.params.size(); ++x) {
-    char nm[32];
-    std::snprintf(nm, sizeof nm, "prm%zu", x);
-    void* dptr = nullptr;
-    size_t bytes = 0;
-    cudaError_t e = cudaLibraryGetGlobal(&dptr, &bytes, m->lib, nm);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaLibraryGetGlobal");
-    e = cudaMemcpyAsync(dptr, &params[x], sizeof(double), cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return cuda_fail(e, "parameter upload");
-  }
-  struct Args {
+  if (ir.params.size() > 16) return fail(OEC_ERR_UNSUPPORTED, "at most 16 scalar parameters");
+  struct Args {   // the generated kernels' argument, passed by value
     const void* in[16];
     void* out[8];
     char* scratch;
+    double prm[16];
   } args{};
+  for (size_t x = 0; x < ir.params.size(); ++x) args.prm[x] = params[x];
   auto base_at = [&](const oec_field_desc& f) {
     int64_t off = 0;
     for (int d = 0; d < 3; ++d) off += (f.origin[d] + lb[d]) * f.stride[d];

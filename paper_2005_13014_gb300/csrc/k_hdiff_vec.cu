@@ -327,7 +327,7 @@ hdiff_tma_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant_
   }
 }
 
-// cuTensorMapEncodeTiled from the driver, looked up once
+// cuTensorMapEncodeTiled from the CUDA driver API, looked up once
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   static std::once_flag once;

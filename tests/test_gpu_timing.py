@@ -78,3 +78,35 @@ def test_bound_apply_matches_apply():
     torch.cuda.synchronize()
     assert torch.equal(a[0].interior((0, 0, 0), n), b[0].interior((0, 0, 0), n))
     assert p.launch_count() == 1
+
+
+def test_captured_generated_launch_keeps_its_parameters():
+    """A generated program's scalar parameters travel with each launch: a
+    CUDA graph captured with one value replays that value after the host
+    array is gone and after applies with other values."""
+    import gc
+    from paper_2005_13014_gb300.api import Program
+    src = programs.TESTSET["p_grad_c"][0]
+    p = Program(src, "f64", generic=True)
+    p.set_schedule(fusion=0)
+    n, h = (40, 24, 6), 3
+    f = inputs.testset_fields("p_grad_c", *n, h)
+    from paper_2005_13014_gb300.api import device_field
+    din = [device_field(f[k], h, "f64") for k in inputs.TESTSET_INPUTS["p_grad_c"]]
+    outs = {x: [device_field(np.zeros_like(f["uc"]), h, "f64") for _ in range(2)] for x in "abc"}
+    p.apply(din, outs["a"], (0, 0, 0), n, (h, h, h), [0.01])
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        p.apply(din, outs["b"], (0, 0, 0), n, (h, h, h), [0.01], stream=s)
+    p.apply(din, outs["c"], (0, 0, 0), n, (h, h, h), [0.5])
+    gc.collect()
+    junk = [np.full(1024, 7.0) for _ in range(64)]   # reuse freed host memory
+    with torch.cuda.stream(s):
+        g.replay()
+    torch.cuda.synchronize()
+    for x in range(2):
+        a, b, c = (outs[y][x].interior((0, 0, 0), n) for y in "abc")
+        assert torch.equal(a, b)
+        assert not torch.equal(a, c)
+    del junk
