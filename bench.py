@@ -580,9 +580,9 @@ def run_testset(args):
 
 
 def run_ensemble(args):
-    """32 uneven hdiff+vadvc members, FP32: one persistent launch replayed from
-    a CUDA graph (tile/arith picked by timing) vs 32 separate launches, plain
-    and graph-captured."""
+    """32 uneven hdiff+vadvc members, FP32: one batch graph (fused: one
+    persistent launch; staged: concurrent per-member chains; form, tile and
+    arith picked by timing) vs 32 separate applies, plain and graph-captured."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -601,13 +601,12 @@ def run_ensemble(args):
     prog = Program(programs.HDIFF_VADVC, "f32")
     tune = {}
     best = None
-    for c in prog.candidates():
-        if c["fusion"] != 0:
-            continue
+    for c in prog.candidates():   # fused (one persistent launch) and staged (concurrent member chains)
         prog.set_schedule(**c)
         b = Batch(prog, members, [2.0])
         ms = _timed(lambda _: b.apply(), 5, 2, stream)
-        tune[f"{c['tile_i']}x{c['tile_j']}_arith{c['arith']}"] = ms
+        form = "fused" if c["fusion"] == 0 else f"staged_kc{c['k_chunk']}"
+        tune[f"{form}_{c['tile_i']}x{c['tile_j']}_arith{c['arith']}"] = ms
         if best is None or ms < best[0]:
             best = (ms, c)
         del b
@@ -627,6 +626,7 @@ def run_ensemble(args):
         separate()
     ms_sep_graph = _timed(lambda _: g.replay(), args.steps, 3, torch.cuda.current_stream())
     out = {"workload": "ensemble of 32 hdiff+vadvc members, FP32, halo 3", "members": shapes, "points": pts,
+           "form": "fused persistent launch" if best[1]["fusion"] == 0 else "staged: concurrent member chains",
            "schedule": best[1], "tuning_ms": tune,
            "batched_graph": {"ms": ms_graph, "gpoints_per_s": pts / ms_graph / 1e6},
            "batched_direct": {"ms": ms_direct, "gpoints_per_s": pts / ms_direct / 1e6},

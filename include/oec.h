@@ -342,14 +342,18 @@ typedef struct oec_batch_member {
 } oec_batch_member;
 
 /*
- * Prepare one launch over an ensemble of domains of different sizes (currently
- * hdiff+vadvc programs): every member is validated as oec_program_apply would
- * validate it, the members' column tiles become one work list (tallest
- * columns first), and a persistent kernel - one CTA per resident slot on every
- * SM - pulls (member, tile) items from an atomic counter and runs the fused
- * column sweep with the program's current schedule (tile shape, arithmetic).
- * The counter reset and the launch are captured once into a CUDA graph.
- * Device memory: the work table, the counter and per-CTA scratch, owned by the
+ * Prepare one graph over an ensemble of domains of different sizes (currently
+ * hdiff+vadvc programs); every member is validated as oec_program_apply would
+ * validate it. With a fused schedule (OEC_FUSE_INLINE) the members' column
+ * tiles become one work list (tallest columns first), and a persistent kernel
+ * - one CTA per resident slot on every SM - pulls (member, tile) items from an
+ * atomic counter and runs the fused column sweep with the program's tile
+ * shape and arithmetic; the counter reset and the launch are captured into
+ * the graph. With a staged schedule (OEC_FUSE_NONE) every member's producer
+ * and column-sweep launches form an independent branch of the graph (members
+ * on up to 16 forked streams, largest first to the least-loaded one), so the
+ * members' sweeps run concurrently. Device memory: the work table, the
+ * counter and per-CTA scratch, or each staged member's scratch, owned by the
  * batch. The program and every member's fields must outlive the batch.
  * params: the program's scalars. Errors: as oec_program_apply, and
  * OEC_ERR_UNSUPPORTED for other program kinds.

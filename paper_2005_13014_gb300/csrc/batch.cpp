@@ -1,5 +1,10 @@
-// batch.cpp - ensembles of domains in one persistent launch, captured into a
-// CUDA graph (include/oec.h, oec_batch_*).
+// batch.cpp - ensembles of domains, captured into one CUDA graph
+// (include/oec.h, oec_batch_*). Fused schedules: one persistent launch over
+// the (member, tile) work items of every member. Staged schedules: every
+// member's producer + column-sweep chain is an independent branch of the
+// graph (members spread over up to 16 forked streams), so the members' column
+// sweeps - latency-bound, with few warps each - run concurrently and fill the
+// GPU together.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -11,9 +16,21 @@
 #include "api_internal.h"
 #include "kernels.h"
 
+struct StagedMember {
+  oec::Dom d{};
+  const void *u = nullptr, *v = nullptr, *w = nullptr, *coeff = nullptr;
+  void *uo = nullptr, *vo = nullptr;
+  size_t scratch_off = 0;
+  int stream = 0;
+};
+
 struct oec_batch {
   int dtype = OEC_F64;
   oec_schedule sched{};
+  bool staged = false;
+  std::vector<StagedMember> staged_members;
+  double dtr = 0.0;
+  int n_streams = 0;
   oec::HVBatchLaunch launch{};
   oec::HVMember* d_members = nullptr;
   int* d_counter = nullptr;
@@ -46,6 +63,80 @@ char* base_at(const oec_field_desc& f, const int64_t lb[3], size_t es) {
   return (char*)f.data + off * (int64_t)es;
 }
 
+
+// Staged batch: per member its own scratch; the chains are captured on up to
+// 16 streams forked from (and joined back into) the capture stream, members
+// assigned largest first to the least-loaded stream.
+cudaError_t record_staged(const oec_batch* b, char* scratch, const std::vector<cudaStream_t>& streams) {
+  cudaError_t e = cudaSuccess;
+  for (const StagedMember& m : b->staged_members) {
+    cudaError_t r = oec::hdiff_vadvc_launch(b->sched, b->dtype, m.d, m.u, m.v, m.w, m.coeff, m.uo, m.vo, b->dtr,
+                                            scratch + m.scratch_off, streams[m.stream % streams.size()]);
+    if (e == cudaSuccess) e = r;
+  }
+  return e;
+}
+
+int create_staged(oec_program* p, const std::vector<oec::HVMember>& tab, double dtr, oec_batch_t* out) {
+  using namespace oec;
+  oec_batch* b = new (std::nothrow) oec_batch();
+  if (!b) return fail(OEC_ERR_INVALID_ARG, "out of host memory");
+  b->dtype = p->dtype;
+  b->sched = p->sched;
+  b->staged = true;
+  b->dtr = dtr;
+  cudaGetDevice(&b->dev);
+  b->n_streams = (int)std::min<size_t>(tab.size(), 16);
+  std::vector<int64_t> load(b->n_streams, 0);
+  size_t off = 0;
+  for (const HVMember& h : tab) {   // tab is sorted tallest / largest first
+    StagedMember m;
+    m.d = Dom{h.ni, h.nj, h.nk, h.sj, h.sk};
+    m.u = h.u;
+    m.v = h.v;
+    m.w = h.w;
+    m.coeff = h.coeff;
+    m.uo = h.uo;
+    m.vo = h.vo;
+    m.scratch_off = off;
+    off = align_up(off + hdiff_vadvc_scratch_bytes(b->sched, b->dtype, m.d), 256);
+    m.stream = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    load[m.stream] += (int64_t)h.ni * h.nj * h.nk;
+    b->staged_members.push_back(m);
+  }
+  cudaError_t e = cudaMalloc(&b->d_scratch, std::max<size_t>(off, 256));
+  if (e != cudaSuccess) { release(b); return cuda_fail(e, "batch scratch"); }
+  cudaStream_t cap = nullptr;
+  std::vector<cudaStream_t> streams(b->n_streams, nullptr);
+  std::vector<cudaEvent_t> ev(b->n_streams + 1, nullptr);
+  e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+  for (auto& st : streams)
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  for (auto& x : ev)
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t r = cudaEventRecord(ev[0], cap);
+    for (auto& st : streams)
+      if (r == cudaSuccess) r = cudaStreamWaitEvent(st, ev[0], 0);
+    if (r == cudaSuccess) r = record_staged(b, (char*)b->d_scratch, streams);
+    for (int x = 0; x < b->n_streams && r == cudaSuccess; ++x) {
+      r = cudaEventRecord(ev[x + 1], streams[x]);
+      if (r == cudaSuccess) r = cudaStreamWaitEvent(cap, ev[x + 1], 0);
+    }
+    e = cudaStreamEndCapture(cap, &b->graph);
+    if (e == cudaSuccess) e = r;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+  for (auto& x : ev)
+    if (x) cudaEventDestroy(x);
+  for (auto& st : streams)
+    if (st) cudaStreamDestroy(st);
+  if (cap) cudaStreamDestroy(cap);
+  if (e != cudaSuccess) { release(b); return cuda_fail(e, "staged batch capture"); }
+  *out = b;
+  return OEC_OK;
+}
 }  // namespace
 
 using namespace oec;
@@ -58,7 +149,8 @@ int oec_batch_create(oec_program_t p, const oec_batch_member* members, int n, co
   if (!p || !members || n < 1 || !out) return fail(OEC_ERR_INVALID_ARG, "null argument or no members");
   *out = nullptr;
   if (p->kind != OEC_KIND_HDIFF_VADVC) return fail(OEC_ERR_UNSUPPORTED, "batches run hdiff+vadvc programs");
-  if (p->sched.fusion != OEC_FUSE_INLINE) return fail(OEC_ERR_UNSUPPORTED, "batches need a fused schedule");
+  if (p->sched.fusion != OEC_FUSE_INLINE && p->sched.fusion != OEC_FUSE_NONE)
+    return fail(OEC_ERR_UNSUPPORTED, "batches need a fused or a staged schedule");
   if (n_params != (int)p->ir.params.size() || (n_params && !params))
     return fail(OEC_ERR_INVALID_ARG, "program has %zu params, got %d", p->ir.params.size(), n_params);
   const size_t es = elem_size(p->dtype);
@@ -102,6 +194,7 @@ int oec_batch_create(oec_program_t p, const oec_batch_member* members, int n, co
     tab.push_back(h);
   }
   if (tab.empty()) return fail(OEC_ERR_INVALID_ARG, "every member has an empty domain");
+  if (s.fusion == OEC_FUSE_NONE) return create_staged(p, tab, params[0], out);
   // longest-processing-time order: tallest columns first, then larger domains
   std::stable_sort(tab.begin(), tab.end(), [](const HVMember& a, const HVMember& b) {
     if (a.nk != b.nk) return a.nk > b.nk;
@@ -165,6 +258,10 @@ int oec_batch_apply(oec_batch_t b, void* stream) {
 int oec_batch_apply_direct(oec_batch_t b, void* stream) {
   clear_error();
   if (!b) return fail(OEC_ERR_INVALID_ARG, "null batch");
+  if (b->staged) {   // the same launches, one after another on the caller's stream
+    cudaError_t e = record_staged(b, (char*)b->d_scratch, std::vector<cudaStream_t>{(cudaStream_t)stream});
+    return e == cudaSuccess ? OEC_OK : cuda_fail(e, "batch launch");
+  }
   cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), (cudaStream_t)stream);
   if (e == cudaSuccess) e = hdiff_vadvc_batch_launch(b->sched, b->dtype, b->launch, (cudaStream_t)stream);
   return e == cudaSuccess ? OEC_OK : cuda_fail(e, "batch launch");
@@ -173,8 +270,8 @@ int oec_batch_apply_direct(oec_batch_t b, void* stream) {
 int oec_batch_info(oec_batch_t b, int* n_items, int* n_ctas) {
   clear_error();
   if (!b || !n_items || !n_ctas) return fail(OEC_ERR_INVALID_ARG, "null argument");
-  *n_items = b->launch.total_items;
-  *n_ctas = b->launch.grid;
+  *n_items = b->staged ? (int)b->staged_members.size() : b->launch.total_items;
+  *n_ctas = b->staged ? b->n_streams : b->launch.grid;
   return OEC_OK;
 }
 

@@ -65,6 +65,36 @@ def test_batch_equals_single_applies_and_oracle(dtype, arith, tile):
             assert np.all(full[mask] == 3.0)
 
 
+@pytest.mark.parametrize("dtype,arith", [("f64", 2), ("f64", 1), ("f32", 1), ("f32", 0)])
+def test_staged_batch_equals_single_applies(dtype, arith):
+    """Staged batches: every member's chain is a graph branch running the same
+    kernels as a single apply, so the bits agree; graph and direct agree."""
+    from paper_2005_13014_gb300.api import Batch, Program, device_field
+    h = 3
+    prog = Program(programs.HDIFF_VADVC, dtype)
+    prog.set_schedule(fusion=1, tile_i=32, tile_j=8, k_chunk=4, arith=arith)
+    ms = _members(dtype, h)
+    batch = Batch(prog, [(d, o, (0, 0, 0), n, (h, h, h)) for (_, d, o, n) in ms], [2.0])
+    assert batch.n_items == len(SHAPES)
+    for graph in (True, False):
+        for (_, _, o, _) in ms:
+            for t in o:
+                t.tensor.fill_(3.0)
+        batch.apply(graph=graph)
+        torch.cuda.synchronize()
+        for (f, d, o, n) in ms:
+            single = [device_field(np.full_like(f["u"], 3.0), h, dtype) for _ in range(2)]
+            prog.apply(d, single, (0, 0, 0), n, (h, h, h), [2.0])
+            torch.cuda.synchronize()
+            for a, b in zip(o, single):
+                assert torch.equal(a.tensor, b.tensor)
+            G = {k: S.Grid.storage(v, h) for k, v in f.items()}
+            ru, rv = S.hdiff_vadvc(G["u"], G["v"], G["w"], G["coeff"], (0, 0, 0), n, 2.0)
+            gu = o[0].interior((0, 0, 0), n).cpu().numpy().astype(np.float64)
+            gv = o[1].interior((0, 0, 0), n).cpu().numpy().astype(np.float64)
+            assert max(rel_err(gu, ru), rel_err(gv, rv)) <= TOL[dtype]
+
+
 def test_batch_config_ensemble_32_members_f32():
     """The 32-member ensemble of uneven domains (i, j in {64..512}, k in
     {60, 80, 137}), FP32, checked on sampled columns against the oracle."""
