@@ -601,7 +601,8 @@ def run_ensemble(args):
     prog = Program(programs.HDIFF_VADVC, "f32")
     tune = {}
     best = None
-    for c in prog.candidates():   # fused (one persistent launch) and staged (concurrent member chains)
+    cands = [json.loads(args.schedule)] if args.schedule else prog.candidates()
+    for c in cands:   # fused (one persistent launch) and staged (concurrent member chains)
         prog.set_schedule(**c)
         b = Batch(prog, members, [2.0])
         ms = _timed(lambda _: b.apply(), 5, 2, stream)

@@ -75,9 +75,13 @@ typedef struct oec_field_desc {
 typedef enum {
   OEC_FUSE_INLINE = 0,   /* all producers inlined into one kernel (paper §V-A)          */
   OEC_FUSE_NONE = 1,     /* one kernel per stage, temporaries in device memory; for
-                            hdiff+vadvc: hdiff of u and v in one kernel (tile_i x
-                            tile_j, k_chunk levels per CTA when they name an SMEM hdiff
-                            tile, else 64 x 4, 4 levels), then the column sweep      */
+                            hdiff+vadvc: hdiff of u and v in one kernel, then the
+                            column sweep. The hdiff kernel: FP32 fields with
+                            OEC_STAGE_REGS staging run the REGS kernel (tile_i x
+                            tile_j/unroll threads, k_chunk levels per CTA; else
+                            64 x 4, unroll 1); otherwise the SMEM tile kernel (tile_i
+                            x tile_j, k_chunk levels when they name an SMEM hdiff
+                            tile, else 64 x 4, 4 levels; FP64 arith 2: fixed point) */
   OEC_FUSE_PARTIAL = 2   /* generated programs: stages read at more than two offsets are
                             materialised, the rest inlined                              */
 } oec_fusion;
@@ -105,7 +109,8 @@ typedef enum {
 
 typedef struct oec_schedule {
   int32_t fusion;        /* oec_fusion                                                   */
-  int32_t staging;       /* oec_staging (fused kernels only)                             */
+  int32_t staging;       /* oec_staging (fused kernels; and the FP32 hdiff+vadvc
+                            producer of OEC_FUSE_NONE)                                  */
   int32_t tile_i;        /* CTA tile extent along i, in points (16..256)                 */
   int32_t tile_j;        /* CTA tile extent along j, in points (1..16)                   */
   int32_t unroll;        /* points per thread along the unroll dimension (1, 2 or 4)     */

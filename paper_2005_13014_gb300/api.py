@@ -151,8 +151,7 @@ class Program:
     def schedule(self) -> dict:
         s = L.Schedule()
         L.check(L.lib().oec_program_get_schedule(self._h, C.byref(s)))
-        return {"fusion": s.fusion, "staging": s.staging, "tile_i": s.tile_i, "tile_j": s.tile_j,
-                "unroll": s.unroll, "k_chunk": s.k_chunk, "arith": s.arith}
+        return schedule_dict(s)
 
     def set_schedule(self, fusion=0, staging=0, tile_i=64, tile_j=4, unroll=1, k_chunk=0, arith=0):
         s = L.Schedule(fusion, staging, tile_i, tile_j, unroll, k_chunk, arith)

@@ -16,7 +16,8 @@
 
 namespace oec {
 
-struct df64 {
+// 8-byte aligned, so a pair moves with one 64-bit load or store
+struct __align__(8) df64 {
   float hi, lo;
 };
 

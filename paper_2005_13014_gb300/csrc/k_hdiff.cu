@@ -90,17 +90,29 @@ struct RegsWin {
   S cf[U];               // coeff (i, jb .. jb+U-1)
 };
 
-template <class P, int U, class Off, int NB>
+//
+// SEP: the output has its own layout (pitch osj, plane osk) and type OutT, and
+// grid z covers two fields (z < nkz: in -> out, else in1 -> out1), as the
+// producer of the staged hdiff+vadvc form uses it; otherwise out shares the
+// input's layout.
+template <class P, int U, class Off, int NB, class OutT, bool SEP>
 __global__ void hdiff_regs_kernel(const typename P::S* __restrict__ in, const typename P::S* __restrict__ coeff,
-                                  typename P::S* __restrict__ out, int ni, int nj, int nk, int64_t sj, int64_t sk,
-                                  int kchunk) {
+                                  OutT* __restrict__ out, int ni, int nj, int nk, int64_t sj, int64_t sk,
+                                  int kchunk, int64_t osj, int64_t osk, int nkz, const typename P::S* __restrict__ in1,
+                                  OutT* __restrict__ out1) {
   typedef typename P::S S;
   typedef typename P::C C;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int jb = (blockIdx.y * blockDim.y + threadIdx.y) * U;
   if (i >= ni || jb >= nj) return;
   const int jmax = nj + 1 - jb;          // last row offset inside the halo-2 window
-  const int k0 = blockIdx.z * kchunk, k1 = min(nk, k0 + kchunk);
+  int z = blockIdx.z;
+  if (SEP && z >= nkz) {
+    in = in1;
+    out = out1;
+    z -= nkz;
+  }
+  const int k0 = z * kchunk, k1 = min(nk, k0 + kchunk);
   // element offsets from the level's (i, jb): rows jb-2 .. jb+U+1 (clamped to
   // the window), computed once; the level offset advances by sk
   Off roff[U + 4];
@@ -108,6 +120,8 @@ __global__ void hdiff_regs_kernel(const typename P::S* __restrict__ in, const ty
   for (int x = 0; x < U + 4; ++x) roff[x] = (Off)min(x - 2, jmax) * (Off)sj;
   const Off ksk = (Off)sk;
   Off lev = (Off)k0 * ksk + (Off)jb * (Off)sj + i;
+  const Off oksk = (Off)osk;
+  Off olev = (Off)k0 * oksk + (Off)jb * (Off)osj + i;   // SEP output offset of the level
   auto load = [&](RegsWin<S, U>& w, Off l) {
 #pragma unroll
     for (int x = 0; x < U + 4; ++x) w.c0[x] = ldg(in + (l + roff[x]));
@@ -130,7 +144,7 @@ __global__ void hdiff_regs_kernel(const typename P::S* __restrict__ in, const ty
 #pragma unroll
   for (int x = 0; x < NB; ++x)
     if (k0 + x < k1) load(win[x], lev + (Off)x * ksk);
-  for (int k = k0; k < k1; k += NB, lev += (Off)NB * ksk) {
+  for (int k = k0; k < k1; k += NB, lev += (Off)NB * ksk, olev += (Off)NB * oksk) {
 #pragma unroll
     for (int x = 0; x < NB; ++x) {
       if (k + x >= k1) break;
@@ -160,7 +174,8 @@ __global__ void hdiff_regs_kernel(const typename P::S* __restrict__ in, const ty
           const C flx_m = hflux(lc[r + 1], lw[r], c, at(-1, r));
           const C fly = hflux(lc[r + 2], lc[r + 1], at(0, r + 1), c);
           const C fly_m = hflux(lc[r + 1], lc[r], c, at(0, r - 1));
-          out[lx + roff[r + 2]] = cvt<S>(hout(c, cvt<C>(cur.cf[r]), flx, flx_m, fly, fly_m));
+          const Off o = SEP ? olev + (Off)x * oksk + (Off)r * (Off)osj : lx + roff[r + 2];
+          out[o] = cvt<OutT>(hout(c, cvt<C>(cur.cf[r]), flx, flx_m, fly, fly_m));
         }
       }
       if (k + x + NB < k1) load(win[x], lx + (Off)NB * ksk);
@@ -554,10 +569,32 @@ cudaError_t run_regs(const oec_schedule& s, const Dom& d, const typename P::S* i
   const int kc = kchunk_of(s, d.nk);
   dim3 b(s.tile_i, s.tile_j / U);
   dim3 g(ceil_div(d.ni, s.tile_i), ceil_div(d.nj, s.tile_j), ceil_div(d.nk, kc));
+  typedef typename P::S S;
   if (offsets_fit_int32(d))
-    hdiff_regs_kernel<P, U, int, REGS_NB><<<g, b, 0, st>>>(in, coeff, out, d.ni, d.nj, d.nk, d.sj, d.sk, kc);
+    hdiff_regs_kernel<P, U, int, REGS_NB, S, false><<<g, b, 0, st>>>(in, coeff, out, d.ni, d.nj, d.nk, d.sj, d.sk, kc,
+                                                                     0, 0, 0, nullptr, nullptr);
   else
-    hdiff_regs_kernel<P, U, int64_t, REGS_NB><<<g, b, 0, st>>>(in, coeff, out, d.ni, d.nj, d.nk, d.sj, d.sk, kc);
+    hdiff_regs_kernel<P, U, int64_t, REGS_NB, S, false><<<g, b, 0, st>>>(in, coeff, out, d.ni, d.nj, d.nk, d.sj, d.sk,
+                                                                         kc, 0, 0, 0, nullptr, nullptr);
+  launched(st);
+  return cudaGetLastError();
+}
+
+// the REGS kernel as the staged producer: fields in0 -> out0 and in1 -> out1
+// (domain layout osj, osk, type OutT) in one launch
+template <class P, int U, class OutT>
+cudaError_t run_regs_to(const oec_schedule& s, const Dom& d, int64_t osj, int64_t osk, const typename P::S* in0,
+                        const typename P::S* in1, const typename P::S* coeff, OutT* out0, OutT* out1,
+                        cudaStream_t st) {
+  const int kc = kchunk_of(s, d.nk), nkz = ceil_div(d.nk, kc);
+  dim3 b(s.tile_i, s.tile_j / U);
+  dim3 g(ceil_div(d.ni, s.tile_i), ceil_div(d.nj, s.tile_j), 2 * nkz);
+  if (offsets_fit_int32(d))
+    hdiff_regs_kernel<P, U, int, REGS_NB, OutT, true><<<g, b, 0, st>>>(in0, coeff, out0, d.ni, d.nj, d.nk, d.sj,
+                                                                       d.sk, kc, osj, osk, nkz, in1, out1);
+  else
+    hdiff_regs_kernel<P, U, int64_t, REGS_NB, OutT, true><<<g, b, 0, st>>>(in0, coeff, out0, d.ni, d.nj, d.nk, d.sj,
+                                                                           d.sk, kc, osj, osk, nkz, in1, out1);
   launched(st);
   return cudaGetLastError();
 }
@@ -654,8 +691,32 @@ cudaError_t hdiff_launch(const oec_schedule& s, int dtype, const Dom& d, const v
 
 cudaError_t hdiff_to_compute(const oec_schedule& sched, int dtype, const Dom& d, const void* in0, const void* in1,
                              const void* coeff, void* out0, void* out1, cudaStream_t st) {
-  // the schedule's tile and k_chunk pick the producer's tile when they name
-  // one of its tiles; otherwise 64 x 4, 4 levels per CTA
+  const int64_t osj = d.ni, osk = (int64_t)d.ni * d.nj;
+  // FP32 fields with REGS staging: the REGS kernel (CTA tile_i x tile_j/unroll
+  // threads, unroll rows per thread, k_chunk levels per CTA); a tile it cannot
+  // run falls back to 64 x 4, unroll 1
+  if (dtype == OEC_F32 && sched.staging == OEC_STAGE_REGS) {
+    oec_schedule s = sched;
+    const int u = s.unroll;
+    const bool ok = (u == 1 || u == 2 || u == 4) && s.tile_i >= 16 && s.tile_i <= 256 && s.tile_i % 16 == 0 &&
+                    s.tile_j >= u && s.tile_j % u == 0 && s.tile_j <= 64 && s.tile_i * (s.tile_j / u) <= 1024;
+    if (!ok) {
+      s.tile_i = 64;
+      s.tile_j = 4;
+      s.unroll = 1;
+    }
+    const float* i0 = (const float*)in0;
+    const float* i1 = (const float*)in1;
+    const float* cf = (const float*)coeff;
+    switch (s.unroll) {
+      case 2: return run_regs_to<P32, 2, float>(s, d, osj, osk, i0, i1, cf, (float*)out0, (float*)out1, st);
+      case 4: return run_regs_to<P32, 4, float>(s, d, osj, osk, i0, i1, cf, (float*)out0, (float*)out1, st);
+      default: return run_regs_to<P32, 1, float>(s, d, osj, osk, i0, i1, cf, (float*)out0, (float*)out1, st);
+    }
+  }
+  // otherwise the SMEM tile kernel (FP64: fixed point for arith 2): the
+  // schedule's tile and k_chunk pick its tile when they name one of its tiles;
+  // otherwise 64 x 4, 4 levels per CTA
   oec_schedule s = sched;
   bool known = false;
 #define X(a, b) known = known || (s.tile_i == a && s.tile_j == b);
@@ -666,7 +727,6 @@ cudaError_t hdiff_to_compute(const oec_schedule& sched, int dtype, const Dom& d,
     s.tile_j = 4;
   }
   if (s.k_chunk <= 0) s.k_chunk = 4;
-  const int64_t osj = d.ni, osk = (int64_t)d.ni * d.nj;
 #define X(a, b)                                                                                                  \
   if (s.tile_i == a && s.tile_j == b) {                                                                          \
     if (dtype == OEC_F64) {                                                                                      \

@@ -20,6 +20,9 @@
 // copies.
 // Batched form: a persistent kernel pulls (member, tile) items of an ensemble
 // of domains from an atomic counter and runs the fused tile sweep on each.
+#include <cmath>
+#include <type_traits>
+
 #include "arith.cuh"
 #include "kcommon.cuh"
 #include "kernels.h"
@@ -354,8 +357,10 @@ template <> __device__ __forceinline__ df64 wsum<df64, double>(double a, double 
 // row s+1 is built while row s is eliminated. g, e_u, e_v go to scratch
 // ([k][g, e_u, e_v][column]) and come back through the same kind of ring for
 // the back substitution. Each thread reads only ring entries its own copies
-// wrote; the one barrier separates the two uses of the ring.
-template <class P, int NC, int DEPTH>
+// wrote; the one barrier separates the two uses of the ring. DTR_P2: dtr is a
+// power of two in float range, so dtr * phi is an exact scaling (for
+// double-float, two float multiplies instead of a pair product).
+template <class P, int NC, int DEPTH, bool DTR_P2>
 __global__ void __launch_bounds__(2 * NC) hv_thomas_kernel(HV<typename P::S> p, const typename P::C* __restrict__ ud,
                                                            const typename P::C* __restrict__ vd, double dtr_d,
                                                            typename P::R* __restrict__ scr) {
@@ -379,6 +384,8 @@ __global__ void __launch_bounds__(2 * NC) hv_thomas_kernel(HV<typename P::S> p, 
   const int nk = p.nk, mid = (nk + 1) / 2;
   const int nsteps = active ? (down ? nk - mid : mid) : 0;
   const C dtr = cvt<C>(dtr_d);
+  const float dtr_f = (float)dtr_d;
+  auto times_dtr = [&](C x) { return DTR_P2 ? mul_p2(x, dtr_f) : dtr * x; };
   const int64_t cbase = (int64_t)j * p.sj + i;
   const S* __restrict__ wcol = p.w + cbase;
   // level of step s, and the level whose w gives the edge behind step s
@@ -386,7 +393,7 @@ __global__ void __launch_bounds__(2 * NC) hv_thomas_kernel(HV<typename P::S> p, 
   auto lev = [&](int st) { return down ? nk - 1 - st : st; };
   auto wlev = [&](int st) { return down ? nk - st : st; };
   auto issue = [&](int st) {
-    if (st <= nsteps) {
+    if (active && st <= nsteps) {
       const int sl = st % DEPTH, k = lev(st), kw = wlev(st);
       if (k >= 0 && k < nk) {
         const int64_t o = (int64_t)k * ncol + col;
@@ -425,8 +432,8 @@ __global__ void __launch_bounds__(2 * NC) hv_thomas_kernel(HV<typename P::S> p, 
       gamma = mul_p2(wfa, 0.25f * sgn);
     }
     b = addf(dtr, abs_(gamma));
-    ru = dtr * u0;
-    rv = dtr * v0;
+    ru = times_dtr(u0);
+    rv = times_dtr(v0);
     if (ahead0) {
       ru = subf(ru, mul_p2(gamma * du0, 0.5f));
       rv = subf(rv, mul_p2(gamma * dv0, 0.5f));
@@ -460,7 +467,7 @@ __global__ void __launch_bounds__(2 * NC) hv_thomas_kernel(HV<typename P::S> p, 
     beta = mul_p2(wfa, -0.25f * sgn);
     gamma = hi ? mul_p2(wf2, 0.25f * sgn) : zero_<C>();
     b = addf(addf(dtr, abs_(beta)), abs_(gamma));
-    const C tu = dtr * u1, tv = dtr * v1;
+    const C tu = times_dtr(u1), tv = times_dtr(v1);
     if (hi) {
       ru = subf(tu, mul_p2(addf(beta * (-du0), gamma * du1), 0.5f));
       rv = subf(tv, mul_p2(addf(beta * (-dv0), gamma * dv1), 0.5f));
@@ -648,9 +655,17 @@ cudaError_t run(const oec_schedule& s, int dtype, const Dom& d, const HV<typenam
     if (e != cudaSuccess) return e;
     constexpr int NC = 32, DEPTH = 16;   // 64 threads: two warps of 16 columns
     const int64_t ncol = (int64_t)d.ni * d.nj;
-    hv_thomas_kernel<P, NC, DEPTH><<<(unsigned)((ncol + NC - 1) / NC), 2 * NC, 0, st>>>(p, ud, vd, dtr,
-                                                                                   (typename P::R*)(scratch + l.thomas));
-                                                                                   launched(st);
+    const unsigned grid = (unsigned)((ncol + NC - 1) / NC);
+    typename P::R* scr = (typename P::R*)(scratch + l.thomas);
+    int e2 = 0;
+    const bool p2 = std::frexp(dtr, &e2) == 0.5 && e2 > -120 && e2 < 120;
+    if constexpr (std::is_same<C, df64>::value) {
+      if (p2) {
+        hv_thomas_kernel<P, NC, DEPTH, true><<<grid, 2 * NC, 0, st>>>(p, ud, vd, dtr, scr); launched(st);
+        return cudaGetLastError();
+      }
+    }
+    hv_thomas_kernel<P, NC, DEPTH, false><<<grid, 2 * NC, 0, st>>>(p, ud, vd, dtr, scr); launched(st);
     return cudaGetLastError();
   }
   return dispatch_fused<P>(s, d, p, dtr, scratch + l.thomas, st);

@@ -50,10 +50,20 @@ std::vector<oec_schedule> candidates(const oec_program* p) {
       }
       break;
     case OEC_KIND_HDIFF_VADVC:
-      // staged: the tile is the hdiff producer's
-      for (int a : p->dtype == OEC_F64 ? std::vector<int>{2, 1, 0} : std::vector<int>{1, 0})
-        for (auto t : {std::pair<int, int>{32, 4}, {32, 8}, {64, 4}, {64, 8}, {128, 4}})
-          for (int kc : {4, 8}) c.push_back(mk(OEC_FUSE_NONE, 0, t.first, t.second, 1, kc, a));
+      // staged: the tile is the hdiff producer's (FP64: the SMEM tile kernel,
+      // staging unused; FP32: the REGS kernel, and the SMEM one at 64 x 4)
+      if (p->dtype == OEC_F64) {
+        for (int a : {2, 1, 0})
+          for (auto t : {std::pair<int, int>{32, 4}, {32, 8}, {64, 4}, {64, 8}, {128, 4}})
+            for (int kc : {4, 8}) c.push_back(mk(OEC_FUSE_NONE, 0, t.first, t.second, 1, kc, a));
+      } else {
+        for (int a : {1, 0}) {
+          for (auto t : {std::pair<int, int>{32, 4}, {32, 8}, {64, 4}, {128, 2}})
+            for (int u : {1, 2})
+              for (int kc : {8, 20}) c.push_back(mk(OEC_FUSE_NONE, OEC_STAGE_REGS, t.first, t.second, u, kc, a));
+          c.push_back(mk(OEC_FUSE_NONE, OEC_STAGE_SMEM, 64, 4, 1, 4, a));
+        }
+      }
       for (int a : {0, 1})
         for (auto t : {std::pair<int, int>{16, 4}, {32, 2}, {8, 8}, {32, 4}, {8, 4}, {16, 2}})
           c.push_back(mk(OEC_FUSE_INLINE, OEC_STAGE_SMEM, t.first, t.second, 1, 0, a));

@@ -42,7 +42,7 @@ def test_double_float_generated_source_compiles(liboec):
         p = _prog(src, "f64")
         p.set_schedule(fusion=0, arith=1)
         gen = p.generated_source((33, 17, 5), 41, 41 * 25, compile=True)
-        assert "struct df64" in gen and "cvt_in(__ldg(" in gen and "df_to_double" in gen
+        assert "struct __align__(8) df64" in gen and "cvt_in(__ldg(" in gen and "df_to_double" in gen
     from paper_2005_13014_gb300 import _lib as L
     with pytest.raises(L.OecError) as e:
         _prog(inputs.random_dag(10001), "f32").set_schedule(fusion=0, arith=1)

@@ -322,3 +322,29 @@ def test_hdiff_vadvc_staged_producer_tiles(dtype, arith, tile, kc):
     the twisted column sweep behind it (ragged tiles, odd column count)."""
     sched = dict(fusion=1, tile_i=tile[0], tile_j=tile[1], k_chunk=kc, arith=arith)
     assert _hv_case((37, 23, 11), 3, dtype, sched) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("unroll", [1, 2, 4])
+@pytest.mark.parametrize("tile", [(32, 4), (32, 8), (64, 4), (128, 2), (16, 8)], ids=str)
+@pytest.mark.parametrize("arith", [0, 1])
+def test_hdiff_vadvc_f32_regs_producer(arith, tile, unroll):
+    """FP32 staged form with the REGS hdiff producer writing both fields in one
+    launch (tiles it cannot run, e.g. 128x2 at unroll 4, fall back to 64x4)."""
+    sched = dict(fusion=1, staging=0, tile_i=tile[0], tile_j=tile[1], unroll=unroll, k_chunk=3, arith=arith)
+    assert _hv_case((37, 23, 11), 3, "f32", sched) <= TOL["f32"]
+    assert _hv_case((33, 5, 2), 3, "f32", sched) <= TOL["f32"]
+
+
+@pytest.mark.parametrize("arith", [0, 1])
+def test_hdiff_vadvc_f32_smem_producer(arith):
+    sched = dict(fusion=1, staging=1, tile_i=64, tile_j=4, k_chunk=4, arith=arith)
+    assert _hv_case((37, 23, 11), 3, "f32", sched) <= TOL["f32"]
+
+
+@pytest.mark.parametrize("dtr", [2.0, 0.5, 64.0, 3.0, 1.0 / 3.0])
+@pytest.mark.parametrize("dtype,arith", [("f64", 1), ("f64", 2), ("f64", 0), ("f32", 1)])
+def test_hdiff_vadvc_staged_dtr(dtype, arith, dtr):
+    """dtr a power of two (the double-float column sweep scales exactly) and
+    not a power of two (the pair product)."""
+    sched = dict(fusion=1, tile_i=32, tile_j=8, k_chunk=4, arith=arith)
+    assert _hv_case((37, 23, 11), 3, dtype, sched, dtr=dtr) <= TOL[dtype]
