@@ -325,27 +325,30 @@ __device__ __forceinline__ long long fx_flux(long long lap_hi, long long lap_lo,
   return lim ? 0ll : f;
 }
 
-// One CTA: a TI x TJ tile of one field over a chunk of levels. Per level:
-// (1) the (TI+4) x (TJ+4) window of raw values is loaded and its largest
-// exponent E reduced; (2) the window is converted to fixed point at scale E,
-// with the limiter keys; (3) the Laplacian over (TI+2) x (TJ+2); (4) every
-// output point forms its four limited fluxes from the Laplacian and keys
-// planes, the divergence, and one FP64 FMA. The raw window and the exponent
-// slot are double-buffered, so the next level's load overlaps this level's
-// step (4) and a level costs three barriers.
-template <class OutT, int TI, int TJ, class Off>
-__global__ void __launch_bounds__(TI * TJ)
+// One CTA: a TI x TJ tile of one field over a chunk of levels, TI x TJ / U
+// threads. Per level: (1) the (TI+4) x (TJ+4) window of raw values is loaded
+// and its largest exponent E reduced; (2) the window is converted to fixed
+// point at scale E, with the limiter keys; (3) the Laplacian over (TI+2) x
+// (TJ+2); (4) every thread walks its U output points up j, forming the
+// limited fluxes from the Laplacian and keys planes (the flux across the edge
+// between two of its points is formed once), the divergence, and one FP64
+// FMA. The raw window and the exponent slot are double-buffered, so the next
+// level's load overlaps this level's step (4) and a level costs three
+// barriers.
+template <class OutT, int TI, int TJ, int U, class Off>
+__global__ void __launch_bounds__(TI * TJ / U)
 hdiff_fixed_kernel(const double* __restrict__ in0, const double* __restrict__ in1, const double* __restrict__ coeff,
                    OutT* __restrict__ out0, OutT* __restrict__ out1, int ni, int nj, int nk, int64_t sj, int64_t sk,
                    int64_t osj, int64_t osk, int kchunk, int nkz) {
-  constexpr int NT = TI * TJ, WI = TI + 4, WJ = TJ + 4, NW = WI * WJ, LI = TI + 2, LJ = TJ + 2, NL = LI * LJ;
+  static_assert(TJ % U == 0, "whole rows per thread");
+  constexpr int NT = TI * TJ / U, WI = TI + 4, WJ = TJ + 4, NW = WI * WJ, LI = TI + 2, LJ = TJ + 2, NL = LI * LJ;
   constexpr int QW = (NW + NT - 1) / NT, QL = (NL + NT - 1) / NT;
   __shared__ double s_raw[2][NW];
   __shared__ long long s_fix[NW];
   __shared__ long long s_key[NW];
   __shared__ long long s_lap[NL];
   __shared__ unsigned s_emax[2];
-  const int tid = threadIdx.x, tx = tid % TI, ty = tid / TI;
+  const int tid = threadIdx.x, tx = tid % TI, ty = (tid / TI) * U;   // first of the thread's U rows
   const int i0 = blockIdx.x * TI, j0 = blockIdx.y * TJ;
   const bool second = (int)blockIdx.z >= nkz;
   const double* __restrict__ in = second ? in1 : in0;
@@ -422,38 +425,47 @@ hdiff_fixed_kernel(const double* __restrict__ in0, const double* __restrict__ in
         s_lap[tid + q * NT] = (f[0] << 2) - f[-1] - f[1] - f[-WI] - f[WI];
       }
     __syncthreads();
-    // (4) limited fluxes, divergence, output
+    // (4) limited fluxes, divergence, output; fyb is the flux across the
+    // edge below the current point
     if (own) {
       const long long* L = s_lap + ol;
       const long long* K = s_key + ow;
-      const long long lc = L[0], kc = K[0];
-      const long long fxp = fx_flux(L[1], lc, K[1], kc);
-      const long long fxm = fx_flux(lc, L[-1], kc, K[-1]);
-      const long long fyp = fx_flux(L[LI], lc, K[WI], kc);
-      const long long fym = fx_flux(lc, L[-LI], kc, K[-WI]);
-      const long long div = (fxp - fxm) + (fyp - fym);
-      double dv = __ll2double_rn(div);
-      // dv * 2^(E - 1078) by exponent arithmetic (dv is 0 or an integer >= 1 in magnitude)
-      dv = div == 0 ? 0.0 : __longlong_as_double(__double_as_longlong(dv) + ((long long)((int)E - 1078) << 52));
-      const double r = __fma_rn(-ldg(coeff + ((Off)k * (Off)sk + oin)), dv, s_raw[bf][ow]);
-      out[(Off)k * (Off)osk + oout] = cvt<OutT>(r);
+      long long fyb = fx_flux(L[0], L[-LI], K[0], K[-WI]);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (ty + u < vj) {
+          const long long lc = L[u * LI], kc = K[u * WI];
+          const long long fxp = fx_flux(L[u * LI + 1], lc, K[u * WI + 1], kc);
+          const long long fxm = fx_flux(lc, L[u * LI - 1], kc, K[u * WI - 1]);
+          const long long fya = fx_flux(L[(u + 1) * LI], lc, K[(u + 1) * WI], kc);
+          const long long div = (fxp - fxm) + (fya - fyb);
+          fyb = fya;
+          double dv = __ll2double_rn(div);
+          // dv * 2^(E - 1078) by exponent arithmetic (dv is 0 or an integer >= 1 in magnitude)
+          dv = div == 0 ? 0.0 : __longlong_as_double(__double_as_longlong(dv) + ((long long)((int)E - 1078) << 52));
+          const double r =
+              __fma_rn(-ldg(coeff + ((Off)k * (Off)sk + oin + (Off)u * (Off)sj)), dv, s_raw[bf][ow + u * WI]);
+          out[(Off)k * (Off)osk + oout + (Off)u * (Off)osj] = cvt<OutT>(r);
+        }
+      }
     }
   }
 }
 
-template <class OutT, int TI, int TJ>
+template <class OutT, int TI, int TJ, int U>
 cudaError_t run_fixed(const oec_schedule& s, const Dom& d, int64_t osj, int64_t osk, const double* in,
                       const double* coeff, OutT* out, cudaStream_t st, const double* in1 = nullptr,
                       OutT* out1 = nullptr) {
   const int kc = (s.k_chunk <= 0 || s.k_chunk > d.nk) ? d.nk : s.k_chunk;
   const int nkz = ceil_div(d.nk, kc);
   dim3 g(ceil_div(d.ni, TI), ceil_div(d.nj, TJ), nkz * (in1 ? 2 : 1));
+  constexpr int NT = TI * TJ / U;
   if (offsets_fit_int32(d))
-    hdiff_fixed_kernel<OutT, TI, TJ, int><<<g, TI * TJ, 0, st>>>(in, in1, coeff, out, out1, d.ni, d.nj, d.nk, d.sj,
-                                                                 d.sk, osj, osk, kc, nkz);
+    hdiff_fixed_kernel<OutT, TI, TJ, U, int><<<g, NT, 0, st>>>(in, in1, coeff, out, out1, d.ni, d.nj, d.nk, d.sj,
+                                                               d.sk, osj, osk, kc, nkz);
   else
-    hdiff_fixed_kernel<OutT, TI, TJ, int64_t><<<g, TI * TJ, 0, st>>>(in, in1, coeff, out, out1, d.ni, d.nj, d.nk, d.sj,
-                                                                     d.sk, osj, osk, kc, nkz);
+    hdiff_fixed_kernel<OutT, TI, TJ, U, int64_t><<<g, NT, 0, st>>>(in, in1, coeff, out, out1, d.ni, d.nj, d.nk, d.sj,
+                                                                   d.sk, osj, osk, kc, nkz);
   launched(st);
   return cudaGetLastError();
 }
@@ -600,6 +612,10 @@ cudaError_t run_regs_to(const oec_schedule& s, const Dom& d, int64_t osj, int64_
 }
 
 #define OEC_SMEM_TILES(X) X(32, 4) X(32, 8) X(64, 2) X(64, 4) X(64, 8) X(128, 2) X(128, 4)
+// fixed-point hdiff: tile_i, tile_j, rows per thread
+#define OEC_FIXED_TILES(X)                                                                                   \
+  X(32, 4, 1) X(32, 8, 1) X(64, 2, 1) X(64, 4, 1) X(64, 8, 1) X(128, 2, 1) X(128, 4, 1) X(32, 8, 2) X(32, 16, 1) \
+  X(32, 16, 2) X(32, 16, 4) X(64, 8, 2)
 #define OEC_STREAM_TILES(X) X(32, 4) X(32, 8) X(64, 4) X(64, 8) X(128, 2) X(128, 4)
 
 template <class P>
@@ -631,8 +647,17 @@ cudaError_t dispatch(const oec_schedule& s, const Dom& d, const typename P::S* i
 
 bool hdiff_schedule_ok(const oec_schedule& s, std::string& why) {
   if (s.arith < 0 || s.arith > 2) { why = "arith must be 0 (native), 1 (double-float) or 2 (fixed point)"; return false; }
-  if (s.arith == 2 && (s.fusion != OEC_FUSE_INLINE || s.staging != OEC_STAGE_SMEM)) {
-    why = "fixed-point arithmetic runs the fused SMEM-staged kernel";
+  if (s.arith == 2) {
+    if (s.fusion != OEC_FUSE_INLINE || s.staging != OEC_STAGE_SMEM) {
+      why = "fixed-point arithmetic runs the fused SMEM-staged kernel";
+      return false;
+    }
+    if (s.k_chunk < 0) { why = "k_chunk must be >= 0"; return false; }
+#define X(a, b, u) if (s.tile_i == a && s.tile_j == b && s.unroll == u) return true;
+    OEC_FIXED_TILES(X)
+#undef X
+    why = "fixed-point tiles (tile_i x tile_j, unroll): 32x4 1, 32x8 1/2, 64x2 1, 64x4 1, 64x8 1/2, 128x2 1, "
+          "128x4 1, 32x16 1/2/4";
     return false;
   }
   if (s.fusion == OEC_FUSE_NONE) return true;
@@ -674,10 +699,10 @@ cudaError_t hdiff_launch(const oec_schedule& s, int dtype, const Dom& d, const v
                          void* scratch, cudaStream_t st) {
   if (s.fusion == OEC_FUSE_INLINE && s.staging == OEC_STAGE_WARP) return hdiff_warp_launch(s, dtype, d, in, coeff, out, st);
   if (dtype == OEC_F64 && s.arith == 2) {
-#define X(a, b)                                                                                               \
-  if (s.tile_i == a && s.tile_j == b)                                                                         \
-    return run_fixed<double, a, b>(s, d, d.sj, d.sk, (const double*)in, (const double*)coeff, (double*)out, st);
-    OEC_SMEM_TILES(X)
+#define X(a, b, u)                                                                                            \
+  if (s.tile_i == a && s.tile_j == b && s.unroll == u)                                                        \
+    return run_fixed<double, a, b, u>(s, d, d.sj, d.sk, (const double*)in, (const double*)coeff, (double*)out, st);
+    OEC_FIXED_TILES(X)
 #undef X
     return cudaErrorInvalidValue;
   }
@@ -714,9 +739,22 @@ cudaError_t hdiff_to_compute(const oec_schedule& sched, int dtype, const Dom& d,
       default: return run_regs_to<P32, 1, float>(s, d, osj, osk, i0, i1, cf, (float*)out0, (float*)out1, st);
     }
   }
-  // otherwise the SMEM tile kernel (FP64: fixed point for arith 2): the
-  // schedule's tile and k_chunk pick its tile when they name one of its tiles;
-  // otherwise 64 x 4, 4 levels per CTA
+  // FP64 arith 2: the fixed-point kernel on the schedule's tile and rows per
+  // thread when they name one of its tiles, else 64 x 4, one row
+  if (dtype == OEC_F64 && sched.arith == 2) {
+    oec_schedule s = sched;
+    if (s.k_chunk <= 0) s.k_chunk = 4;
+    const double* i0 = (const double*)in0;
+    const double* i1 = (const double*)in1;
+    const double* cf = (const double*)coeff;
+#define X(a, b, u) \
+  if (s.tile_i == a && s.tile_j == b && s.unroll == u) return run_fixed<df64, a, b, u>(s, d, osj, osk, i0, cf, (df64*)out0, st, i1, (df64*)out1);
+    OEC_FIXED_TILES(X)
+#undef X
+    return run_fixed<df64, 64, 4, 1>(s, d, osj, osk, i0, cf, (df64*)out0, st, i1, (df64*)out1);
+  }
+  // otherwise the SMEM tile kernel: the schedule's tile and k_chunk pick its
+  // tile when they name one of its tiles; otherwise 64 x 4, 4 levels per CTA
   oec_schedule s = sched;
   bool known = false;
 #define X(a, b) known = known || (s.tile_i == a && s.tile_j == b);
@@ -730,9 +768,6 @@ cudaError_t hdiff_to_compute(const oec_schedule& sched, int dtype, const Dom& d,
 #define X(a, b)                                                                                                  \
   if (s.tile_i == a && s.tile_j == b) {                                                                          \
     if (dtype == OEC_F64) {                                                                                      \
-      if (s.arith == 2)                                                                                          \
-        return run_fixed<df64, a, b>(s, d, osj, osk, (const double*)in0, (const double*)coeff, (df64*)out0, st,  \
-                                     (const double*)in1, (df64*)out1);                                           \
       if (s.arith == 1)                                                                                          \
         return run_smem<P64D, df64, a, b>(s, d, osj, osk, (const double*)in0, (const double*)coeff, (df64*)out0, \
                                           st, (const double*)in1, (df64*)out1);                                  \

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <vector>
 
 #include "../../include/oec.h"
@@ -31,9 +32,13 @@ std::vector<oec_schedule> candidates(const oec_program* p) {
   const std::vector<int> ariths = p->dtype == OEC_F64 ? std::vector<int>{0, 1} : std::vector<int>{0};
   switch (p->kind) {
     case OEC_KIND_HDIFF:
-      if (p->dtype == OEC_F64)
+      if (p->dtype == OEC_F64) {
         for (auto t : {std::pair<int, int>{32, 4}, {32, 8}, {64, 2}, {64, 4}, {64, 8}, {128, 2}, {128, 4}})
           for (int kc : {1, 2, 4, 8}) c.push_back(mk(OEC_FUSE_INLINE, OEC_STAGE_SMEM, t.first, t.second, 1, kc, 2));
+        // fixed point, several rows per thread
+        for (auto t : {std::array<int, 3>{32, 8, 2}, {32, 16, 1}, {32, 16, 2}, {32, 16, 4}, {64, 8, 2}})
+          for (int kc : {2, 4, 8}) c.push_back(mk(OEC_FUSE_INLINE, OEC_STAGE_SMEM, t[0], t[1], t[2], kc, 2));
+      }
       for (int a : ariths) {
         c.push_back(mk(OEC_FUSE_NONE, 0, 32, 8, 1, 0, a));
         for (auto t : {std::pair<int, int>{32, 4}, {32, 8}, {64, 2}, {64, 4}, {64, 8}, {128, 2}, {128, 4}})
@@ -56,6 +61,9 @@ std::vector<oec_schedule> candidates(const oec_program* p) {
         for (int a : {2, 1, 0})
           for (auto t : {std::pair<int, int>{32, 4}, {32, 8}, {64, 4}, {64, 8}, {128, 4}})
             for (int kc : {4, 8}) c.push_back(mk(OEC_FUSE_NONE, 0, t.first, t.second, 1, kc, a));
+        // the fixed-point producer with several rows per thread
+        for (auto t : {std::array<int, 3>{32, 8, 2}, {32, 16, 1}, {32, 16, 2}, {32, 16, 4}, {64, 8, 2}})
+          for (int kc : {4, 8}) c.push_back(mk(OEC_FUSE_NONE, 0, t[0], t[1], t[2], kc, 2));
       } else {
         for (int a : {1, 0}) {
           for (auto t : {std::pair<int, int>{32, 4}, {32, 8}, {64, 4}, {128, 2}})

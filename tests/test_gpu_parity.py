@@ -259,13 +259,33 @@ def test_hdiff_f64_identity_on_edge_values(arith):
 
 # ----------------------------------------------------- FP64 fixed-point hdiff
 
-FIXED_SCHEDS = [dict(fusion=0, staging=1, tile_i=a, tile_j=b, k_chunk=kc, arith=2)
-                for (a, b) in [(32, 4), (32, 8), (64, 2), (64, 4), (64, 8), (128, 2), (128, 4)] for kc in (0, 3)]
+FIXED_SCHEDS = ([dict(fusion=0, staging=1, tile_i=a, tile_j=b, k_chunk=kc, arith=2)
+                 for (a, b) in [(32, 4), (32, 8), (64, 2), (64, 4), (64, 8), (128, 2), (128, 4)] for kc in (0, 3)]
+                + [dict(fusion=0, staging=1, tile_i=a, tile_j=b, unroll=u, k_chunk=3, arith=2)
+                   for (a, b, u) in [(32, 8, 2), (32, 16, 1), (32, 16, 2), (32, 16, 4), (64, 8, 2)]])
 
 
 @pytest.mark.parametrize("sched", FIXED_SCHEDS, ids=str)
 def test_hdiff_fixed_point_ragged(sched):
     assert _hdiff_case((37, 29, 5), 2, "f64", sched) <= TOL["f64"]
+
+
+@pytest.mark.parametrize("n", [(37, 29, 5), (33, 18, 3), (64, 64, 4)], ids=str)
+def test_hdiff_fixed_point_rows_per_thread_bitwise(n):
+    """Several rows per thread share the flux across the edges between their
+    points; the integer arithmetic is the same, so the bits are."""
+    from paper_2005_13014_gb300.api import Program, device_field
+    h = 2
+    f = inputs.hdiff_fields(*n, h, seed=41)
+    outs = []
+    for u in (1, 2, 4):
+        p = Program(programs.HDIFF, "f64")
+        p.set_schedule(fusion=0, staging=1, tile_i=32, tile_j=16, unroll=u, k_chunk=2, arith=2)
+        o = device_field(np.zeros_like(f["in"]), h, "f64")
+        p.apply([device_field(f["in"], h, "f64"), device_field(f["coeff"], h, "f64")], [o], (0, 0, 0), n, (h, h, h))
+        torch.cuda.synchronize()
+        outs.append(o.tensor.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
 
 
 def test_hdiff_fixed_point_config_sizes():
@@ -322,6 +342,13 @@ def test_hdiff_vadvc_staged_producer_tiles(dtype, arith, tile, kc):
     the twisted column sweep behind it (ragged tiles, odd column count)."""
     sched = dict(fusion=1, tile_i=tile[0], tile_j=tile[1], k_chunk=kc, arith=arith)
     assert _hv_case((37, 23, 11), 3, dtype, sched) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("tile", [(32, 8, 2), (32, 16, 1), (32, 16, 2), (32, 16, 4), (64, 8, 2)], ids=str)
+def test_hdiff_vadvc_staged_fixed_rows_per_thread(tile):
+    sched = dict(fusion=1, tile_i=tile[0], tile_j=tile[1], unroll=tile[2], k_chunk=4, arith=2)
+    assert _hv_case((37, 23, 11), 3, "f64", sched) <= TOL["f64"]
+    assert _hv_case((128, 128, 80), 3, "f64", sched) <= TOL["f64"]
 
 
 @pytest.mark.parametrize("unroll", [1, 2, 4])
