@@ -93,7 +93,9 @@ typedef enum {
                             levels' windows copied asynchronously into a shared-memory
                             ring while the current level is computed. fastwaves: a
                             thread walks its column, carrying the k-shared values from
-                            level to level, next level's loads in flight            */
+                            level to level, next level's loads in flight; with unroll
+                            2 (tiles 32x4, 32x8, 64x4, 128x2) the CTA's u/v windows
+                            come through a shared-memory ring                       */
   OEC_STAGE_WARP = 3,    /* horizontal diffusion: a warp owns `unroll` (1, 2, 4) rows of
                             32 x 16-byte vectors of columns; neighbours across vectors by
                             warp shuffles; the next level loaded ahead. Needs 16-byte

@@ -216,6 +216,146 @@ __global__ void fw_stream_kernel(FW<typename P::S> p, double dt_d, double alpha_
   }
 }
 
+// k-streaming with the divergence's inputs staged: as fw_stream_kernel, but a
+// CTA's u_in and v_in windows of each level ((TJ+1) x (TI+5) of u: rows j, j+1,
+// columns i-2 .. i+3; (TJ+5) x (TI+1) of v: rows j-2 .. j+3, columns i, i+1)
+// are copied asynchronously into a D-level shared-memory ring, D-1 levels
+// ahead, so the 20 stencil reads of a point come from shared memory and the
+// loads in flight do not occupy registers. The point's 15 other values (pp,
+// wgtfac, hhl of the next level at three columns; fx, rho at three columns,
+// utens, vtens) keep the two-window register prefetch. Same arithmetic, in
+// the same order, as fw_stream_kernel.
+template <class P, int TI, int TJ, class Off>
+__global__ void __launch_bounds__(TI * TJ) fw_tile_kernel(FW<typename P::S> p, double dt_d, double alpha_d, int kchunk) {
+  typedef typename P::C T;
+  typedef typename P::S S;
+  constexpr int NT = TI * TJ, UI = TI + 5, UJ = TJ + 1, VI = TI + 1, VJ = TJ + 5;
+  constexpr int NU = UI * UJ, NV = VI * VJ, SLOT = NU + NV, Q = (SLOT + NT - 1) / NT, D = 4;
+  __shared__ __align__(16) S ring[D * SLOT];
+  const T dt = kd<T>(dt_d), alpha = kd<T>(alpha_d);
+  const int tid = threadIdx.x, tx = tid % TI, ty = tid / TI;
+  const int i0 = blockIdx.x * TI, j0 = blockIdx.y * TJ;
+  const int i = i0 + tx, j = j0 + ty;
+  const bool own = i < p.ni && j < p.nj;
+  const int k0 = blockIdx.z * kchunk, k1 = min(p.nk, k0 + kchunk);
+  const Off sj = (Off)p.sj, sk = (Off)p.sk;
+  // this thread's copies: element e of the slot (u window, then v window),
+  // its offset from the field's level base and whether the point exists
+  // (u: columns up to ni+2, rows up to nj; v: columns up to ni, rows up to
+  // nj+2: what the domain's points read)
+  Off goff[Q];
+  int cfield[Q];   // 0 none, 1 u, 2 v
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int e = tid + q * NT;
+    cfield[q] = 0;
+    goff[q] = 0;
+    if (e < NU) {
+      const int r = e / UI, c = e - r * UI, ii = i0 - 2 + c, jj = j0 + r;
+      if (ii <= p.ni + 2 && jj <= p.nj) {
+        cfield[q] = 1;
+        goff[q] = (Off)jj * sj + ii;
+      }
+    } else if (e < SLOT) {
+      const int f = e - NU, r = f / VI, c = f - r * VI, ii = i0 + c, jj = j0 - 2 + r;
+      if (ii <= p.ni && jj <= p.nj + 2) {
+        cfield[q] = 2;
+        goff[q] = (Off)jj * sj + ii;
+      }
+    }
+  }
+  auto issue = [&](int k, S* slot) {
+    if (k < k1) {
+      const Off ko = (Off)k * sk;
+#pragma unroll
+      for (int q = 0; q < Q; ++q)
+        if (cfield[q]) cp_async(slot + tid + q * NT, (cfield[q] == 1 ? p.u_in : p.v_in) + (ko + goff[q]));
+    }
+    cp_async_commit();
+  };
+  const Off col = (Off)j * sj + i;
+  const Off cn[3] = {0, 1, sj};
+  auto ld = [&](const S* f, Off o) { return ldg(f + o); };
+  struct Win {
+    S pp1[3], wg1[3], hh1[3];
+    S fx, rho, rho_e, rho_n, ut, vt;
+  };
+  auto load = [&](Win& w, int k) {
+    const Off o = (Off)k * sk + col, o1 = o + sk;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      w.pp1[c] = ld(p.pp, o1 + cn[c]);
+      w.wg1[c] = ld(p.wgtfac, o1 + cn[c]);
+      w.hh1[c] = ld(p.hhl, o1 + cn[c]);
+    }
+    w.fx = ld(p.fx, o);
+    w.rho = ld(p.rho, o);
+    w.rho_e = ld(p.rho, o + 1);
+    w.rho_n = ld(p.rho, o + sj);
+    w.ut = ld(p.utens, o);
+    w.vt = ld(p.vtens, o);
+  };
+#pragma unroll
+  for (int x = 0; x < D - 1; ++x) issue(k0 + x, ring + x * SLOT);
+  T pk[3], ppv[3], hh[3];
+  Win win[2];
+  if (own) {
+    const Off o = (Off)k0 * sk + col;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      ppv[c] = cvt<T>(ld(p.pp, o + cn[c]));
+      pk[c] = fw_ppgk(cvt<T>(ld(p.wgtfac, o + cn[c])), ppv[c], cvt<T>(ld(p.pp, o + cn[c] - sk)));
+      hh[c] = cvt<T>(ld(p.hhl, o + cn[c]));
+    }
+    load(win[0], k0);
+    if (k0 + 1 < k1) load(win[1], k0 + 1);
+  }
+  int sl = 0;   // ring slot of level k
+  for (int k = k0; k < k1; k += 2) {
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      if (k + b >= k1) break;
+      cp_async_wait<D - 2>();   // this thread's copies of level k+b have landed
+      __syncthreads();          // everyone's have; everyone is done with level k+b-1
+      issue(k + b + D - 1, ring + (sl == 0 ? D - 1 : sl - 1) * SLOT);   // into level k+b-1's slot
+      const S* W = ring + sl * SLOT;
+      sl = sl == D - 1 ? 0 : sl + 1;
+      if (!own) continue;
+      const Win& w = win[b];
+      const Off o = (Off)(k + b) * sk + col;
+      T pk1[3], pc[3], h1[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        pk1[c] = fw_ppgk(cvt<T>(w.wg1[c]), cvt<T>(w.pp1[c]), ppv[c]);
+        pc[c] = pk1[c] - pk[c];
+        h1[c] = cvt<T>(w.hh1[c]);
+      }
+      const T ppgu = fw_pgrad(ppv[1], ppv[0], pc[1], pc[0], h1[0], hh[0], h1[1], hh[1]);
+      const T ppgv = fw_pgrad(ppv[2], ppv[0], pc[2], pc[0], h1[0], hh[0], h1[2], hh[2]);
+      const S* su = W + ty * UI + tx + 2;    // u_in(i, j); the next row is j+1
+      const S* sv = W + NU + (ty + 2) * VI + tx;   // v_in(i, j); the next column is i+1
+      auto U0 = [&](int x) { return cvt<T>(su[x]); };             // u_in(i+x, j)
+      auto U1 = [&](int x) { return cvt<T>(su[UI + x]); };        // u_in(i+x, j+1)
+      auto V0 = [&](int y) { return cvt<T>(sv[y * VI]); };        // v_in(i, j+y)
+      auto V1 = [&](int y) { return cvt<T>(sv[y * VI + 1]); };    // v_in(i+1, j+y)
+      const T dv = fw_d4(U0(-2), U0(-1), U0(1), U0(2)) + fw_d4(V0(-2), V0(-1), V0(1), V0(2));
+      const T dv_e = fw_d4(U0(-1), U0(0), U0(2), U0(3)) + fw_d4(V1(-2), V1(-1), V1(1), V1(2));
+      const T dv_n = fw_d4(U1(-2), U1(-1), U1(1), U1(2)) + fw_d4(V0(-1), V0(0), V0(2), V0(3));
+      const T fx = cvt<T>(w.fx), rho = cvt<T>(w.rho);
+      p.u_out[o] = cvt<S>(fw_out(U0(0), dt, cvt<T>(w.ut), ppgu, fx, cvt<T>(w.rho_e), rho, alpha, dv_e, dv));
+      p.v_out[o] = cvt<S>(fw_out(V0(0), dt, cvt<T>(w.vt), ppgv, fx, cvt<T>(w.rho_n), rho, alpha, dv_n, dv));
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        pk[c] = pk1[c];
+        ppv[c] = cvt<T>(w.pp1[c]);
+        hh[c] = h1[c];
+      }
+      if (k + b + 2 < k1) load(win[b], k + b + 2);
+    }
+  }
+  cp_async_wait<0>();
+}
+
 template <class P, int TI, int TJ>
 __global__ void __launch_bounds__(TI * TJ) fw_smem_kernel(FW<typename P::S> p, double dt_d, double alpha_d, int kchunk) {
   typedef typename P::C T;
@@ -333,6 +473,8 @@ bool offsets_fit_fw(const Dom& d) {
 }
 
 #define OEC_FW_TILES(X) X(32, 4) X(32, 8) X(64, 2) X(64, 4) X(128, 2)
+// shared-memory u/v windows in the k-streaming form (OEC_STAGE_STREAM, unroll 2)
+#define OEC_FWTILE_TILES(X) X(32, 4) X(32, 8) X(64, 4) X(128, 2)
 
 template <class P>
 cudaError_t dispatch(const oec_schedule& s, const Dom& d, const FW<typename P::S>& p, double dt, double alpha,
@@ -352,6 +494,22 @@ cudaError_t dispatch(const oec_schedule& s, const Dom& d, const FW<typename P::S
     fw_s5<P><<<g, b, 0, st>>>(p, dv); launched(st);
     fw_s6<P><<<gd, b, 0, st>>>(p, pu, pv, dv, dt, alpha); launched(st);
     return cudaGetLastError();
+  }
+  if (s.staging == OEC_STAGE_STREAM && s.unroll == 2) {
+    const int kc = kchunk_of(s, d.nk);
+#define X(a, b)                                                                                       \
+  if (s.tile_i == a && s.tile_j == b) {                                                               \
+    dim3 g(ceil_div(d.ni, a), ceil_div(d.nj, b), ceil_div(d.nk, kc));                                 \
+    if (offsets_fit_fw(d))                                                                            \
+      fw_tile_kernel<P, a, b, int><<<g, a * b, 0, st>>>(p, dt, alpha, kc);                            \
+    else                                                                                              \
+      fw_tile_kernel<P, a, b, int64_t><<<g, a * b, 0, st>>>(p, dt, alpha, kc);                        \
+    launched(st);                                                                                     \
+    return cudaGetLastError();                                                                        \
+  }
+    OEC_FWTILE_TILES(X)
+#undef X
+    return cudaErrorInvalidValue;
   }
   if (s.staging == OEC_STAGE_STREAM) {
     const int kc = kchunk_of(s, d.nk);
@@ -402,6 +560,14 @@ bool fastwaves_schedule_ok(const oec_schedule& s, std::string& why) {
     return false;
   }
   if (s.staging != OEC_STAGE_REGS && s.staging != OEC_STAGE_STREAM) { why = "unknown staging"; return false; }
+  if (s.staging == OEC_STAGE_STREAM && s.unroll == 2) {
+#define X(a, b) if (s.tile_i == a && s.tile_j == b) return true;
+    OEC_FWTILE_TILES(X)
+#undef X
+    why = "fastwaves STREAM with shared-memory u/v windows (unroll 2): tiles 32x4, 32x8, 64x4, 128x2";
+    return false;
+  }
+  if (s.staging == OEC_STAGE_STREAM && s.unroll != 1) { why = "fastwaves STREAM: unroll 1 or 2"; return false; }
   if (s.staging == OEC_STAGE_REGS && s.unroll != 1 && s.unroll != 2 && s.unroll != 4) {
     why = "unroll (along k) must be 1, 2 or 4";
     return false;

@@ -201,7 +201,9 @@ FW_SCHEDS = ([dict(fusion=1)]
              + [dict(fusion=0, staging=0, tile_i=a, tile_j=b, unroll=u)
                 for (a, b, u) in [(32, 4, 1), (64, 4, 2), (32, 8, 4), (128, 2, 4)]]
              + [dict(fusion=0, staging=2, tile_i=a, tile_j=b, k_chunk=kc)
-                for (a, b) in [(32, 4), (64, 4), (128, 2)] for kc in (0, 3, 4)])
+                for (a, b) in [(32, 4), (64, 4), (128, 2)] for kc in (0, 3, 4)]
+             + [dict(fusion=0, staging=2, tile_i=a, tile_j=b, unroll=2, k_chunk=kc)
+                for (a, b) in [(32, 4), (32, 8), (64, 4), (128, 2)] for kc in (0, 3, 4)])
 
 
 def _fw_case(n, h, dtype, sched, dt=0.5, alpha=0.0625):
@@ -224,6 +226,27 @@ def _fw_case(n, h, dtype, sched, dt=0.5, alpha=0.0625):
 @pytest.mark.parametrize("dtype,arith", PRECISIONS)
 def test_fastwaves_ragged(sched, dtype, arith):
     assert _fw_case((37, 29, 7), 3, dtype, _with(sched, arith)) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("n", [(37, 29, 7), (130, 9, 5), (256, 256, 80)], ids=str)
+@pytest.mark.parametrize("dtype,arith", PRECISIONS)
+def test_fastwaves_stream_smem_windows_bitwise(n, dtype, arith):
+    """k-streaming with shared-memory u/v windows against the k-streaming
+    kernel that loads them per point: the same arithmetic, so the same bits."""
+    h = 3
+    f = inputs.fastwaves_fields(*n, h, seed=34)
+    g = {k: _round(v, dtype) for k, v in f.items()}
+    outs = []
+    for unroll in (1, 2):
+        p = _prog(programs.FASTWAVES, dtype, dict(fusion=0, staging=2, tile_i=32, tile_j=8, unroll=unroll,
+                                                  k_chunk=8, arith=arith))
+        d = [_dev(g[name], h, dtype) for name in inputs.FASTWAVES_NAMES]
+        o = [_dev(np.zeros_like(g["pp"]), h, dtype) for _ in range(2)]
+        p.apply(d, o, (0, 0, 0), n, (h, h, h), [0.5, 0.0625])
+        torch.cuda.synchronize()
+        outs.append([x.tensor.cpu().numpy() for x in o])
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
 
 
 @pytest.mark.parametrize("dtype,arith", PRECISIONS)
