@@ -106,7 +106,10 @@ typedef enum {
                             windows of the next 4 units are copied by the tensor memory
                             accelerator (cp.async.bulk.tensor) into a shared-memory ring.
                             Same alignment needs, and 16-byte aligned storage; k_chunk
-                            unused                                                     */
+                            unused. fastwaves: k-streaming CTA tiles (32x4, 32x8, 64x4)
+                            whose nine input boxes per level are copied by TMA into a
+                            4-stage ring; needs 16-byte aligned storage and j/k strides
+                            (any domain corner), else OEC_ERR_UNSUPPORTED            */
 } oec_staging;
 
 typedef struct oec_schedule {

@@ -72,6 +72,23 @@ int dispatch_apply(oec_program* p, const oec_field_desc* in, const oec_field_des
       rc = ensure_scratch(p, fastwaves_scratch_bytes(p->sched, p->dtype, d));
       if (rc) return rc;
       FastwavesPtrs f{I[0], I[1], I[2], I[3], I[4], I[5], I[6], I[7], I[8], O[0], O[1]};
+      if (p->sched.fusion == OEC_FUSE_INLINE && p->sched.staging == OEC_STAGE_TMA) {
+        // tensor maps: 16-byte aligned storage and j/k strides
+        if ((sj * (int64_t)es) % 16 != 0 || (sk * (int64_t)es) % 16 != 0)
+          return fail(OEC_ERR_UNSUPPORTED, "TMA staging: j/k strides must be multiples of 16 bytes");
+        TmaField t[9];
+        for (int x = 0; x < 9; ++x) {
+          if ((uintptr_t)in[x].data % 16 != 0) return fail(OEC_ERR_UNSUPPORTED, "TMA staging: storage not 16-byte aligned");
+          t[x].base = in[x].data;
+          for (int a = 0; a < 3; ++a) {
+            t[x].size[a] = in[x].size[a];
+            t[x].corner[a] = in[x].origin[a] + lb[a];
+          }
+        }
+        e = fastwaves_launch(p->sched, p->dtype, d, f, params[0], params[1], p->scratch, st, t);
+        if (e == cudaErrorNotSupported) return fail(OEC_ERR_UNSUPPORTED, "TMA staging: tensor maps unavailable");
+        break;
+      }
       e = fastwaves_launch(p->sched, p->dtype, d, f, params[0], params[1], p->scratch, st);
       break;
     }

@@ -20,9 +20,12 @@
 //     tiling + k-streaming, paper §VII-D);
 //   unfused: one kernel per stage, temporaries over their inferred ranges.
 // Templated on an arithmetic policy (arith.cuh): S storage, C compute type.
+#include <mutex>
+
 #include "arith.cuh"
 #include "kcommon.cuh"
 #include "kernels.h"
+#include "tma.cuh"
 
 namespace oec {
 namespace {
@@ -356,6 +359,151 @@ __global__ void __launch_bounds__(TI * TJ) fw_tile_kernel(FW<typename P::S> p, d
   cp_async_wait<0>();
 }
 
+// k-streaming with every input staged by the tensor memory accelerator
+// (OEC_STAGE_TMA): per level a CTA's nine boxes (u_in rows j, j+1, columns
+// i-2 .. i+3; v_in rows j-2 .. j+3, columns i, i+1; pp, wgtfac, hhl of level
+// k+1 and rho at columns i, i+1, rows j, j+1; fx, utens, vtens at the points)
+// are copied by one thread with cp.async.bulk.tensor into a D-stage ring,
+// completion counted on the stage's mbarrier, D levels ahead. A box starts at
+// the 16-byte boundary at or below its first column; its element offset o
+// into the box is the same for every tile, since tiles start at multiples of
+// TI. Same arithmetic, in the same order, as fw_stream_kernel. A wait that
+// gives up counts a timeout and the CTA stops after waiting (bounded) for the
+// copies it still has in flight.
+template <class S, int TI, int TJ>
+struct FwTmaGeom {
+  static constexpr int E = 16 / (int)sizeof(S);   // elements per 16 bytes
+  static constexpr int rup(int x) { return (x + E - 1) / E * E; }
+  static constexpr int BXU = rup(TI + 5 + E - 1), BYU = TJ + 1;   // u_in
+  static constexpr int BXV = rup(TI + 1 + E - 1), BYV = TJ + 5;   // v_in
+  static constexpr int BXC = rup(TI + 1 + E - 1), BYC = TJ + 1;   // pp, wgtfac, hhl (level k+1), rho
+  static constexpr int BXP = rup(TI + E - 1), BYP = TJ;           // fx, utens, vtens
+  static constexpr size_t al(size_t b) { return (b + 127) / 128 * 128; }
+  static constexpr size_t SU = al(size_t(BXU) * BYU * sizeof(S)), SV = al(size_t(BXV) * BYV * sizeof(S));
+  static constexpr size_t SC = al(size_t(BXC) * BYC * sizeof(S)), SP = al(size_t(BXP) * BYP * sizeof(S));
+  // byte offsets in a stage (128-byte aligned), fields in FASTWAVES input
+  // order: u_in, v_in, utens, vtens, pp, rho, wgtfac, hhl, fx
+  __host__ __device__ static constexpr size_t off(int f) {
+    return f == 0 ? 0 : f == 1 ? SU : f <= 3 ? SU + SV + (f - 2) * SP : f <= 7 ? SU + SV + 2 * SP + (f - 4) * SC
+                                                                              : SU + SV + 2 * SP + 4 * SC;
+  }
+  static constexpr size_t STAGE = SU + SV + 3 * SP + 4 * SC;
+  static constexpr unsigned TX =
+      unsigned((size_t(BXU) * BYU + size_t(BXV) * BYV + 4 * size_t(BXC) * BYC + 3 * size_t(BXP) * BYP) * sizeof(S));
+  static constexpr int D = 4;
+  static constexpr size_t SMEM = D * STAGE + D * sizeof(unsigned long long);
+};
+
+struct FwMaps {
+  CUtensorMap m[9];
+  int x0[9], y0[9], z0[9], o[9];   // box corner of the tile at (0, 0, k = 0), element offset of the first column
+};
+
+template <class P, int TI, int TJ, class Off>
+__global__ void __launch_bounds__(TI * TJ) fw_tma_kernel(const __grid_constant__ FwMaps mp, FW<typename P::S> p,
+                                                          double dt_d, double alpha_d, int kchunk,
+                                                          unsigned* __restrict__ timeouts) {
+  typedef typename P::C T;
+  typedef typename P::S S;
+  typedef FwTmaGeom<S, TI, TJ> G;
+  constexpr int D = G::D;
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem + size_t(D) * G::STAGE);
+  const T dt = kd<T>(dt_d), alpha = kd<T>(alpha_d);
+  const int tid = threadIdx.x, tx = tid % TI, ty = tid / TI;
+  const int i0 = blockIdx.x * TI, j0 = blockIdx.y * TJ;
+  const int i = i0 + tx, j = j0 + ty;
+  const bool own = i < p.ni && j < p.nj;
+  const int k0 = blockIdx.z * kchunk, k1 = min(p.nk, k0 + kchunk);
+  if (tid == 0) {
+    for (int x = 0; x < D; ++x) mbar_init(smem_u32(&bars[x]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  auto issue = [&](int k) {   // thread 0 only: level k into stage (k - k0) % D
+    const int sl = (k - k0) % D;
+    unsigned char* st_ = smem + size_t(sl) * G::STAGE;
+    const unsigned bar = smem_u32(&bars[sl]);
+    mbar_expect_tx(bar, G::TX);
+#pragma unroll
+    for (int f = 0; f < 9; ++f) tma_load_3d(st_ + G::off(f), &mp.m[f], mp.x0[f] + i0, mp.y0[f] + j0, mp.z0[f] + k, bar);
+  };
+  if (tid == 0)
+    for (int k = k0; k < min(k1, k0 + D); ++k) issue(k);
+  int issued_to = min(k1, k0 + D);   // levels [k0, issued_to) issued (thread 0's view)
+  int failed_at = -1;
+  const Off sj = (Off)p.sj, sk = (Off)p.sk;
+  const Off col = (Off)j * sj + i;
+  const Off cn[3] = {0, 1, sj};
+  T pk[3], ppv[3], hh[3];
+  if (own) {
+    const Off o = (Off)k0 * sk + col;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      ppv[c] = cvt<T>(ldg(p.pp + (o + cn[c])));
+      pk[c] = fw_ppgk(cvt<T>(ldg(p.wgtfac + (o + cn[c]))), ppv[c], cvt<T>(ldg(p.pp + (o + cn[c] - sk))));
+      hh[c] = cvt<T>(ldg(p.hhl + (o + cn[c])));
+    }
+  }
+  for (int k = k0; k < k1; ++k) {
+    const int sl = (k - k0) % D;
+    const bool ok = mbar_wait(smem_u32(&bars[sl]), (unsigned)(((k - k0) / D) & 1));
+    if (__syncthreads_or(!ok)) {
+      failed_at = k;
+      if (tid == 0) atomicAdd(timeouts, 1u);
+      break;
+    }
+    if (own) {
+      const unsigned char* st_ = smem + size_t(sl) * G::STAGE;
+      auto box = [&](int f) { return reinterpret_cast<const S*>(st_ + G::off(f)); };
+      const S* su = box(0) + ty * G::BXU + mp.o[0] + 2 + tx;   // u_in(i, j); next row j+1
+      const S* sv = box(1) + (ty + 2) * G::BXV + mp.o[1] + tx;   // v_in(i, j); next column i+1
+      const int cp = ty * G::BXC + tx, pq = ty * G::BXP + tx;
+      const S* spp = box(4) + cp + mp.o[4];
+      const S* srh = box(5) + cp + mp.o[5];
+      const S* swg = box(6) + cp + mp.o[6];
+      const S* shh = box(7) + cp + mp.o[7];
+      const int cc[3] = {0, 1, G::BXC};
+      T pk1[3], pc[3], h1[3], pp1[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        pp1[c] = cvt<T>(spp[cc[c]]);
+        pk1[c] = fw_ppgk(cvt<T>(swg[cc[c]]), pp1[c], ppv[c]);
+        pc[c] = pk1[c] - pk[c];
+        h1[c] = cvt<T>(shh[cc[c]]);
+      }
+      const T ppgu = fw_pgrad(ppv[1], ppv[0], pc[1], pc[0], h1[0], hh[0], h1[1], hh[1]);
+      const T ppgv = fw_pgrad(ppv[2], ppv[0], pc[2], pc[0], h1[0], hh[0], h1[2], hh[2]);
+      auto U0 = [&](int x) { return cvt<T>(su[x]); };
+      auto U1 = [&](int x) { return cvt<T>(su[G::BXU + x]); };
+      auto V0 = [&](int y) { return cvt<T>(sv[y * G::BXV]); };
+      auto V1 = [&](int y) { return cvt<T>(sv[y * G::BXV + 1]); };
+      const T dv = fw_d4(U0(-2), U0(-1), U0(1), U0(2)) + fw_d4(V0(-2), V0(-1), V0(1), V0(2));
+      const T dv_e = fw_d4(U0(-1), U0(0), U0(2), U0(3)) + fw_d4(V1(-2), V1(-1), V1(1), V1(2));
+      const T dv_n = fw_d4(U1(-2), U1(-1), U1(1), U1(2)) + fw_d4(V0(-1), V0(0), V0(2), V0(3));
+      const T fx = cvt<T>(box(8)[pq + mp.o[8]]), rho = cvt<T>(srh[0]);
+      const T ut = cvt<T>(box(2)[pq + mp.o[2]]), vt = cvt<T>(box(3)[pq + mp.o[3]]);
+      const Off o = (Off)k * sk + col;
+      p.u_out[o] = cvt<S>(fw_out(U0(0), dt, ut, ppgu, fx, cvt<T>(srh[1]), rho, alpha, dv_e, dv));
+      p.v_out[o] = cvt<S>(fw_out(V0(0), dt, vt, ppgv, fx, cvt<T>(srh[G::BXC]), rho, alpha, dv_n, dv));
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        pk[c] = pk1[c];
+        ppv[c] = pp1[c];
+        hh[c] = h1[c];
+      }
+    }
+    __syncthreads();   // every thread is done with this stage
+    if (tid == 0 && k + D < k1) {
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      issue(k + D);
+      issued_to = k + D + 1;
+    }
+  }
+  if (failed_at >= 0 && tid == 0)
+    for (int k = failed_at; k < issued_to; ++k) mbar_wait(smem_u32(&bars[(k - k0) % D]), (unsigned)(((k - k0) / D) & 1));
+}
+
 template <class P, int TI, int TJ>
 __global__ void __launch_bounds__(TI * TJ) fw_smem_kernel(FW<typename P::S> p, double dt_d, double alpha_d, int kchunk) {
   typedef typename P::C T;
@@ -472,13 +620,65 @@ bool offsets_fit_fw(const Dom& d) {
   return hi < INT32_MAX && lo > INT32_MIN;
 }
 
+// tiles of the TMA-staged kernel (TI a multiple of 16 elements keeps every
+// box corner on a 16-byte boundary)
+#define OEC_FWTMA_TILES(X) X(32, 4) X(32, 8) X(64, 4)
+
+template <class P, int TI, int TJ>
+cudaError_t run_fw_tma(const oec_schedule& s, const Dom& d, const TmaField* tf, const FW<typename P::S>& p, double dt,
+                       double alpha, cudaStream_t st) {
+  typedef typename P::S S;
+  typedef FwTmaGeom<S, TI, TJ> G;
+  static_assert(TI % G::E == 0, "tile columns on 16-byte boundaries");
+  // per field (FASTWAVES input order): columns and rows before the point
+  // that its box starts at, level offset, box extents
+  const int hx[9] = {2, 0, 0, 0, 0, 0, 0, 0, 0}, hy[9] = {0, 2, 0, 0, 0, 0, 0, 0, 0};
+  const int kz[9] = {0, 0, 0, 0, 1, 0, 1, 1, 0};
+  const int bx[9] = {G::BXU, G::BXV, G::BXP, G::BXP, G::BXC, G::BXC, G::BXC, G::BXC, G::BXP};
+  const int by[9] = {G::BYU, G::BYV, G::BYP, G::BYP, G::BYC, G::BYC, G::BYC, G::BYC, G::BYP};
+  FwMaps mp;
+  for (int f = 0; f < 9; ++f) {
+    const int64_t cx = tf[f].corner[0] - hx[f];
+    const int o = (int)(((cx % G::E) + G::E) % G::E);
+    mp.x0[f] = (int)(cx - o);
+    mp.o[f] = o;
+    mp.y0[f] = (int)(tf[f].corner[1] - hy[f]);
+    mp.z0[f] = (int)(tf[f].corner[2] + kz[f]);
+    if (mp.x0[f] % G::E != 0) return cudaErrorMisalignedAddress;
+    if (!encode_map<S>(&mp.m[f], tf[f], d.sj, d.sk, bx[f], by[f])) return cudaErrorNotSupported;
+  }
+  unsigned* timeouts = wait_timeout_counter();
+  if (!timeouts) return cudaErrorNotSupported;
+  const int kc = (s.k_chunk <= 0 || s.k_chunk > d.nk) ? d.nk : s.k_chunk;
+  dim3 g(ceil_div(d.ni, TI), ceil_div(d.nj, TJ), ceil_div(d.nk, kc));
+  static std::once_flag attr;
+  std::call_once(attr, [] {
+    cudaFuncSetAttribute(fw_tma_kernel<P, TI, TJ, int>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
+    cudaFuncSetAttribute(fw_tma_kernel<P, TI, TJ, int64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)G::SMEM);
+  });
+  if (offsets_fit_fw(d))
+    fw_tma_kernel<P, TI, TJ, int><<<g, TI * TJ, G::SMEM, st>>>(mp, p, dt, alpha, kc, timeouts);
+  else
+    fw_tma_kernel<P, TI, TJ, int64_t><<<g, TI * TJ, G::SMEM, st>>>(mp, p, dt, alpha, kc, timeouts);
+  launched(st);
+  return cudaGetLastError();
+}
+
 #define OEC_FW_TILES(X) X(32, 4) X(32, 8) X(64, 2) X(64, 4) X(128, 2)
 // shared-memory u/v windows in the k-streaming form (OEC_STAGE_STREAM, unroll 2)
 #define OEC_FWTILE_TILES(X) X(32, 4) X(32, 8) X(64, 4) X(128, 2)
 
 template <class P>
 cudaError_t dispatch(const oec_schedule& s, const Dom& d, const FW<typename P::S>& p, double dt, double alpha,
-                     char* scratch, cudaStream_t st) {
+                     char* scratch, cudaStream_t st, const TmaField* tf) {
+  if (s.fusion == OEC_FUSE_INLINE && s.staging == OEC_STAGE_TMA) {
+    if (!tf) return cudaErrorInvalidValue;
+#define X(a, b) if (s.tile_i == a && s.tile_j == b) return run_fw_tma<P, a, b>(s, d, tf, p, dt, alpha, st);
+    OEC_FWTMA_TILES(X)
+#undef X
+    return cudaErrorInvalidValue;
+  }
   typedef typename P::C T;
   if (s.fusion == OEC_FUSE_NONE) {
     Tmp t = tmp_layout(sizeof(T), d);
@@ -559,6 +759,13 @@ bool fastwaves_schedule_ok(const oec_schedule& s, std::string& why) {
     why = "fastwaves SMEM tiles: 32x4, 32x8, 64x2, 64x4, 128x2";
     return false;
   }
+  if (s.staging == OEC_STAGE_TMA) {
+#define X(a, b) if (s.tile_i == a && s.tile_j == b && s.unroll == 1) return true;
+    OEC_FWTMA_TILES(X)
+#undef X
+    why = "fastwaves TMA tiles: 32x4, 32x8, 64x4 with unroll 1";
+    return false;
+  }
   if (s.staging != OEC_STAGE_REGS && s.staging != OEC_STAGE_STREAM) { why = "unknown staging"; return false; }
   if (s.staging == OEC_STAGE_STREAM && s.unroll == 2) {
 #define X(a, b) if (s.tile_i == a && s.tile_j == b) return true;
@@ -584,20 +791,20 @@ size_t fastwaves_scratch_bytes(const oec_schedule& s, int dtype, const Dom& d) {
 }
 
 cudaError_t fastwaves_launch(const oec_schedule& s, int dtype, const Dom& d, const FastwavesPtrs& f, double dt,
-                             double alpha, void* scratch, cudaStream_t st) {
+                             double alpha, void* scratch, cudaStream_t st, const TmaField* tf) {
   if (dtype == OEC_F64) {
     typedef double T;
     FW<T> p{(const T*)f.u_in, (const T*)f.v_in, (const T*)f.utens, (const T*)f.vtens, (const T*)f.pp,
             (const T*)f.rho, (const T*)f.wgtfac, (const T*)f.hhl, (const T*)f.fx, (T*)f.u_out, (T*)f.v_out,
             d.ni, d.nj, d.nk, d.sj, d.sk};
-    if (s.arith == 1) return dispatch<P64D>(s, d, p, dt, alpha, (char*)scratch, st);
-    return dispatch<P64>(s, d, p, dt, alpha, (char*)scratch, st);
+    if (s.arith == 1) return dispatch<P64D>(s, d, p, dt, alpha, (char*)scratch, st, tf);
+    return dispatch<P64>(s, d, p, dt, alpha, (char*)scratch, st, tf);
   }
   typedef float T;
   FW<T> p{(const T*)f.u_in, (const T*)f.v_in, (const T*)f.utens, (const T*)f.vtens, (const T*)f.pp,
           (const T*)f.rho, (const T*)f.wgtfac, (const T*)f.hhl, (const T*)f.fx, (T*)f.u_out, (T*)f.v_out,
           d.ni, d.nj, d.nk, d.sj, d.sk};
-  return dispatch<P32>(s, d, p, dt, alpha, (char*)scratch, st);
+  return dispatch<P32>(s, d, p, dt, alpha, (char*)scratch, st, tf);
 }
 
 }  // namespace oec

@@ -81,8 +81,9 @@ struct FastwavesPtrs {
 };
 bool fastwaves_schedule_ok(const oec_schedule& s, std::string& why);
 size_t fastwaves_scratch_bytes(const oec_schedule& s, int dtype, const Dom& d);
+// tf: the nine inputs' storage (FASTWAVES input order), for OEC_STAGE_TMA
 cudaError_t fastwaves_launch(const oec_schedule& s, int dtype, const Dom& d, const FastwavesPtrs& f, double dt,
-                             double alpha, void* scratch, cudaStream_t st);
+                             double alpha, void* scratch, cudaStream_t st, const TmaField* tf = nullptr);
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 

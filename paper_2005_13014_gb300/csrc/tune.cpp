@@ -88,6 +88,8 @@ std::vector<oec_schedule> candidates(const oec_program* p) {
         for (auto t : {std::pair<int, int>{32, 4}, {32, 8}, {64, 4}, {128, 2}})
           for (int u : {1, 2})   // 2: u/v windows through shared memory
             for (int kc : {8, 20, 40}) c.push_back(mk(OEC_FUSE_INLINE, OEC_STAGE_STREAM, t.first, t.second, u, kc, a));
+        for (auto t : {std::pair<int, int>{32, 4}, {32, 8}, {64, 4}})   // aligned storage only
+          for (int kc : {8, 20, 40}) c.push_back(mk(OEC_FUSE_INLINE, OEC_STAGE_TMA, t.first, t.second, 1, kc, a));
       }
       break;
     default:

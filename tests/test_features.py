@@ -17,7 +17,7 @@ def test_candidate_sets(liboec):
     assert len(_prog(programs.HDIFF, "f32", generic=False).candidates()) == 95
     assert len(_prog(programs.HDIFF_VADVC, "f64", generic=False).candidates()) == 52
     c = _prog(programs.FASTWAVES, "f64", generic=False).candidates()
-    assert len(c) == 134 and {x["arith"] for x in c} == {0, 1}
+    assert len(c) == 152 and {x["arith"] for x in c} == {0, 1}
 
 
 def test_features_shape_and_schedule_dependence(liboec):

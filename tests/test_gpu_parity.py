@@ -206,13 +206,14 @@ FW_SCHEDS = ([dict(fusion=1)]
                 for (a, b) in [(32, 4), (32, 8), (64, 4), (128, 2)] for kc in (0, 3, 4)])
 
 
-def _fw_case(n, h, dtype, sched, dt=0.5, alpha=0.0625):
+def _fw_case(n, h, dtype, sched, dt=0.5, alpha=0.0625, align=0, pad_i=0):
     f = inputs.fastwaves_fields(*n, h, seed=33)
     g = {k: _round(v, dtype) for k, v in f.items()}
     p = _prog(programs.FASTWAVES, dtype, sched)
-    d = [_dev(g[name], h, dtype) for name in inputs.FASTWAVES_NAMES]
-    uo = _dev(np.full_like(g["pp"], 555.0), h, dtype)
-    vo = _dev(np.full_like(g["pp"], 555.0), h, dtype)
+    from paper_2005_13014_gb300.api import device_field
+    d = [device_field(g[name], h, dtype, align_bytes=align, pad_i=pad_i) for name in inputs.FASTWAVES_NAMES]
+    uo = device_field(np.full_like(g["pp"], 555.0), h, dtype, align_bytes=align, pad_i=pad_i)
+    vo = device_field(np.full_like(g["pp"], 555.0), h, dtype, align_bytes=align, pad_i=pad_i)
     p.apply(d, [uo, vo], (0, 0, 0), n, (h, h, h), [dt, alpha])
     torch.cuda.synchronize()
     G = {k: S.Grid.storage(v, h) for k, v in g.items()}
@@ -226,6 +227,51 @@ def _fw_case(n, h, dtype, sched, dt=0.5, alpha=0.0625):
 @pytest.mark.parametrize("dtype,arith", PRECISIONS)
 def test_fastwaves_ragged(sched, dtype, arith):
     assert _fw_case((37, 29, 7), 3, dtype, _with(sched, arith)) <= TOL[dtype]
+
+
+FW_TMA_SCHEDS = [dict(fusion=0, staging=4, tile_i=a, tile_j=b, k_chunk=kc)
+                 for (a, b) in [(32, 4), (32, 8), (64, 4)] for kc in (0, 3)]
+
+
+@pytest.mark.parametrize("sched", FW_TMA_SCHEDS, ids=str)
+@pytest.mark.parametrize("dtype,arith", PRECISIONS)
+def test_fastwaves_tma(sched, dtype, arith):
+    """TMA-staged boxes: rows aligned at the domain corner (align 16: box
+    offsets 2 and 0 elements for FP32), and rows of 44 elements with the
+    corner at column 3 (offsets 1 and 3)."""
+    s = _with(sched, arith)
+    assert _fw_case((37, 29, 7), 3, dtype, s, align=16) <= TOL[dtype]
+    assert _fw_case((37, 29, 7), 3, dtype, s, pad_i=1) <= TOL[dtype]
+
+
+def test_fastwaves_tma_needs_aligned_pitch():
+    from paper_2005_13014_gb300._lib import OecError
+    with pytest.raises(OecError, match="16 bytes"):
+        _fw_case((37, 29, 7), 3, "f32", FW_TMA_SCHEDS[0])   # rows of 43 floats
+
+
+@pytest.mark.parametrize("n", [(37, 29, 7), (130, 9, 5), (256, 256, 80)], ids=str)
+@pytest.mark.parametrize("dtype,arith", PRECISIONS)
+def test_fastwaves_tma_bitwise(n, dtype, arith):
+    """Every input through TMA boxes against the k-streaming kernel that
+    loads per point: the same arithmetic, so the same bits."""
+    from paper_2005_13014_gb300 import _lib as L
+    from paper_2005_13014_gb300.api import device_field
+    h = 3
+    f = inputs.fastwaves_fields(*n, h, seed=35)
+    g = {k: _round(v, dtype) for k, v in f.items()}
+    outs = []
+    for sched in (dict(fusion=0, staging=2, tile_i=32, tile_j=8, k_chunk=8, arith=arith),
+                  dict(fusion=0, staging=4, tile_i=32, tile_j=4, k_chunk=8, arith=arith)):
+        p = _prog(programs.FASTWAVES, dtype, sched)
+        d = [device_field(g[name], h, dtype, align_bytes=16) for name in inputs.FASTWAVES_NAMES]
+        o = [device_field(np.zeros_like(g["pp"]), h, dtype, align_bytes=16) for _ in range(2)]
+        p.apply(d, o, (0, 0, 0), n, (h, h, h), [0.5, 0.0625])
+        torch.cuda.synchronize()
+        outs.append([x.tensor.cpu().numpy() for x in o])
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+    assert L.lib().oec_device_status(None) == 0
 
 
 @pytest.mark.parametrize("n", [(37, 29, 7), (130, 9, 5), (256, 256, 80)], ids=str)
