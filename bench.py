@@ -285,24 +285,25 @@ def run_gpu(args):
     total_ms = float(tmax.item())
     value = points * args.steps * ws / (total_ms * 1e-3)
 
-    # end to end through the same ABI call: pinned host inputs -> device, apply,
-    # outputs -> pinned host, every step inside the timed region
-    host_in = [torch.from_numpy(f[k]).pin_memory() for k in ("u", "v", "w", "coeff")]
-    host_out = [torch.empty_like(host_in[0]).pin_memory() for _ in range(2)]
-    d0, o0 = sets[0]
-    h2d = sum(t.numel() * t.element_size() for t in host_in)
-    d2h = sum(t.numel() * t.element_size() for t in host_out)
+    # end to end through the host-memory ABI call (oec_program_apply_host):
+    # every step copies its inputs' storage from page-locked host memory to
+    # the library's device staging, applies, and copies the outputs' domain
+    # back; all inside the timed region (the library overlaps a step's input
+    # copies with the previous step's compute and output copies)
+    from paper_2005_13014_gb300.api import host_field
+    host_in = [host_field(f[k], H, "f64") for k in ("u", "v", "w", "coeff")]
+    host_out = [host_field(np.zeros_like(f["u"]), H, "f64") for _ in range(2)]
+    h2d = sum(t.tensor.numel() * t.tensor.element_size() for t in host_in)   # the inputs' storage
+    d2h = 2 * points * 8
     e2e_steps = max(10, min(args.steps, 200))
+    for _ in range(3):   # staging allocated, copies warm
+        prog.apply_host(host_in, host_out, lb, ub, halo, [DTR], stream=stream)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(stream):
         e0.record(stream)
         for _ in range(e2e_steps):
-            for t_h, fd in zip(host_in, d0):
-                fd.tensor.copy_(t_h, non_blocking=True)
-            prog.apply(d0, o0, lb, ub, halo, [DTR], stream=stream)
-            for t_h, fd in zip(host_out, o0):
-                t_h.copy_(fd.tensor, non_blocking=True)
+            prog.apply_host(host_in, host_out, lb, ub, halo, [DTR], stream=stream)
         e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / e2e_steps

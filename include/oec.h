@@ -238,6 +238,27 @@ OEC_API int oec_program_apply(oec_program_t p, const oec_field_desc* in, int n_i
                       const double* params, int n_params, void* cuda_stream);
 
 /*
+ * oec_program_apply with every field in HOST memory: `data` of each
+ * descriptor is a host pointer (page-locked memory keeps the call
+ * asynchronous; pageable memory works, with the copies synchronous). The
+ * library copies each input's storage span (what its size and strides
+ * cover) into device staging buffers it owns, applies the program there, and
+ * copies back each output's domain box [lb, ub) only: host output storage
+ * outside the domain is left as it was. Staging buffers come in two sets used
+ * in turn, allocated at the first call and again when field shapes change;
+ * the input copies run on a library stream, so the next call's inputs cross
+ * while this call computes and its outputs cross on `cuda_stream`.
+ * Ordered on `cuda_stream`: the host outputs are complete once it has been
+ * synchronised. Fields need a unit i stride and positive j/k strides
+ * (OEC_ERR_UNSUPPORTED). Not for stream capture.
+ * Errors: those of oec_program_apply, and OEC_ERR_CUDA for allocations and
+ * copies.
+ */
+OEC_API int oec_program_apply_host(oec_program_t p, const oec_field_desc* in, int n_in, const oec_field_desc* out,
+                                   int n_out, const int64_t lb[3], const int64_t ub[3], const int64_t halo[3],
+                                   const double* params, int n_params, void* cuda_stream);
+
+/*
  * Compile and load the generated kernels of a program without a hand-written
  * kernel for a domain extent and field j/k strides (what the first apply at
  * that shape would do), so that applies and stream capture that follow

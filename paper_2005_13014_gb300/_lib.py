@@ -82,6 +82,8 @@ def lib():
         "oec_program_get_schedule": (C.c_int, [P, C.POINTER(Schedule)]),
         "oec_program_apply": (C.c_int, [P, C.POINTER(FieldDesc), C.c_int, C.POINTER(FieldDesc), C.c_int,
                                         I64x3, I64x3, I64x3, C.POINTER(C.c_double), C.c_int, P]),
+        "oec_program_apply_host": (C.c_int, [P, C.POINTER(FieldDesc), C.c_int, C.POINTER(FieldDesc), C.c_int,
+                                             I64x3, I64x3, I64x3, C.POINTER(C.c_double), C.c_int, P]),
         "oec_program_algorithmic_bytes": (C.c_int, [P, I64x3, I64x3, C.POINTER(C.c_int64)]),
         "oec_device_status": (C.c_int, [P]),
         "oec_costmodel_save": (C.c_int, [P, C.c_char_p]),

@@ -92,6 +92,15 @@ def device_field(arr: np.ndarray, h, dtype="f64", device="cuda", align_bytes=0, 
     return Field(t, (front + hi, hj, hk))
 
 
+def host_field(arr: np.ndarray, h, dtype="f64", pinned=True, align_bytes=0, pad_i=0, pad_value=0.0):
+    """``device_field``'s layout in host memory (page-locked unless
+    ``pinned`` is false), for ``Program.apply_host``."""
+    f = device_field(arr, h, dtype, device="cpu", align_bytes=align_bytes, pad_i=pad_i, pad_value=pad_value)
+    if pinned:
+        f.tensor = f.tensor.pin_memory()
+    return f
+
+
 class BoundApply:
     """One program apply with its arguments marshalled once (Program.bind)."""
 
@@ -269,6 +278,17 @@ class Program:
             stream = stream.cuda_stream
         L.check(L.lib().oec_program_apply(self._h, ins, len(inputs), outs, len(outputs), L.I64x3(*lb),
                                           L.I64x3(*ub), L.I64x3(*halo), par, len(params), C.c_void_p(stream)))
+
+    def apply_host(self, inputs, outputs, lb, ub, halo, params=(), stream=None):
+        """``apply`` with fields in host memory (``host_field``): the library
+        copies the inputs in and the outputs' domain back, ordered on
+        ``stream``; the host outputs are complete after it is synchronised."""
+        ins = (L.FieldDesc * max(1, len(inputs)))(*[f.desc() for f in inputs])
+        outs = (L.FieldDesc * max(1, len(outputs)))(*[f.desc() for f in outputs])
+        par = (C.c_double * max(1, len(params)))(*params)
+        L.check(L.lib().oec_program_apply_host(self._h, ins, len(inputs), outs, len(outputs), L.I64x3(*lb),
+                                               L.I64x3(*ub), L.I64x3(*halo), par, len(params),
+                                               C.c_void_p(_stream_handle(stream))))
 
 
 def _stream_handle(stream):

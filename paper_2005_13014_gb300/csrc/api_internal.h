@@ -27,6 +27,16 @@ struct oec_program {
   int ev_used = 0;
   std::vector<int> ev_first, ev_count;
   int last_launches = 0;
+  // oec_program_apply_host: two sets of device staging buffers (inputs then
+  // outputs, bytes[x] each), the input-copy streams and the sets' events
+  static constexpr int kCopyStreams = 1;
+  struct HostStage {
+    cudaStream_t copy[kCopyStreams] = {};
+    cudaEvent_t inputs_in[2][kCopyStreams] = {}, released[2] = {nullptr, nullptr};
+    std::vector<void*> buf[2];
+    std::vector<size_t> bytes;
+    int dev = -1, next = 0;
+  } host;
 };
 
 namespace oec {

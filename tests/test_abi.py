@@ -114,6 +114,27 @@ def test_validation_errors_without_gpu(liboec):
     assert "inverted" in msg
 
 
+def test_apply_host_validation_without_gpu(liboec):
+    """Host-memory apply: shape errors and empty domains are settled before
+    any device call."""
+    p = _prog(programs.HDIFF)
+    n, h = (16, 12, 5), 2
+    shp = (n[0] + 2 * h, n[1] + 2 * h, n[2] + 2 * h)
+    fin, fco, fout = (_fake(a, shp, (h, h, h)) for a in (1 << 20, 2 << 20, 3 << 20))
+    bad = _fake(4 << 20, shp, (h, h, h))
+    bad.stride = L.I64x3(2, 2 * shp[0], 2 * shp[0] * shp[1])
+
+    def host(ins, outs, ub):
+        a = (L.FieldDesc * len(ins))(*ins)
+        b = (L.FieldDesc * len(outs))(*outs)
+        return L.lib().oec_program_apply_host(p.handle, a, len(ins), b, len(outs), L.I64x3(0, 0, 0), L.I64x3(*ub),
+                                              L.I64x3(h, h, h), (C.c_double * 1)(), 0, None)
+    assert host([fin, fco], [bad], n) == -7                        # UNSUPPORTED: i stride 2
+    assert "unit i stride" in L.lib().oec_last_error().decode()
+    assert host([fin], [fout], n) == -1                            # wrong input count
+    assert host([fin, fco], [fout], (16, 12, 0)) == 0              # empty domain: nothing to do
+
+
 def test_bad_schedule_rejected(liboec):
     p = _prog(programs.HDIFF)
     with pytest.raises(L.OecError):
