@@ -306,6 +306,50 @@ OEC_API int oec_program_autotune(oec_program_t p, const oec_field_desc* in, int 
                                  const double* params, int n_params, const oec_schedule* candidates, int n_candidates,
                                  int reps, void* cuda_stream, double* times_ms, int* best);
 
+/* ---- tuning database (the autotuner's results kept across runs) ---------- */
+typedef struct oec_tunedb* oec_tunedb_t;
+
+/*
+ * Open a tuning database: entries map a key - the program (hash of its
+ * canonical text, recognised kind, dtype), the domain extent, the fields'
+ * shared j/k strides, whether every field's domain corner and the strides
+ * are 16-byte aligned, and the device (name, SM count, compute capability) -
+ * to a schedule and its time in milliseconds. path: a text file ("oec-tunedb
+ * 1" then one tab-separated entry per line), loaded if it exists, else the
+ * database starts empty; NULL keeps it in memory. Errors: OEC_ERR_INVALID_ARG
+ * (the file exists but is not a database, with the line in the message).
+ */
+OEC_API int oec_tunedb_open(const char* path, oec_tunedb_t* out);
+/* Write every entry to path (NULL: the path given at open) through a
+ * temporary file renamed over it. Errors: OEC_ERR_INVALID_ARG (no path, not
+ * writable). */
+OEC_API int oec_tunedb_save(oec_tunedb_t db, const char* path);
+/* Number of entries (>= 0), or OEC_ERR_INVALID_ARG. */
+OEC_API int oec_tunedb_count(oec_tunedb_t db);
+OEC_API void oec_tunedb_close(oec_tunedb_t db);
+/* Look up the key of an apply (fields and domain as for oec_program_apply;
+ * nothing is read from the fields' memory). *found = 1 and *s, *ms (each may
+ * be NULL) set when present, else *found = 0. No GPU work. */
+OEC_API int oec_tunedb_find(oec_tunedb_t db, oec_program_t p, const oec_field_desc* in, int n_in,
+                            const oec_field_desc* out, int n_out, const int64_t lb[3], const int64_t ub[3],
+                            oec_schedule* s, double* ms, int* found);
+/* Record (or replace) the entry of an apply's key. Errors: OEC_ERR_INVALID_ARG,
+ * OEC_ERR_UNSUPPORTED (a schedule the program cannot run). */
+OEC_API int oec_tunedb_record(oec_tunedb_t db, oec_program_t p, const oec_field_desc* in, int n_in,
+                              const oec_field_desc* out, int n_out, const int64_t lb[3], const int64_t ub[3],
+                              const oec_schedule* s, double ms);
+/*
+ * Autotune through the database: when the key of this apply is recorded (and
+ * its schedule still valid) the program takes that schedule and *from_db = 1,
+ * with no GPU work; otherwise oec_program_autotune times every candidate,
+ * the fastest becomes the schedule and is recorded, *from_db = 0. The
+ * database is not saved. Errors: as oec_program_autotune.
+ */
+OEC_API int oec_program_autotune_db(oec_program_t p, oec_tunedb_t db, const oec_field_desc* in, int n_in,
+                                    const oec_field_desc* out, int n_out, const int64_t lb[3], const int64_t ub[3],
+                                    const int64_t halo[3], const double* params, int n_params, int reps,
+                                    void* cuda_stream, int* from_db);
+
 /*
  * Features of (program, domain extent, field strides, schedule) for the learned
  * cost model (no counterpart in the paper): 42 floats - program structure

@@ -84,6 +84,17 @@ def lib():
                                         I64x3, I64x3, I64x3, C.POINTER(C.c_double), C.c_int, P]),
         "oec_program_apply_host": (C.c_int, [P, C.POINTER(FieldDesc), C.c_int, C.POINTER(FieldDesc), C.c_int,
                                              I64x3, I64x3, I64x3, C.POINTER(C.c_double), C.c_int, P]),
+        "oec_tunedb_open": (C.c_int, [C.c_char_p, C.POINTER(P)]),
+        "oec_tunedb_save": (C.c_int, [P, C.c_char_p]),
+        "oec_tunedb_count": (C.c_int, [P]),
+        "oec_tunedb_close": (None, [P]),
+        "oec_tunedb_find": (C.c_int, [P, P, C.POINTER(FieldDesc), C.c_int, C.POINTER(FieldDesc), C.c_int, I64x3,
+                                      I64x3, C.POINTER(Schedule), C.POINTER(C.c_double), C.POINTER(C.c_int)]),
+        "oec_tunedb_record": (C.c_int, [P, P, C.POINTER(FieldDesc), C.c_int, C.POINTER(FieldDesc), C.c_int, I64x3,
+                                        I64x3, C.POINTER(Schedule), C.c_double]),
+        "oec_program_autotune_db": (C.c_int, [P, P, C.POINTER(FieldDesc), C.c_int, C.POINTER(FieldDesc), C.c_int,
+                                              I64x3, I64x3, I64x3, C.POINTER(C.c_double), C.c_int, C.c_int, P,
+                                              C.POINTER(C.c_int)]),
         "oec_program_algorithmic_bytes": (C.c_int, [P, I64x3, I64x3, C.POINTER(C.c_int64)]),
         "oec_device_status": (C.c_int, [P]),
         "oec_costmodel_save": (C.c_int, [P, C.c_char_p]),

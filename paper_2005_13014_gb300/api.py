@@ -92,6 +92,52 @@ def device_field(arr: np.ndarray, h, dtype="f64", device="cuda", align_bytes=0, 
     return Field(t, (front + hi, hj, hk))
 
 
+class TuneDB:
+    """The tuning database (oec_tunedb_*): best schedules by (program, dtype,
+    domain, strides, alignment, device), loaded from and saved to ``path``
+    (None: memory only)."""
+
+    def __init__(self, path=None):
+        h = C.c_void_p()
+        L.check(L.lib().oec_tunedb_open(path.encode() if path else None, C.byref(h)))
+        self._h = h
+
+    def __len__(self):
+        n = L.lib().oec_tunedb_count(self._h)
+        L.check(min(n, 0))
+        return n
+
+    def save(self, path=None):
+        L.check(L.lib().oec_tunedb_save(self._h, path.encode() if path else None))
+
+    def _fields(self, inputs, outputs):
+        ins = (L.FieldDesc * max(1, len(inputs)))(*[f.desc() for f in inputs])
+        outs = (L.FieldDesc * max(1, len(outputs)))(*[f.desc() for f in outputs])
+        return ins, outs
+
+    def find(self, prog, inputs, outputs, lb, ub):
+        """(schedule dict, ms) recorded for this apply, or None."""
+        ins, outs = self._fields(inputs, outputs)
+        s, ms, found = L.Schedule(), C.c_double(), C.c_int()
+        L.check(L.lib().oec_tunedb_find(self._h, prog.handle, ins, len(inputs), outs, len(outputs), L.I64x3(*lb),
+                                        L.I64x3(*ub), C.byref(s), C.byref(ms), C.byref(found)))
+        return (schedule_dict(s), ms.value) if found.value else None
+
+    def record(self, prog, inputs, outputs, lb, ub, schedule, ms):
+        ins, outs = self._fields(inputs, outputs)
+        s = schedule_struct(schedule)
+        L.check(L.lib().oec_tunedb_record(self._h, prog.handle, ins, len(inputs), outs, len(outputs), L.I64x3(*lb),
+                                          L.I64x3(*ub), C.byref(s), float(ms)))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            L.lib().oec_tunedb_close(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+
 def host_field(arr: np.ndarray, h, dtype="f64", pinned=True, align_bytes=0, pad_i=0, pad_value=0.0):
     """``device_field``'s layout in host memory (page-locked unless
     ``pinned`` is false), for ``Program.apply_host``."""
@@ -278,6 +324,19 @@ class Program:
             stream = stream.cuda_stream
         L.check(L.lib().oec_program_apply(self._h, ins, len(inputs), outs, len(outputs), L.I64x3(*lb),
                                           L.I64x3(*ub), L.I64x3(*halo), par, len(params), C.c_void_p(stream)))
+
+    def autotune_db(self, db, inputs, outputs, lb, ub, halo, params=(), reps=5, stream=None):
+        """Autotune through a ``TuneDB``: a recorded case takes its schedule
+        without timing; otherwise every candidate is timed and the fastest
+        recorded. Returns True when the schedule came from the database."""
+        ins = (L.FieldDesc * max(1, len(inputs)))(*[f.desc() for f in inputs])
+        outs = (L.FieldDesc * max(1, len(outputs)))(*[f.desc() for f in outputs])
+        par = (C.c_double * max(1, len(params)))(*params)
+        hit = C.c_int()
+        L.check(L.lib().oec_program_autotune_db(self._h, db._h, ins, len(inputs), outs, len(outputs), L.I64x3(*lb),
+                                                L.I64x3(*ub), L.I64x3(*halo), par, len(params), reps,
+                                                C.c_void_p(_stream_handle(stream)), C.byref(hit)))
+        return bool(hit.value)
 
     def apply_host(self, inputs, outputs, lb, ub, halo, params=(), stream=None):
         """``apply`` with fields in host memory (``host_field``): the library
