@@ -166,6 +166,14 @@ TESTSET_INPUTS = {
                  "rdxc": (0.5, 1.5), "rdyc": (0.5, 1.5)},
     "hadvuv": {n: (-1, 1) for n in ("uin", "vin", "uatupos", "vatupos", "uatvpos", "vatvpos")},
     "fvtp2d_flux": {n: (-1, 1) for n in ("q", "crx", "cry", "xfx", "yfx", "al", "bl")},
+    "hdiffsmag": {"u": (-1, 1), "v": (-1, 1), "hdmask": (0.0, 1.0), "crlavo": (0.9, 1.1), "crlavu": (0.9, 1.1),
+                  "crlato": (0.9, 1.1), "crlatu": (0.9, 1.1), "acrlat0": (0.9, 1.1)},
+    "hadvuv5th": {n: (-1, 1) for n in ("uin", "vin", "uatupos", "vatupos", "uatvpos", "vatvpos")},
+    "nh_p_grad": {"u": (-1, 1), "v": (-1, 1), "rdx": (0.5, 1.5), "rdy": (0.5, 1.5), "gz": "kdown", "pp": (-1, 1),
+                  "pk3": "kup", "delp": (1.0, 2.0)},
+    "fvtp2d_qi": {"q": (-1, 1), "crx": (-1, 1), "xfx": (-1, 1), "area": (0.5, 1.5), "ra_x": (0.5, 1.5)},
+    "fvtp2d_qj": {"q": (-1, 1), "cry": (-1, 1), "yfx": (-1, 1), "area": (0.5, 1.5), "ra_y": (0.5, 1.5),
+                  "mfy": (-1, 1)},
 }
 
 

@@ -73,9 +73,13 @@ BUILTIN = {"hdiff": HDIFF, "hdiff_vadvc": HDIFF_VADVC, "fastwaves": FASTWAVES}
 # The paper gives only the shape of its COSMO/FV3 benchmarks (applies,
 # inputs/outputs, control flow), not their formulas; these programs have the
 # listed shapes with stencils of the same kind (averaging, pressure gradients
-# over a k-staggered grid, third-order upwind advection with an `if` written
-# as select, and upwind flux selection), and run through the generic code
-# generator. They are stand-ins, not the COSMO/FV3 kernels.
+# over a k-staggered grid, third- and fifth-order upwind advection with an
+# `if` written as select, a clipped Smagorinsky coefficient, interface values
+# and upwind flux selection), and run through the generic code generator.
+# Every select decides on an input field, never on a computed value, so FP32
+# and FP64 take the same branch. They are stand-ins, not the COSMO/FV3
+# kernels. With hdiff (hdiffsa) and fastwaves (fastwavesuv) they cover all
+# eleven rows of Table II.
 
 # uvbke (FV3): 2 applies, 4 inputs / 2 outputs
 UVBKE = """
@@ -122,12 +126,87 @@ stage fy = yfx*fy1
 output fx, fy
 """
 
+# hdiffsmag (COSMO): 6 applies, 8 inputs / 2 outputs, min/max (Smagorinsky
+# coefficient clipped to [0, 0.5]; the deformation enters squared)
+HDIFFSMAG = """
+input u, v, hdmask, crlavo, crlavu, crlato, crlatu, acrlat0
+param eddlat, eddlon, tau_smag, weight_smag
+stage t = eddlon*(u - u[-1,0,0]) - eddlat*acrlat0*(v - v[0,-1,0])
+stage s = eddlat*crlavo*(u[0,1,0] - u) + eddlon*(v[1,0,0] - v)
+stage smag_u = min(0.5, max(0.0, tau_smag*(t*t + s[0,-1,0]*s[0,-1,0]) - weight_smag))
+stage smag_v = min(0.5, max(0.0, tau_smag*(t[0,1,0]*t[0,1,0] + s[-1,0,0]*s[-1,0,0]) - weight_smag))
+stage u_out = u + hdmask*smag_u*(u[1,0,0] + u[-1,0,0] - 2.0*u + crlato*(u[0,1,0] - u) + crlatu*(u[0,-1,0] - u))
+stage v_out = v + hdmask*smag_v*(v[1,0,0] + v[-1,0,0] - 2.0*v + crlavo*(v[0,1,0] - v) + crlavu*(v[0,-1,0] - v))
+output u_out, v_out
+"""
+
+# hadvuv5th (COSMO): 8 applies, 6 inputs / 2 outputs, `if` (upwind
+# direction), fifth-order upwind stencils (offsets up to 3)
+HADVUV5TH = """
+input uin, vin, uatupos, vatupos, uatvpos, vatvpos
+param eddlat, eddlon
+stage axu = select(uatupos > 0.0, uatupos*(-2.0*uin[-3,0,0] + 15.0*uin[-2,0,0] - 60.0*uin[-1,0,0] + 20.0*uin + 30.0*uin[1,0,0] - 3.0*uin[2,0,0]), uatupos*(3.0*uin[-2,0,0] - 30.0*uin[-1,0,0] - 20.0*uin + 60.0*uin[1,0,0] - 15.0*uin[2,0,0] + 2.0*uin[3,0,0]))
+stage ayu = select(vatupos > 0.0, vatupos*(-2.0*uin[0,-3,0] + 15.0*uin[0,-2,0] - 60.0*uin[0,-1,0] + 20.0*uin + 30.0*uin[0,1,0] - 3.0*uin[0,2,0]), vatupos*(3.0*uin[0,-2,0] - 30.0*uin[0,-1,0] - 20.0*uin + 60.0*uin[0,1,0] - 15.0*uin[0,2,0] + 2.0*uin[0,3,0]))
+stage axv = select(uatvpos > 0.0, uatvpos*(-2.0*vin[-3,0,0] + 15.0*vin[-2,0,0] - 60.0*vin[-1,0,0] + 20.0*vin + 30.0*vin[1,0,0] - 3.0*vin[2,0,0]), uatvpos*(3.0*vin[-2,0,0] - 30.0*vin[-1,0,0] - 20.0*vin + 60.0*vin[1,0,0] - 15.0*vin[2,0,0] + 2.0*vin[3,0,0]))
+stage ayv = select(vatvpos > 0.0, vatvpos*(-2.0*vin[0,-3,0] + 15.0*vin[0,-2,0] - 60.0*vin[0,-1,0] + 20.0*vin + 30.0*vin[0,1,0] - 3.0*vin[0,2,0]), vatvpos*(3.0*vin[0,-2,0] - 30.0*vin[0,-1,0] - 20.0*vin + 60.0*vin[0,1,0] - 15.0*vin[0,2,0] + 2.0*vin[0,3,0]))
+stage advu = (eddlon*axu + eddlat*ayu)/60.0
+stage advv = (eddlon*axv + eddlat*ayv)/60.0
+stage uout = uin - advu
+stage vout = vin - advv
+output uout, vout
+"""
+
+# nh_p_grad (FV3): 5 applies, 8 inputs / 2 outputs, 3-D (non-hydrostatic
+# pressure gradient over a k-staggered grid)
+NH_P_GRAD = """
+input u, v, rdx, rdy, gz, pp, pk3, delp
+param dt
+stage wk = pk3[0,0,1] - pk3
+stage du = dt/(wk + wk[1,0,0])*((gz[0,0,1] - gz[1,0,0])*(pk3[1,0,1] - pk3) + (gz - gz[1,0,1])*(pk3[0,0,1] - pk3[1,0,0]))
+stage dv = dt/(wk + wk[0,1,0])*((gz[0,0,1] - gz[0,1,0])*(pk3[0,1,1] - pk3) + (gz - gz[0,1,1])*(pk3[0,0,1] - pk3[0,1,0]))
+stage u_out = (u + du*rdx) + dt*rdx*(pp[1,0,0] - pp)/(delp + delp[1,0,0])
+stage v_out = (v + dv*rdy) + dt*rdy*(pp[0,1,0] - pp)/(delp + delp[0,1,0])
+output u_out, v_out
+"""
+
+# fvtp2d_qi (FV3): 5 applies, 5 inputs / 2 outputs, `if` (upwind side):
+# fourth-order interface values along i, an upwind flux, the flux-form update
+FVTP2D_QI = """
+input q, crx, xfx, area, ra_x
+stage al = 0.5833333333333334*(q[-1,0,0] + q) - 0.08333333333333333*(q[-2,0,0] + q[1,0,0])
+stage bl = al - q
+stage br = al[1,0,0] - q
+stage fx1 = select(crx > 0.0, q[-1,0,0] + (1.0 - crx)*(br[-1,0,0] - crx*(bl[-1,0,0] + br[-1,0,0])), q + (1.0 + crx)*(bl + crx*(bl + br)))
+stage q_i = (q*area + fx1*xfx - fx1[1,0,0]*xfx[1,0,0])/ra_x
+output fx1, q_i
+"""
+
+# fvtp2d_qj (FV3): 8 applies, 6 inputs / 3 outputs, `if` (upwind side):
+# as fvtp2d_qi along j, with a smoothness bound and a mass flux
+FVTP2D_QJ = """
+input q, cry, yfx, area, ra_y, mfy
+stage al = 0.5833333333333334*(q[0,-1,0] + q) - 0.08333333333333333*(q[0,-2,0] + q[0,1,0])
+stage bl = al - q
+stage br = al[0,1,0] - q
+stage b0 = min(abs(bl), abs(br))*(bl + br)
+stage fy1 = select(cry > 0.0, q[0,-1,0] + (1.0 - cry)*(br[0,-1,0] - cry*b0[0,-1,0]), q + (1.0 + cry)*(bl + cry*b0))
+stage fy = yfx*fy1
+stage q_j = (q*area + fy - fy[0,1,0])/ra_y
+stage mf = mfy*fy1
+output fy, q_j, mf
+"""
+
 # name: (text, scalar parameters, (applies, inputs, outputs) as Table II lists them)
 TESTSET = {
     "uvbke": (UVBKE, [0.5], (2, 4, 2)),
     "p_grad_c": (P_GRAD_C, [0.01], (3, 7, 2)),
     "hadvuv": (HADVUV, [0.1, 0.1], (8, 6, 2)),
     "fvtp2d_flux": (FVTP2D_FLUX, [], (5, 7, 2)),
+    "hdiffsmag": (HDIFFSMAG, [0.5, 0.5, 0.1, 0.01], (6, 8, 2)),
+    "hadvuv5th": (HADVUV5TH, [0.1, 0.1], (8, 6, 2)),
+    "nh_p_grad": (NH_P_GRAD, [0.01], (5, 8, 2)),
+    "fvtp2d_qi": (FVTP2D_QI, [], (5, 5, 2)),
+    "fvtp2d_qj": (FVTP2D_QJ, [], (8, 6, 3)),
 }
 
 # default scalar parameters of the synthetic workloads

@@ -21,6 +21,20 @@ HALOS = {
                **{n: ((0, 0),) * 3 for n in ("uatupos", "vatupos", "uatvpos", "vatvpos")}},
     "fvtp2d_flux": {"q": ((1, 1), (1, 0), (0, 0)),
                     **{n: ((0, 0),) * 3 for n in ("crx", "cry", "xfx", "yfx", "al", "bl")}},
+    # t at (0,0),(0,1); s at (0,-1),(-1,0); updates at +-1 in i and j
+    "hdiffsmag": {"u": ((1, 1), (1, 1), (0, 0)), "v": ((1, 1), (1, 1), (0, 0)), "crlavo": ((1, 0), (1, 0), (0, 0)),
+                  "acrlat0": ((0, 0), (0, 1), (0, 0)),
+                  **{n: ((0, 0),) * 3 for n in ("hdmask", "crlavu", "crlato", "crlatu")}},
+    "hadvuv5th": {"uin": ((3, 3), (3, 3), (0, 0)), "vin": ((3, 3), (3, 3), (0, 0)),
+                  **{n: ((0, 0),) * 3 for n in ("uatupos", "vatupos", "uatvpos", "vatvpos")}},
+    # wk at (0,0),(1,0),(0,1), each spanning k and k+1
+    "nh_p_grad": {"gz": ((0, 1), (0, 1), (0, 1)), "pk3": ((0, 1), (0, 1), (0, 1)), "pp": ((0, 1), (0, 1), (0, 0)),
+                  "delp": ((0, 1), (0, 1), (0, 0)), **{n: ((0, 0),) * 3 for n in ("u", "v", "rdx", "rdy")}},
+    # fx1 at i and i+1 reads al at i-1 .. i+2, al reads q at -2 .. +1
+    "fvtp2d_qi": {"q": ((3, 3), (0, 0), (0, 0)), "crx": ((0, 1), (0, 0), (0, 0)), "xfx": ((0, 1), (0, 0), (0, 0)),
+                  "area": ((0, 0),) * 3, "ra_x": ((0, 0),) * 3},
+    "fvtp2d_qj": {"q": ((0, 0), (3, 3), (0, 0)), "cry": ((0, 0), (0, 1), (0, 0)), "yfx": ((0, 0), (0, 1), (0, 0)),
+                  **{n: ((0, 0),) * 3 for n in ("area", "ra_y", "mfy")}},
 }
 
 
@@ -30,8 +44,10 @@ def test_shape_matches_table_ii(name):
     p = OP.parse(src)
     assert len(p.stmts) == applies and len(p.inputs) == n_in and len(p.outputs) == n_out
     assert len(params) == len(p.params)
-    if name in ("hadvuv", "fvtp2d_flux"):
+    if name in ("hadvuv", "hadvuv5th", "fvtp2d_flux", "fvtp2d_qi", "fvtp2d_qj"):
         assert "select(" in src   # the table's `if`
+    if name == "hdiffsmag":
+        assert "min(" in src and "max(" in src
 
 
 @pytest.mark.parametrize("name", list(programs.TESTSET))
