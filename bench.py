@@ -680,8 +680,16 @@ def run_costmodel(args):
     dflt = [x for x, c in enumerate(cands) if c["fusion"] == 0 and c["tile_i"] == 64 and c["tile_j"] == 4]
     dflt_u1 = [x for x in dflt if cands[x]["unroll"] == 1]
     rng = np.random.default_rng(0)
+    # greedy non-learned baseline: at the paper's default tile, the fusion
+    # (inline / none / partial) whose roofline estimate max(bytes / HBM,
+    # operations / FP32 issue rate) from the generated code's per-point
+    # counts is lowest; untimed at unroll 1, or its unrolls timed
+    hbm = float(_peaks().get("hbm_gbs", 6800.0)) * 1e9
+    f_ops = 3e13   # FP32 instructions per second, ~152 SMs x 128 lanes x 1.9 GHz / ~1.2 per op
+    d64x4 = [x for x, c in enumerate(cands) if c["tile_i"] == 64 and c["tile_j"] == 4]
     R = {k: [] for k in ("model_top1", "model_top2", "model_top3", "model_top2_plus_fixed",
-                         "paper_default_tuned_unroll", "paper_default_unroll1", "best_fixed_from_training", "random")}
+                         "paper_default_tuned_unroll", "paper_default_unroll1", "greedy_roofline_fusion_unroll1",
+                         "greedy_roofline_fusion_tuned_unroll", "best_fixed_from_training", "random")}
     for d in range(Fte.shape[0]):
         t = np.where(Tte[d] > 0, Tte[d], np.inf)
         best = t.min()
@@ -692,10 +700,17 @@ def run_costmodel(args):
         R["model_top2_plus_fixed"].append(min(t[x] for x in order[:2] + [fixed]) / best - 1)
         R["paper_default_tuned_unroll"].append(min(t[x] for x in dflt) / best - 1)
         R["paper_default_unroll1"].append(min(t[x] for x in dflt_u1) / best - 1)
+        est = np.maximum(Fte[d][:, 36] / hbm, Fte[d][:, 30] / f_ops)
+        u1 = [x for x in d64x4 if cands[x]["unroll"] == 1 and np.isfinite(t[x])]
+        g = min(u1, key=lambda x: est[x])
+        R["greedy_roofline_fusion_unroll1"].append(t[g] / best - 1)
+        R["greedy_roofline_fusion_tuned_unroll"].append(
+            min(t[x] for x in d64x4 if cands[x]["fusion"] == cands[g]["fusion"]) / best - 1)
         R["best_fixed_from_training"].append(t[fixed] / best - 1)
         R["random"].append(t[rng.choice(np.flatnonzero(np.isfinite(t)))] / best - 1)
     timed = {"model_top1": 1, "model_top2": 2, "model_top3": 3, "model_top2_plus_fixed": 3,
-             "paper_default_tuned_unroll": len(dflt), "paper_default_unroll1": 0, "best_fixed_from_training": 0,
+             "paper_default_tuned_unroll": len(dflt), "paper_default_unroll1": 0,
+             "greedy_roofline_fusion_unroll1": 0, "greedy_roofline_fusion_tuned_unroll": 3, "best_fixed_from_training": 0,
              "random": 0, "exhaustive": len(cands)}
     out = {"workload": "cost model: random DAGs 256x256x80 FP32", "train_dags": len(train_seeds),
            "train_timings": int(X.shape[0]), "test_dags": len(test_seeds), "candidates": len(cands),
