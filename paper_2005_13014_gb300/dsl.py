@@ -6,7 +6,7 @@ trace is printed in the textual form that ``oec_program_create`` parses
 (paper §IV: ``input`` loads, one ``stage`` per stencil.apply with constant
 offset accesses, ``column`` solves, ``output`` stores). It plays the role of
 the Python front ends that lower to the stencil dialect (GT4Py-like, paper
-§VIII). Nothing here computes: the library does, from the text.
+§VII-E). Nothing here computes: the library does, from the text.
 
     from paper_2005_13014_gb300 import dsl
 
