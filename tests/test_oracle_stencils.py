@@ -67,6 +67,26 @@ def test_hdiff_impulse_matches_hand_derivation():
     assert np.sum(out - inp[h:-h, h:-h, h:-h]) == 0.0
 
 
+def test_hdiff_flux_form_telescopes():
+    """With a constant coeff c the interior sum of out - in is -c times the net
+    flux through the domain's boundary (flux form: interior fluxes cancel);
+    random data, so the sums agree to rounding."""
+    h, n, c = 2, (12, 9, 3), 0.0625
+    f = inputs.hdiff_fields(*n, h, seed=17)
+    coeff = np.full_like(f["in"], c)
+    st = S.hdiff_stages(_grid(f["in"], h), _grid(coeff, h), (0, 0, 0), n)
+    flx, fly = st["flx"], st["fly"]
+    net = 0.0
+    for k in range(n[2]):
+        for j in range(n[1]):
+            net += flx.value(n[0] - 1, j, k) - flx.value(-1, j, k)
+        for i in range(n[0]):
+            net += fly.value(i, n[1] - 1, k) - fly.value(i, -1, k)
+    lhs = float(np.sum(st["out"].arr - f["in"][h:-h, h:-h, h:-h]))
+    assert abs(lhs - (-c * net)) <= 1e-12 * max(1.0, abs(c * net))
+    assert abs(net) > 1e-3   # a case where the boundary flux is not zero
+
+
 def test_hdiff_transpose_symmetry():
     h, n = 2, (8, 8, 3)
     f = inputs.hdiff_fields(*n, h)
