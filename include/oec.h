@@ -401,6 +401,12 @@ OEC_API int oec_program_algorithmic_bytes(oec_program_t p, const int64_t lb[3], 
  * otherwise, and clears the record. Errors: OEC_ERR_CUDA.
  */
 OEC_API int oec_device_status(void* cuda_stream);
+/* Exercise the give-up path of the bounded waits: enqueue a one-thread kernel
+ * whose mbarrier wait on a phase that never completes gives up after `polls`
+ * polls (1..65536) and records a timeout, so the next oec_device_status
+ * reports OEC_ERR_TIMEOUT. No copies are involved; the GPU context stays
+ * usable. Errors: OEC_ERR_INVALID_ARG, OEC_ERR_CUDA. */
+OEC_API int oec_device_wait_selftest(int polls, void* cuda_stream);
 OEC_API int oec_program_launch_count(oec_program_t p);
 OEC_API int oec_program_set_timing(oec_program_t p, int enable);
 OEC_API int oec_program_kernel_times(oec_program_t p, float* ms, int cap, int* n_applies, int* n_kernels);

@@ -344,6 +344,25 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
+namespace {
+// an mbarrier that nothing arrives on: the wait gives up after `polls` polls,
+// counts a timeout and the kernel returns (no copies were issued)
+__global__ void wait_selftest_kernel(unsigned polls) {
+  __shared__ __align__(8) unsigned long long bar;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait_n(smem_u32(&bar), 0u, polls)) atomicAdd(&g_wait_timeouts, 1u);
+}
+}  // namespace
+
+cudaError_t wait_selftest_launch(unsigned polls, cudaStream_t st) {
+  wait_selftest_kernel<<<1, 32, 0, st>>>(polls);
+  return cudaGetLastError();
+}
+
 unsigned* wait_timeout_counter() {
   static unsigned* addr = nullptr;
   static std::once_flag once;

@@ -53,6 +53,9 @@ cudaError_t hdiff_tma_launch(const oec_schedule& s, int dtype, const Dom& d, con
 // number of bounded device-side waits that gave up since the last call (the
 // stream is synchronised first); clears the count
 int device_wait_timeouts(cudaStream_t st, unsigned* count);
+// launch a kernel whose mbarrier wait on a phase that never completes gives
+// up after `polls` polls and counts a timeout (the give-up path, tested)
+cudaError_t wait_selftest_launch(unsigned polls, cudaStream_t st);
 cudaError_t hdiff_launch(const oec_schedule& s, int dtype, const Dom& d, const void* in, const void* coeff,
                          void* out, void* scratch, cudaStream_t st);
 

@@ -21,10 +21,10 @@ __device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
 __device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
 }
-// bounded wait for the phase with the given parity to complete; false when
-// it gave up (about a second of polling)
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
-  for (int it = 0; it < (1 << 20); ++it) {
+// bounded wait for the phase with the given parity to complete: at most
+// `polls` polls; false when it gave up
+__device__ __forceinline__ bool mbar_wait_n(unsigned bar, unsigned parity, unsigned polls) {
+  for (unsigned it = 0; it < polls; ++it) {
     unsigned done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -35,6 +35,8 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
   }
   return false;
 }
+// the kernels' wait: about a second of polling
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) { return mbar_wait_n(bar, parity, 1u << 20); }
 // 3-D tile load global -> shared, completion counted on bar; x must be a
 // multiple of 16 bytes / element size and dst 128-byte aligned (the callers
 // guarantee both)

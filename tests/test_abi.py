@@ -135,6 +135,11 @@ def test_apply_host_validation_without_gpu(liboec):
     assert host([fin, fco], [fout], (16, 12, 0)) == 0              # empty domain: nothing to do
 
 
+def test_wait_selftest_validation_without_gpu(liboec):
+    assert L.lib().oec_device_wait_selftest(0, None) == -1
+    assert L.lib().oec_device_wait_selftest(70000, None) == -1
+
+
 def test_bad_schedule_rejected(liboec):
     p = _prog(programs.HDIFF)
     with pytest.raises(L.OecError):

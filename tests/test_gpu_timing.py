@@ -110,3 +110,19 @@ def test_captured_generated_launch_keeps_its_parameters():
         assert torch.equal(a, b)
         assert not torch.equal(a, c)
     del junk
+
+
+def test_bounded_wait_gives_up_and_is_reported():
+    """The give-up path of the kernels' bounded mbarrier waits: a wait on a
+    phase that never completes stops after its poll limit, the timeout is
+    reported once by oec_device_status, and the context keeps working."""
+    from paper_2005_13014_gb300 import _lib as L
+    lib = L.lib()
+    assert lib.oec_device_status(None) == 0
+    assert lib.oec_device_wait_selftest(64, None) == 0
+    assert lib.oec_device_status(None) == -10   # OEC_ERR_TIMEOUT
+    assert "gave up" in lib.oec_last_error().decode()
+    assert lib.oec_device_status(None) == 0     # cleared
+    t = torch.ones(1024, device="cuda")
+    assert float((t * 2).sum()) == 2048.0
+    assert lib.oec_device_wait_selftest(0, None) == -1
