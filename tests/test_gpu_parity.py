@@ -244,6 +244,35 @@ def test_fastwaves_tma(sched, dtype, arith):
     assert _fw_case((37, 29, 7), 3, dtype, s, pad_i=1) <= TOL[dtype]
 
 
+@pytest.mark.parametrize("dtype,arith", PRECISIONS)
+@pytest.mark.parametrize("lb,ub", [((3, 2, 1), (33, 27, 7)), ((1, 5, 2), (70, 9, 3))], ids=str)
+def test_fastwaves_tma_subdomain(dtype, arith, lb, ub):
+    """TMA boxes for a domain that starts inside the storage at an odd column:
+    box corners round down from origin + lb; nothing is written outside the
+    domain."""
+    from paper_2005_13014_gb300.api import device_field
+    n_st, h = (72, 32, 9), 3
+    f = inputs.fastwaves_fields(*n_st, h, seed=36)
+    g = {k: _round(v, dtype) for k, v in f.items()}
+    p = _prog(programs.FASTWAVES, dtype, dict(fusion=0, staging=4, tile_i=32, tile_j=4, k_chunk=3, arith=arith))
+    d = [device_field(g[name], h, dtype, align_bytes=16) for name in inputs.FASTWAVES_NAMES]
+    o = [device_field(np.full_like(g["pp"], 555.0), h, dtype, align_bytes=16) for _ in range(2)]
+    p.apply(d, o, lb, ub, (h, h, h), [0.5, 0.0625])
+    torch.cuda.synchronize()
+    G = {k: S.Grid.storage(v, h) for k, v in g.items()}
+    ru, rv = S.fastwaves(G, lb, ub, 0.5, 0.0625)
+    gu = o[0].interior(lb, ub).cpu().numpy().astype(np.float64)
+    gv = o[1].interior(lb, ub).cpu().numpy().astype(np.float64)
+    assert max(rel_err(gu, ru), rel_err(gv, rv)) <= TOL[dtype]
+    full = o[0].tensor.cpu().numpy()
+    oi, oj, ok = o[0].origin
+    mask = np.ones(full.shape, bool)
+    mask[ok + lb[2]:ok + ub[2], oj + lb[1]:oj + ub[1], oi + lb[0]:oi + ub[0]] = False
+    assert np.all(full[mask] == 555.0)
+    from paper_2005_13014_gb300 import _lib as L
+    assert L.lib().oec_device_status(None) == 0
+
+
 def test_fastwaves_tma_needs_aligned_pitch():
     from paper_2005_13014_gb300._lib import OecError
     with pytest.raises(OecError, match="16 bytes"):
