@@ -77,7 +77,10 @@ typedef enum {
   OEC_FUSE_NONE = 1,     /* one kernel per stage, temporaries in device memory; for
                             hdiff+vadvc: hdiff of u and v in one kernel, then the
                             column sweep. The hdiff kernel: FP32 fields with
-                            OEC_STAGE_REGS staging run the REGS kernel (tile_i x
+                            OEC_STAGE_WARP staging and 16-byte aligned rows (ni a
+                            multiple of 4) run the vector-row kernel (unroll rows
+                            per warp); with OEC_STAGE_REGS staging, or WARP on
+                            unaligned fields, the REGS kernel (tile_i x
                             tile_j/unroll threads, k_chunk levels per CTA; else
                             64 x 4, unroll 1); otherwise the SMEM tile kernel (tile_i
                             x tile_j, k_chunk levels when they name an SMEM hdiff

@@ -717,10 +717,21 @@ cudaError_t hdiff_launch(const oec_schedule& s, int dtype, const Dom& d, const v
 cudaError_t hdiff_to_compute(const oec_schedule& sched, int dtype, const Dom& d, const void* in0, const void* in1,
                              const void* coeff, void* out0, void* out1, cudaStream_t st) {
   const int64_t osj = d.ni, osk = (int64_t)d.ni * d.nj;
+  // FP32 fields with WARP staging whose rows are 16-byte aligned (inputs at
+  // the domain corner, strides, and ni for the outputs): the vector-row
+  // kernel (unroll rows per warp, k_chunk levels per CTA); unaligned fields
+  // take the REGS kernel below
+  if (dtype == OEC_F32 && sched.staging == OEC_STAGE_WARP) {
+    const bool aligned = ((uintptr_t)in0 | (uintptr_t)in1 | (uintptr_t)coeff | (uintptr_t)out0 | (uintptr_t)out1) % 16 == 0 &&
+                         d.sj % 4 == 0 && d.sk % 4 == 0 && d.ni % 4 == 0;
+    if (aligned)
+      return hdiff_warp_to_compute(sched, d, osj, osk, (const float*)in0, (const float*)in1, (const float*)coeff,
+                                   (float*)out0, (float*)out1, st);
+  }
   // FP32 fields with REGS staging: the REGS kernel (CTA tile_i x tile_j/unroll
   // threads, unroll rows per thread, k_chunk levels per CTA); a tile it cannot
   // run falls back to 64 x 4, unroll 1
-  if (dtype == OEC_F32 && sched.staging == OEC_STAGE_REGS) {
+  if (dtype == OEC_F32 && (sched.staging == OEC_STAGE_REGS || sched.staging == OEC_STAGE_WARP)) {
     oec_schedule s = sched;
     const int u = s.unroll;
     const bool ok = (u == 1 || u == 2 || u == 4) && s.tile_i >= 16 && s.tile_i <= 256 && s.tile_i % 16 == 0 &&

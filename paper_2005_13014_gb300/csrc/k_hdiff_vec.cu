@@ -116,10 +116,16 @@ __device__ __forceinline__ void vec_rows(const VecWin<typename P::S, U, Vec16<ty
 // The level loop keeps NB register windows in rotation (unrolled by NB, no
 // copies): a window is refilled with level k+NB right after level k is
 // computed, so the loads of NB-1 levels are in flight during each level.
-template <class P, int U, class Off, int NB>
+//
+// SEP: the output has its own layout (pitch osj, plane osk; rows 16-byte
+// aligned) and grid z covers two fields (z < nkz: in -> out, else in1 ->
+// out1), as the FP32 producer of the staged hdiff+vadvc form uses it.
+template <class P, int U, class Off, int NB, bool SEP>
 __global__ void __launch_bounds__(128)
 hdiff_vec_kernel(const typename P::S* __restrict__ in, const typename P::S* __restrict__ coeff,
-                 typename P::S* __restrict__ out, int ni, int nj, int nk, int64_t sj, int64_t sk, int kchunk) {
+                 typename P::S* __restrict__ out, int ni, int nj, int nk, int64_t sj, int64_t sk, int kchunk,
+                 int64_t osj, int64_t osk, int nkz, const typename P::S* __restrict__ in1,
+                 typename P::S* __restrict__ out1) {
   typedef typename P::S S;
   typedef typename Vec16<S>::T VT;
   constexpr int V = Vec16<S>::V, W = 32 * V;
@@ -128,7 +134,13 @@ hdiff_vec_kernel(const typename P::S* __restrict__ in, const typename P::S* __re
   const int jb = (blockIdx.y * 4 + wid) * U;
   if (jb >= nj) return;                                  // whole warp
   const int jmax = nj + 1 - jb;                          // last row offset inside the halo-2 window
-  const int k0 = blockIdx.z * kchunk, k1 = min(nk, k0 + kchunk);
+  int z = blockIdx.z;
+  if (SEP && z >= nkz) {
+    in = in1;
+    out = out1;
+    z -= nkz;
+  }
+  const int k0 = z * kchunk, k1 = min(nk, k0 + kchunk);
   const bool vin_full = c0 + V - 1 <= ni + 1;            // whole vector inside the input range [-2, ni+2)
   const bool vout_full = c0 + V - 1 < ni;                // whole vector inside the domain
   const bool edge = lane == 0 || lane == 31;
@@ -175,7 +187,10 @@ hdiff_vec_kernel(const typename P::S* __restrict__ in, const typename P::S* __re
     for (int b = 0; b < NB; ++b) {
       if (k + b >= k1) break;
       const Off lx = lev + (Off)b * ksk;
-      vec_rows<P, U>(win[b], lane, c0, jb, ni, nj, out + (lx + c0), sj);
+      if (SEP)
+        vec_rows<P, U>(win[b], lane, c0, jb, ni, nj, out + ((int64_t)(k + b) * osk + (int64_t)jb * osj + c0), osj);
+      else
+        vec_rows<P, U>(win[b], lane, c0, jb, ni, nj, out + (lx + c0), sj);
       if (k + b + NB < k1) load(win[b], lx + (Off)NB * ksk);
     }
   }
@@ -188,9 +203,30 @@ cudaError_t run_vec(const oec_schedule& s, const Dom& d, const typename P::S* in
   const int kc = (s.k_chunk <= 0 || s.k_chunk > d.nk) ? d.nk : s.k_chunk;
   dim3 g(ceil_div(d.ni, W), ceil_div(d.nj, 4 * U), ceil_div(d.nk, kc));
   if (offsets_fit_int32(d))
-    hdiff_vec_kernel<P, U, int, 2><<<g, 128, 0, st>>>(in, coeff, out, d.ni, d.nj, d.nk, d.sj, d.sk, kc);
+    hdiff_vec_kernel<P, U, int, 2, false><<<g, 128, 0, st>>>(in, coeff, out, d.ni, d.nj, d.nk, d.sj, d.sk, kc, 0, 0, 0,
+                                                             nullptr, nullptr);
   else
-    hdiff_vec_kernel<P, U, int64_t, 2><<<g, 128, 0, st>>>(in, coeff, out, d.ni, d.nj, d.nk, d.sj, d.sk, kc);
+    hdiff_vec_kernel<P, U, int64_t, 2, false><<<g, 128, 0, st>>>(in, coeff, out, d.ni, d.nj, d.nk, d.sj, d.sk, kc, 0,
+                                                                 0, 0, nullptr, nullptr);
+  launched(st);
+  return cudaGetLastError();
+}
+
+// the vector-row kernel as the staged producer: in0 -> out0 and in1 -> out1
+// (domain layout osj, osk) in one launch
+template <class P, int U>
+cudaError_t run_vec_to(const oec_schedule& s, const Dom& d, int64_t osj, int64_t osk, const typename P::S* in0,
+                       const typename P::S* in1, const typename P::S* coeff, typename P::S* out0,
+                       typename P::S* out1, cudaStream_t st) {
+  constexpr int W = 32 * Vec16<typename P::S>::V;
+  const int kc = (s.k_chunk <= 0 || s.k_chunk > d.nk) ? d.nk : s.k_chunk, nkz = ceil_div(d.nk, kc);
+  dim3 g(ceil_div(d.ni, W), ceil_div(d.nj, 4 * U), 2 * nkz);
+  if (offsets_fit_int32(d))
+    hdiff_vec_kernel<P, U, int, 2, true><<<g, 128, 0, st>>>(in0, coeff, out0, d.ni, d.nj, d.nk, d.sj, d.sk, kc, osj,
+                                                            osk, nkz, in1, out1);
+  else
+    hdiff_vec_kernel<P, U, int64_t, 2, true><<<g, 128, 0, st>>>(in0, coeff, out0, d.ni, d.nj, d.nk, d.sj, d.sk, kc,
+                                                                osj, osk, nkz, in1, out1);
   launched(st);
   return cudaGetLastError();
 }
@@ -388,6 +424,15 @@ cudaError_t hdiff_warp_launch(const oec_schedule& s, int dtype, const Dom& d, co
   }
   OEC_VEC_U(P32, float)
 #undef OEC_VEC_U
+}
+
+cudaError_t hdiff_warp_to_compute(const oec_schedule& s, const Dom& d, int64_t osj, int64_t osk, const float* in0,
+                                  const float* in1, const float* coeff, float* out0, float* out1, cudaStream_t st) {
+  switch (s.unroll) {
+    case 2: return run_vec_to<P32, 2>(s, d, osj, osk, in0, in1, coeff, out0, out1, st);
+    case 4: return run_vec_to<P32, 4>(s, d, osj, osk, in0, in1, coeff, out0, out1, st);
+    default: return run_vec_to<P32, 1>(s, d, osj, osk, in0, in1, coeff, out0, out1, st);
+  }
 }
 
 cudaError_t hdiff_tma_launch(const oec_schedule& s, int dtype, const Dom& d, const TmaField& in, const TmaField& coeff,

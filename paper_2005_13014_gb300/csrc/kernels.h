@@ -48,6 +48,10 @@ struct TmaField {
   int64_t size[3];
   int64_t corner[3];
 };
+// FP32 vector-row hdiff of two fields into the staged hdiff+vadvc compute
+// buffers (domain layout osj, osk); every row 16-byte aligned (caller checks)
+cudaError_t hdiff_warp_to_compute(const oec_schedule& s, const Dom& d, int64_t osj, int64_t osk, const float* in0,
+                                  const float* in1, const float* coeff, float* out0, float* out1, cudaStream_t st);
 cudaError_t hdiff_tma_launch(const oec_schedule& s, int dtype, const Dom& d, const TmaField& in,
                              const TmaField& coeff, void* out, cudaStream_t st);
 // number of bounded device-side waits that gave up since the last call (the

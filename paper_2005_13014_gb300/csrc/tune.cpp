@@ -69,6 +69,8 @@ std::vector<oec_schedule> candidates(const oec_program* p) {
           for (auto t : {std::pair<int, int>{32, 4}, {32, 8}, {64, 4}, {128, 2}})
             for (int u : {1, 2})
               for (int kc : {8, 20}) c.push_back(mk(OEC_FUSE_NONE, OEC_STAGE_REGS, t.first, t.second, u, kc, a));
+          for (int u : {1, 2, 4})   // vector rows (aligned fields; else the REGS kernel)
+            for (int kc : {8, 20}) c.push_back(mk(OEC_FUSE_NONE, OEC_STAGE_WARP, 32, 4 * u, u, kc, a));
           c.push_back(mk(OEC_FUSE_NONE, OEC_STAGE_SMEM, 64, 4, 1, 4, a));
         }
       }

@@ -256,7 +256,7 @@ def test_fastwaves_tma_subdomain(dtype, arith, lb, ub):
     g = {k: _round(v, dtype) for k, v in f.items()}
     p = _prog(programs.FASTWAVES, dtype, dict(fusion=0, staging=4, tile_i=32, tile_j=4, k_chunk=3, arith=arith))
     d = [device_field(g[name], h, dtype, align_bytes=16) for name in inputs.FASTWAVES_NAMES]
-    o = [device_field(np.full_like(g["pp"], 555.0), h, dtype, align_bytes=16) for _ in range(2)]
+    o = [device_field(np.full_like(g["pp"], 555.0), h, dtype, align_bytes=16, pad_value=555.0) for _ in range(2)]
     p.apply(d, o, lb, ub, (h, h, h), [0.5, 0.0625])
     torch.cuda.synchronize()
     G = {k: S.Grid.storage(v, h) for k, v in g.items()}
@@ -458,6 +458,34 @@ def test_hdiff_vadvc_f32_regs_producer(arith, tile, unroll):
     sched = dict(fusion=1, staging=0, tile_i=tile[0], tile_j=tile[1], unroll=unroll, k_chunk=3, arith=arith)
     assert _hv_case((37, 23, 11), 3, "f32", sched) <= TOL["f32"]
     assert _hv_case((33, 5, 2), 3, "f32", sched) <= TOL["f32"]
+
+
+@pytest.mark.parametrize("unroll", [1, 2, 4])
+@pytest.mark.parametrize("arith", [0, 1])
+@pytest.mark.parametrize("n,align", [((36, 23, 11), 16), ((128, 128, 80), 16), ((37, 23, 11), 16),
+                                     ((36, 23, 11), 0)], ids=str)
+def test_hdiff_vadvc_f32_vector_producer(n, align, arith, unroll):
+    """FP32 staged form with the vector-row producer (aligned rows, ni a
+    multiple of 4) and its REGS fallback (ni = 37, or unaligned storage)."""
+    h = 3
+    f = inputs.hdiff_vadvc_fields(*n, h, seed=37)
+    g = {k: _round(v, "f32") for k, v in f.items()}
+    p = _prog(programs.HDIFF_VADVC, "f32", dict(fusion=1, staging=3, tile_i=32, tile_j=4 * unroll, unroll=unroll,
+                                                 k_chunk=8, arith=arith))
+    d = {k: _dev(v, h, "f32", align) for k, v in g.items()}
+    o = [_dev(np.full_like(g["u"], 777.0), h, "f32", align, pad_value=777.0) for _ in range(2)]
+    p.apply([d["u"], d["v"], d["w"], d["coeff"]], o, (0, 0, 0), n, (h, h, h), [2.0])
+    torch.cuda.synchronize()
+    G = {k: S.Grid.storage(v, h) for k, v in g.items()}
+    ru, rv = S.hdiff_vadvc(G["u"], G["v"], G["w"], G["coeff"], (0, 0, 0), n, 2.0)
+    gu = o[0].interior((0, 0, 0), n).cpu().numpy().astype(np.float64)
+    gv = o[1].interior((0, 0, 0), n).cpu().numpy().astype(np.float64)
+    assert max(rel_err(gu, ru), rel_err(gv, rv)) <= TOL["f32"]
+    full = o[0].tensor.cpu().numpy()
+    oi, oj, ok = o[0].origin
+    mask = np.ones(full.shape, bool)
+    mask[ok:ok + n[2], oj:oj + n[1], oi:oi + n[0]] = False
+    assert np.all(full[mask] == 777.0)
 
 
 @pytest.mark.parametrize("arith", [0, 1])
