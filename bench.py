@@ -378,15 +378,15 @@ def _l2_bytes():
     return getattr(props, "L2_cache_size", 128 << 20)
 
 
-def _run_program(prog_name, dtype, arith, steps, schedule=None, cache=None):
-    """One stencil program at 256x256x80, halo 3: autotuned (or the given
-    schedule) and timed over rotating resident copies of its fields (> 3 x L2,
-    so every apply reads HBM); error per output against the library's
-    unfused native-FP64 kernels."""
+def _run_program(prog_name, dtype, arith, steps, schedule=None, cache=None, size=None):
+    """One stencil program at 256x256x80 (or `size`), halo 3: autotuned (or the
+    given schedule) and timed over rotating resident copies of its fields
+    (> 3 x L2, so every apply reads HBM); error per output against the
+    library's unfused native-FP64 kernels."""
     import torch
     from paper_2005_13014_gb300 import inputs, programs
     from paper_2005_13014_gb300.api import Program, device_field
-    n, h = (N if prog_name == "hdiff_vadvc" else MIXED_N), 3
+    n, h = tuple(size) if size else (N if prog_name == "hdiff_vadvc" else MIXED_N), 3
     pts = n[0] * n[1] * n[2]
     stream = torch.cuda.current_stream()
     cache = {} if cache is None else cache
@@ -504,9 +504,11 @@ def run_single(args):
     --arith and an optional --schedule."""
     import __graft_entry__
     __graft_entry__.build()
+    size = tuple(int(x) for x in args.size.split(",")) if args.size else None
     r = _run_program(args.workload, args.dtype, args.arith, args.steps,
-                     schedule=json.loads(args.schedule) if args.schedule else None)
-    print(json.dumps({"workload": f"{args.workload} {args.dtype} arith {args.arith} 256x256x80 halo 3",
+                     schedule=json.loads(args.schedule) if args.schedule else None, size=size)
+    dims = "x".join(str(x) for x in (size or MIXED_N))
+    print(json.dumps({"workload": f"{args.workload} {args.dtype} arith {args.arith} {dims} halo 3",
                       "l2": "inputs rotated over > 3 x L2", "result": r}))
     return 0
 
@@ -754,6 +756,7 @@ def main():
     ap.add_argument("--cm-save", default=None)
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"], help="--workload hdiff|fastwaves")
     ap.add_argument("--arith", type=int, default=0, help="--workload hdiff|fastwaves: autotune within this arith")
+    ap.add_argument("--size", default=None, help="--workload hdiff|fastwaves: domain ni,nj,nk (default 256,256,80)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
