@@ -500,8 +500,8 @@ def run_mixed(args):
 
 
 def run_single(args):
-    """One program (--workload hdiff|fastwaves) at 256x256x80 with --dtype,
-    --arith and an optional --schedule."""
+    """One program (--workload hdiff|fastwaves, or hdiff_vadvc with --size) at
+    256x256x80 or --size, with --dtype, --arith and an optional --schedule."""
     import __graft_entry__
     __graft_entry__.build()
     size = tuple(int(x) for x in args.size.split(",")) if args.size else None
@@ -756,7 +756,8 @@ def main():
     ap.add_argument("--cm-save", default=None)
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"], help="--workload hdiff|fastwaves")
     ap.add_argument("--arith", type=int, default=0, help="--workload hdiff|fastwaves: autotune within this arith")
-    ap.add_argument("--size", default=None, help="--workload hdiff|fastwaves: domain ni,nj,nk (default 256,256,80)")
+    ap.add_argument("--size", default=None, help="--workload hdiff|fastwaves (default 256,256,80), or hdiff_vadvc "
+                    "(a report of one size instead of the headline line): domain ni,nj,nk")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -766,7 +767,7 @@ def main():
         return run_ensemble(args)
     if args.workload == "costmodel":
         return run_costmodel(args)
-    if args.workload in ("hdiff", "fastwaves"):
+    if args.workload in ("hdiff", "fastwaves") or (args.workload == "hdiff_vadvc" and args.size):
         return run_single(args)
     if args.workload == "testset":
         return run_testset(args)
