@@ -210,7 +210,10 @@ OEC_API int oec_program_input_range(oec_program_t p, int index, const int64_t lb
  * Select the schedule used by later applies (fusion, staging, tile, unroll,
  * k-chunk). Values outside the supported set give OEC_ERR_UNSUPPORTED and
  * leave the schedule unchanged. A new program starts with the library's
- * default schedule for its kind.
+ * default schedule for its kind and dtype (hdiff+vadvc: the staged form the
+ * autotuner picks at 128x128x80 - FP64 fixed-point producer 32x8 with 4
+ * levels per CTA, FP32 vector-row producer with 20 levels per CTA, both with
+ * the double-float column sweep).
  */
 OEC_API int oec_program_set_schedule(oec_program_t p, const oec_schedule* s);
 OEC_API int oec_program_get_schedule(oec_program_t p, oec_schedule* s);
@@ -520,16 +523,19 @@ OEC_API int oec_program_autotune_model(oec_program_t p, oec_costmodel_t m, const
  * break the capture), code that must stay inside a device-memory budget owned
  * by another allocator, and latency-critical loops where cudaMalloc/cudaFree
  * may synchronise the device. oec_program_apply allocates scratch on its first
- * apply at a new size; this call never does: it runs the fused column sweep
- * with its Thomas scratch in a fixed 32 MiB array inside the library's device
- * image (held on every GPU where the library's device code is loaded, until
- * the process exits).
+ * apply at a new size; this call never does: its scratch is a fixed 64 MiB
+ * array inside the library's device image (held on every GPU where the
+ * library's device code is loaded, until the process exits). It runs the
+ * staged form (hdiff of u and v, then the twisted column sweep; FP64: fixed
+ * point producer and double-float sweep, FP32: vector-row or REGS producer and
+ * double-float sweep) when its scratch fits, else the fused column sweep.
  *   dtype   OEC_F32 or OEC_F64 (all six fields)
  *   in[4]   u, v, w, coeff; u and v must hold [lb-2, ub+2) in i and j, w must
  *           hold [lb, ub+1) in i, coeff the domain
  *   out[2]  u_out, v_out, written over [lb, ub)
  *   dtr     the scalar parameter of the vertical advection
- * Limit: 24 bytes of scratch per grid point, so at most 1,398,101 points
+ * Limit: staged 40 (FP64) / 32 (FP32) bytes of scratch per grid point, so
+ * 1,677,721 / 2,097,152 points; fused 24 bytes, so at most 2,796,202 points
  * (OEC_ERR_UNSUPPORTED above that). The first call on each device looks up the
  * array's device address (cudaGetSymbolAddress) with that device current; make
  * that first call before any stream capture. All calls share the one array and

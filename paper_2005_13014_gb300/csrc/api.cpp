@@ -53,7 +53,7 @@ static const std::string& builtin_canon(int kind) {
   return c[kind];
 }
 
-oec_schedule default_schedule(int kind) {
+oec_schedule default_schedule(int kind, int dtype) {
   oec_schedule s{};
   s.fusion = OEC_FUSE_INLINE;
   s.unroll = 1;
@@ -66,10 +66,15 @@ oec_schedule default_schedule(int kind) {
       s.arith = OEC_ARITH_DOUBLE_FLOAT;
       break;
     case OEC_KIND_HDIFF_VADVC:
-      s.staging = OEC_STAGE_SMEM;
-      s.tile_i = 16;
-      s.tile_j = 4;
-      s.arith = OEC_ARITH_DOUBLE_FLOAT;
+      // the staged form the autotuner picks at 128x128x80: FP64 fixed-point
+      // producer 32x8, 4 levels per CTA; FP32 vector-row producer (REGS on
+      // unaligned fields), 20 levels per CTA; double-float column sweep
+      s.fusion = OEC_FUSE_NONE;
+      s.staging = dtype == OEC_F64 ? OEC_STAGE_REGS : OEC_STAGE_WARP;
+      s.tile_i = 32;
+      s.tile_j = dtype == OEC_F64 ? 8 : 4;
+      s.k_chunk = dtype == OEC_F64 ? 4 : 20;
+      s.arith = dtype == OEC_F64 ? OEC_ARITH_FIXED : OEC_ARITH_DOUBLE_FLOAT;
       break;
     case OEC_KIND_FASTWAVES:
       s.staging = OEC_STAGE_REGS;
@@ -251,7 +256,7 @@ int oec_program_create(const char* source, const oec_program_options* opts, oec_
     for (int k = 1; k < 4; ++k)
       if (c == builtin_canon(k)) p->kind = k;
   }
-  p->sched = default_schedule(p->kind);
+  p->sched = default_schedule(p->kind, dtype);
   *out = p;
   return OEC_OK;
 }

@@ -45,7 +45,7 @@ int fail(int code, const char* fmt, ...);
 void clear_error();
 int cuda_fail(cudaError_t e, const char* where);
 size_t elem_size(int dtype);
-oec_schedule default_schedule(int kind);
+oec_schedule default_schedule(int kind, int dtype);
 bool schedule_ok(int kind, const oec_schedule& s, std::string& why);
 int ensure_scratch(oec_program* p, size_t bytes);
 int validate_fields(const oec_program* p, const oec_field_desc* in, int n_in, const oec_field_desc* out, int n_out,

@@ -7,9 +7,11 @@
 // (a framework's caching allocator, a pool sized at start-up), and
 // latency-critical loops where an allocation or free may synchronise the whole
 // device. oec_program_apply allocates its scratch on the first apply at a new
-// size, so it does not suit them. The entry point below runs the fused
-// hdiff+vadvc column sweep with its Thomas scratch (c', d' per level and
-// column) placed in a fixed array that is part of the library's device image.
+// size, so it does not suit them. The entry point below runs hdiff+vadvc with
+// its scratch placed in a fixed array that is part of the library's device
+// image: the staged form (hdiff of u and v, then the twisted column sweep;
+// the schedule the autotuner picks at 128x128x80) when the domain's staged
+// scratch fits, else the fused column sweep, which needs less.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -20,9 +22,11 @@
 
 namespace {
 
-// 32 MiB: 3 FP64 values (c', d'_u, d'_v) per grid point, i.e. up to 1,398,101
-// points per call (128 x 128 x 85 and smaller domains).
-constexpr size_t kNoallocScratchBytes = size_t(32) << 20;
+// 64 MiB. The staged form needs 40 bytes per grid point in FP64 (hdiff(u),
+// hdiff(v) as double-float pairs, and g, e_u, e_v of the sweep), 32 in FP32:
+// up to 1,677,721 / 2,097,152 points; the fused form 24 (c', d'_u, d'_v):
+// up to 2,796,202 points.
+constexpr size_t kNoallocScratchBytes = size_t(64) << 20;
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
 // Device address of g_noalloc_scratch, looked up once per device. In host code
@@ -111,7 +115,18 @@ extern "C" OEC_API int oec_hdiff_vadvc_apply_noalloc(int32_t dtype, const oec_fi
     }
   }
   const Dom d{int(ub[0] - lb[0]), int(ub[1] - lb[1]), int(ub[2] - lb[2]), sj, sk};
-  const oec_schedule s = default_schedule(OEC_KIND_HDIFF_VADVC);   // fused column sweep
+  // the programs' default (staged) schedule; the fused column sweep (16x4
+  // tiles, double-float) when its scratch does not fit
+  oec_schedule s = default_schedule(OEC_KIND_HDIFF_VADVC, dtype);
+  if (hdiff_vadvc_scratch_bytes(s, dtype, d) > kNoallocScratchBytes) {
+    s = oec_schedule{};
+    s.fusion = OEC_FUSE_INLINE;
+    s.staging = OEC_STAGE_SMEM;
+    s.tile_i = 16;
+    s.tile_j = 4;
+    s.unroll = 1;
+    s.arith = OEC_ARITH_DOUBLE_FLOAT;
+  }
   const size_t need = hdiff_vadvc_scratch_bytes(s, dtype, d);
   if (need > kNoallocScratchBytes)
     return fail(OEC_ERR_UNSUPPORTED, "domain needs %zu scratch bytes; the no-allocation entry point holds %zu",
