@@ -247,8 +247,10 @@ OEC_API int oec_program_apply(oec_program_t p, const oec_field_desc* in, int n_i
  * oec_program_apply with every field in HOST memory: `data` of each
  * descriptor is a host pointer (page-locked memory keeps the call
  * asynchronous; pageable memory works, with the copies synchronous). The
- * library copies each input's storage span (what its size and strides
- * cover) into device staging buffers it owns, applies the program there, and
+ * library copies each input's storage from the first to the last element of
+ * its access box (the range shape inference gives it for [lb, ub), paper
+ * §IV), widened to 4 KiB boundaries of the host address, into device staging
+ * buffers laid out like the host storage, applies the program there, and
  * copies back each output's domain box [lb, ub) only: host output storage
  * outside the domain is left as it was. Staging buffers come in two sets used
  * in turn, allocated at the first call and again when field shapes change;
