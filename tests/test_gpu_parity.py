@@ -188,6 +188,15 @@ def test_hdiff_vadvc_config_128x128x80_f64(sched, arith):
     assert _hv_case((128, 128, 80), 3, "f64", _with(sched, arith)) <= TOL["f64"]
 
 
+@pytest.mark.parametrize("n", [(33, 5, 1001), (16, 16, 137), (20, 12, 256), (1, 1, 80), (1, 1, 1)], ids=str)
+@pytest.mark.parametrize("dtype,arith", [("f64", 2), ("f64", 1), ("f32", 1)])
+def test_hdiff_vadvc_staged_long_columns(n, dtype, arith):
+    """The twisted column sweep on long columns (odd and even level counts):
+    the two halves of up to 501 rows each meet in the middle."""
+    sched = dict(fusion=1, tile_i=32, tile_j=8, k_chunk=4, arith=arith)
+    assert _hv_case(n, 3, dtype, sched) <= TOL[dtype]
+
+
 @pytest.mark.parametrize("arith", [0, 1])
 def test_hdiff_vadvc_config_128x128x137_f32(arith):
     assert _hv_case((128, 128, 137), 3, "f32", dict(fusion=0, staging=1, tile_i=16, tile_j=4, arith=arith)) <= TOL["f32"]
