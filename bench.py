@@ -477,11 +477,12 @@ def _l2_bytes():
     return getattr(props, "L2_cache_size", 128 << 20)
 
 
-def _run_program(prog_name, dtype, arith, steps, schedule=None, cache=None, size=None):
+def _run_program(prog_name, dtype, arith, steps, schedule=None, cache=None, size=None, index_bits=0, generic=False):
     """One stencil program at 256x256x80 (or `size`), halo 3: autotuned (or the
     given schedule) and timed over rotating resident copies of its fields
     (> 3 x L2, so every apply reads HBM); error per output against the
-    library's unfused native-FP64 kernels."""
+    library's unfused native-FP64 kernels. index_bits: the offset width the
+    autotuner's candidates carry; generic: the program's generated kernels."""
     import torch
     from paper_2005_13014_gb300 import inputs, programs
     from paper_2005_13014_gb300.api import Program, device_field
@@ -494,21 +495,21 @@ def _run_program(prog_name, dtype, arith, steps, schedule=None, cache=None, size
         if "hv_fields" not in cache:
             cache["hv_fields"] = inputs.hdiff_vadvc_fields(*n, h)
         f = {k: rnd(v) for k, v in cache["hv_fields"].items()}
-        prog = Program(programs.HDIFF_VADVC, dtype)
+        prog = Program(programs.HDIFF_VADVC, dtype, generic=generic)
         names, n_out, params = ["u", "v", "w", "coeff"], 2, [DTR]
     elif prog_name == "hdiff":
         if "hdiff_fields" not in cache:
             cache["hdiff_fields"] = inputs.hdiff_fields(*n, h)
         f0 = cache["hdiff_fields"]
         f = {k: rnd(v) for k, v in f0.items()}
-        prog = Program(programs.HDIFF, dtype)
+        prog = Program(programs.HDIFF, dtype, generic=generic)
         names, n_out, params = ["in", "coeff"], 1, []
     else:
         if "fw_fields" not in cache:
             cache["fw_fields"] = inputs.fastwaves_fields(*n, h)
         f0 = cache["fw_fields"]
         f = {k: rnd(v) for k, v in f0.items()}
-        prog = Program(programs.FASTWAVES, dtype)
+        prog = Program(programs.FASTWAVES, dtype, generic=generic)
         names, n_out, params = list(inputs.FASTWAVES_NAMES), 2, [0.5, 0.0625]
     set_bytes = (len(names) + n_out) * f[names[0]].size * (4 if dtype == "f32" else 8)
     n_sets = max(1, int(np.ceil(3 * _l2_bytes() / set_bytes)))
@@ -521,7 +522,7 @@ def _run_program(prog_name, dtype, arith, steps, schedule=None, cache=None, size
     if schedule:
         prog.set_schedule(**schedule)
     else:
-        cands = [c for c in prog.candidates() if c["arith"] == arith]
+        cands = [dict(c, index_bits=index_bits) for c in prog.candidates() if c["arith"] == arith]
         prog.autotune(ins, outs, (0, 0, 0), n, (h, h, h), params, candidates=cands, reps=5)
     # direct: one C-ABI call per apply from Python (host overhead included),
     # arguments marshalled per call (apply) and once (bind)
@@ -609,6 +610,36 @@ def run_single(args):
     dims = "x".join(str(x) for x in (size or MIXED_N))
     print(json.dumps({"workload": f"{args.workload} {args.dtype} arith {args.arith} {dims} halo 3",
                       "l2": "inputs rotated over > 3 x L2", "result": r}))
+    return 0
+
+
+def run_index_width(args):
+    """32-bit against 64-bit element offsets (the paper's index type, §V-B,
+    §VII-C) in the kernels that have both forms: per program, the best schedule
+    the autotuner finds with automatic offsets (32-bit wherever they fit) and
+    with 64-bit offsets forced, and the automatic winner re-timed with 64-bit
+    offsets. Schedules whose kernels have one form only time the same code
+    twice, so the best-of figures also carry timing noise."""
+    import __graft_entry__
+    __graft_entry__.build()
+    cases = [("hdiff", "f32", 0, (256, 256, 80), False), ("hdiff", "f32", 0, (512, 512, 137), False),
+             ("hdiff", "f64", 2, (256, 256, 80), False), ("hdiff_vadvc", "f64", 2, (128, 128, 80), False),
+             ("hdiff_vadvc", "f32", 1, (128, 128, 80), False), ("hdiff", "f32", 0, (256, 256, 80), True),
+             ("fastwaves", "f32", 0, (256, 256, 80), True)]
+    res = []
+    for prog_name, dtype, arith, size, generic in cases:
+        a = _run_program(prog_name, dtype, arith, args.steps, size=size, generic=generic)
+        b = _run_program(prog_name, dtype, arith, args.steps, size=size, generic=generic, index_bits=64)
+        c = _run_program(prog_name, dtype, arith, args.steps, size=size, generic=generic,
+                         schedule=dict(a["schedule"], index_bits=64))
+        res.append({"program": prog_name + (" (generated kernels)" if generic else ""), "dtype": dtype,
+                    "arith": arith, "size": "x".join(map(str, size)),
+                    "best_auto": {"ms": a["ms"], "schedule": a["schedule"]},
+                    "best_64": {"ms": b["ms"], "schedule": b["schedule"]},
+                    "auto_winner_at_64": {"ms": c["ms"]},
+                    "ratio_best_64_over_auto": b["ms"] / a["ms"], "ratio_same_schedule": c["ms"] / a["ms"]})
+    print(json.dumps({"workload": "offset width: automatic (32-bit where it fits) vs 64-bit, halo 3",
+                      "l2": "inputs rotated over > 3 x L2", "timing": "CUDA-graph replay", "results": res}))
     return 0
 
 
@@ -847,7 +878,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="hdiff_vadvc",
-                    choices=["hdiff_vadvc", "mixed", "ensemble", "costmodel", "hdiff", "fastwaves", "testset"],
+                    choices=["hdiff_vadvc", "mixed", "ensemble", "costmodel", "hdiff", "fastwaves", "testset",
+                             "index_width"],
                     help="hdiff_vadvc: the headline line; the others print their own report")
     ap.add_argument("--cm-train", type=int, default=180)
     ap.add_argument("--cm-test", type=int, default=200)
@@ -868,6 +900,8 @@ def main():
         return run_costmodel(args)
     if args.workload in ("hdiff", "fastwaves") or (args.workload == "hdiff_vadvc" and args.size):
         return run_single(args)
+    if args.workload == "index_width":
+        return run_index_width(args)
     if args.workload == "testset":
         return run_testset(args)
     return run_gpu(args)

@@ -124,8 +124,20 @@ typedef struct oec_schedule {
   int32_t unroll;        /* points per thread along the unroll dimension (1, 2 or 4)     */
   int32_t k_chunk;       /* levels per CTA for horizontal programs (0 = whole column)    */
   int32_t arith;         /* OEC_ARITH_*                                                   */
-  int32_t reserved[5];   /* zero                                                          */
+  int32_t index_bits;    /* OEC_INDEX_AUTO (0) or OEC_INDEX_64 (64)                       */
+  int32_t reserved[4];   /* zero                                                          */
 } oec_schedule;
+
+/* Width of the element offsets that kernels form from their fields' base
+ * pointers (the paper's index type, §V-B and §VII-C). OEC_INDEX_AUTO: the
+ * kernels that have a 32-bit form (fused horizontal diffusion with OEC_STAGE_REGS
+ * or OEC_STAGE_WARP or OEC_ARITH_FIXED, the hdiff producers of the
+ * stage-by-stage hdiff+vadvc form, and generated kernels) use 32-bit offsets
+ * when every offset they form fits in an int32, else 64-bit; all other kernels
+ * use 64-bit offsets. OEC_INDEX_64: 64-bit offsets in every kernel. Both give
+ * the same results bit for bit: only address arithmetic differs. */
+#define OEC_INDEX_AUTO 0
+#define OEC_INDEX_64 64
 
 /* Arithmetic of a schedule. OEC_ARITH_NATIVE evaluates in the dtype's own
  * IEEE arithmetic (FP32 programs keep their column recurrence in native FP64).

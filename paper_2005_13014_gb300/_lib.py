@@ -29,7 +29,8 @@ class FieldDesc(C.Structure):
 
 class Schedule(C.Structure):
     _fields_ = [("fusion", C.c_int32), ("staging", C.c_int32), ("tile_i", C.c_int32), ("tile_j", C.c_int32),
-                ("unroll", C.c_int32), ("k_chunk", C.c_int32), ("arith", C.c_int32), ("reserved", C.c_int32 * 5)]
+                ("unroll", C.c_int32), ("k_chunk", C.c_int32), ("arith", C.c_int32), ("index_bits", C.c_int32),
+                ("reserved", C.c_int32 * 4)]
 
 
 class ProgramOptions(C.Structure):

@@ -19,7 +19,7 @@ def _torch():
     return torch
 
 
-SCHEDULE_KEYS = ("fusion", "staging", "tile_i", "tile_j", "unroll", "k_chunk", "arith")
+SCHEDULE_KEYS = ("fusion", "staging", "tile_i", "tile_j", "unroll", "k_chunk", "arith", "index_bits")
 
 
 def schedule_struct(d: dict) -> L.Schedule:
@@ -208,8 +208,8 @@ class Program:
         L.check(L.lib().oec_program_get_schedule(self._h, C.byref(s)))
         return schedule_dict(s)
 
-    def set_schedule(self, fusion=0, staging=0, tile_i=64, tile_j=4, unroll=1, k_chunk=0, arith=0):
-        s = L.Schedule(fusion, staging, tile_i, tile_j, unroll, k_chunk, arith)
+    def set_schedule(self, fusion=0, staging=0, tile_i=64, tile_j=4, unroll=1, k_chunk=0, arith=0, index_bits=0):
+        s = L.Schedule(fusion, staging, tile_i, tile_j, unroll, k_chunk, arith, index_bits)
         L.check(L.lib().oec_program_set_schedule(self._h, C.byref(s)))
 
     def input_range(self, index, lb, ub):

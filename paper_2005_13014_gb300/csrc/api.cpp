@@ -95,6 +95,10 @@ oec_schedule default_schedule(int kind, int dtype) {
 bool schedule_ok(int kind, const oec_schedule& s, std::string& why) {
   for (int r : s.reserved)
     if (r != 0) { why = "reserved schedule fields must be zero"; return false; }
+  if (s.index_bits != OEC_INDEX_AUTO && s.index_bits != OEC_INDEX_64) {
+    why = "index_bits must be OEC_INDEX_AUTO (0) or OEC_INDEX_64 (64)";
+    return false;
+  }
   switch (kind) {
     case OEC_KIND_HDIFF: return hdiff_schedule_ok(s, why);
     case OEC_KIND_HDIFF_VADVC: return hdiff_vadvc_schedule_ok(s, why);

@@ -115,8 +115,9 @@ struct Variant {
 struct ShapeKey {
   int64_t ni, nj, nk, sj, sk;
   int arith = 0;   // 1: FP64 programs evaluated in double-float
+  int idx64 = 0;   // 1: 64-bit element offsets asked for (OEC_INDEX_64)
   bool operator<(const ShapeKey& o) const {
-    return std::tie(ni, nj, nk, sj, sk, arith) < std::tie(o.ni, o.nj, o.nk, o.sj, o.sk, o.arith);
+    return std::tie(ni, nj, nk, sj, sk, arith, idx64) < std::tie(o.ni, o.nj, o.nk, o.sj, o.sk, o.arith, o.idx64);
   }
 };
 
@@ -329,8 +330,24 @@ Variant plan_variant(const Program& p, const std::vector<Box>& ranges, const Sha
   return v;
 }
 
+// true when every element offset the generated kernels form from a field's
+// domain corner (points of the inferred ranges) fits in an int32
+bool field_offsets_fit_int32(const std::vector<Box>& ranges, const ShapeKey& sh) {
+  if (sh.sj >= INT32_MAX || sh.sk >= INT32_MAX) return false;
+  const int64_t s[3] = {1, sh.sj, sh.sk};
+  int64_t lo[3] = {0, 0, 0}, hi[3] = {sh.ni, sh.nj, sh.nk};
+  for (const Box& b : ranges)
+    if (b.valid)
+      for (int d = 0; d < 3; ++d) { lo[d] = std::min(lo[d], b.lo[d]); hi[d] = std::max(hi[d], b.hi[d]); }
+  int64_t m = 0;
+  for (int d = 0; d < 3; ++d) m += std::max(std::abs(lo[d]), std::abs(hi[d])) * s[d];
+  return m < INT32_MAX;
+}
+
+// o32: the element offsets (the thread's point in the fields and in the
+// temporaries) are computed in 32-bit ints, else in 64-bit
 std::string kernel_source(const Program& p, const std::vector<Box>& ranges, const Variant& v, const KernelPlan& kp,
-                          const ShapeKey& sh, const char* T) {
+                          const ShapeKey& sh, const char* T, bool o32) {
   std::set<int> mat_except_self = v.materialised;
   for (int si : kp.stmts) mat_except_self.erase(si);
   Emitter e{p, ranges, mat_except_self, v.layout, sh, T};
@@ -345,17 +362,25 @@ std::string kernel_source(const Program& p, const std::vector<Box>& ranges, cons
   src += fmt("  if (kk > %lld) kk = %lld;\n", (long long)(bnk - kp.unroll), (long long)(bnk - kp.unroll));
   src += fmt("  const int i = ii + (%lld), j = jj + (%lld), k = kk + (%lld);\n", (long long)b.lo[0], (long long)b.lo[1],
              (long long)b.lo[2]);
-  src += "  const long long fo = (long long)k * " + fmt("%lldLL", (long long)sh.sk) + " + (long long)j * " +
-         fmt("%lldLL", (long long)sh.sj) + " + i;\n";
+  if (o32)
+    src += fmt("  const int fo = k * %lld + j * %lld + i;\n", (long long)sh.sk, (long long)sh.sj);
+  else
+    src += "  const long long fo = (long long)k * " + fmt("%lldLL", (long long)sh.sk) + " + (long long)j * " +
+           fmt("%lldLL", (long long)sh.sj) + " + i;\n";
   for (size_t x = 0; x < p.inputs.size(); ++x)
     src += fmt("  const S_* __restrict__ in%zu = a.in[%zu] + fo;\n", x, x);
   for (size_t x = 0; x < p.params.size(); ++x) src += fmt("  const %s P%zu = cvt_in(a.prm[%zu]);\n", T, x, x);
   for (auto& t : v.layout.tmp) {
     const Box& tb = t.second.second;
     const long long tj = tb.hi[0] - tb.lo[0], tk = tj * (tb.hi[1] - tb.lo[1]);
-    src += fmt("  %s* __restrict__ tp%d = (%s*)(a.scratch + %zuULL) + ((long long)(k - (%lld)) * %lldLL + "
-               "(long long)(j - (%lld)) * %lldLL + (i - (%lld)));\n",
-               T, t.first, T, t.second.first, (long long)tb.lo[2], tk, (long long)tb.lo[1], tj, (long long)tb.lo[0]);
+    if (o32)
+      src += fmt("  %s* __restrict__ tp%d = (%s*)(a.scratch + %zuULL) + ((k - (%lld)) * %lld + (j - (%lld)) * %lld + "
+                 "(i - (%lld)));\n",
+                 T, t.first, T, t.second.first, (long long)tb.lo[2], tk, (long long)tb.lo[1], tj, (long long)tb.lo[0]);
+    else
+      src += fmt("  %s* __restrict__ tp%d = (%s*)(a.scratch + %zuULL) + ((long long)(k - (%lld)) * %lldLL + "
+                 "(long long)(j - (%lld)) * %lldLL + (i - (%lld)));\n",
+                 T, t.first, T, t.second.first, (long long)tb.lo[2], tk, (long long)tb.lo[1], tj, (long long)tb.lo[0]);
   }
   for (int u = 0; u < kp.unroll; ++u) {
     for (int si : kp.stmts) {
@@ -412,10 +437,12 @@ std::string module_source(oec_program* prog, const ShapeKey& sh, const std::vect
   // layout shared with the host; the scalar parameters travel by value with
   // every launch (a launch captured into a CUDA graph keeps its own values)
   src += "struct Args { const S_* in[16]; S_* out[8]; char* scratch; double prm[16]; };\n";
+  const bool f32 = !sh.idx64 && field_offsets_fit_int32(ranges, sh);
   for (int fusion : {OEC_FUSE_INLINE, OEC_FUSE_NONE, OEC_FUSE_PARTIAL})
     for (int unroll : {1, 2, 4}) {
       Variant v = plan_variant(p, ranges, sh, fusion, unroll, es);
-      for (const KernelPlan& kp : v.kernels) src += kernel_source(p, ranges, v, kp, sh, T);
+      const bool o32 = f32 && v.layout.bytes / es < (size_t)INT32_MAX;
+      for (const KernelPlan& kp : v.kernels) src += kernel_source(p, ranges, v, kp, sh, T, o32);
       m.variants[{fusion, unroll}] = std::move(v);
     }
   return src;
@@ -633,7 +660,8 @@ int generic_apply(oec_program* p, const oec_field_desc* in, const oec_field_desc
   if (n_in > 16 || n_out > 8) return fail(OEC_ERR_UNSUPPORTED, "at most 16 inputs and 8 outputs");
   if (p->sched.arith == 1 && p->dtype != OEC_F64)
     return fail(OEC_ERR_UNSUPPORTED, "double-float generated kernels are for FP64 programs");
-  const ShapeKey key{ub[0] - lb[0], ub[1] - lb[1], ub[2] - lb[2], sj, sk, p->sched.arith};
+  const ShapeKey key{ub[0] - lb[0], ub[1] - lb[1], ub[2] - lb[2], sj, sk, p->sched.arith,
+                     p->sched.index_bits == OEC_INDEX_64 ? 1 : 0};
   Module* m = nullptr;
   int rc = get_module(p, key, &m);
   if (rc) return rc;
@@ -701,7 +729,8 @@ extern "C" int oec_program_prepare(oec_program_t p, const int64_t extent[3], int
     return fail(OEC_ERR_INVALID_ARG, "bad extent or strides");
   Module* m = nullptr;
   const int arith = p->dtype == OEC_F64 && p->sched.arith == 1 ? 1 : 0;
-  return get_module(p, ShapeKey{extent[0], extent[1], extent[2], sj, sk, arith}, &m);
+  return get_module(p, ShapeKey{extent[0], extent[1], extent[2], sj, sk, arith, p->sched.index_bits == OEC_INDEX_64 ? 1 : 0},
+                    &m);
 }
 
 extern "C" int oec_program_codegen(oec_program_t p, const int64_t extent[3], int64_t sj, int64_t sk, int compile,
@@ -712,7 +741,8 @@ extern "C" int oec_program_codegen(oec_program_t p, const int64_t extent[3], int
     if (s.kind == StmtKind::Column) return fail(OEC_ERR_UNSUPPORTED, "generated kernels do not solve columns");
   if (extent[0] < 1 || extent[1] < 1 || extent[2] < 1 || sj < extent[0] || sk < sj)
     return fail(OEC_ERR_INVALID_ARG, "bad extent or strides");
-  const ShapeKey key{extent[0], extent[1], extent[2], sj, sk, p->dtype == OEC_F64 && p->sched.arith == 1 ? 1 : 0};
+  const ShapeKey key{extent[0], extent[1], extent[2], sj, sk, p->dtype == OEC_F64 && p->sched.arith == 1 ? 1 : 0,
+                     p->sched.index_bits == OEC_INDEX_64 ? 1 : 0};
   const int64_t zlb[3] = {0, 0, 0}, zub[3] = {extent[0], extent[1], extent[2]};
   std::vector<Box> ranges;
   std::string err;

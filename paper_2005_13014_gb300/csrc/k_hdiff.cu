@@ -460,7 +460,7 @@ cudaError_t run_fixed(const oec_schedule& s, const Dom& d, int64_t osj, int64_t 
   const int nkz = ceil_div(d.nk, kc);
   dim3 g(ceil_div(d.ni, TI), ceil_div(d.nj, TJ), nkz * (in1 ? 2 : 1));
   constexpr int NT = TI * TJ / U;
-  if (offsets_fit_int32(d))
+  if (use_int32(s, d))
     hdiff_fixed_kernel<OutT, TI, TJ, U, int><<<g, NT, 0, st>>>(in, in1, coeff, out, out1, d.ni, d.nj, d.nk, d.sj,
                                                                d.sk, osj, osk, kc, nkz);
   else
@@ -582,7 +582,7 @@ cudaError_t run_regs(const oec_schedule& s, const Dom& d, const typename P::S* i
   dim3 b(s.tile_i, s.tile_j / U);
   dim3 g(ceil_div(d.ni, s.tile_i), ceil_div(d.nj, s.tile_j), ceil_div(d.nk, kc));
   typedef typename P::S S;
-  if (offsets_fit_int32(d))
+  if (use_int32(s, d))
     hdiff_regs_kernel<P, U, int, REGS_NB, S, false><<<g, b, 0, st>>>(in, coeff, out, d.ni, d.nj, d.nk, d.sj, d.sk, kc,
                                                                      0, 0, 0, nullptr, nullptr);
   else
@@ -601,7 +601,7 @@ cudaError_t run_regs_to(const oec_schedule& s, const Dom& d, int64_t osj, int64_
   const int kc = kchunk_of(s, d.nk), nkz = ceil_div(d.nk, kc);
   dim3 b(s.tile_i, s.tile_j / U);
   dim3 g(ceil_div(d.ni, s.tile_i), ceil_div(d.nj, s.tile_j), 2 * nkz);
-  if (offsets_fit_int32(d))
+  if (use_int32(s, d))
     hdiff_regs_kernel<P, U, int, REGS_NB, OutT, true><<<g, b, 0, st>>>(in0, coeff, out0, d.ni, d.nj, d.nk, d.sj,
                                                                        d.sk, kc, osj, osk, nkz, in1, out1);
   else

@@ -202,7 +202,7 @@ cudaError_t run_vec(const oec_schedule& s, const Dom& d, const typename P::S* in
   constexpr int W = 32 * Vec16<typename P::S>::V;
   const int kc = (s.k_chunk <= 0 || s.k_chunk > d.nk) ? d.nk : s.k_chunk;
   dim3 g(ceil_div(d.ni, W), ceil_div(d.nj, 4 * U), ceil_div(d.nk, kc));
-  if (offsets_fit_int32(d))
+  if (use_int32(s, d))
     hdiff_vec_kernel<P, U, int, 2, false><<<g, 128, 0, st>>>(in, coeff, out, d.ni, d.nj, d.nk, d.sj, d.sk, kc, 0, 0, 0,
                                                              nullptr, nullptr);
   else
@@ -221,7 +221,7 @@ cudaError_t run_vec_to(const oec_schedule& s, const Dom& d, int64_t osj, int64_t
   constexpr int W = 32 * Vec16<typename P::S>::V;
   const int kc = (s.k_chunk <= 0 || s.k_chunk > d.nk) ? d.nk : s.k_chunk, nkz = ceil_div(d.nk, kc);
   dim3 g(ceil_div(d.ni, W), ceil_div(d.nj, 4 * U), 2 * nkz);
-  if (offsets_fit_int32(d))
+  if (use_int32(s, d))
     hdiff_vec_kernel<P, U, int, 2, true><<<g, 128, 0, st>>>(in0, coeff, out0, d.ni, d.nj, d.nk, d.sj, d.sk, kc, osj,
                                                             osk, nkz, in1, out1);
   else

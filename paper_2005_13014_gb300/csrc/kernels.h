@@ -34,6 +34,12 @@ inline bool offsets_fit_int32(const Dom& d) {
   return hi < INT32_MAX && lo > INT32_MIN;
 }
 
+// the kernels with both offset widths take the 32-bit form unless the
+// schedule asks for 64-bit offsets or the offsets do not fit
+inline bool use_int32(const oec_schedule& s, const Dom& d) {
+  return s.index_bits != OEC_INDEX_64 && offsets_fit_int32(d);
+}
+
 // ---- horizontal diffusion: in, coeff -> out --------------------------------
 bool hdiff_schedule_ok(const oec_schedule& s, std::string& why);
 size_t hdiff_scratch_bytes(const oec_schedule& s, int dtype, const Dom& d);

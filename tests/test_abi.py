@@ -150,6 +150,20 @@ def test_bad_schedule_rejected(liboec):
     assert p.schedule["unroll"] == 2
 
 
+def test_index_bits_values(liboec):
+    """index_bits is OEC_INDEX_AUTO (0) or OEC_INDEX_64 (64); anything else
+    is refused with the reason, and the accepted value reads back."""
+    p = _prog(programs.HDIFF)
+    for bad in (32, 1, -64):
+        with pytest.raises(L.OecError) as e:
+            p.set_schedule(fusion=0, staging=0, tile_i=64, tile_j=4, index_bits=bad)
+        assert "index_bits" in str(e.value)
+    p.set_schedule(fusion=0, staging=0, tile_i=64, tile_j=4, index_bits=64)
+    assert p.schedule["index_bits"] == 64
+    p.set_schedule(fusion=0, staging=0, tile_i=64, tile_j=4)
+    assert p.schedule["index_bits"] == 0
+
+
 def test_timing_calls_without_gpu(liboec):
     """Launch counting and kernel timing need no GPU until an apply runs."""
     import ctypes as C

@@ -35,6 +35,26 @@ def test_builtin_texts_compile_generically(liboec):
     assert e.value.name == "UNSUPPORTED"
 
 
+def test_offset_width_of_generated_kernels(liboec):
+    """Generated kernels form the thread's element offset in 32-bit ints
+    when every offset of the inferred ranges fits (OEC_INDEX_AUTO), in
+    64-bit when the schedule asks for it (OEC_INDEX_64) or when the offsets
+    do not fit; both compile."""
+    p = _prog(inputs.random_dag(10003))
+    src = p.generated_source((40, 24, 9), 60, 60 * 44, compile=True)
+    assert "const int fo = " in src and "long long fo" not in src
+    sched = p.schedule
+    sched["index_bits"] = 64
+    p.set_schedule(**sched)
+    src = p.generated_source((40, 24, 9), 60, 60 * 44, compile=True)
+    assert "const long long fo = " in src and "const int fo" not in src
+    sched["index_bits"] = 0
+    p.set_schedule(**sched)
+    big = 1 << 28   # a plane stride of 2^28 elements: k offsets up to 9 * 2^28 > 2^31
+    src = p.generated_source((40, 24, 9), 60, big, compile=False)
+    assert "const long long fo = " in src and "const int fo" not in src
+
+
 def test_double_float_generated_source_compiles(liboec):
     """FP64 programs with arith 1: the generated module carries the
     double-float arithmetic and compiles with NVRTC for sm_103a."""

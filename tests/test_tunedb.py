@@ -90,6 +90,31 @@ def test_record_find_save_reload(liboec, tmp_path):
     L.lib().oec_tunedb_close(db)
 
 
+def test_index_bits_survive_a_reload(liboec, tmp_path):
+    """The schedule's offset width is stored; entries written without it
+    (seven schedule fields) read back as OEC_INDEX_AUTO."""
+    path = str(tmp_path / "tune.db")
+    db = _open(path)
+    hd = _prog(programs.HDIFF, "f32")
+    n = (64, 64, 8)
+    assert _record(db, hd, *_case(hd, n), n, (0, 0, 64, 4, 2, 0, 0, 64), 0.01) == 0
+    L.check(L.lib().oec_tunedb_save(db, None))
+    L.lib().oec_tunedb_close(db)
+    lines = open(path).read().splitlines()
+    assert lines[1].split("\t")[1] == "0 0 64 4 2 0 0 64"
+    db = _open(path)
+    s, _ = _find(db, hd, *_case(hd, n), n)
+    assert (s.tile_i, s.unroll, s.index_bits) == (64, 2, 64)
+    L.lib().oec_tunedb_close(db)
+    key = lines[1].split("\t")[0]
+    with open(path, "w") as f:
+        f.write(f"oec-tunedb 1\n{key}\t0 0 64 4 2 0 0\t0.01\n")
+    db = _open(path)
+    s, _ = _find(db, hd, *_case(hd, n), n)
+    assert (s.tile_i, s.unroll, s.index_bits) == (64, 2, 0)
+    L.lib().oec_tunedb_close(db)
+
+
 def test_alignment_is_part_of_the_key(liboec):
     db = _open(None)
     hd = _prog(programs.HDIFF, "f32")
