@@ -131,8 +131,9 @@ typedef struct oec_schedule {
 /* Width of the element offsets that kernels form from their fields' base
  * pointers (the paper's index type, §V-B and §VII-C). OEC_INDEX_AUTO: the
  * kernels that have a 32-bit form (fused horizontal diffusion with OEC_STAGE_REGS
- * or OEC_STAGE_WARP or OEC_ARITH_FIXED, the hdiff producers of the
- * stage-by-stage hdiff+vadvc form, and generated kernels) use 32-bit offsets
+ * or OEC_STAGE_WARP or OEC_ARITH_FIXED, the hdiff producers and the column
+ * sweep of the stage-by-stage hdiff+vadvc form, and generated kernels) use
+ * 32-bit offsets
  * when every offset they form fits in an int32, else 64-bit; all other kernels
  * use 64-bit offsets. OEC_INDEX_64: 64-bit offsets in every kernel. Both give
  * the same results bit for bit: only address arithmetic differs. */

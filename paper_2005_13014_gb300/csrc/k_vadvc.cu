@@ -360,7 +360,7 @@ template <> __device__ __forceinline__ df64 wsum<df64, double>(double a, double 
 // wrote; the one barrier separates the two uses of the ring. DTR_P2: dtr is a
 // power of two in float range, so dtr * phi is an exact scaling (for
 // double-float, two float multiplies instead of a pair product).
-template <class P, int NC, int DEPTH, bool DTR_P2>
+template <class P, int NC, int DEPTH, bool DTR_P2, class Off>
 __global__ void __launch_bounds__(2 * NC) hv_thomas_kernel(HV<typename P::S> p, const typename P::C* __restrict__ ud,
                                                            const typename P::C* __restrict__ vd, double dtr_d,
                                                            typename P::R* __restrict__ scr) {
@@ -388,6 +388,8 @@ __global__ void __launch_bounds__(2 * NC) hv_thomas_kernel(HV<typename P::S> p, 
   auto times_dtr = [&](C x) { return DTR_P2 ? mul_p2(x, dtr_f) : dtr * x; };
   const int64_t cbase = (int64_t)j * p.sj + i;
   const S* __restrict__ wcol = p.w + cbase;
+  // element offsets per level in Off (32-bit when every offset fits)
+  const Off ncol_o = (Off)ncol, col_o = (Off)col, sk_o = (Off)p.sk;
   // level of step s, and the level whose w gives the edge behind step s
   // (the edge between levels k-1 and k belongs to w at level k)
   auto lev = [&](int st) { return down ? nk - 1 - st : st; };
@@ -396,13 +398,13 @@ __global__ void __launch_bounds__(2 * NC) hv_thomas_kernel(HV<typename P::S> p, 
     if (active && st <= nsteps) {
       const int sl = st % DEPTH, k = lev(st), kw = wlev(st);
       if (k >= 0 && k < nk) {
-        const int64_t o = (int64_t)k * ncol + col;
+        const Off o = (Off)k * ncol_o + col_o;
         cp_async(&su[sl][t], ud + o);
         cp_async(&sv[sl][t], vd + o);
       }
       if (kw < nk) {
-        cp_async(&sw0[sl][t], wcol + (int64_t)kw * p.sk);
-        cp_async(&sw1[sl][t], wcol + (int64_t)kw * p.sk + 1);
+        cp_async(&sw0[sl][t], wcol + (Off)kw * sk_o);
+        cp_async(&sw1[sl][t], wcol + (Off)kw * sk_o + 1);
       }
     }
     cp_async_commit();
@@ -448,10 +450,10 @@ __global__ void __launch_bounds__(2 * NC) hv_thomas_kernel(HV<typename P::S> p, 
     g = cvt<R>(gamma) * inv;
     eu = subf(cvt<R>(ru), rb * eu) * inv;
     ev = subf(cvt<R>(rv), rb * ev) * inv;
-    R* sp = scr + (int64_t)lev(st) * 3 * ncol + col;
+    R* sp = scr + ((Off)lev(st) * 3 * ncol_o + col_o);
     sp[0] = g;
-    sp[ncol] = eu;
-    sp[2 * ncol] = ev;
+    sp[ncol_o] = eu;
+    sp[2 * ncol_o] = ev;
   };
   // row of step st+1 (it has a level behind; hi: it has one ahead)
   auto build_next = [&](int st, bool hi) {
@@ -518,18 +520,18 @@ __global__ void __launch_bounds__(2 * NC) hv_thomas_kernel(HV<typename P::S> p, 
     const int sb = nsteps - 2 - mm;
     if (sb >= 0) {
       const int sl = mm % DEPTH;
-      const R* sp = scr + (int64_t)lev(sb) * 3 * ncol + col;
+      const R* sp = scr + ((Off)lev(sb) * 3 * ncol_o + col_o);
       cp_async(&sg[sl][t], sp);
-      cp_async(&seu[sl][t], sp + ncol);
-      cp_async(&sev[sl][t], sp + 2 * ncol);
+      cp_async(&seu[sl][t], sp + ncol_o);
+      cp_async(&sev[sl][t], sp + 2 * ncol_o);
     }
     cp_async_commit();
   };
   if (nsteps == 0) return;
 #pragma unroll 1
   for (int mm = 0; mm < DEPTH - 1; ++mm) issue_b(mm);
-  int64_t o = (int64_t)lev(nsteps - 1) * p.sk + cbase;
-  const int64_t ostep = down ? p.sk : -p.sk;   // outwards
+  Off o = (Off)lev(nsteps - 1) * sk_o + (Off)cbase;
+  const Off ostep = down ? sk_o : -sk_o;   // outwards
   p.uo[o] = cvt<S>(xu);
   p.vo[o] = cvt<S>(xv);
 #pragma unroll 4
@@ -659,13 +661,24 @@ cudaError_t run(const oec_schedule& s, int dtype, const Dom& d, const HV<typenam
     typename P::R* scr = (typename P::R*)(scratch + l.thomas);
     int e2 = 0;
     const bool p2 = std::frexp(dtr, &e2) == 0.5 && e2 > -120 && e2 < 120;
+    // 32-bit offsets: the fields' (as for the producer) and the column
+    // scratch's (3 values per point) all fit
+    const bool o32 = use_int32(s, d) && 3 * ncol * d.nk < INT32_MAX;
     if constexpr (std::is_same<C, df64>::value) {
       if (p2) {
-        hv_thomas_kernel<P, NC, DEPTH, true><<<grid, 2 * NC, 0, st>>>(p, ud, vd, dtr, scr); launched(st);
+        if (o32)
+          hv_thomas_kernel<P, NC, DEPTH, true, int><<<grid, 2 * NC, 0, st>>>(p, ud, vd, dtr, scr);
+        else
+          hv_thomas_kernel<P, NC, DEPTH, true, int64_t><<<grid, 2 * NC, 0, st>>>(p, ud, vd, dtr, scr);
+        launched(st);
         return cudaGetLastError();
       }
     }
-    hv_thomas_kernel<P, NC, DEPTH, false><<<grid, 2 * NC, 0, st>>>(p, ud, vd, dtr, scr); launched(st);
+    if (o32)
+      hv_thomas_kernel<P, NC, DEPTH, false, int><<<grid, 2 * NC, 0, st>>>(p, ud, vd, dtr, scr);
+    else
+      hv_thomas_kernel<P, NC, DEPTH, false, int64_t><<<grid, 2 * NC, 0, st>>>(p, ud, vd, dtr, scr);
+    launched(st);
     return cudaGetLastError();
   }
   return dispatch_fused<P>(s, d, p, dtr, scratch + l.thomas, st);
