@@ -22,6 +22,13 @@
  *  - Apply calls are asynchronous: they enqueue work on the caller's CUDA
  *    stream (a cudaStream_t passed as void*, NULL = legacy default stream)
  *    and never synchronise with the host.
+ *  - Each apply call (oec_program_apply, oec_program_apply_host,
+ *    oec_batch_apply, oec_batch_apply_direct) is an NVTX range of that name,
+ *    for profilers that filter by range.
+ *  - Host-side fault injection for tests: the environment variable OEC_FAULT
+ *    set to "compile" makes run-time compilation of generated kernels fail
+ *    (OEC_ERR_COMPILE); set to "alloc" it makes a program's scratch
+ *    allocation fail (OEC_ERR_CUDA). Nothing is injected on the device.
  */
 #ifndef OEC_H
 #define OEC_H

@@ -194,6 +194,8 @@ int ensure_scratch(oec_program* p, size_t bytes) {
     p->scratch = nullptr;
     p->scratch_bytes = 0;
   }
+  if (fault_injected("alloc"))
+    return fail(OEC_ERR_CUDA, "scratch allocation of %zu bytes failed (injected by OEC_FAULT=alloc)", bytes);
   e = cudaMalloc(&p->scratch, bytes);
   if (e != cudaSuccess) {
     p->scratch = nullptr;
@@ -394,6 +396,7 @@ int oec_program_apply_host(oec_program_t p, const oec_field_desc* in, int n_in, 
                            int n_out, const int64_t lb[3], const int64_t ub[3], const int64_t halo[3],
                            const double* params, int n_params, void* cuda_stream) {
   clear_error();
+  NvtxRange range("oec_program_apply_host");
   if (!p || !lb || !ub || !halo) return fail(OEC_ERR_INVALID_ARG, "null argument");
   const Program& ir = p->ir;
   if (n_in != (int)ir.inputs.size() || (n_in && !in))
@@ -515,6 +518,7 @@ int oec_program_apply(oec_program_t p, const oec_field_desc* in, int n_in, const
                       const int64_t lb[3], const int64_t ub[3], const int64_t halo[3], const double* params,
                       int n_params, void* cuda_stream) {
   clear_error();
+  NvtxRange range("oec_program_apply");
   if (!p || !lb || !ub || !halo) return fail(OEC_ERR_INVALID_ARG, "null argument");
   p->last_launches = 0;
   const Program& ir = p->ir;

@@ -2,7 +2,10 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
+#include <cstdlib>
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -40,6 +43,23 @@ struct oec_program {
 };
 
 namespace oec {
+
+// a named NVTX range over one ABI call, for profilers that filter or group
+// by range (ncu --nvtx); costs a pointer test when no tool is attached
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+// host-side fault injection: the environment variable OEC_FAULT names one
+// failure to make ("compile": run-time compilation of generated kernels,
+// "alloc": the program's scratch allocation)
+inline bool fault_injected(const char* what) {
+  const char* f = std::getenv("OEC_FAULT");
+  return f && std::strcmp(f, what) == 0;
+}
 
 int fail(int code, const char* fmt, ...);
 void clear_error();

@@ -250,6 +250,7 @@ int oec_batch_create(oec_program_t p, const oec_batch_member* members, int n, co
 
 int oec_batch_apply(oec_batch_t b, void* stream) {
   clear_error();
+  NvtxRange range("oec_batch_apply");
   if (!b) return fail(OEC_ERR_INVALID_ARG, "null batch");
   cudaError_t e = cudaGraphLaunch(b->exec, (cudaStream_t)stream);
   return e == cudaSuccess ? OEC_OK : cuda_fail(e, "cudaGraphLaunch");
@@ -257,6 +258,7 @@ int oec_batch_apply(oec_batch_t b, void* stream) {
 
 int oec_batch_apply_direct(oec_batch_t b, void* stream) {
   clear_error();
+  NvtxRange range("oec_batch_apply_direct");
   if (!b) return fail(OEC_ERR_INVALID_ARG, "null batch");
   if (b->staged) {   // the same launches, one after another on the caller's stream
     cudaError_t e = record_staged(b, (char*)b->d_scratch, std::vector<cudaStream_t>{(cudaStream_t)stream});

@@ -449,8 +449,7 @@ std::string module_source(oec_program* prog, const ShapeKey& sh, const std::vect
 }
 
 int nvrtc_compile(const std::string& src, std::vector<char>& cubin) {
-  if (const char* f = std::getenv("OEC_FAULT"))
-    if (std::strcmp(f, "compile") == 0) return fail(OEC_ERR_COMPILE, "compile failure injected by OEC_FAULT=compile");
+  if (fault_injected("compile")) return fail(OEC_ERR_COMPILE, "compile failure injected by OEC_FAULT=compile");
   Nvrtc& nv = nvrtc();
   if (!nv.ok) return fail(OEC_ERR_COMPILE, "%s", nv.err.c_str());
   nvrtcProgram_ np = nullptr;

@@ -126,3 +126,35 @@ def test_bounded_wait_gives_up_and_is_reported():
     t = torch.ones(1024, device="cuda")
     assert float((t * 2).sum()) == 2048.0
     assert lib.oec_device_wait_selftest(0, None) == -1
+
+
+def test_injected_scratch_allocation_failure(monkeypatch):
+    """OEC_FAULT=alloc: an apply that needs scratch returns OEC_ERR_CUDA with
+    the reason and enqueues nothing; without it the same program runs and
+    agrees with the library's native-FP64 unfused kernels."""
+    from paper_2005_13014_gb300 import _lib as L
+    from paper_2005_13014_gb300.api import Program, device_field
+    n, h = (40, 24, 9), 3
+    f = inputs.hdiff_vadvc_fields(*n, h, seed=5)
+    din = [device_field(f[k], h, "f64") for k in ("u", "v", "w", "coeff")]
+    outs = [device_field(np.full_like(f["u"], 3.0), h, "f64") for _ in range(2)]
+    p = Program(programs.HDIFF_VADVC, "f64")
+    p.set_schedule(fusion=1, staging=0, tile_i=32, tile_j=8, k_chunk=4, arith=2)
+    monkeypatch.setenv("OEC_FAULT", "alloc")
+    with pytest.raises(L.OecError) as e:
+        p.apply(din, outs, (0, 0, 0), n, (h, h, h), [2.0])
+    assert e.value.name == "CUDA" and "OEC_FAULT=alloc" in str(e.value)
+    assert p.launch_count() == 0
+    torch.cuda.synchronize()
+    assert bool((outs[0].tensor == 3.0).all())
+    monkeypatch.delenv("OEC_FAULT")
+    p.apply(din, outs, (0, 0, 0), n, (h, h, h), [2.0])
+    r = Program(programs.HDIFF_VADVC, "f64")
+    r.set_schedule(fusion=1, arith=0)
+    ref = [device_field(np.zeros_like(f["u"]), h, "f64") for _ in range(2)]
+    r.apply(din, ref, (0, 0, 0), n, (h, h, h), [2.0])
+    torch.cuda.synchronize()
+    for o, q in zip(outs, ref):
+        a = o.interior((0, 0, 0), n).cpu().numpy()
+        b = q.interior((0, 0, 0), n).cpu().numpy()
+        assert np.max(np.abs(a - b)) <= 1e-13 * np.max(np.abs(b))
