@@ -62,6 +62,11 @@ __device__ __forceinline__ bool prod_gt0(df64 a, df64 b) {
 __device__ __forceinline__ float rcp_(float a) { return 1.0f / a; }
 __device__ __forceinline__ double rcp_(double a) { return 1.0 / a; }
 __device__ __forceinline__ df64 rcp_(df64 a) { return df_rcp(a); }
+// reciprocal of a pivot bounded away from zero and overflow (diagonally
+// dominant recurrences): double-float takes the approximate hardware seed
+__device__ __forceinline__ float rcp_pivot(float a) { return 1.0f / a; }
+__device__ __forceinline__ double rcp_pivot(double a) { return 1.0 / a; }
+__device__ __forceinline__ df64 rcp_pivot(df64 a) { return df_rcp_approx_seed(a); }
 
 template <class T> __device__ __forceinline__ T zero_() { return kc<T>(0.0f); }
 

@@ -103,6 +103,16 @@ __device__ __forceinline__ df64 df_rcp(df64 b) {
   return df_norm(x0, __fmul_rn(r.hi, x0));
 }
 
+// 1 / b seeded by the hardware's approximate reciprocal (rcp.approx.ftz.f32,
+// relative error about 2^-23), then the same Newton step: error about 2^-45.
+// For b.hi normal and below 2^126 (the column recurrence's pivots).
+__device__ __forceinline__ df64 df_rcp_approx_seed(df64 b) {
+  float x0;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(x0) : "f"(b.hi));
+  const df64 r = df_sub_fast(df64{1.0f, 0.0f}, df_mulf(b, x0));
+  return df_norm(x0, __fmul_rn(r.hi, x0));
+}
+
 __device__ __forceinline__ bool df_gt0(df64 a) { return a.hi > 0.0f; }   // sign of a normalised pair
 __device__ __forceinline__ df64 df_abs(df64 a) { return a.hi < 0.0f ? -a : a; }
 

@@ -421,24 +421,31 @@ __global__ void __launch_bounds__(2 * NC) hv_thomas_kernel(HV<typename P::S> p, 
   cp_async_wait<DEPTH - 3>();   // slots 0 and 1 have landed
   // row of step 0: no level behind; ahead: slot 1 (absent only when nk == 1)
   const bool ahead0 = nsteps > 0 && lev(1) >= 0 && lev(1) < nk;
-  C u1 = zero_<C>(), v1 = zero_<C>(), wfa = zero_<C>(), du0 = zero_<C>(), dv0 = zero_<C>();
+  // pu, pv: wf * (phi(next) - phi) of the edge ahead of the current row,
+  // unscaled. The explicit part of a row is -(beta (phi(k-1) - phi(k)) +
+  // gamma (phi(k+1) - phi(k))) / 2 = -sgn/8 (p_behind + p_ahead), and a row's
+  // p_ahead is the next row's p_behind, so each product is formed once. The
+  // scalings by +-1/4, 1/2 and +-1/8 are exact, so this is bit for bit the
+  // value of the two products written out.
+  C u1 = zero_<C>(), v1 = zero_<C>(), wfa = zero_<C>(), pu = zero_<C>(), pv = zero_<C>();
   C beta = zero_<C>(), gamma = zero_<C>(), b = dtr, ru = zero_<C>(), rv = zero_<C>();
+  const float sgn8 = 0.125f * sgn;
   if (nsteps > 0) {
     const C u0 = su[0][t], v0 = sv[0][t];
     if (ahead0) {
       u1 = su[1][t];
       v1 = sv[1][t];
       wfa = wf_of(1);
-      du0 = subf(u1, u0);
-      dv0 = subf(v1, v0);
+      pu = wfa * subf(u1, u0);
+      pv = wfa * subf(v1, v0);
       gamma = mul_p2(wfa, 0.25f * sgn);
     }
     b = addf(dtr, abs_(gamma));
     ru = times_dtr(u0);
     rv = times_dtr(v0);
     if (ahead0) {
-      ru = subf(ru, mul_p2(gamma * du0, 0.5f));
-      rv = subf(rv, mul_p2(gamma * dv0, 0.5f));
+      ru = subf(ru, mul_p2(pu, sgn8));
+      rv = subf(rv, mul_p2(pv, sgn8));
     }
   }
   // elimination of the row of step st (step 0 needs no special case:
@@ -446,7 +453,7 @@ __global__ void __launch_bounds__(2 * NC) hv_thomas_kernel(HV<typename P::S> p, 
   auto eliminate = [&](int st) {
     const R rb = cvt<R>(beta);
     const R m = subf(cvt<R>(b), rb * g);
-    const R inv = rcp_(m);
+    const R inv = rcp_pivot(m);
     g = cvt<R>(gamma) * inv;
     eu = subf(cvt<R>(ru), rb * eu) * inv;
     ev = subf(cvt<R>(rv), rb * ev) * inv;
@@ -457,30 +464,30 @@ __global__ void __launch_bounds__(2 * NC) hv_thomas_kernel(HV<typename P::S> p, 
   };
   // row of step st+1 (it has a level behind; hi: it has one ahead)
   auto build_next = [&](int st, bool hi) {
-    C u2 = zero_<C>(), v2 = zero_<C>(), wf2 = zero_<C>(), du1 = zero_<C>(), dv1 = zero_<C>();
+    C u2 = zero_<C>(), v2 = zero_<C>(), wf2 = zero_<C>(), qu = zero_<C>(), qv = zero_<C>();
     if (hi) {
       const int sl = (st + 2) % DEPTH;
       u2 = su[sl][t];
       v2 = sv[sl][t];
       wf2 = wf_of(st + 2);
-      du1 = subf(u2, u1);
-      dv1 = subf(v2, v1);
+      qu = wf2 * subf(u2, u1);
+      qv = wf2 * subf(v2, v1);
     }
     beta = mul_p2(wfa, -0.25f * sgn);
     gamma = hi ? mul_p2(wf2, 0.25f * sgn) : zero_<C>();
     b = addf(addf(dtr, abs_(beta)), abs_(gamma));
     const C tu = times_dtr(u1), tv = times_dtr(v1);
     if (hi) {
-      ru = subf(tu, mul_p2(addf(beta * (-du0), gamma * du1), 0.5f));
-      rv = subf(tv, mul_p2(addf(beta * (-dv0), gamma * dv1), 0.5f));
+      ru = subf(tu, mul_p2(addf(pu, qu), sgn8));
+      rv = subf(tv, mul_p2(addf(pv, qv), sgn8));
     } else {
-      ru = subf(tu, mul_p2(beta * (-du0), 0.5f));
-      rv = subf(tv, mul_p2(beta * (-dv0), 0.5f));
+      ru = subf(tu, mul_p2(pu, sgn8));
+      rv = subf(tv, mul_p2(pv, sgn8));
     }
     u1 = u2;
     v1 = v2;
-    du0 = du1;
-    dv0 = dv1;
+    pu = qu;
+    pv = qv;
     wfa = wf2;
   };
   // every row a half builds has a level ahead (the other half's first row is
@@ -501,7 +508,7 @@ __global__ void __launch_bounds__(2 * NC) hv_thomas_kernel(HV<typename P::S> p, 
   // the halves meet: x_lo = x_{mid-1} (upward half's last row), x_hi = x_mid
   const R g_o = shfl_xor_(g, 16), eu_o = shfl_xor_(eu, 16), ev_o = shfl_xor_(ev, 16);
   const R g_lo = down ? g_o : g, g_hi = down ? g : g_o;
-  const R inv = rcp_(subf(cvt<R>(1.0f), g_lo * g_hi));
+  const R inv = rcp_pivot(subf(cvt<R>(1.0f), g_lo * g_hi));
   R xu, xv;
   {
     const R eu_lo = down ? eu_o : eu, eu_hi = down ? eu : eu_o;
