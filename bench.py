@@ -111,6 +111,24 @@ def _dist():
     return ws, rank, local
 
 
+def _max_over_ranks(ms, dist=None):
+    """The slowest rank's time (ms); this rank's own time when there is no
+    process group. Every rank must call it (it is a collective)."""
+    if dist is None:
+        return float(ms)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _job_rate(units_per_rank, ms, ws, dist=None):
+    """Whole-job throughput: the units every rank processed (replicas, so
+    ws x units_per_rank) over the slowest rank's time."""
+    return units_per_rank * ws / (_max_over_ranks(ms, dist) * 1e-3)
+
+
 # the kernels one apply launches, per schedule form, with the source files
 # each is built from, the algorithmic FP64 operations per grid point it
 # performs, and the ncu summary that holds its DRAM traffic per launch
@@ -352,11 +370,8 @@ def run_gpu(args):
     step_ms = per_kernel.sum(axis=1)
     k_avg = per_kernel.mean(axis=0)
     dom = int(np.argmax(k_avg))
-    tmax = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-    total_ms = float(tmax.item())
-    value = points * args.steps * ws / (total_ms * 1e-3)
+    total_ms = _max_over_ranks(total_ms, dist)
+    value = _job_rate(points * args.steps, total_ms, ws)
 
     # end to end through the host-memory ABI call (oec_program_apply_host):
     # every step copies its inputs' storage from page-locked host memory to
@@ -381,6 +396,8 @@ def run_gpu(args):
     for _ in range(3):   # staging allocated, copies warm
         prog.apply_host(host_in, host_out, lb, ub, halo, [DTR], stream=stream)
     torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(stream):
         e0.record(stream)
@@ -388,8 +405,7 @@ def run_gpu(args):
             prog.apply_host(host_in, host_out, lb, ub, halo, [DTR], stream=stream)
         e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / e2e_steps
-    e2e_value = points * ws / (e2e_ms * 1e-3)
+    e2e_value = _job_rate(points, e0.elapsed_time(e1) / e2e_steps, ws, dist)
 
     alg_bytes = prog.algorithmic_bytes(lb, ub)
     peaks = _peaks()
