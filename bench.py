@@ -212,10 +212,18 @@ class OraclePool:
 
     def __init__(self, cores=None):
         import multiprocessing as mp
-        self.cores = max(1, cores or os.cpu_count() or 1)
+        try:   # the cores this process may run on (a CPU set can be smaller than the machine)
+            avail = len(os.sched_getaffinity(0))
+        except (AttributeError, OSError):
+            avail = os.cpu_count() or 1
+        self.cores = max(1, cores or avail)
         self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_oracle_worker_init)
-        self.rows(N[1])
-        self.step()   # workers up, fields built
+        try:
+            self.rows(N[1])
+            self.step()   # workers up, fields built
+        except BaseException:
+            self.pool.terminate()
+            raise
 
     def rows(self, nj):
         """Steps cover the j-rows [0, nj) of the domain (all of it by default)."""
@@ -231,24 +239,32 @@ class OraclePool:
         self.pool.close()
         self.pool.join()
 
+    def __enter__(self):
+        return self
+
+    def __exit__(self, exc_type, *_):
+        if exc_type is None:
+            self.close()
+        else:
+            self.pool.terminate()
+
 
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
     try:   # one step: the domain, j-rows split over every host core
-        op = OraclePool()
-        t0 = time.perf_counter()
-        for _ in range(max(1, args.warmup)):
-            op.step()
-        t_step = (time.perf_counter() - t0) / max(1, args.warmup)
-        if args.steps * t_step > 120.0:   # keep the timed run near two minutes: fewer rows per step
-            op.rows(max(op.cores, int(N[1] * 120.0 / (args.steps * t_step))))
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            op.step()
-        el = time.perf_counter() - t0
-        op.close()
+        with OraclePool() as op:
+            t0 = time.perf_counter()
+            for _ in range(max(1, args.warmup)):
+                op.step()
+            t_step = (time.perf_counter() - t0) / max(1, args.warmup)
+            if args.steps * t_step > 120.0:   # keep the timed run near two minutes: fewer rows per step
+                op.rows(max(op.cores, int(N[1] * 120.0 / (args.steps * t_step))))
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                op.step()
+            el = time.perf_counter() - t0
         value = N[0] * op.nj * N[2] * args.steps / el
         sample = (f"numpy FP64 oracle on {N[0]}x{op.nj}x{N[2]} points of the 128x128x80 domain per step, j-rows "
                   f"split over {op.cores} worker processes")
@@ -447,13 +463,12 @@ def run_gpu(args):
         # one core beside it
         rate1, reps1 = cpu_oracle_rate(args.cpu_seconds / 3)
         try:
-            op = OraclePool()
-            reps, t0 = 0, time.perf_counter()
-            while time.perf_counter() - t0 < args.cpu_seconds:
-                op.step()
-                reps += 1
-            el = time.perf_counter() - t0
-            op.close()
+            with OraclePool() as op:
+                reps, t0 = 0, time.perf_counter()
+                while time.perf_counter() - t0 < args.cpu_seconds:
+                    op.step()
+                    reps += 1
+                el = time.perf_counter() - t0
             line["cpu_baseline"] = {"value": N[0] * N[1] * N[2] * reps / el, "unit": "grid-points/s",
                                     "cores": op.cores, "kind": "oracle",
                                     "sample": f"numpy FP64 oracle on the full 128x128x80 domain, {reps} repetitions, "
