@@ -199,7 +199,12 @@ typedef struct oec_program_info {
  *   column x = thomas(a, b, c, d)                  tridiagonal solve along k
  *   output x              stored values           (stencil.store)
  * Expressions: + - * / unary -, min, max, abs, select(x > y, a, b) (also <, >=,
- * <=), numbers, params, `kpos` (k minus the domain's lower k) and `ksize`.
+ * <=), numbers, params, `kpos` (k minus the domain's lower k) and `ksize`,
+ * and control flow inside an apply (paper §IV-C, scf.if / scf.yield):
+ *   if (x > y) { let t = expr; yield e1 } else { yield e2 }
+ * whose value is the yield of the region the condition picks; a region's lets
+ * are visible in it only. Regions are pure, so the library evaluates the if
+ * as select(x > y, e1, e2) with the regions' lets bound in the stage.
  * On success *out receives a handle. No GPU work happens here.
  * Errors: OEC_ERR_INVALID_ARG, OEC_ERR_PARSE (message gives the position).
  */

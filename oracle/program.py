@@ -18,6 +18,12 @@ Expressions: numbers, names (offset [0,0,0]), name[di,dj,dk], unary -, + - * /
 (left-associative, * and / bind tighter), min(a,b), max(a,b), abs(a),
 select(x OP y, a, b) with OP in > < >= <=, and two level intrinsics: ``kpos``
 (k minus the domain's lower k bound) and ``ksize`` (domain extent in k).
+Control flow inside an operator (§IV-C, scf.if with scf.yield) is written
+
+    if (x OP y) { let t = ...; yield a } else { yield b }
+
+an expression whose value is the yield of the region the condition picks;
+each region may bind its own lets. At a point only that region is evaluated.
 
 Shape inference follows §V-B: statements are walked in reverse; a value's
 range is the bounding box of the extents its consumers read (an output's
@@ -75,6 +81,7 @@ def _tokens(src: str):
 # expression nodes are tuples:
 #   ("num", value) ("acc", name, (di,dj,dk)) ("ref", name) ("param", name) ("kpos",) ("ksize",)
 #   ("neg", e) ("bin", op, a, b) ("min", a, b) ("max", a, b) ("abs", a) ("sel", rel, x, y, a, b)
+#   ("if", rel, x, y, then_lets, then_yield, else_lets, else_yield), lets as [(name, expr)]
 
 
 @dataclass
@@ -169,6 +176,18 @@ class _Parser:
             b = self.expr(scope)
             self.expect("op", ")")
             return ("sel", rel[1], x, y, a, b)
+        if val == "if":
+            self.expect("op", "(")
+            x = self.expr(scope)
+            rel = self.next()
+            if rel[0] != "op" or rel[1] not in (">", "<", ">=", "<="):
+                raise ParseError("if needs a comparison")
+            y = self.expr(scope)
+            self.expect("op", ")")
+            tl, te = self.region(scope)
+            self.expect("id", "else")
+            fl, fe = self.region(scope)
+            return ("if", rel[1], x, y, tl, te, fl, fe)
         if val == "kpos":
             return ("kpos",)
         if val == "ksize":
@@ -191,6 +210,27 @@ class _Parser:
         if cls == "param":
             return ("param", val)
         raise ParseError(f"unknown name {val!r}")
+
+    def region(self, scope):
+        """{ let n = e; ... yield e }: the region's lets (visible in it only)
+        and its yielded value."""
+        self.expect("op", "{")
+        local, lets = dict(scope), []
+        while self.peek() == ("id", "let"):
+            self.next()
+            n = self.expect("id")
+            self.expect("op", "=")
+            e = self.expr(local)
+            if n in local or n in _RESERVED:
+                raise ParseError(f"let {n!r} shadows a name")
+            local[n] = "let"
+            lets.append((n, e))
+            self.accept(";")
+        self.expect("id", "yield")
+        e = self.expr(local)
+        self.accept(";")
+        self.expect("op", "}")
+        return lets, e
 
     def unary(self, scope):
         if self.accept("-"):
@@ -216,7 +256,7 @@ class _Parser:
         scope = {}
 
         def define(name, cls):
-            if name in scope or name in ("min", "max", "abs", "select", "kpos", "ksize", "let", "return"):
+            if name in scope or name in _RESERVED:
                 raise ParseError(f"name {name!r} defined twice or reserved")
             scope[name] = cls
 
@@ -246,7 +286,7 @@ class _Parser:
                         n = self.expect("id")
                         self.expect("op", "=")
                         e = self.expr(local)
-                        if n in local:
+                        if n in local or n in _RESERVED:
                             raise ParseError(f"let {n!r} shadows a name")
                         local[n] = "let"
                         st.lets.append((n, e))
@@ -286,6 +326,9 @@ class _Parser:
         return Program(inputs, params, stmts, outputs)
 
 
+_RESERVED = ("min", "max", "abs", "select", "kpos", "ksize", "let", "return", "if", "else", "yield")
+
+
 def parse(src: str) -> Program:
     return _Parser(src).program()
 
@@ -309,6 +352,13 @@ def _accesses(e, out):
     elif tag == "sel":
         for s in e[2:]:
             _accesses(s, out)
+    elif tag == "if":   # both regions' accesses: either may run at a point of the range
+        _accesses(e[2], out)
+        _accesses(e[3], out)
+        for lets, y in ((e[4], e[5]), (e[6], e[7])):
+            for _, x in lets:
+                _accesses(x, out)
+            _accesses(y, out)
     return out
 
 
@@ -400,6 +450,16 @@ def _eval_box(e, box, env, lets, params, kdom):
         return np.abs(ev(e[1]))
     if tag == "sel":
         return np.where(_REL[e[1]](ev(e[2]), ev(e[3])), ev(e[4]), ev(e[5]))
+    if tag == "if":
+        # over a box each region is evaluated everywhere and the condition
+        # picks per point; regions are pure, so every point gets the value of
+        # the region that runs there
+        def region(rlets, y):
+            loc = dict(lets)
+            for n, x in rlets:
+                loc[n] = _eval_box(x, box, env, loc, params, kdom)
+            return _eval_box(y, box, env, loc, params, kdom)
+        return np.where(_REL[e[1]](ev(e[2]), ev(e[3])), region(e[4], e[5]), region(e[6], e[7]))
     raise ValueError(tag)
 
 
@@ -517,6 +577,14 @@ def run_inlined(src_or_prog, fields: dict, lb, ub, params=None, points=None):
             # both branches are evaluated, as select does on value-semantic temps
             a, b = ev(e[4], i, j, k, lets), ev(e[5], i, j, k, lets)
             return a if cond else b
+        if tag == "if":   # only the region the condition picks runs (scf.if)
+            x, y = ev(e[2], i, j, k, lets), ev(e[3], i, j, k, lets)
+            cond = {">": x > y, "<": x < y, ">=": x >= y, "<=": x <= y}[e[1]]
+            rlets, yv = (e[4], e[5]) if cond else (e[6], e[7])
+            loc = dict(lets)
+            for n, x in rlets:
+                loc[n] = ev(x, i, j, k, loc)
+            return ev(yv, i, j, k, loc)
         raise ValueError(tag)
 
     if points is None:

@@ -79,6 +79,7 @@ struct Parser {
   size_t pos = 0;
   Program& p;
   std::map<std::string, std::pair<NameKind, int>> scope;  // name -> (kind, id)
+  Stmt* cur = nullptr;   // the stage being parsed (its lets receive the regions' lets)
 
   Parser(const char* src, Program& prog) : t(lex(src)), p(prog) {}
 
@@ -121,7 +122,7 @@ struct Parser {
   }
   static bool reserved(const std::string& n) {
     static const char* r[] = {"input", "param", "stage", "column", "output", "let", "return", "min", "max",
-                              "abs", "select", "kpos", "ksize", "thomas"};
+                              "abs", "select", "kpos", "ksize", "thomas", "if", "else", "yield"};
     for (const char* x : r) if (n == x) return true;
     return false;
   }
@@ -182,6 +183,27 @@ struct Parser {
       expect(")");
       return node(e);
     }
+    if (n == "if") {
+      // if (x REL y) { lets; yield a } else { lets; yield b }: the value of
+      // the region the condition picks (paper §IV-C, scf.if / scf.yield).
+      // Regions are pure, so this is select(x REL y, a, b) with the regions'
+      // lets bound in the enclosing stage (visible only inside their region).
+      expect("(");
+      e.op = Op::Sel;
+      e.a = expr();
+      if (accept(">")) e.rel = Rel::GT;
+      else if (accept("<")) e.rel = Rel::LT;
+      else if (accept(">=")) e.rel = Rel::GE;
+      else if (accept("<=")) e.rel = Rel::LE;
+      else fail("if needs a comparison");
+      e.b = expr();
+      expect(")");
+      e.c = region();
+      if (!is_id("else")) fail("expected 'else'");
+      ++pos;
+      e.d = region();
+      return node(e);
+    }
     if (n == "kpos") { e.op = Op::KPos; return node(e); }
     if (n == "ksize") { e.op = Op::KSize; return node(e); }
     auto it = scope.find(n);
@@ -207,6 +229,33 @@ struct Parser {
     }
     e.ref = it->second.second;
     return node(e);
+  }
+  // { let n = e; ... yield e } of an if: its lets join the current stage's
+  // lets (evaluated before the expression that holds the if) under names
+  // visible in this region only; returns the yielded expression
+  int region() {
+    if (!cur) fail("if outside a stage");
+    expect("{");
+    std::vector<std::string> local;
+    while (is_id("let")) {
+      ++pos;
+      std::string n = ident();
+      expect("=");
+      int e = expr();
+      p.lets.push_back(n);
+      int lid = int(p.lets.size()) - 1;
+      define(n, NameKind::Let, lid);
+      local.push_back(n);
+      cur->lets.push_back({lid, e});
+      accept(";");
+    }
+    if (!is_id("yield")) fail("expected 'yield'");
+    ++pos;
+    int v = expr();
+    accept(";");
+    expect("}");
+    for (auto& n : local) scope.erase(n);
+    return v;
   }
   int unary() {
     if (accept("-")) {
@@ -273,6 +322,7 @@ struct Parser {
         expect("=");
         Stmt st;
         st.kind = StmtKind::Stage;
+        cur = &st;
         std::vector<std::string> local;
         if (accept("{")) {
           while (is_id("let")) {
@@ -296,6 +346,7 @@ struct Parser {
         } else {
           st.rets.push_back(expr());
         }
+        cur = nullptr;
         for (auto& n : local) scope.erase(n);   // lets are local to their stage
         if (st.rets.size() != res.size()) fail("number of results and returned values differ");
         int sid = int(p.stmts.size());
