@@ -104,10 +104,10 @@ output uc_out, vc_out
 HADVUV = """
 input uin, vin, uatupos, vatupos, uatvpos, vatvpos
 param eddlat, eddlon
-stage axu = select(uatupos > 0.0, uatupos*(2.0*uin[1,0,0] + 3.0*uin - 6.0*uin[-1,0,0] + uin[-2,0,0]), uatupos*(-uin[2,0,0] + 6.0*uin[1,0,0] - 3.0*uin - 2.0*uin[-1,0,0]))
-stage ayu = select(vatupos > 0.0, vatupos*(2.0*uin[0,1,0] + 3.0*uin - 6.0*uin[0,-1,0] + uin[0,-2,0]), vatupos*(-uin[0,2,0] + 6.0*uin[0,1,0] - 3.0*uin - 2.0*uin[0,-1,0]))
-stage axv = select(uatvpos > 0.0, uatvpos*(2.0*vin[1,0,0] + 3.0*vin - 6.0*vin[-1,0,0] + vin[-2,0,0]), uatvpos*(-vin[2,0,0] + 6.0*vin[1,0,0] - 3.0*vin - 2.0*vin[-1,0,0]))
-stage ayv = select(vatvpos > 0.0, vatvpos*(2.0*vin[0,1,0] + 3.0*vin - 6.0*vin[0,-1,0] + vin[0,-2,0]), vatvpos*(-vin[0,2,0] + 6.0*vin[0,1,0] - 3.0*vin - 2.0*vin[0,-1,0]))
+stage axu = if (uatupos > 0.0) { yield uatupos*(2.0*uin[1,0,0] + 3.0*uin - 6.0*uin[-1,0,0] + uin[-2,0,0]) } else { yield uatupos*(-uin[2,0,0] + 6.0*uin[1,0,0] - 3.0*uin - 2.0*uin[-1,0,0]) }
+stage ayu = if (vatupos > 0.0) { yield vatupos*(2.0*uin[0,1,0] + 3.0*uin - 6.0*uin[0,-1,0] + uin[0,-2,0]) } else { yield vatupos*(-uin[0,2,0] + 6.0*uin[0,1,0] - 3.0*uin - 2.0*uin[0,-1,0]) }
+stage axv = if (uatvpos > 0.0) { yield uatvpos*(2.0*vin[1,0,0] + 3.0*vin - 6.0*vin[-1,0,0] + vin[-2,0,0]) } else { yield uatvpos*(-vin[2,0,0] + 6.0*vin[1,0,0] - 3.0*vin - 2.0*vin[-1,0,0]) }
+stage ayv = if (vatvpos > 0.0) { yield vatvpos*(2.0*vin[0,1,0] + 3.0*vin - 6.0*vin[0,-1,0] + vin[0,-2,0]) } else { yield vatvpos*(-vin[0,2,0] + 6.0*vin[0,1,0] - 3.0*vin - 2.0*vin[0,-1,0]) }
 stage advu = (eddlon*axu + eddlat*ayu)/6.0
 stage advv = (eddlon*axv + eddlat*ayv)/6.0
 stage uout = uin - advu
@@ -119,8 +119,8 @@ output uout, vout
 FVTP2D_FLUX = """
 input q, crx, cry, xfx, yfx, al, bl
 stage qm = 0.5*(q[1,0,0] + q[-1,0,0])
-stage fx1 = select(crx > 0.0, q[-1,0,0] + (1.0 - crx)*(al - q[-1,0,0]), q + (1.0 + crx)*(al - qm))
-stage fy1 = select(cry > 0.0, q[0,-1,0] + (1.0 - cry)*(bl - q[0,-1,0]), q + (1.0 + cry)*(bl - q))
+stage fx1 = if (crx > 0.0) { yield q[-1,0,0] + (1.0 - crx)*(al - q[-1,0,0]) } else { yield q + (1.0 + crx)*(al - qm) }
+stage fy1 = if (cry > 0.0) { yield q[0,-1,0] + (1.0 - cry)*(bl - q[0,-1,0]) } else { yield q + (1.0 + cry)*(bl - q) }
 stage fx = xfx*fx1
 stage fy = yfx*fy1
 output fx, fy
@@ -145,10 +145,10 @@ output u_out, v_out
 HADVUV5TH = """
 input uin, vin, uatupos, vatupos, uatvpos, vatvpos
 param eddlat, eddlon
-stage axu = select(uatupos > 0.0, uatupos*(-2.0*uin[-3,0,0] + 15.0*uin[-2,0,0] - 60.0*uin[-1,0,0] + 20.0*uin + 30.0*uin[1,0,0] - 3.0*uin[2,0,0]), uatupos*(3.0*uin[-2,0,0] - 30.0*uin[-1,0,0] - 20.0*uin + 60.0*uin[1,0,0] - 15.0*uin[2,0,0] + 2.0*uin[3,0,0]))
-stage ayu = select(vatupos > 0.0, vatupos*(-2.0*uin[0,-3,0] + 15.0*uin[0,-2,0] - 60.0*uin[0,-1,0] + 20.0*uin + 30.0*uin[0,1,0] - 3.0*uin[0,2,0]), vatupos*(3.0*uin[0,-2,0] - 30.0*uin[0,-1,0] - 20.0*uin + 60.0*uin[0,1,0] - 15.0*uin[0,2,0] + 2.0*uin[0,3,0]))
-stage axv = select(uatvpos > 0.0, uatvpos*(-2.0*vin[-3,0,0] + 15.0*vin[-2,0,0] - 60.0*vin[-1,0,0] + 20.0*vin + 30.0*vin[1,0,0] - 3.0*vin[2,0,0]), uatvpos*(3.0*vin[-2,0,0] - 30.0*vin[-1,0,0] - 20.0*vin + 60.0*vin[1,0,0] - 15.0*vin[2,0,0] + 2.0*vin[3,0,0]))
-stage ayv = select(vatvpos > 0.0, vatvpos*(-2.0*vin[0,-3,0] + 15.0*vin[0,-2,0] - 60.0*vin[0,-1,0] + 20.0*vin + 30.0*vin[0,1,0] - 3.0*vin[0,2,0]), vatvpos*(3.0*vin[0,-2,0] - 30.0*vin[0,-1,0] - 20.0*vin + 60.0*vin[0,1,0] - 15.0*vin[0,2,0] + 2.0*vin[0,3,0]))
+stage axu = if (uatupos > 0.0) { yield uatupos*(-2.0*uin[-3,0,0] + 15.0*uin[-2,0,0] - 60.0*uin[-1,0,0] + 20.0*uin + 30.0*uin[1,0,0] - 3.0*uin[2,0,0]) } else { yield uatupos*(3.0*uin[-2,0,0] - 30.0*uin[-1,0,0] - 20.0*uin + 60.0*uin[1,0,0] - 15.0*uin[2,0,0] + 2.0*uin[3,0,0]) }
+stage ayu = if (vatupos > 0.0) { yield vatupos*(-2.0*uin[0,-3,0] + 15.0*uin[0,-2,0] - 60.0*uin[0,-1,0] + 20.0*uin + 30.0*uin[0,1,0] - 3.0*uin[0,2,0]) } else { yield vatupos*(3.0*uin[0,-2,0] - 30.0*uin[0,-1,0] - 20.0*uin + 60.0*uin[0,1,0] - 15.0*uin[0,2,0] + 2.0*uin[0,3,0]) }
+stage axv = if (uatvpos > 0.0) { yield uatvpos*(-2.0*vin[-3,0,0] + 15.0*vin[-2,0,0] - 60.0*vin[-1,0,0] + 20.0*vin + 30.0*vin[1,0,0] - 3.0*vin[2,0,0]) } else { yield uatvpos*(3.0*vin[-2,0,0] - 30.0*vin[-1,0,0] - 20.0*vin + 60.0*vin[1,0,0] - 15.0*vin[2,0,0] + 2.0*vin[3,0,0]) }
+stage ayv = if (vatvpos > 0.0) { yield vatvpos*(-2.0*vin[0,-3,0] + 15.0*vin[0,-2,0] - 60.0*vin[0,-1,0] + 20.0*vin + 30.0*vin[0,1,0] - 3.0*vin[0,2,0]) } else { yield vatvpos*(3.0*vin[0,-2,0] - 30.0*vin[0,-1,0] - 20.0*vin + 60.0*vin[0,1,0] - 15.0*vin[0,2,0] + 2.0*vin[0,3,0]) }
 stage advu = (eddlon*axu + eddlat*ayu)/60.0
 stage advv = (eddlon*axv + eddlat*ayv)/60.0
 stage uout = uin - advu
@@ -176,7 +176,7 @@ input q, crx, xfx, area, ra_x
 stage al = 0.5833333333333334*(q[-1,0,0] + q) - 0.08333333333333333*(q[-2,0,0] + q[1,0,0])
 stage bl = al - q
 stage br = al[1,0,0] - q
-stage fx1 = select(crx > 0.0, q[-1,0,0] + (1.0 - crx)*(br[-1,0,0] - crx*(bl[-1,0,0] + br[-1,0,0])), q + (1.0 + crx)*(bl + crx*(bl + br)))
+stage fx1 = if (crx > 0.0) { yield q[-1,0,0] + (1.0 - crx)*(br[-1,0,0] - crx*(bl[-1,0,0] + br[-1,0,0])) } else { yield q + (1.0 + crx)*(bl + crx*(bl + br)) }
 stage q_i = (q*area + fx1*xfx - fx1[1,0,0]*xfx[1,0,0])/ra_x
 output fx1, q_i
 """
@@ -189,7 +189,7 @@ stage al = 0.5833333333333334*(q[0,-1,0] + q) - 0.08333333333333333*(q[0,-2,0] +
 stage bl = al - q
 stage br = al[0,1,0] - q
 stage b0 = min(abs(bl), abs(br))*(bl + br)
-stage fy1 = select(cry > 0.0, q[0,-1,0] + (1.0 - cry)*(br[0,-1,0] - cry*b0[0,-1,0]), q + (1.0 + cry)*(bl + cry*b0))
+stage fy1 = if (cry > 0.0) { yield q[0,-1,0] + (1.0 - cry)*(br[0,-1,0] - cry*b0[0,-1,0]) } else { yield q + (1.0 + cry)*(bl + cry*b0) }
 stage fy = yfx*fy1
 stage q_j = (q*area + fy - fy[0,1,0])/ra_y
 stage mf = mfy*fy1

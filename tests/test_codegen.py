@@ -228,3 +228,36 @@ def test_if_program_matches_oracle(dtype):
         for o, name in zip(outs, prog.outputs):
             got = o.interior((0, 0, 0), n).cpu().numpy().astype(np.float64)
             assert rel_err(got, ref[name]) <= TOL[dtype]
+
+
+def _as_select(text):
+    """The textual lowering of region ifs without lets to selects:
+    if (c) { yield a } else { yield b }  ->  select(c, a, b)."""
+    out, i = [], 0
+    while True:
+        j = text.find("if (", i)
+        if j < 0:
+            return "".join(out) + text[i:]
+        out.append(text[i:j])
+        pos, parts = j + 3, []
+        for open_, close in (("(", ")"), ("{", "}"), ("{", "}")):
+            pos = text.index(open_, pos)
+            depth, m = 1, pos + 1
+            while depth:
+                depth += {open_: 1, close: -1}.get(text[m], 0)
+                m += 1
+            body = text[pos + 1:m - 1].strip()
+            parts.append(_as_select(body[len("yield"):].strip() if body.startswith("yield") else body))
+            pos = m
+        out.append(f"select({parts[0]}, {parts[1]}, {parts[2]})")
+        i = pos
+
+
+@pytest.mark.parametrize("name", ["hadvuv", "hadvuv5th", "fvtp2d_qi", "fvtp2d_qj", "fvtp2d_flux"])
+def test_testset_if_regions_generate_the_select_kernels(liboec, name):
+    src = programs.TESTSET[name][0]
+    sel = _as_select(src)
+    assert "if (" in src and "if (" not in sel and "select(" in sel
+    for dt in ("f32", "f64"):
+        assert _prog(src, dt).generated_source((33, 17, 5), 41, 41 * 25) == \
+            _prog(sel, dt).generated_source((33, 17, 5), 41, 41 * 25)

@@ -45,7 +45,9 @@ def test_shape_matches_table_ii(name):
     assert len(p.stmts) == applies and len(p.inputs) == n_in and len(p.outputs) == n_out
     assert len(params) == len(p.params)
     if name in ("hadvuv", "hadvuv5th", "fvtp2d_flux", "fvtp2d_qi", "fvtp2d_qj"):
-        assert "select(" in src   # the table's `if`
+        # the table's `if`: region control flow whose regions are upwind choices
+        assert "if (" in src and "yield" in src
+        assert any(e[0] == "if" for st in p.stmts for e in st.rets + [x for _, x in st.lets])
     if name == "hdiffsmag":
         assert "min(" in src and "max(" in src
 
