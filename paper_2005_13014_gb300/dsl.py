@@ -23,7 +23,9 @@ Rules: offsets apply to named values (inputs, stages); indexing any other
 expression makes it a stage first. ``let`` binds a subexpression locally in
 the next stage (the text's ``let``). A program written with the same stages,
 lets and operation order as one of the library's hand-written programs is
-recognised as that program and runs its kernels. ``select(a > b, x, y)``, ``minimum``,
+recognised as that program and runs its kernels. ``if_(a > b, x, y)`` is the
+text's region ``if`` (the value of x where a > b holds, else of y).
+``select(a > b, x, y)``, ``minimum``,
 ``maximum``, ``absolute``, ``kpos`` and ``ksize`` map to the text's
 ``select``, ``min``, ``max``, ``abs``, ``kpos`` and ``ksize``; ``thomas(a, b,
 c, d...)`` is a column solve. Parameters are arguments annotated
@@ -32,8 +34,8 @@ c, d...)`` is a column solve. Parameters are arguments annotated
 
 import inspect
 
-__all__ = ["Field", "Param", "program", "stage", "let", "select", "minimum", "maximum", "absolute", "thomas", "kpos",
-           "ksize", "Program"]
+__all__ = ["Field", "Param", "program", "stage", "let", "select", "if_", "minimum", "maximum", "absolute", "thomas",
+           "kpos", "ksize", "Program"]
 
 
 class Field:
@@ -185,6 +187,16 @@ def select(cond, a, b):
         raise TypeError("select needs a comparison such as x > 0.0")
     a, b = _wrap(a), _wrap(b)
     return Expr(f"select({cond.a.text} {cond.rel} {cond.b.text}, {a.text}, {b.text})")
+
+
+def if_(cond, then, otherwise):
+    """Control flow inside a stage (paper §IV-C, scf.if): the value of
+    ``then`` where the comparison holds, else of ``otherwise``; printed as the
+    text's ``if (...) { yield ... } else { yield ... }``."""
+    if not isinstance(cond, _Cond):
+        raise TypeError("if_ needs a comparison such as x > 0.0")
+    a, b = _wrap(then), _wrap(otherwise)
+    return Expr(f"if ({cond.a.text} {cond.rel} {cond.b.text}) {{ yield {a.text} }} else {{ yield {b.text} }}")
 
 
 def minimum(a, b):

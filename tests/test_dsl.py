@@ -84,6 +84,27 @@ def test_recognised_as_hand_written_programs(liboec):
     assert UVBKE.compile("f32").kind == "generic"
 
 
+def test_if_regions(liboec):
+    """dsl.if_ prints a region if; hdiff written with it is still hdiff, and
+    the oracle gives the same bits as for the select form."""
+    @dsl.program
+    def hd_if(inp: dsl.Field, coeff: dsl.Field):
+        lap = dsl.stage(4.0 * inp - inp[-1, 0, 0] - inp[1, 0, 0] - inp[0, -1, 0] - inp[0, 1, 0], "lap")
+        f = dsl.let(lap[1, 0, 0] - lap)
+        flx = dsl.stage(dsl.if_(f * (inp[1, 0, 0] - inp) > 0.0, 0.0, f), "flx")
+        f = dsl.let(lap[0, 1, 0] - lap)
+        fly = dsl.stage(dsl.if_(f * (inp[0, 1, 0] - inp) > 0.0, 0.0, f), "fly")
+        return {"out": inp - coeff * ((flx - flx[-1, 0, 0]) + (fly - fly[0, -1, 0]))}
+    assert "return if (l0*(inp[1,0,0] - inp) > 0.0) { yield 0.0 } else { yield l0 }" in hd_if.text
+    assert hd_if.compile("f64").kind == "hdiff"
+    f = inputs.hdiff_fields(9, 7, 3, 2, seed=4)
+    _same_results(hd_if.text, programs.HDIFF, {"inp": f["in"], "coeff": f["coeff"]}, (9, 7, 3), 2)
+    with pytest.raises(TypeError, match="comparison"):
+        @dsl.program
+        def bad(a: dsl.Field):
+            return dsl.if_(a, a, a)
+
+
 def test_indexing_an_expression_makes_a_stage():
     @dsl.program
     def p(a: dsl.Field):
