@@ -180,3 +180,36 @@ def test_timing_calls_without_gpu(liboec):
         assert liboec.oec_program_launch_count(None) == -1   # OEC_ERR_INVALID_ARG
     finally:
         liboec.oec_program_destroy(p)
+
+
+def test_library_and_oracle_parsers_agree():
+    """The library's parser and the oracle's (written separately) accept and
+    reject the same texts: every program of the package, random stage DAGs,
+    and a set of malformed texts."""
+    good = [programs.HDIFF, programs.HDIFF_VADVC, programs.FASTWAVES]
+    good += [src for src, _, _ in programs.TESTSET.values()]
+    good += [inputs.random_dag(s) for s in range(10000, 10040)]
+    good += ["input a\nstage s = if (a > 0.0) { let t = a*a; yield t } else { let t = -a; yield t }\noutput s\n"]
+    bad = [
+        "input a\nstage b = a[1,0]\noutput b\n",
+        "input a\nstage b = c\noutput b\n",
+        "input a\nstage b = a\n",
+        "input a\nstage a = a\noutput a\n",
+        "input a\nstage b = { let t = a; return t, t }\noutput b\n",
+        "input a\nstage b = select(a, a, a)\noutput b\n",
+        "input a\nstage b = if (a > 0.0) { yield a }\noutput b\n",
+        "input a\nstage b = if (a > 0.0) { let t = a; yield t } else { yield t }\noutput b\n",
+        "input a\nstage let = a\noutput let\n",
+        "input a\nstage b = a\noutput a\n",
+        "input a\nparam p\nstage b = p[1,0,0]\noutput b\n",
+        "input a\nstage b = { let t = a; let t = a; return t }\noutput b\n",
+    ]
+    for src in good:
+        OP.parse(src)
+        _prog(src)
+    for src in bad:
+        with pytest.raises(OP.ParseError):
+            OP.parse(src)
+        with pytest.raises(L.OecError) as e:
+            _prog(src)
+        assert e.value.name == "PARSE", src
