@@ -75,6 +75,30 @@ def test_adam_step_matches_oracle():
     assert np.max(np.abs(moved - want)) <= 1e-5
 
 
+def test_three_adam_steps_match_oracle():
+    """Three steps with beta1 = 0.5, beta2 = 0.75: from the second step on the
+    update depends on both betas and on the bias corrections, which the first
+    step alone does not show. The oracle takes its own three steps (its
+    gradient at its own parameters each time); the moves agree element by
+    element."""
+    from paper_2005_13014_gb300.costmodel import CostModel
+    m, p = _model(F=7, H=5)
+    X, t = _data(n=40, F=7)
+    Xd, td = torch.from_numpy(X).cuda(), torch.from_numpy(t).cuda()
+    q = {k: v.copy() for k, v in p.items()}
+    mm = {k: np.zeros_like(v) for k, v in p.items()}
+    vv = {k: np.zeros_like(v) for k, v in p.items()}
+    for step in (1, 2, 3):
+        m.train_step(Xd, td, lr=1e-2, beta1=0.5, beta2=0.75, eps=1e-8)
+        y, cache = OM.forward(q, X.astype(np.float64))
+        g = OM.backward(q, cache, y, t.astype(np.float64))
+        OM.adam_step(q, g, mm, vv, step, lr=1e-2, beta1=0.5, beta2=0.75, eps=1e-8)
+        torch.cuda.synchronize()
+        moved = m.get_params() - CostModel.flatten(p)
+        want = CostModel.flatten(q) - CostModel.flatten(p)
+        assert np.max(np.abs(moved - want)) <= 2e-5 * step, step
+
+
 def test_training_reduces_loss_and_checkpoint_roundtrip(tmp_path):
     m, _ = _model()
     X, t = _data(n=2000)

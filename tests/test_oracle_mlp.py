@@ -1,5 +1,8 @@
 """Pins of the FP64 MLP oracle: gradients against central finite differences,
-a one-hidden-unit network computed by hand, and Adam's first step."""
+a one-hidden-unit network computed by hand, Adam's first step, and three
+Adam steps derived by hand (tests/golden/adam_three_steps.txt)."""
+
+import os
 
 import numpy as np
 
@@ -59,3 +62,21 @@ def test_adam_first_step_moves_by_lr():
         # bias-corrected first step: lr * g / (|g| + eps)
         want = 1.0 - 0.01 * g[k][0] / (abs(g[k][0]) + 1e-8)
         assert abs(p[k][0] - want) < 1e-15
+
+
+def test_adam_three_steps_match_hand_derivation():
+    rows = []
+    with open(os.path.join(os.path.dirname(__file__), "golden", "adam_three_steps.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                rows.append([float(x) for x in line.split()])
+    assert len(rows) == 3
+    p = {k: np.array([1.0]) for k in mlp.PARAM_NAMES}
+    m = {k: np.zeros(1) for k in mlp.PARAM_NAMES}
+    v = {k: np.zeros(1) for k in mlp.PARAM_NAMES}
+    for step, grad, m_want, v_want, num, den in rows:
+        g = {k: np.array([grad]) for k in mlp.PARAM_NAMES}
+        mlp.adam_step(p, g, m, v, int(step), lr=0.5, beta1=0.5, beta2=0.75, eps=0.0)
+        for k in mlp.PARAM_NAMES:
+            assert m[k][0] == m_want and v[k][0] == v_want, (step, k)
+            assert abs(p[k][0] - num / den) <= 1e-15, (step, k, p[k][0], num / den)

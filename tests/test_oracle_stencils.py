@@ -242,3 +242,29 @@ def test_fastwaves_staged_equals_inlined():
             for i in range(n[0]):
                 pu, pv = S.fastwaves_point(f, i, j, k, 0.5, 0.0625)
                 assert pu == uo[k, j, i] and pv == vo[k, j, i]
+
+
+def test_fastwaves_every_term_matches_hand_derivation():
+    """tests/golden/fastwaves_point.txt: fields chosen so that S1's k-1
+    weighting, S2's difference, the terrain term of S3/S4, S5's fourth-order
+    coefficients and S6's density/fx term are all non-zero at one point, with
+    the stage values and both outputs derived by hand (dyadic, so exact)."""
+    h, n = 3, (1, 1, 1)
+    shape = inputs.storage_shape(*n, h)
+    k, j, i = np.meshgrid(*(np.arange(s_) - h for s_ in shape), indexing="ij")
+    i, j, k = i.astype(np.float64), j.astype(np.float64), k.astype(np.float64)
+    f = {"pp": (1 + i + 2 * j) * k ** 2 + 2 * k + 3 * i - 2 * j,
+         "wgtfac": 0.75 - 0.25 * k,
+         "hhl": 100 - 10 * k + (2 + 4 * k) * i + (1 + 12 * k) * j,
+         "u_in": i ** 3 + 5 * j ** 2 + 1, "v_in": j ** 2 - 3 * i ** 2 + 2,
+         "utens": 0.5 + 0.125 * i, "vtens": -0.25 + 0.125 * j,
+         "rho": 1.5 - i + j, "fx": 0.75 + 0.25 * i}
+    g = _fw_grids(f, h)
+    st = S.fastwaves_stages(g, (0, 0, 0), n, 0.5, 0.0625)
+    rows = _read_golden("fastwaves_point.txt")
+    assert len(rows) == 16
+    for name, a, b, c, want in rows:
+        got = st[name].value(int(a), int(b), int(c))
+        assert got == float(want), (name, a, b, c, got, want)
+    pu, pv = S.fastwaves_point(g, 0, 0, 0, 0.5, 0.0625)
+    assert pu == st["u_out"].value(0, 0, 0) and pv == st["v_out"].value(0, 0, 0)
