@@ -40,8 +40,9 @@ DTR = 2.0
 # and Thomas 35
 FLOPS_PER_POINT = 71
 FLOPS_HDIFF, FLOPS_COLUMN = 36, 35
-TIMING_EVERY = 8          # steps between per-kernel timing samples
+ATTRIB_STEPS = 200        # steps of the per-kernel attribution pass (every step timed per kernel)
 METRIC = "grid-points/s"
+SMS, ISSUE_PER_SM = 152, 4   # GB300: SMs, warp instructions issued per SM and clock (4 sub-partitions)
 
 
 def _peaks():
@@ -129,19 +130,38 @@ def _job_rate(units_per_rank, ms, ws, dist=None):
     return units_per_rank * ws / (_max_over_ranks(ms, dist) * 1e-3)
 
 
-# the kernels one apply launches, per schedule form, with the source files
-# each is built from, the algorithmic FP64 operations per grid point it
-# performs, and the ncu summary that holds its DRAM traffic per launch
+# the kernels one apply launches, per schedule form: the source files each
+# is built from, the algorithmic FP64 operations per grid point it performs,
+# the program fields it moves between HBM and the chip (its share of the
+# algorithmic bytes), and the ncu summary that holds its DRAM traffic and
+# warp instructions per launch
 def _kernels_of(sched):
     common = ["kcommon.cuh", "arith.cuh", "df64.cuh"]
     if sched["fusion"] == 0:
         return [{"name": "hv_fused_kernel", "src": ["k_vadvc.cu"] + common, "flops": FLOPS_PER_POINT,
-                 "profile": None}]
-    hd = "hdiff_fixed_kernel" if sched.get("arith", 0) == 2 else "hdiff_smem_kernel"
-    return [{"name": hd, "src": ["k_hdiff.cu"] + common, "flops": FLOPS_HDIFF,
-             "profile": f"{hd}_f64_2fields_128x128x80.md"},
+                 "fields": ("u", "v", "w", "coeff", "u_out", "v_out"), "profile": None}]
+    arith = sched.get("arith", 0)
+    hd = "hdiff_fixed_kernel" if arith == 2 else "hdiff_smem_kernel"
+    return [{"name": hd, "src": ["k_hdiff.cu"] + common, "flops": FLOPS_HDIFF, "fields": ("u", "v", "coeff"),
+             "profile": f"{hd}_f64_2fields_128x128x80.md" if arith == 2 else None},
             {"name": "hv_thomas_kernel", "src": ["k_vadvc.cu"] + common, "flops": FLOPS_COLUMN,
-             "profile": "hv_thomas_kernel_f64_128x128x80.md"}]
+             "fields": ("w", "u_out", "v_out"),
+             "profile": "hv_thomas_kernel_f64_128x128x80.md" if arith == 2 else None}]
+
+
+ARITH_NAMES = {0: "native binary64 throughout",
+               1: "double-float (float pairs, ~48-bit significand) throughout, binary64 storage",
+               2: "hdiff in exact int64 fixed point (one binary64 FMA per output), tridiagonal build and Thomas "
+                  "sweep in double-float (float pairs, ~48-bit significand), binary64 storage"}
+
+
+def _field_bytes(name, n=N, es=8):
+    """Algorithmic bytes of one field of hdiff+vadvc (SURVEY-style access
+    boxes: u, v with the i/j halo of 2, w with the i+1 column, the rest the
+    domain)."""
+    ni, nj, nk = n
+    pts = {"u": (ni + 4) * (nj + 4) * nk, "v": (ni + 4) * (nj + 4) * nk, "w": (ni + 1) * nj * nk}
+    return pts.get(name, ni * nj * nk) * es
 
 
 def _kernel_source_hash(files):
@@ -152,9 +172,10 @@ def _kernel_source_hash(files):
     return h.hexdigest()[:16]
 
 
-def _ncu_traffic(kernel):
-    """DRAM bytes per launch of a kernel from its committed ncu summary, if
-    the summary was taken on the current source of that kernel."""
+def _ncu_figure(kernel, key):
+    """A per-launch figure (dram_bytes_per_launch, warp_instructions_per_launch)
+    of a kernel from its committed ncu summary, if the summary was taken on
+    the current source of that kernel."""
     if not kernel["profile"]:
         return None
     try:
@@ -162,10 +183,20 @@ def _ncu_traffic(kernel):
     except OSError:
         return None
     m = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
-    t = re.search(r"dram_bytes_per_launch:\s*([0-9]+)", text)
+    t = re.search(key + r":\s*([0-9]+)", text)
     if not m or not t or m.group(1) != _kernel_source_hash(kernel["src"]):
         return None
     return int(t.group(1))
+
+
+def _ncu_traffic(kernel):
+    return _ncu_figure(kernel, "dram_bytes_per_launch")
+
+
+def _quartiles(x):
+    x = np.asarray(x, np.float64)
+    return {"median": float(np.median(x)), "q1": float(np.percentile(x, 25)), "q3": float(np.percentile(x, 75)),
+            "mean": float(np.mean(x)), "n": int(x.size)}
 
 
 def cpu_oracle_rate(seconds=10.0, sub=None):
@@ -366,28 +397,55 @@ def run_gpu(args):
         with torch.cuda.stream(stream):
             t_start.record(stream)
             for s in range(args.steps):
-                # every TIMING_EVERY-th step the library records an event
-                # before and after each of its kernels (per-kernel durations)
-                prog.set_timing(s % TIMING_EVERY == 0)
                 step(s)
             t_end.record(stream)
         torch.cuda.synchronize()
-        prog.set_timing(False)
         if dist:
             dist.barrier()
         total_ms = t_start.elapsed_time(t_end)
-        time.sleep(0.1)
         clocks = clk.summary(mark)
+        # attribution pass (not part of the timed region above): the same
+        # steps again with an event recorded before and after each of the
+        # library's kernels on the stream they run on, every step
+        n_attr = max(1, min(args.steps, ATTRIB_STEPS))
+        prog.set_timing(True)
+        with torch.cuda.stream(stream):
+            for s in range(n_attr):
+                step(s)
+        torch.cuda.synchronize()
+        prog.set_timing(False)
+        time.sleep(0.1)
     launches = prog.launch_count()
-    per_kernel = prog.kernel_times()          # [sampled steps, kernels of one apply], ms
+    per_kernel = prog.kernel_times()          # [attributed steps, kernels of one apply], ms
     kernels = _kernels_of(sched)
-    assert per_kernel.shape == ((args.steps + TIMING_EVERY - 1) // TIMING_EVERY, len(kernels)) \
-        and launches == len(kernels), (per_kernel.shape, launches, kernels)
+    assert per_kernel.shape == (n_attr, len(kernels)) and launches == len(kernels), \
+        (per_kernel.shape, launches, kernels)
     step_ms = per_kernel.sum(axis=1)
-    k_avg = per_kernel.mean(axis=0)
-    dom = int(np.argmax(k_avg))
+    k_med = np.median(per_kernel, axis=0)
+    dom = int(np.argmax(k_med))
     total_ms = _max_over_ranks(total_ms, dist)
     value = _job_rate(points * args.steps, total_ms, ws)
+
+    # the same staged schedule in native binary64 arithmetic (arith 0), timed
+    # the same way on the same resident sets: the like-for-like FP64 figure
+    native = None
+    if sched["fusion"] == 1 and sched.get("arith", 0) != 0:
+        prog.set_schedule(**dict(sched, arith=0))
+        n_nat = max(3, min(args.steps, ATTRIB_STEPS))
+        with torch.cuda.stream(stream):
+            for w in range(3):
+                step(w)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for s in range(n_nat):
+                step(s)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        nat_ms = _max_over_ranks(e0.elapsed_time(e1) / n_nat, dist)
+        native = {"value": _job_rate(points, nat_ms, ws), "unit": "grid-points/s", "ms_per_step": nat_ms,
+                  "steps": n_nat, "schedule": prog.schedule, "arith": ARITH_NAMES[0]}
+        prog.set_schedule(**sched)
 
     # end to end through the host-memory ABI call (oec_program_apply_host):
     # every step copies its inputs' storage from page-locked host memory to
@@ -423,37 +481,59 @@ def run_gpu(args):
     torch.cuda.synchronize()
     e2e_value = _job_rate(points, e0.elapsed_time(e1) / e2e_steps, ws, dist)
 
-    alg_bytes = prog.algorithmic_bytes(lb, ub)
+    # HBM roofline (algorithmic bytes: every input's access box and every
+    # output's domain, once; temporaries excluded), against the measured copy
+    # bandwidth. The dominant kernel's own share of those bytes over its
+    # median duration, and the whole program's over the step time.
     peaks = _peaks()
-    fp64_peak = 1250.0        # GFLOP/s, GB300 nominal dense FP64
-    step_avg_ms = total_ms / args.steps
+    hbm_peak = peaks.get("hbm_gbs")
+    peak_source = "MEASURED_PEAKS.json hbm_gbs (measured)"
+    if hbm_peak is None:
+        hbm_peak, peak_source = 6800.0, "fallback 6.8 TB/s (profiling recipe)"
+    step_ms_avg = total_ms / args.steps
     kd = kernels[dom]
-    achieved_gflops = kd["flops"] * points / (float(k_avg[dom]) * 1e-3) / 1e9
-    step_gflops = FLOPS_PER_POINT * points / (step_avg_ms * 1e-3) / 1e9
-    achieved_gbs = alg_bytes / (step_avg_ms * 1e-3) / 1e9
-    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    kd_bytes = sum(_field_bytes(f) for f in kd["fields"])
+    step_bytes = sum(_field_bytes(f) for f in ("u", "v", "w", "coeff", "u_out", "v_out"))
+    kd_ms = float(k_med[dom])
+    achieved = kd_bytes / (kd_ms * 1e-3) / 1e9
+    step_gbs = step_bytes / (step_ms_avg * 1e-3) / 1e9
+    # issue rate: warp instructions per launch (ncu summary of the current
+    # source) over what the SMs can issue in the kernel's time at the sampled
+    # SM clock
+    sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz") or 2070.0
+    issue = []
+    for x, k in enumerate(kernels):
+        inst = _ncu_figure(k, "warp_instructions_per_launch")
+        if inst is not None:
+            cap = SMS * ISSUE_PER_SM * sm_mhz * 1e6 * float(k_med[x]) * 1e-3
+            issue.append({"kernel": k["name"], "warp_instructions": inst, "frac_of_issue_peak": inst / cap,
+                          "sm_mhz": sm_mhz})
     line = {
         "metric": METRIC, "value": value, "unit": "grid-points/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "hdiff+vadvc FP64 interior 128x128x80 halo 3 (u,v,w ~ U[-1,1], coeff ~ U[0,0.1], dtr=2)",
                    "program": WORKLOAD, "schedule": sched,
+                   "arith": ARITH_NAMES.get(sched.get("arith", 0)),
                    "l2": f"rotating {n_sets} resident input/output sets ({n_sets * set_bytes / 1e6:.0f} MB > L2 {l2 / 1e6:.0f} MB)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU",
                    "autotune_ms": tuning},
-        "roofline": {"bound": "alu", "achieved": achieved_gflops, "peak": fp64_peak, "unit": "GFLOP/s (FP64)",
-                     "frac": achieved_gflops / fp64_peak, "traffic": _ncu_traffic(kd),
-                     "kernel": kd["name"], "kernel_ms": float(k_avg[dom]), "flops_per_point": kd["flops"],
-                     "peak_source": "GB300 nominal dense FP64 1.25 TFLOP/s (profiling recipe table)"},
-        "roofline_step": {"achieved": step_gflops, "peak": fp64_peak, "unit": "GFLOP/s (FP64)",
-                          "frac": step_gflops / fp64_peak, "flops_per_point": FLOPS_PER_POINT},
-        "roofline_hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": achieved_gbs / hbm_peak,
-                         "algorithmic_bytes_per_step": alg_bytes, "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"},
-        "kernels": [{"name": k["name"], "ms_mean": float(k_avg[x]), "share": float(k_avg[x] / k_avg.sum()),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                     "traffic": _ncu_traffic(kd), "kernel": kd["name"], "kernel_ms_median": kd_ms,
+                     "kernel_algorithmic_bytes": kd_bytes, "kernel_fields": list(kd["fields"]),
+                     "peak_source": peak_source,
+                     "step": {"achieved": step_gbs, "frac": step_gbs / hbm_peak, "algorithmic_bytes": step_bytes,
+                              "ms": step_ms_avg}},
+        "issue_rate": issue,
+        "fp64_equivalent_rate": {"unit": "G FP64-equivalent operations/s", "ops_per_point": FLOPS_PER_POINT,
+                                 "step": FLOPS_PER_POINT * points / (step_ms_avg * 1e-3) / 1e9,
+                                 "note": "algorithmic operations counted as if in binary64; the arithmetic runs on the "
+                                         "integer and FP32 pipes (config.arith), so no FP64 peak applies"},
+        "native_f64": native,
+        "kernels": [{"name": k["name"], **_quartiles(per_kernel[:, x]), "share": float(k_med[x] / k_med.sum()),
                      "traffic": _ncu_traffic(k)} for x, k in enumerate(kernels)],
-        "kernel_sum_ms": {"sampled_steps": int(len(step_ms)), "mean": float(np.mean(step_ms)),
-                          "median": float(np.median(step_ms)), "q1": float(np.percentile(step_ms, 25)),
-                          "q3": float(np.percentile(step_ms, 75))},
+        "kernel_sum_ms": dict(_quartiles(step_ms), note="attribution pass after the timed region: events around "
+                              "every kernel of every step"),
         "e2e": {"value": e2e_value, "unit": "grid-points/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps * launches,
         "clocks": clocks,
