@@ -950,9 +950,7 @@ def run_costmodel(args):
         R["model_top2_plus_fixed"].append(min(t[x] for x in order[:2] + [fixed]) / best - 1)
         R["paper_default_tuned_unroll"].append(min(t[x] for x in dflt) / best - 1)
         R["paper_default_unroll1"].append(min(t[x] for x in dflt_u1) / best - 1)
-        est = np.maximum(Fte[d][:, 36] / hbm, Fte[d][:, 30] / f_ops)
-        u1 = [x for x in d64x4 if cands[x]["unroll"] == 1 and np.isfinite(t[x])]
-        g = min(u1, key=lambda x: est[x])
+        g = CM.greedy_fusion(Fte[d], cands, hbm, f_ops, tile=(64, 4), unroll=1, usable=np.isfinite(t))
         R["greedy_roofline_fusion_unroll1"].append(t[g] / best - 1)
         R["greedy_roofline_fusion_tuned_unroll"].append(
             min(t[x] for x in d64x4 if cands[x]["fusion"] == cands[g]["fusion"]) / best - 1)

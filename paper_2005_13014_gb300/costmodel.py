@@ -30,6 +30,19 @@ from .api import Program, device_field
 
 N_FEATURES = 42
 
+# the features oec_program_features writes, in order (per point: of the
+# generated code for the schedule; l2_*: log2)
+FEATURE_NAMES = (
+    "stages", "inputs", "outputs", "accesses", "arith_ops", "selects", "min_max", "divisions",
+    "max_offset_i", "max_offset_j", "max_offset_k", "depth", "halo_i", "halo_j", "halo_k", "input_amplification",
+    "l2_ni", "l2_nj", "l2_nk", "l2_points", "element_bytes", "fuse_inline", "fuse_none", "fuse_partial",
+    "l2_unroll", "l2_tile_i", "l2_tile_j", "l2_tile_threads", "kernels", "loads_per_point", "ops_per_point",
+    "stores_per_point", "temp_bytes_per_point", "l2_max_blocks", "tile_efficiency_i", "tile_efficiency_j",
+    "bytes_per_point", "inline_ops_per_point", "ops_over_unfused_ops", "materialised_stages", "waves",
+    "l2_total_ops")
+F = {name: x for x, name in enumerate(FEATURE_NAMES)}
+assert len(FEATURE_NAMES) == N_FEATURES
+
 
 def _torch():
     import torch
@@ -227,3 +240,26 @@ def regret_stats(r):
     r = np.asarray(r)
     return {"mean": float(np.mean(r)), "median": float(np.median(r)), "p90": float(np.percentile(r, 90)),
             "max": float(np.max(r)), "frac_within_5pct": float(np.mean(r <= 0.05))}
+
+
+def roofline_seconds_per_point(features, hbm_bytes_per_s, ops_per_s):
+    """Roofline estimate per grid point of each candidate (rows of a feature
+    matrix): max(bytes per point / HBM bandwidth, operations per point /
+    operation rate)."""
+    f = np.asarray(features, np.float64)
+    return np.maximum(f[:, F["bytes_per_point"]] / hbm_bytes_per_s, f[:, F["ops_per_point"]] / ops_per_s)
+
+
+def greedy_fusion(features, candidates, hbm_bytes_per_s, ops_per_s, tile=(64, 4), unroll=1, usable=None):
+    """Non-learned baseline between inlining everything and the learned model
+    (the paper inlines every stage, §V-A): among the candidates at the given
+    tile and unroll, the fusion choice (inline, none, partial) whose roofline
+    estimate is lowest. Returns that candidate's index (ties: the first in
+    candidate order). usable (optional boolean mask): candidates that can run."""
+    est = roofline_seconds_per_point(features, hbm_bytes_per_s, ops_per_s)
+    pool = [x for x, c in enumerate(candidates)
+            if c["tile_i"] == tile[0] and c["tile_j"] == tile[1] and c["unroll"] == unroll
+            and (usable is None or usable[x])]
+    if not pool:
+        raise ValueError("no candidate at the given tile and unroll")
+    return min(pool, key=lambda x: (est[x], x))
