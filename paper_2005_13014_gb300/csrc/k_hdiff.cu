@@ -14,6 +14,7 @@
 // Each form is templated on an arithmetic policy (arith.cuh): FP32, native
 // FP64, or FP64 storage with double-float arithmetic on the FP32 pipes.
 #include "arith.cuh"
+#include "fixedpt.cuh"
 #include "kcommon.cuh"
 #include "kernels.h"
 
@@ -288,43 +289,7 @@ cudaError_t run_stream(const oec_schedule& s, const Dom& d, const typename P::S*
   return cudaGetLastError();
 }
 
-// ---- exact fixed-point FP64 hdiff (arith 2) --------------------------------
-// hdiff is linear in `in` apart from the limiter's sign tests and the final
-// product with coeff, so the Laplacian, fluxes and flux divergence of binary64
-// inputs are evaluated exactly in 64-bit integers. Per tile and level, E (the
-// largest biased exponent of the window's values) fixes the scale: value x =
-// m * 2^(e-1075) becomes X = m << (e - E + 3) (truncated toward zero when the
-// shift is negative), so |X| < 2^56 and |lap| < 2^59, |flux| < 2^60,
-// |divergence| < 2^62: no overflow. The limiter tests the sign of the flux
-// (exact) against the sign of in(i+1) - in(i) taken exactly from the raw
-// binary64 values (ordered integer keys). The output is one rounding of the
-// exact result: out = fma(-coeff, div * 2^(E - 1078), in). Only values more
-// than 2^53 times smaller than the tile's largest lose bits (absolute error
-// below 2^(E-1078) per value). Tiles whose values are all below 2^-923 are
-// treated as zero-diffusion (out = in). Inputs must be finite.
-__device__ __forceinline__ long long fx_of(double x, unsigned E) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const int e = (int)((b >> 52) & 0x7FFu);
-  const long long m = (long long)((b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull);
-  const int sh = e - (int)E + 3;
-  long long X = sh >= 0 ? (m << sh) : (sh > -53 ? (m >> -sh) : 0ll);
-  X = e == 0 ? 0ll : X;
-  return (long long)(b >> 63) ? -X : X;
-}
-// total order of binary64 values as signed integers (-0 mapped to +0)
-__device__ __forceinline__ long long fx_key(double x) {
-  long long b = __double_as_longlong(x);
-  b = b == (long long)0x8000000000000000ull ? 0ll : b;
-  return b < 0 ? (b ^ 0x7FFFFFFFFFFFFFFFll) : b;
-}
-// flux with the limiter: zero where the flux and in_hi - in_lo (given by
-// their ordered keys) have the same strict sign
-__device__ __forceinline__ long long fx_flux(long long lap_hi, long long lap_lo, long long key_hi, long long key_lo) {
-  const long long f = lap_hi - lap_lo;
-  const bool lim = (f > 0 && key_hi > key_lo) || (f < 0 && key_hi < key_lo);
-  return lim ? 0ll : f;
-}
-
+// ---- exact fixed-point FP64 hdiff (arith 2; arithmetic in fixedpt.cuh) -------
 // One CTA: a TI x TJ tile of one field over a chunk of levels, TI x TJ / U
 // threads. Per level: (1) the (TI+4) x (TJ+4) window of raw values is loaded
 // and its largest exponent E reduced; (2) the window is converted to fixed
@@ -440,9 +405,7 @@ hdiff_fixed_kernel(const double* __restrict__ in0, const double* __restrict__ in
           const long long fya = fx_flux(L[(u + 1) * LI], lc, K[(u + 1) * WI], kc);
           const long long div = (fxp - fxm) + (fya - fyb);
           fyb = fya;
-          double dv = __ll2double_rn(div);
-          // dv * 2^(E - 1078) by exponent arithmetic (dv is 0 or an integer >= 1 in magnitude)
-          dv = div == 0 ? 0.0 : __longlong_as_double(__double_as_longlong(dv) + ((long long)((int)E - 1078) << 52));
+          const double dv = fx_scaled(div, E);
           const double r =
               __fma_rn(-ldg(coeff + ((Off)k * (Off)sk + oin + (Off)u * (Off)sj)), dv, s_raw[bf][ow + u * WI]);
           out[(Off)k * (Off)osk + oout + (Off)u * (Off)osj] = cvt<OutT>(r);
