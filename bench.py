@@ -141,12 +141,17 @@ def _kernels_of(sched):
         return [{"name": "hv_fused_kernel", "src": ["k_vadvc.cu"] + common, "flops": FLOPS_PER_POINT,
                  "fields": ("u", "v", "w", "coeff", "u_out", "v_out"), "profile": None}]
     arith = sched.get("arith", 0)
+    if sched.get("slabs", 0) > 1:   # the slab pipeline: producer and sweep of each slab on two streams, timed as one
+        return [{"name": f"slab pipeline ({sched['slabs']} slabs: hdiff producer, then column sweep, per slab)",
+                 "src": ["k_vadvc.cu", "k_hdiff.cu", "fixedpt.cuh"] + common, "flops": FLOPS_PER_POINT,
+                 "fields": ("u", "v", "w", "coeff", "u_out", "v_out"), "profile": None}]
+    sweep = "hv_thomas_split_kernel" if sched.get("sweep", 0) == 1 else "hv_thomas_kernel"
     hd = "hdiff_fixed_kernel" if arith == 2 else "hdiff_smem_kernel"
-    return [{"name": hd, "src": ["k_hdiff.cu"] + common, "flops": FLOPS_HDIFF, "fields": ("u", "v", "coeff"),
+    return [{"name": hd, "src": ["k_hdiff.cu", "fixedpt.cuh"] + common, "flops": FLOPS_HDIFF, "fields": ("u", "v", "coeff"),
              "profile": f"{hd}_f64_2fields_128x128x80.md" if arith == 2 else None},
-            {"name": "hv_thomas_kernel", "src": ["k_vadvc.cu"] + common, "flops": FLOPS_COLUMN,
+            {"name": sweep, "src": ["k_vadvc.cu"] + common, "flops": FLOPS_COLUMN,
              "fields": ("w", "u_out", "v_out"),
-             "profile": "hv_thomas_kernel_f64_128x128x80.md" if arith == 2 else None}]
+             "profile": f"{sweep}_f64_128x128x80.md" if arith == 2 else None}]
 
 
 ARITH_NAMES = {0: "native binary64 throughout",
@@ -418,8 +423,7 @@ def run_gpu(args):
     launches = prog.launch_count()
     per_kernel = prog.kernel_times()          # [attributed steps, kernels of one apply], ms
     kernels = _kernels_of(sched)
-    assert per_kernel.shape == (n_attr, len(kernels)) and launches == len(kernels), \
-        (per_kernel.shape, launches, kernels)
+    assert per_kernel.shape == (n_attr, len(kernels)), (per_kernel.shape, launches, kernels)
     step_ms = per_kernel.sum(axis=1)
     k_med = np.median(per_kernel, axis=0)
     dom = int(np.argmax(k_med))
@@ -588,7 +592,8 @@ def _l2_bytes():
     return getattr(props, "L2_cache_size", 128 << 20)
 
 
-def _run_program(prog_name, dtype, arith, steps, schedule=None, cache=None, size=None, index_bits=0, generic=False):
+def _run_program(prog_name, dtype, arith, steps, schedule=None, cache=None, size=None, index_bits=0, generic=False,
+                 halo=3):
     """One stencil program at 256x256x80 (or `size`), halo 3: autotuned (or the
     given schedule) and timed over rotating resident copies of its fields
     (> 3 x L2, so every apply reads HBM); error per output against the
@@ -597,28 +602,28 @@ def _run_program(prog_name, dtype, arith, steps, schedule=None, cache=None, size
     import torch
     from paper_2005_13014_gb300 import inputs, programs
     from paper_2005_13014_gb300.api import Program, device_field
-    n, h = tuple(size) if size else (N if prog_name == "hdiff_vadvc" else MIXED_N), 3
+    n, h = tuple(size) if size else (N if prog_name == "hdiff_vadvc" else MIXED_N), halo
     pts = n[0] * n[1] * n[2]
     stream = torch.cuda.current_stream()
     cache = {} if cache is None else cache
     rnd = (lambda a: a.astype(np.float32).astype(np.float64)) if dtype == "f32" else (lambda a: a)
     if prog_name == "hdiff_vadvc":
-        if "hv_fields" not in cache:
-            cache["hv_fields"] = inputs.hdiff_vadvc_fields(*n, h)
-        f = {k: rnd(v) for k, v in cache["hv_fields"].items()}
+        if ("hv_fields", n, h) not in cache:
+            cache[("hv_fields", n, h)] = inputs.hdiff_vadvc_fields(*n, h)
+        f = {k: rnd(v) for k, v in cache[("hv_fields", n, h)].items()}
         prog = Program(programs.HDIFF_VADVC, dtype, generic=generic)
         names, n_out, params = ["u", "v", "w", "coeff"], 2, [DTR]
     elif prog_name == "hdiff":
-        if "hdiff_fields" not in cache:
-            cache["hdiff_fields"] = inputs.hdiff_fields(*n, h)
-        f0 = cache["hdiff_fields"]
+        if ("hdiff_fields", n, h) not in cache:
+            cache[("hdiff_fields", n, h)] = inputs.hdiff_fields(*n, h)
+        f0 = cache[("hdiff_fields", n, h)]
         f = {k: rnd(v) for k, v in f0.items()}
         prog = Program(programs.HDIFF, dtype, generic=generic)
         names, n_out, params = ["in", "coeff"], 1, []
     else:
-        if "fw_fields" not in cache:
-            cache["fw_fields"] = inputs.fastwaves_fields(*n, h)
-        f0 = cache["fw_fields"]
+        if ("fw_fields", n, h) not in cache:
+            cache[("fw_fields", n, h)] = inputs.fastwaves_fields(*n, h)
+        f0 = cache[("fw_fields", n, h)]
         f = {k: rnd(v) for k, v in f0.items()}
         prog = Program(programs.FASTWAVES, dtype, generic=generic)
         names, n_out, params = list(inputs.FASTWAVES_NAMES), 2, [0.5, 0.0625]
@@ -657,7 +662,7 @@ def _run_program(prog_name, dtype, arith, steps, schedule=None, cache=None, size
     # error against the library's unfused native-FP64 kernels on the same
     # (for FP32: FP32-rounded) inputs; the parity tests hold those to 1e-13 of
     # the CPU oracle, which itself runs only in the CPU-baseline legs
-    key = (prog_name, dtype)
+    key = (prog_name, dtype, n, h)
     if key not in cache:
         text = {"hdiff": programs.HDIFF, "hdiff_vadvc": programs.HDIFF_VADVC}.get(prog_name, programs.FASTWAVES)
         rp = Program(text, "f64")
@@ -751,6 +756,54 @@ def run_index_width(args):
                     "ratio_best_64_over_auto": b["ms"] / a["ms"], "ratio_same_schedule": c["ms"] / a["ms"]})
     print(json.dumps({"workload": "offset width: automatic (32-bit where it fits) vs 64-bit, halo 3",
                       "l2": "inputs rotated over > 3 x L2", "timing": "CUDA-graph replay", "results": res}))
+    return 0
+
+
+def run_levels(args):
+    """The paper's optimisation levels (§VII-C: original, inlined, inlined and
+    unrolled by 2 and 4), FP32 and FP64, timed like the other single-program
+    workloads (graph replay, inputs rotated past L2). hdiff and fastwaves run
+    the generated kernels (the compiler-like path: one kernel per stage, or
+    everything inlined with the k-loop unrolled) at the 64x4 tile, next to the
+    tuned hand-written kernels; hdiff+vadvc runs its hand-written staged
+    (hdiff kernel, then the column kernel) and inlined (one kernel) forms."""
+    import __graft_entry__
+    __graft_entry__.build()
+    cache = {}
+    levels = [("original (one kernel per stage)", 1, 1), ("inlined", 0, 1), ("inlined, unroll 2", 0, 2),
+              ("inlined, unroll 4", 0, 4)]
+    rows = []
+
+    def entry(program, size, halo, dtype, arith, level, r):
+        rows.append({"program": program, "size": "x".join(map(str, size)), "halo": halo, "dtype": dtype,
+                     "arith": arith, "level": level, "ms": r["ms"], "gpoints_per_s": r["gpoints_per_s"],
+                     "algorithmic_GBps": r["algorithmic_GBps"], "frac_of_measured_hbm": r["frac_of_measured_hbm"],
+                     "max_rel_err_per_output": r["max_rel_err_per_output"], "schedule": r["schedule"],
+                     "launches_per_apply": r["launches_per_apply"]})
+
+    for prog_name, size, halo in (("hdiff", (64, 64, 60), 2), ("hdiff", (256, 256, 60), 2),
+                                  ("fastwaves", (256, 256, 60), 3)):
+        for dtype in ("f32", "f64"):
+            for level, fusion, unroll in levels:
+                sched = dict(fusion=fusion, staging=0, tile_i=64, tile_j=4, unroll=unroll, k_chunk=0, arith=0)
+                r = _run_program(prog_name, dtype, 0, args.steps, schedule=sched, cache=cache, size=size,
+                                 generic=True, halo=halo)
+                entry(prog_name + " (generated kernels)", size, halo, dtype, 0, level, r)
+            for arith in ((0,) if dtype == "f32" else (0, 1, 2) if prog_name == "hdiff" else (0, 1)):
+                r = _run_program(prog_name, dtype, arith, args.steps, cache=cache, size=size, halo=halo)
+                entry(prog_name + " (hand-written kernels, tuned)", size, halo, dtype, arith, "best", r)
+    size = N
+    for dtype, ariths in (("f32", (0, 1)), ("f64", (0, 1, 2))):
+        for arith in ariths:
+            r = _run_program("hdiff_vadvc", dtype, arith, args.steps, cache=cache, size=size)
+            entry("hdiff_vadvc", size, 3, dtype, arith, "best (tuned)", r)
+            if arith != 2:
+                for tile in ((16, 4), (32, 4), (8, 8)):
+                    r = _run_program("hdiff_vadvc", dtype, arith, args.steps, cache=cache, size=size,
+                                     schedule=dict(fusion=0, staging=1, tile_i=tile[0], tile_j=tile[1], arith=arith))
+                    entry("hdiff_vadvc", size, 3, dtype, arith, f"inlined (one kernel, {tile[0]}x{tile[1]})", r)
+    print(json.dumps({"workload": "optimisation levels (paper §VII-C)", "l2": "inputs rotated over > 3 x L2",
+                      "timing": "CUDA-graph replay", "results": rows}))
     return 0
 
 
@@ -898,8 +951,8 @@ def run_costmodel(args):
     __graft_entry__.build()
     from paper_2005_13014_gb300 import inputs
     from paper_2005_13014_gb300 import costmodel as CM
-    shape = (256, 256, 80)
-    pts = shape[0] * shape[1] * shape[2]
+    varied = args.cm_shapes == "varied"
+    shape = inputs.dag_shape if varied else (256, 256, 80)
     train_seeds = list(range(20000, 20000 + args.cm_train))
     test_seeds = list(range(10000, 10000 + args.cm_test))
     log = {}
@@ -960,7 +1013,9 @@ def run_costmodel(args):
              "paper_default_tuned_unroll": len(dflt), "paper_default_unroll1": 0,
              "greedy_roofline_fusion_unroll1": 0, "greedy_roofline_fusion_tuned_unroll": 3, "best_fixed_from_training": 0,
              "random": 0, "exhaustive": len(cands)}
-    out = {"workload": "cost model: random DAGs 256x256x80 FP32", "train_dags": len(train_seeds),
+    out = {"workload": "cost model: random DAGs FP32, " + ("domains drawn per program from {64,128,256,512}^2 x "
+                                                            "{60,80,137}" if varied else "256x256x80"),
+           "train_dags": len(train_seeds),
            "train_timings": int(X.shape[0]), "test_dags": len(test_seeds), "candidates": len(cands),
            "target": "log(t / t_best) per program", "epochs": args.cm_epochs,
            "first_train_loss": losses[0], "final_train_loss": losses[-1], "train_seconds": t_train,
@@ -988,12 +1043,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="hdiff_vadvc",
                     choices=["hdiff_vadvc", "mixed", "ensemble", "costmodel", "hdiff", "fastwaves", "testset",
-                             "index_width"],
+                             "index_width", "levels"],
                     help="hdiff_vadvc: the headline line; the others print their own report")
     ap.add_argument("--cm-train", type=int, default=180)
     ap.add_argument("--cm-test", type=int, default=200)
     ap.add_argument("--cm-epochs", type=int, default=300)
     ap.add_argument("--cm-save", default=None)
+    ap.add_argument("--cm-shapes", default="fixed", choices=["fixed", "varied"],
+                    help="--workload costmodel: every program on 256x256x80, or a domain drawn per program")
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"], help="--workload hdiff|fastwaves")
     ap.add_argument("--arith", type=int, default=0, help="--workload hdiff|fastwaves: autotune within this arith")
     ap.add_argument("--size", default=None, help="--workload hdiff|fastwaves (default 256,256,80), or hdiff_vadvc "
@@ -1013,6 +1070,8 @@ def main():
         return run_index_width(args)
     if args.workload == "testset":
         return run_testset(args)
+    if args.workload == "levels":
+        return run_levels(args)
     return run_gpu(args)
 
 

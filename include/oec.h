@@ -132,8 +132,24 @@ typedef struct oec_schedule {
   int32_t k_chunk;       /* levels per CTA for horizontal programs (0 = whole column)    */
   int32_t arith;         /* OEC_ARITH_*                                                   */
   int32_t index_bits;    /* OEC_INDEX_AUTO (0) or OEC_INDEX_64 (64)                       */
-  int32_t reserved[4];   /* zero                                                          */
+  int32_t sweep;         /* column sweep of the stage-by-stage hdiff+vadvc form:
+                            OEC_SWEEP_PAIR (0) or OEC_SWEEP_SPLIT (1); 0 elsewhere        */
+  int32_t slabs;         /* stage-by-stage hdiff+vadvc: the domain's j-rows in this many
+                            slabs (0 or 1: one), each slab's column sweep on a stream of
+                            its own once that slab's hdiff is done, overlapping the
+                            later slabs' hdiff (1..16); 0 elsewhere                      */
+  int32_t reserved[2];   /* zero                                                          */
 } oec_schedule;
+
+/* Column sweep of the stage-by-stage hdiff+vadvc form (the twisted Thomas
+ * factorisation: every column solved from both ends at once by two threads).
+ * OEC_SWEEP_PAIR: the two threads carry both right-hand sides (u and v);
+ * OEC_SWEEP_SPLIT: four threads per column, one field each (the matrix part of
+ * the recurrence is then computed twice, but each thread's dependent chain
+ * is shorter and twice as many warps hide its latency). Same results up to
+ * rounding (the same operations per field). */
+#define OEC_SWEEP_PAIR 0
+#define OEC_SWEEP_SPLIT 1
 
 /* Width of the element offsets that kernels form from their fields' base
  * pointers (the paper's index type, §V-B and §VII-C). OEC_INDEX_AUTO: the
@@ -417,7 +433,9 @@ OEC_API int oec_program_algorithmic_bytes(oec_program_t p, const int64_t lb[3], 
  * CUDA event on its stream before its first kernel and one after each kernel
  * (events owned by the program, created on first use on the current device);
  * an apply that fails records nothing. 0 stops recording; recorded applies
- * are kept.
+ * are kept. The staged hdiff+vadvc pipeline (schedule field slabs > 1) runs
+ * its kernels on two streams, overlapped: it records one event after all of
+ * them, so its applies report one duration (the whole pipeline).
  *
  * oec_program_kernel_times: waits for the recorded events, writes the
  * duration of kernel x of recorded apply a to ms[a * *n_kernels + x] (in
@@ -545,31 +563,36 @@ OEC_API int oec_program_autotune_model(oec_program_t p, oec_costmodel_t m, const
 /*
  * hdiff+vadvc without any device allocation. There is no counterpart in the
  * paper; this entry point exists for callers that cannot allocate device
- * memory while they run the program: code running while its stream is being
- * captured into a CUDA graph (an allocation is not captured work and can
- * break the capture), code that must stay inside a device-memory budget owned
- * by another allocator, and latency-critical loops where cudaMalloc/cudaFree
- * may synchronise the device. oec_program_apply allocates scratch on its first
- * apply at a new size; this call never does: its scratch is a fixed 64 MiB
- * array inside the library's device image (held on every GPU where the
- * library's device code is loaded, until the process exits). It runs the
- * staged form (hdiff of u and v, then the twisted column sweep; FP64: fixed
- * point producer and double-float sweep, FP32: vector-row or REGS producer and
- * double-float sweep) when its scratch fits, else the fused column sweep.
+ * memory while they run the program: code that must stay inside a
+ * device-memory budget owned by another allocator (a framework's caching
+ * allocator, a pool sized at start-up) and latency-critical loops where
+ * cudaMalloc/cudaFree may synchronise the device. oec_program_apply allocates
+ * scratch on its first apply at a new size; this call never does: its scratch
+ * is a fixed 64 MiB array inside the library's device image (held on every
+ * GPU where the library's device code is loaded, until the process exits).
+ * It runs the staged form (hdiff of u and v, then the twisted column sweep,
+ * two threads per column; FP64: fixed-point producer and double-float sweep,
+ * FP32: vector-row or REGS producer and double-float sweep) on the caller's
+ * stream when its scratch fits, else the fused column sweep.
  *   dtype   OEC_F32 or OEC_F64 (all six fields)
  *   in[4]   u, v, w, coeff; u and v must hold [lb-2, ub+2) in i and j, w must
  *           hold [lb, ub+1) in i, coeff the domain
  *   out[2]  u_out, v_out, written over [lb, ub)
  *   dtr     the scalar parameter of the vertical advection
- * Limit: staged 40 (FP64) / 32 (FP32) bytes of scratch per grid point, so
- * 1,677,721 / 2,097,152 points; fused 24 bytes, so at most 2,796,202 points
- * (OEC_ERR_UNSUPPORTED above that). The first call on each device looks up the
- * array's device address (cudaGetSymbolAddress) with that device current; make
- * that first call before any stream capture. All calls share the one array and
- * it keeps the last call's contents (nothing in it needs to start at zero:
- * every value is written before it is read): calls whose kernels overlap on
- * the GPU race and corrupt each other's results, so serialise them (one
- * stream, or events). Returns as oec_program_apply does.
+ * Limit, for a domain of ni x nj x nk points: the staged form needs
+ * 40 * ni * nj * nk bytes in FP64 (32 in FP32), each of its two parts rounded
+ * up to 256 bytes; beyond 64 MiB the fused form needs
+ * 24 * ceil16(ni) * ceil4(nj) * nk bytes (ceilN: rounded up to a multiple of
+ * N); a domain whose fused form needs more than 64 MiB is rejected with
+ * OEC_ERR_UNSUPPORTED before anything is enqueued. The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current and keeps it for the life of the process; make that first
+ * call before any stream capture. A device reset (cudaDeviceReset) after that
+ * first call is not supported: the kept address would be stale. All calls
+ * share the one array and it keeps the last call's contents (nothing in it
+ * needs to start at zero: every value is written before it is read): calls
+ * whose kernels overlap on the GPU race and corrupt each other's results, so
+ * serialise them (one stream, or events). Returns as oec_program_apply does.
  */
 OEC_API int oec_hdiff_vadvc_apply_noalloc(int32_t dtype, const oec_field_desc* in, const oec_field_desc* out,
                                           const int64_t lb[3], const int64_t ub[3], double dtr, void* cuda_stream);

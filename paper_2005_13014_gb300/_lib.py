@@ -30,7 +30,7 @@ class FieldDesc(C.Structure):
 class Schedule(C.Structure):
     _fields_ = [("fusion", C.c_int32), ("staging", C.c_int32), ("tile_i", C.c_int32), ("tile_j", C.c_int32),
                 ("unroll", C.c_int32), ("k_chunk", C.c_int32), ("arith", C.c_int32), ("index_bits", C.c_int32),
-                ("reserved", C.c_int32 * 4)]
+                ("sweep", C.c_int32), ("slabs", C.c_int32), ("reserved", C.c_int32 * 2)]
 
 
 class ProgramOptions(C.Structure):

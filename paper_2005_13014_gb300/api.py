@@ -19,7 +19,8 @@ def _torch():
     return torch
 
 
-SCHEDULE_KEYS = ("fusion", "staging", "tile_i", "tile_j", "unroll", "k_chunk", "arith", "index_bits")
+SCHEDULE_KEYS = ("fusion", "staging", "tile_i", "tile_j", "unroll", "k_chunk", "arith", "index_bits", "sweep",
+                 "slabs")
 
 
 def schedule_struct(d: dict) -> L.Schedule:
@@ -208,8 +209,9 @@ class Program:
         L.check(L.lib().oec_program_get_schedule(self._h, C.byref(s)))
         return schedule_dict(s)
 
-    def set_schedule(self, fusion=0, staging=0, tile_i=64, tile_j=4, unroll=1, k_chunk=0, arith=0, index_bits=0):
-        s = L.Schedule(fusion, staging, tile_i, tile_j, unroll, k_chunk, arith, index_bits)
+    def set_schedule(self, fusion=0, staging=0, tile_i=64, tile_j=4, unroll=1, k_chunk=0, arith=0, index_bits=0,
+                     sweep=0, slabs=0):
+        s = L.Schedule(fusion, staging, tile_i, tile_j, unroll, k_chunk, arith, index_bits, sweep, slabs)
         L.check(L.lib().oec_program_set_schedule(self._h, C.byref(s)))
 
     def input_range(self, index, lb, ub):

@@ -99,6 +99,15 @@ bool schedule_ok(int kind, const oec_schedule& s, std::string& why) {
     why = "index_bits must be OEC_INDEX_AUTO (0) or OEC_INDEX_64 (64)";
     return false;
   }
+  const bool staged_hv = kind == OEC_KIND_HDIFF_VADVC && s.fusion == OEC_FUSE_NONE;
+  if (s.sweep != OEC_SWEEP_PAIR && !(staged_hv && s.sweep == OEC_SWEEP_SPLIT)) {
+    why = "sweep: OEC_SWEEP_PAIR (0), or OEC_SWEEP_SPLIT (1) for the stage-by-stage hdiff+vadvc form";
+    return false;
+  }
+  if (s.slabs != 0 && !(staged_hv && s.slabs >= 1 && s.slabs <= 16)) {
+    why = "slabs: 0, or 1..16 for the stage-by-stage hdiff+vadvc form";
+    return false;
+  }
   switch (kind) {
     case OEC_KIND_HDIFF: return hdiff_schedule_ok(s, why);
     case OEC_KIND_HDIFF_VADVC: return hdiff_vadvc_schedule_ok(s, why);
@@ -230,11 +239,23 @@ int record_event(oec_program* p, cudaStream_t st) {
 }
 }  // namespace
 
+namespace {
+thread_local bool t_group = false;   // inside launch_group_begin/end
+}
+
 void launched(cudaStream_t st) {
   oec_program* p = t_applying;
   if (!p) return;
   ++p->last_launches;
-  if (p->timing) record_event(p, st);
+  if (p->timing && !t_group && record_event(p, st) == OEC_OK) ++p->last_timed;
+}
+
+void launch_group_begin() { t_group = true; }
+
+void launch_group_end(cudaStream_t st) {
+  t_group = false;
+  oec_program* p = t_applying;
+  if (p && p->timing && record_event(p, st) == OEC_OK) ++p->last_timed;
 }
 }  // namespace oec
 
@@ -521,6 +542,7 @@ int oec_program_apply(oec_program_t p, const oec_field_desc* in, int n_in, const
   NvtxRange range("oec_program_apply");
   if (!p || !lb || !ub || !halo) return fail(OEC_ERR_INVALID_ARG, "null argument");
   p->last_launches = 0;
+  p->last_timed = 0;
   const Program& ir = p->ir;
   if (n_in != (int)ir.inputs.size() || (n_in && !in))
     return fail(OEC_ERR_INVALID_ARG, "program has %zu inputs, got %d", ir.inputs.size(), n_in);
@@ -544,7 +566,7 @@ int oec_program_apply(oec_program_t p, const oec_field_desc* in, int n_in, const
   rc = dispatch_apply(p, in, out, lb, ub, params, st);
   t_applying = nullptr;
   if (p->timing) {
-    if (rc || p->ev_used != first + 1 + p->last_launches) {
+    if (rc || p->ev_used != first + 1 + p->last_timed) {
       p->ev_used = first;   // drop a partly recorded apply
     } else {
       p->ev_first.push_back(first);

@@ -20,7 +20,9 @@
 // copies.
 // Batched form: a persistent kernel pulls (member, tile) items of an ensemble
 // of domains from an atomic counter and runs the fused tile sweep on each.
+#include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <type_traits>
 
 #include "arith.cuh"
@@ -556,6 +558,166 @@ __global__ void __launch_bounds__(2 * NC) hv_thomas_kernel(HV<typename P::S> p, 
   cp_async_wait<0>();
 }
 
+// The same column sweep with the two fields in separate warps (schedule
+// field sweep = OEC_SWEEP_SPLIT): warp 0 of a CTA solves 16 columns for u,
+// warp 1 the same columns for v (lanes 0..15 upwards, 16..31 downwards, as
+// above). Each thread builds the matrix part of its rows (w, beta, gamma, b,
+// the g recurrence) itself, so that part is computed twice per column, but
+// every thread's sequential chain carries one right-hand side instead of two
+// and twice as many warps share the SMs: the sweep is bound by the latency of
+// its dependent chains, not by instruction throughput. Per level a thread
+// writes g and its e to its field's half of the scratch ([field][k][g, e][column]).
+template <class P, int DEPTH, bool DTR_P2, class Off>
+__global__ void __launch_bounds__(64) hv_thomas_split_kernel(HV<typename P::S> p, const typename P::C* __restrict__ ud,
+                                                             const typename P::C* __restrict__ vd, double dtr_d,
+                                                             typename P::R* __restrict__ scr) {
+  typedef typename P::S S;
+  typedef typename P::C C;
+  typedef typename P::R R;
+  constexpr int NT = 64;
+  constexpr size_t FB = size_t(DEPTH) * NT * (sizeof(C) + 2 * sizeof(S));
+  constexpr size_t BB = size_t(DEPTH) * NT * 2 * sizeof(R);
+  __shared__ __align__(16) unsigned char ring[FB > BB ? FB : BB];
+  C(*sphi)[NT] = reinterpret_cast<C(*)[NT]>(ring);
+  S(*sw0)[NT] = reinterpret_cast<S(*)[NT]>(sphi + DEPTH);
+  S(*sw1)[NT] = sw0 + DEPTH;
+  const int t = threadIdx.x, lane = t & 31, fld = t >> 5;
+  const bool down = lane >= 16;
+  const int64_t ncol = (int64_t)p.ni * p.nj;
+  const int64_t col = (int64_t)blockIdx.x * 16 + (lane & 15);
+  const bool active = col < ncol;
+  const int i = active ? int(col % p.ni) : 0, j = active ? int(col / p.ni) : 0;
+  const int nk = p.nk, mid = (nk + 1) / 2;
+  const int nsteps = active ? (down ? nk - mid : mid) : 0;
+  const C dtr = cvt<C>(dtr_d);
+  const float dtr_f = (float)dtr_d;
+  auto times_dtr = [&](C x) { return DTR_P2 ? mul_p2(x, dtr_f) : dtr * x; };
+  const int64_t cbase = (int64_t)j * p.sj + i;
+  const S* __restrict__ wcol = p.w + cbase;
+  const C* __restrict__ phi = fld ? vd : ud;
+  const Off ncol_o = (Off)ncol, col_o = (Off)col, sk_o = (Off)p.sk;
+  R* __restrict__ fscr = scr + (Off)fld * (Off)2 * (Off)nk * ncol_o;   // this field's [k][g, e][column]
+  auto lev = [&](int st) { return down ? nk - 1 - st : st; };
+  auto wlev = [&](int st) { return down ? nk - st : st; };
+  auto issue = [&](int st) {
+    if (active && st <= nsteps) {
+      const int sl = st % DEPTH, k = lev(st), kw = wlev(st);
+      if (k >= 0 && k < nk) cp_async(&sphi[sl][t], phi + ((Off)k * ncol_o + col_o));
+      if (kw < nk) {
+        cp_async(&sw0[sl][t], wcol + (Off)kw * sk_o);
+        cp_async(&sw1[sl][t], wcol + (Off)kw * sk_o + 1);
+      }
+    }
+    cp_async_commit();
+  };
+  auto wf_of = [&](int st) {
+    const int sl = st % DEPTH;
+    return wlev(st) < nk ? mul_p2(wsum<C>(sw0[sl][t], sw1[sl][t]), 0.5f) : zero_<C>();
+  };
+  const float sgn = down ? -1.0f : 1.0f;
+  R g = cvt<R>(0.0f), e = cvt<R>(0.0f);
+#pragma unroll 1
+  for (int st = 0; st < DEPTH - 1; ++st) issue(st);
+  cp_async_wait<DEPTH - 3>();   // slots 0 and 1 have landed
+  const bool ahead0 = nsteps > 0 && lev(1) >= 0 && lev(1) < nk;
+  C f1 = zero_<C>(), wfa = zero_<C>(), pf = zero_<C>();
+  C beta = zero_<C>(), gamma = zero_<C>(), b = dtr, rf = zero_<C>();
+  const float sgn8 = 0.125f * sgn;
+  if (nsteps > 0) {
+    const C f0 = sphi[0][t];
+    if (ahead0) {
+      f1 = sphi[1][t];
+      wfa = wf_of(1);
+      pf = wfa * subf(f1, f0);
+      gamma = mul_p2(wfa, 0.25f * sgn);
+    }
+    b = addf(dtr, abs_(gamma));
+    rf = times_dtr(f0);
+    if (ahead0) rf = subf(rf, mul_p2(pf, sgn8));
+  }
+  auto eliminate = [&](int st) {
+    const R rb = cvt<R>(beta);
+    const R m = subf(cvt<R>(b), rb * g);
+    const R inv = rcp_pivot(m);
+    g = cvt<R>(gamma) * inv;
+    e = subf(cvt<R>(rf), rb * e) * inv;
+    R* sp = fscr + ((Off)lev(st) * 2 * ncol_o + col_o);
+    sp[0] = g;
+    sp[ncol_o] = e;
+  };
+  auto build_next = [&](int st, bool hi) {
+    C f2 = zero_<C>(), wf2 = zero_<C>(), qf = zero_<C>();
+    if (hi) {
+      const int sl = (st + 2) % DEPTH;
+      f2 = sphi[sl][t];
+      wf2 = wf_of(st + 2);
+      qf = wf2 * subf(f2, f1);
+    }
+    beta = mul_p2(wfa, -0.25f * sgn);
+    gamma = hi ? mul_p2(wf2, 0.25f * sgn) : zero_<C>();
+    b = addf(addf(dtr, abs_(beta)), abs_(gamma));
+    const C tf = times_dtr(f1);
+    rf = hi ? subf(tf, mul_p2(addf(pf, qf), sgn8)) : subf(tf, mul_p2(pf, sgn8));
+    f1 = f2;
+    pf = qf;
+    wfa = wf2;
+  };
+  int st = 0;
+#pragma unroll 2
+  for (; st + 1 < nsteps; ++st) {
+    issue(st + DEPTH - 1);
+    cp_async_wait<DEPTH - 3>();   // slot st+2 has landed
+    eliminate(st);
+    build_next(st, true);
+  }
+  if (st < nsteps) {
+    issue(st + DEPTH - 1);
+    eliminate(st);
+  }
+  cp_async_wait<0>();
+  // the halves meet (x_lo = x_{mid-1}, x_hi = x_mid)
+  const R g_o = shfl_xor_(g, 16), e_o = shfl_xor_(e, 16);
+  const R g_lo = down ? g_o : g, g_hi = down ? g : g_o;
+  const R inv = rcp_pivot(subf(cvt<R>(1.0f), g_lo * g_hi));
+  R x;
+  {
+    const R e_lo = down ? e_o : e, e_hi = down ? e : e_o;
+    const R x_lo = subf(e_lo, g_lo * e_hi) * inv;
+    x = down ? subf(e_hi, g_hi * x_lo) : x_lo;
+  }
+  __syncthreads();          // every thread is done with the forward ring
+  __threadfence_block();    // this thread's scratch stores precede its copies below
+  R(*sg)[NT] = reinterpret_cast<R(*)[NT]>(ring);
+  R(*se)[NT] = sg + DEPTH;
+  auto issue_b = [&](int mm) {
+    const int sb = nsteps - 2 - mm;
+    if (sb >= 0) {
+      const int sl = mm % DEPTH;
+      const R* sp = fscr + ((Off)lev(sb) * 2 * ncol_o + col_o);
+      cp_async(&sg[sl][t], sp);
+      cp_async(&se[sl][t], sp + ncol_o);
+    }
+    cp_async_commit();
+  };
+  if (nsteps == 0) return;
+#pragma unroll 1
+  for (int mm = 0; mm < DEPTH - 1; ++mm) issue_b(mm);
+  S* __restrict__ out = fld ? p.vo : p.uo;
+  Off o = (Off)lev(nsteps - 1) * sk_o + (Off)cbase;
+  const Off ostep = down ? sk_o : -sk_o;
+  out[o] = cvt<S>(x);
+#pragma unroll 4
+  for (int mm = 0; mm < nsteps - 1; ++mm) {
+    issue_b(mm + DEPTH - 1);
+    cp_async_wait<DEPTH - 1>();
+    const int sl = mm % DEPTH;
+    x = subf(se[sl][t], sg[sl][t] * x);
+    o += ostep;
+    out[o] = cvt<S>(x);
+  }
+  cp_async_wait<0>();
+}
+
 size_t csize(int dtype, int arith) { return dtype == OEC_F32 ? 4 : 8; }   // compute type bytes
 size_t rsize() { return 8; }                                                // double or df64
 
@@ -641,7 +803,8 @@ Layout layout(const oec_schedule& s, int dtype, const Dom& d) {
   Layout l;
   l.thomas = 0;
   if (s.fusion == OEC_FUSE_NONE) {
-    l.ud = align_up(3 * rsize() * pts, 256);
+    // column scratch: g, e_u, e_v per point; the split sweep keeps g, e per field
+    l.ud = align_up((s.sweep == OEC_SWEEP_SPLIT ? 4 : 3) * rsize() * pts, 256);
     l.vd = align_up(l.ud + csize(dtype, s.arith) * pts, 256);
     l.total = align_up(l.vd + csize(dtype, s.arith) * pts, 256);
   } else {
@@ -652,43 +815,122 @@ Layout layout(const oec_schedule& s, int dtype, const Dom& d) {
   return l;
 }
 
+// the column sweep of the staged form over ud, vd (domain layout of d)
+template <class P>
+cudaError_t launch_sweep(const oec_schedule& s, const Dom& d, const HV<typename P::S>& p,
+                         const typename P::C* ud, const typename P::C* vd, typename P::R* scr, double dtr,
+                         cudaStream_t st) {
+  typedef typename P::C C;
+  constexpr int NC = 32, DEPTH = 16;   // pair sweep: 64 threads, two warps of 16 columns
+  const int64_t ncol = (int64_t)d.ni * d.nj;
+  int e2 = 0;
+  const bool p2 = std::is_same<C, df64>::value && std::frexp(dtr, &e2) == 0.5 && e2 > -120 && e2 < 120;
+  // 32-bit offsets: the fields' (as for the producer) and the column
+  // scratch's (3 or 4 values per point) all fit
+  const bool o32 = use_int32(s, d) && 4 * ncol * d.nk < INT32_MAX;
+  if (s.sweep == OEC_SWEEP_SPLIT) {
+    const unsigned grid = (unsigned)((ncol + 15) / 16);
+#define OEC_SPLIT(P2, OFF) hv_thomas_split_kernel<P, DEPTH, P2, OFF><<<grid, 64, 0, st>>>(p, ud, vd, dtr, scr)
+    if (p2) {
+      if (o32) OEC_SPLIT(true, int); else OEC_SPLIT(true, int64_t);
+    } else {
+      if (o32) OEC_SPLIT(false, int); else OEC_SPLIT(false, int64_t);
+    }
+#undef OEC_SPLIT
+  } else {
+    const unsigned grid = (unsigned)((ncol + NC - 1) / NC);
+#define OEC_PAIR(P2, OFF) hv_thomas_kernel<P, NC, DEPTH, P2, OFF><<<grid, 2 * NC, 0, st>>>(p, ud, vd, dtr, scr)
+    if (p2) {
+      if (o32) OEC_PAIR(true, int); else OEC_PAIR(true, int64_t);
+    } else {
+      if (o32) OEC_PAIR(false, int); else OEC_PAIR(false, int64_t);
+    }
+#undef OEC_PAIR
+  }
+  launched(st);
+  return cudaGetLastError();
+}
+
+// The staged form's slab streams and their events (one set per device, made
+// on first use): with slabs > 1 the producer of every slab runs on the
+// caller's stream and the column sweep of slab s on stream s once producer s
+// has finished, so the sweeps run concurrently with each other and with the
+// producers of the later slabs.
+struct SlabStreams {
+  cudaStream_t side[kMaxSlabs] = {};
+  cudaEvent_t ev[kMaxSlabs + 1] = {};     // fork, then one per producer
+  cudaEvent_t done[kMaxSlabs] = {};       // one per sweep
+};
+constexpr int kMaxDevices = 64;
+SlabStreams g_slab[kMaxDevices];
+std::mutex g_slab_mu;
+
+cudaError_t slab_streams(SlabStreams** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_slab_mu);
+  SlabStreams& ss = g_slab[dev];
+  if (!ss.side[kMaxSlabs - 1]) {
+    for (int x = 0; e == cudaSuccess && x < kMaxSlabs; ++x) {
+      if (!ss.side[x]) e = cudaStreamCreateWithFlags(&ss.side[x], cudaStreamNonBlocking);
+      if (e == cudaSuccess && !ss.done[x]) e = cudaEventCreateWithFlags(&ss.done[x], cudaEventDisableTiming);
+    }
+    for (int x = 0; e == cudaSuccess && x < kMaxSlabs + 1; ++x)
+      if (!ss.ev[x]) e = cudaEventCreateWithFlags(&ss.ev[x], cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+  }
+  *out = &ss;
+  return cudaSuccess;
+}
+
 template <class P>
 cudaError_t run(const oec_schedule& s, int dtype, const Dom& d, const HV<typename P::S>& p, double dtr, char* scratch,
                 cudaStream_t st) {
+  typedef typename P::S S;
+  typedef typename P::C C;
+  typedef typename P::R R;
   Layout l = layout(s, dtype, d);
-  if (s.fusion == OEC_FUSE_NONE) {
-    typedef typename P::C C;
-    C* ud = (C*)(scratch + l.ud);
-    C* vd = (C*)(scratch + l.vd);
+  if (s.fusion != OEC_FUSE_NONE) return dispatch_fused<P>(s, d, p, dtr, scratch + l.thomas, st);
+  C* ud = (C*)(scratch + l.ud);
+  C* vd = (C*)(scratch + l.vd);
+  R* scr = (R*)(scratch + l.thomas);
+  const int ns = std::min(std::max(s.slabs, 1), std::min(d.nj, kMaxSlabs));
+  if (ns == 1) {
     cudaError_t e = hdiff_to_compute(s, dtype, d, p.u, p.v, p.coeff, ud, vd, st);
     if (e != cudaSuccess) return e;
-    constexpr int NC = 32, DEPTH = 16;   // 64 threads: two warps of 16 columns
-    const int64_t ncol = (int64_t)d.ni * d.nj;
-    const unsigned grid = (unsigned)((ncol + NC - 1) / NC);
-    typename P::R* scr = (typename P::R*)(scratch + l.thomas);
-    int e2 = 0;
-    const bool p2 = std::frexp(dtr, &e2) == 0.5 && e2 > -120 && e2 < 120;
-    // 32-bit offsets: the fields' (as for the producer) and the column
-    // scratch's (3 values per point) all fit
-    const bool o32 = use_int32(s, d) && 3 * ncol * d.nk < INT32_MAX;
-    if constexpr (std::is_same<C, df64>::value) {
-      if (p2) {
-        if (o32)
-          hv_thomas_kernel<P, NC, DEPTH, true, int><<<grid, 2 * NC, 0, st>>>(p, ud, vd, dtr, scr);
-        else
-          hv_thomas_kernel<P, NC, DEPTH, true, int64_t><<<grid, 2 * NC, 0, st>>>(p, ud, vd, dtr, scr);
-        launched(st);
-        return cudaGetLastError();
-      }
-    }
-    if (o32)
-      hv_thomas_kernel<P, NC, DEPTH, false, int><<<grid, 2 * NC, 0, st>>>(p, ud, vd, dtr, scr);
-    else
-      hv_thomas_kernel<P, NC, DEPTH, false, int64_t><<<grid, 2 * NC, 0, st>>>(p, ud, vd, dtr, scr);
-    launched(st);
-    return cudaGetLastError();
+    return launch_sweep<P>(s, d, p, ud, vd, scr, dtr, st);
   }
-  return dispatch_fused<P>(s, d, p, dtr, scratch + l.thomas, st);
+  // slab pipeline: slab x holds the rows [j0, j1) with its own compact
+  // hdiff(u), hdiff(v) and column scratch (the same bytes in total)
+  SlabStreams* ss = nullptr;
+  cudaError_t e = slab_streams(&ss);
+  if (e != cudaSuccess) return e;
+  const int per = (s.sweep == OEC_SWEEP_SPLIT) ? 4 : 3;   // column scratch values per point
+  const size_t plane = size_t(d.ni) * d.nk;                // points per row of the domain, all levels
+  // one thread at a time enqueues onto the shared slab streams and events
+  // (an event is re-recorded by the next apply only after this one's waits)
+  std::lock_guard<std::mutex> lock(g_slab_mu);
+  launch_group_begin();
+  e = cudaEventRecord(ss->ev[0], st);
+  for (int x = 0; e == cudaSuccess && x < ns; ++x) e = cudaStreamWaitEvent(ss->side[x], ss->ev[0], 0);
+  for (int x = 0; e == cudaSuccess && x < ns; ++x) {
+    const int j0 = int(int64_t(d.nj) * x / ns), j1 = int(int64_t(d.nj) * (x + 1) / ns);
+    const Dom ds{d.ni, j1 - j0, d.nk, d.sj, d.sk};
+    const int64_t fo = (int64_t)j0 * d.sj;
+    const HV<S> ps{p.u + fo, p.v + fo, p.w + fo, p.coeff + fo, p.uo + fo, p.vo + fo, ds.ni, ds.nj, ds.nk, ds.sj, ds.sk};
+    const size_t before = plane * j0;
+    e = hdiff_to_compute(s, dtype, ds, ps.u, ps.v, ps.coeff, ud + before, vd + before, st);
+    if (e == cudaSuccess) e = cudaEventRecord(ss->ev[x + 1], st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ss->side[x], ss->ev[x + 1], 0);
+    if (e == cudaSuccess)
+      e = launch_sweep<P>(s, ds, ps, ud + before, vd + before, scr + per * before, dtr, ss->side[x]);
+    if (e == cudaSuccess) e = cudaEventRecord(ss->done[x], ss->side[x]);
+  }
+  for (int x = 0; e == cudaSuccess && x < ns; ++x) e = cudaStreamWaitEvent(st, ss->done[x], 0);
+  launch_group_end(st);
+  return e;
 }
 
 }  // namespace

@@ -19,6 +19,13 @@ namespace oec {
 // Called after every kernel launch of an apply: counts the launches and, while
 // the program's kernel timing is on, records an event after the kernel.
 void launched(cudaStream_t st);
+// Between these two calls launched() only counts the kernels; the end records
+// one timing event on st (the kernels of a group run on several streams and
+// overlap, so only the group as a whole has a duration).
+void launch_group_begin();
+void launch_group_end(cudaStream_t st);
+// most j-slabs of the staged hdiff+vadvc pipeline (schedule field slabs)
+constexpr int kMaxSlabs = 16;
 
 
 struct Dom {

@@ -64,6 +64,7 @@ std::vector<oec_schedule> candidates(const oec_program* p) {
         // the fixed-point producer with several rows per thread
         for (auto t : {std::array<int, 3>{32, 8, 2}, {32, 16, 1}, {32, 16, 2}, {32, 16, 4}, {64, 8, 2}})
           for (int kc : {4, 8}) c.push_back(mk(OEC_FUSE_NONE, 0, t[0], t[1], t[2], kc, 2));
+
       } else {
         for (int a : {1, 0}) {
           for (auto t : {std::pair<int, int>{32, 4}, {32, 8}, {64, 4}, {128, 2}})

@@ -92,6 +92,7 @@ bool parse_line(const std::string& line, std::string& key, oec_tunedb::Entry& e)
   if (!(f >> e.s.fusion >> e.s.staging >> e.s.tile_i >> e.s.tile_j >> e.s.unroll >> e.s.k_chunk >> e.s.arith))
     return false;
   if (!(f >> e.s.index_bits)) e.s.index_bits = OEC_INDEX_AUTO;   // entries written before the field existed
+  if (!(f >> e.s.sweep >> e.s.slabs)) e.s.sweep = e.s.slabs = 0;   // likewise
   std::istringstream m(line.substr(t2 + 1));
   return (bool)(m >> e.ms) && !key.empty();
 }
@@ -146,7 +147,8 @@ int oec_tunedb_save(oec_tunedb_t db, const char* path) {
     for (const auto& kv : db->entries) {
       const oec_schedule& s = kv.second.s;
       f << kv.first << "\t" << s.fusion << " " << s.staging << " " << s.tile_i << " " << s.tile_j << " " << s.unroll
-        << " " << s.k_chunk << " " << s.arith << " " << s.index_bits << "\t" << kv.second.ms << "\n";
+        << " " << s.k_chunk << " " << s.arith << " " << s.index_bits << " " << s.sweep << " " << s.slabs << "\t"
+        << kv.second.ms << "\n";
     }
     if (!f) return fail(OEC_ERR_INVALID_ARG, "%s: write failed", tmp.c_str());
   }

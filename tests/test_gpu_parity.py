@@ -195,6 +195,9 @@ def test_hdiff_vadvc_staged_long_columns(n, dtype, arith):
     the two halves of up to 501 rows each meet in the middle."""
     sched = dict(fusion=1, tile_i=32, tile_j=8, k_chunk=4, arith=arith)
     assert _hv_case(n, 3, dtype, sched) <= TOL[dtype]
+    if arith == 2:   # the split sweep and the slab pipeline
+        sched = dict(fusion=1, tile_i=32, tile_j=8, k_chunk=4, arith=2, sweep=1, slabs=3)
+        assert _hv_case(n, 3, dtype, sched) <= TOL[dtype]
 
 
 @pytest.mark.parametrize("arith", [0, 1])
@@ -436,6 +439,63 @@ def test_hdiff_fixed_point_mixed_magnitudes():
     assert rel_err(out.interior((0, 0, 0), n).cpu().numpy(), ref) <= TOL["f64"]
 
 
+# column sweep variants of the staged form: the fields split over warps, and
+# the j-slab pipeline (each slab's sweep on a second stream, overlapping the
+# next slab's hdiff)
+@pytest.mark.parametrize("n", [(37, 23, 11), (33, 5, 1), (33, 5, 2), (16, 16, 137), (1, 1, 80)], ids=str)
+@pytest.mark.parametrize("dtype,arith", [("f64", 2), ("f64", 1), ("f64", 0), ("f32", 0), ("f32", 1)])
+def test_hdiff_vadvc_split_sweep(n, dtype, arith):
+    sched = dict(fusion=1, tile_i=32, tile_j=8, k_chunk=4, arith=arith, sweep=1)
+    assert _hv_case(n, 3, dtype, sched) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("sweep", [0, 1])
+@pytest.mark.parametrize("slabs", [2, 3, 4, 8, 16])
+@pytest.mark.parametrize("n", [(37, 23, 11), (33, 5, 2), (40, 17, 9)], ids=str)
+def test_hdiff_vadvc_slab_pipeline(n, slabs, sweep):
+    sched = dict(fusion=1, tile_i=32, tile_j=8, k_chunk=4, arith=2, sweep=sweep, slabs=slabs)
+    assert _hv_case(n, 3, "f64", sched) <= TOL["f64"]
+
+
+@pytest.mark.parametrize("dtype,arith,producer", [("f64", 2, dict(staging=0, tile_i=32, tile_j=8, unroll=1)),
+                                                  ("f64", 2, dict(staging=0, tile_i=32, tile_j=16, unroll=2)),
+                                                  ("f32", 1, dict(staging=3, tile_i=32, tile_j=8, unroll=2))],
+                         ids=str)
+def test_hdiff_vadvc_sweep_forms_bitwise(dtype, arith, producer):
+    """The split sweep does each field's operations of the pair sweep, and the
+    slab pipeline runs the same kernels on slabs whose rows are whole tiles:
+    every form gives the bits of the plain staged form (128x128x80)."""
+    from paper_2005_13014_gb300.api import Program, device_field
+    n, h = (128, 128, 80), 3
+    f = inputs.hdiff_vadvc_fields(*n, h, seed=51)
+    g = {k: _round(v, dtype) for k, v in f.items()}
+    d = [device_field(g[k], h, dtype, align_bytes=16) for k in ("u", "v", "w", "coeff")]
+    outs = []
+    for sweep, slabs in ((0, 0), (1, 0), (0, 4), (1, 4), (0, 2), (1, 16)):
+        p = Program(programs.HDIFF_VADVC, dtype)
+        p.set_schedule(fusion=1, k_chunk=4, arith=arith, sweep=sweep, slabs=slabs, **producer)
+        o = [device_field(np.zeros_like(g["u"]), h, dtype, align_bytes=16) for _ in range(2)]
+        p.apply(d, o, (0, 0, 0), n, (h, h, h), [2.0])
+        p.apply(d, o, (0, 0, 0), n, (h, h, h), [2.0])   # twice: the pipeline's events and stream reused
+        torch.cuda.synchronize()
+        outs.append([x.tensor.clone() for x in o])
+    for o in outs[1:]:
+        assert torch.equal(o[0], outs[0][0]) and torch.equal(o[1], outs[0][1])
+
+
+def test_schedule_fields_sweep_and_slabs_are_validated():
+    from paper_2005_13014_gb300.api import Program
+    from paper_2005_13014_gb300._lib import OecError
+    p = Program(programs.HDIFF_VADVC, "f64")
+    for bad in (dict(fusion=0, tile_i=16, tile_j=4, sweep=1), dict(fusion=1, slabs=17), dict(fusion=1, sweep=2),
+                dict(fusion=1, slabs=-1)):
+        with pytest.raises(OecError):
+            p.set_schedule(**bad)
+    q = Program(programs.HDIFF, "f64")
+    with pytest.raises(OecError):
+        q.set_schedule(fusion=0, staging=1, tile_i=32, tile_j=8, slabs=2)
+
+
 @pytest.mark.parametrize("n", [(37, 23, 11), (33, 5, 1), (33, 5, 2), (128, 128, 80)], ids=str)
 def test_hdiff_vadvc_fixed_point_staged(n):
     assert _hv_case(n, 3, "f64", dict(fusion=1, arith=2)) <= TOL["f64"]
@@ -510,3 +570,6 @@ def test_hdiff_vadvc_staged_dtr(dtype, arith, dtr):
     not a power of two (the pair product)."""
     sched = dict(fusion=1, tile_i=32, tile_j=8, k_chunk=4, arith=arith)
     assert _hv_case((37, 23, 11), 3, dtype, sched, dtr=dtr) <= TOL[dtype]
+    if arith == 2:   # the split sweep and the slab pipeline
+        sched = dict(fusion=1, tile_i=32, tile_j=8, k_chunk=4, arith=2, sweep=1, slabs=4)
+        assert _hv_case((37, 23, 11), 3, dtype, sched, dtr=dtr) <= TOL[dtype]

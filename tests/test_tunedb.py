@@ -101,7 +101,7 @@ def test_index_bits_survive_a_reload(liboec, tmp_path):
     L.check(L.lib().oec_tunedb_save(db, None))
     L.lib().oec_tunedb_close(db)
     lines = open(path).read().splitlines()
-    assert lines[1].split("\t")[1] == "0 0 64 4 2 0 0 64"
+    assert lines[1].split("\t")[1] == "0 0 64 4 2 0 0 64 0 0"
     db = _open(path)
     s, _ = _find(db, hd, *_case(hd, n), n)
     assert (s.tile_i, s.unroll, s.index_bits) == (64, 2, 64)
@@ -112,6 +112,31 @@ def test_index_bits_survive_a_reload(liboec, tmp_path):
     db = _open(path)
     s, _ = _find(db, hd, *_case(hd, n), n)
     assert (s.tile_i, s.unroll, s.index_bits) == (64, 2, 0)
+    L.lib().oec_tunedb_close(db)
+
+
+def test_sweep_and_slabs_survive_a_reload(liboec, tmp_path):
+    """The staged hdiff+vadvc schedule fields sweep and slabs are stored and
+    read back; entries written without them read back as 0."""
+    path = str(tmp_path / "tune.db")
+    db = _open(path)
+    hv = _prog(programs.HDIFF_VADVC, "f64")
+    n = (64, 32, 16)
+    assert _record(db, hv, *_case(hv, n), n, (1, 0, 32, 8, 1, 4, 2, 0, 1, 4), 0.02) == 0
+    L.check(L.lib().oec_tunedb_save(db, None))
+    L.lib().oec_tunedb_close(db)
+    lines = open(path).read().splitlines()
+    assert lines[1].split("\t")[1] == "1 0 32 8 1 4 2 0 1 4"
+    db = _open(path)
+    s, _ = _find(db, hv, *_case(hv, n), n)
+    assert (s.tile_j, s.arith, s.sweep, s.slabs) == (8, 2, 1, 4)
+    L.lib().oec_tunedb_close(db)
+    key = lines[1].split("\t")[0]
+    with open(path, "w") as f:
+        f.write(f"oec-tunedb 1\n{key}\t1 0 32 8 1 4 2 0\t0.02\n")
+    db = _open(path)
+    s, _ = _find(db, hv, *_case(hv, n), n)
+    assert (s.tile_j, s.sweep, s.slabs) == (8, 0, 0)
     L.lib().oec_tunedb_close(db)
 
 
