@@ -179,9 +179,11 @@ class DagCase:
 
 
 def measure_dags(seeds, shape, dtype="f32", reps=3, threads=8, log=None):
-    """For each DAG seed: candidate features and exhaustive timings."""
+    """For each DAG seed: candidate features and exhaustive timings. shape: one
+    domain for every program, or a function of the seed (e.g.
+    inputs.dag_shape)."""
     from . import inputs
-    cases = [DagCase(inputs.random_dag(s), shape, dtype, seed=s) for s in seeds]
+    cases = [DagCase(inputs.random_dag(s), shape(s) if callable(shape) else shape, dtype, seed=s) for s in seeds]
     t0 = time.time()
     with ThreadPoolExecutor(max_workers=threads) as ex:       # NVRTC compiles in parallel
         list(ex.map(lambda c: c.prepare(), cases))

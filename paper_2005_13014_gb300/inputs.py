@@ -74,6 +74,16 @@ def ensemble_members(n=32, seed=SEED):
     return [(int(rng.choice(ij)), int(rng.choice(ij)), int(rng.choice(ks))) for _ in range(n)]
 
 
+def dag_shape(seed):
+    """Domain of a random program in the varied-shape cost-model experiment:
+    i and j each from {64,128,256,512}, k from {60,80,137} (the ensemble
+    members' distribution), drawn from the program's seed."""
+    rng = np.random.default_rng(seed + 777)
+    ij = np.array([64, 128, 256, 512])
+    ks = np.array([60, 80, 137])
+    return (int(rng.choice(ij)), int(rng.choice(ij)), int(rng.choice(ks)))
+
+
 def random_dag(seed, max_halo_ij=8, max_halo_k=4):
     """Random stencil program text: 3-12 stages, 1-4 input fields, each stage
     reading 1-3 earlier values at offsets |di|,|dj| <= 2, |dk| <= 1, built from
