@@ -832,18 +832,18 @@ cudaError_t launch_sweep(const oec_schedule& s, const Dom& d, const HV<typename 
     const unsigned grid = (unsigned)((ncol + 15) / 16);
 #define OEC_SPLIT(P2, OFF) hv_thomas_split_kernel<P, DEPTH, P2, OFF><<<grid, 64, 0, st>>>(p, ud, vd, dtr, scr)
     if (p2) {
-      if (o32) OEC_SPLIT(true, int); else OEC_SPLIT(true, int64_t);
+      if (o32) { OEC_SPLIT(true, int); } else { OEC_SPLIT(true, int64_t); }
     } else {
-      if (o32) OEC_SPLIT(false, int); else OEC_SPLIT(false, int64_t);
+      if (o32) { OEC_SPLIT(false, int); } else { OEC_SPLIT(false, int64_t); }
     }
 #undef OEC_SPLIT
   } else {
     const unsigned grid = (unsigned)((ncol + NC - 1) / NC);
 #define OEC_PAIR(P2, OFF) hv_thomas_kernel<P, NC, DEPTH, P2, OFF><<<grid, 2 * NC, 0, st>>>(p, ud, vd, dtr, scr)
     if (p2) {
-      if (o32) OEC_PAIR(true, int); else OEC_PAIR(true, int64_t);
+      if (o32) { OEC_PAIR(true, int); } else { OEC_PAIR(true, int64_t); }
     } else {
-      if (o32) OEC_PAIR(false, int); else OEC_PAIR(false, int64_t);
+      if (o32) { OEC_PAIR(false, int); } else { OEC_PAIR(false, int64_t); }
     }
 #undef OEC_PAIR
   }
