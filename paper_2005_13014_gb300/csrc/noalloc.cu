@@ -1,17 +1,16 @@
 // noalloc.cu - hdiff+vadvc for callers that must not allocate device memory.
 //
 // Some callers cannot call cudaMalloc at the moment they run the program: code
-// that executes while its stream is being captured into a CUDA graph (an
-// allocation is not part of the captured work and can invalidate the capture),
-// code that owns a fixed device-memory budget handed out by another allocator
-// (a framework's caching allocator, a pool sized at start-up), and
-// latency-critical loops where an allocation or free may synchronise the whole
-// device. oec_program_apply allocates its scratch on the first apply at a new
-// size, so it does not suit them. The entry point below runs hdiff+vadvc with
-// its scratch placed in a fixed array that is part of the library's device
-// image: the staged form (hdiff of u and v, then the twisted column sweep;
-// the schedule the autotuner picks at 128x128x80) when the domain's staged
-// scratch fits, else the fused column sweep, which needs less.
+// that owns a fixed device-memory budget handed out by another allocator (a
+// framework's caching allocator, a pool sized at start-up) and must not take
+// memory behind its back, and latency-critical loops where an allocation or
+// free may synchronise the whole device. oec_program_apply allocates its
+// scratch on the first apply at a new size, so it does not suit them. The
+// entry point below runs hdiff+vadvc with its scratch placed in a fixed array
+// that is part of the library's device image: the staged form (hdiff of u and
+// v, then the twisted column sweep of two threads per column, all on the
+// caller's stream) when the domain's staged scratch fits, else the fused
+// column sweep, which needs less.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -23,9 +22,10 @@
 namespace {
 
 // 64 MiB. The staged form needs 40 bytes per grid point in FP64 (hdiff(u),
-// hdiff(v) as double-float pairs, and g, e_u, e_v of the sweep), 32 in FP32:
-// up to 1,677,721 / 2,097,152 points; the fused form 24 (c', d'_u, d'_v):
-// up to 2,796,202 points.
+// hdiff(v) as double-float pairs, and g, e_u, e_v of the sweep) and 32 in FP32
+// (each rounded up to 256 bytes): up to 1,677,721 / 2,097,152 points. The
+// fused form needs 24 * ceil16(ni) * ceil4(nj) * nk bytes (c', d'_u, d'_v per
+// column of its 16 x 4 tiles).
 constexpr size_t kNoallocScratchBytes = size_t(64) << 20;
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
@@ -118,6 +118,8 @@ extern "C" OEC_API int oec_hdiff_vadvc_apply_noalloc(int32_t dtype, const oec_fi
   // the programs' default (staged) schedule; the fused column sweep (16x4
   // tiles, double-float) when its scratch does not fit
   oec_schedule s = default_schedule(OEC_KIND_HDIFF_VADVC, dtype);
+  s.sweep = OEC_SWEEP_PAIR;   // the sweep with the smaller scratch
+  s.slabs = 0;                // one stream: the caller's
   if (hdiff_vadvc_scratch_bytes(s, dtype, d) > kNoallocScratchBytes) {
     s = oec_schedule{};
     s.fusion = OEC_FUSE_INLINE;

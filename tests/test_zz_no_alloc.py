@@ -1,8 +1,8 @@
 """The allocation-free hdiff+vadvc entry point (for callers that cannot call
-cudaMalloc while they run, e.g. during stream capture or under a fixed memory
-budget) must give the same results as oec_program_apply, call after call,
-although every call reuses the same fixed scratch array. Kept in its own file
-so that pytest collects it last."""
+cudaMalloc while they run, e.g. under a device-memory budget owned by another
+allocator) must give the same results as oec_program_apply, call after call,
+although every call reuses the same fixed scratch array, and must take no
+device memory. Kept in its own file so that pytest collects it last."""
 
 import ctypes as C
 
@@ -42,18 +42,32 @@ def test_noalloc_matches_program_apply_on_two_calls(liboec, dtype):
             assert rel_err(a, b) <= TOL[dtype], f"call {call}"
 
 
+FUSED_DF = dict(fusion=0, staging=1, tile_i=16, tile_j=4, arith=1)
+
+
 @pytest.mark.parametrize("dtype,n,sched", [
-    ("f64", (128, 128, 80), dict(fusion=1, staging=0, tile_i=32, tile_j=8, unroll=1, k_chunk=4, arith=2)),
-    ("f32", (128, 128, 80), dict(fusion=1, staging=3, tile_i=32, tile_j=4, unroll=1, k_chunk=20, arith=1)),
-    ("f64", (128, 128, 120), dict(fusion=0, staging=1, tile_i=16, tile_j=4, arith=1))], ids=str)
+    ("f64", (128, 128, 80), None),
+    ("f32", (128, 128, 80), None),
+    ("f64", (128, 128, 102), None),
+    ("f64", (128, 128, 103), FUSED_DF),
+    ("f64", (128, 128, 120), FUSED_DF),
+    ("f64", (128, 128, 170), FUSED_DF),
+    ("f32", (160, 128, 110), FUSED_DF)], ids=str)
 def test_noalloc_bits_of_the_schedule_it_runs(liboec, dtype, n, sched):
-    """Staged where its scratch fits (128x128x80), fused beyond (128x128x120,
-    1.97 M points in FP64): bit for bit the apply with that schedule."""
+    """Staged (the program's default schedule, two threads per column, one
+    stream) where 40 B (FP64) / 32 B (FP32) per point fit in 64 MiB: at
+    128x128x80 and just below the limit (128x128x102); the fused 16x4
+    double-float sweep beyond it: just above (128x128x103), at 128x128x120,
+    at the fused form's own limit (128x128x170: 24*128*128*170 bytes), and in
+    FP32 (160x128x110, 2.25 M points). Bit for bit the apply with that
+    schedule."""
     from paper_2005_13014_gb300.api import Program, device_field
     h = 3
     prog = Program(programs.HDIFF_VADVC, dtype)
     if sched:
         prog.set_schedule(**sched)
+    else:
+        prog.set_schedule(**dict(prog.schedule, sweep=0, slabs=0))
     f = inputs.hdiff_vadvc_fields(*n, h, seed=77)
     d = [device_field(f[k], h, dtype) for k in ("u", "v", "w", "coeff")]
     ref = [device_field(np.zeros_like(f["u"]), h, dtype) for _ in range(2)]
@@ -69,14 +83,15 @@ def test_noalloc_bits_of_the_schedule_it_runs(liboec, dtype, n, sched):
         assert torch.equal(g.tensor, r.tensor)
 
 
-def test_noalloc_rejects_oversized_domain(liboec):
-    # 2,796,203 points need more than the fixed 64 MiB even in the fused
-    # form; rejected before any launch
+@pytest.mark.parametrize("n", [(2796203, 1, 1), (128, 128, 171)], ids=str)
+def test_noalloc_rejects_oversized_domain(liboec, n):
+    # more than the fixed 64 MiB even in the fused form (24 * ceil16(ni) *
+    # ceil4(nj) * nk bytes): rejected before any launch (the pointers are
+    # never dereferenced)
     d = L.FieldDesc()
     d.data, d.dtype, d.ndim = 1 << 30, L.F64, 3
-    n = (2796203, 1, 1)
-    d.size = L.I64x3(n[0] + 6, 7, 7)
-    d.stride = L.I64x3(1, n[0] + 6, (n[0] + 6) * 7)
+    d.size = L.I64x3(n[0] + 6, n[1] + 6, n[2] + 6)
+    d.stride = L.I64x3(1, n[0] + 6, (n[0] + 6) * (n[1] + 6))
     d.origin = L.I64x3(3, 3, 3)
     ins = (L.FieldDesc * 4)(*[d for _ in range(4)])
     fields = []
@@ -89,3 +104,40 @@ def test_noalloc_rejects_oversized_domain(liboec):
     rc = liboec.oec_hdiff_vadvc_apply_noalloc(L.F64, ins, outs, L.I64x3(0, 0, 0), L.I64x3(*n), 2.0, None)
     assert rc == -7
     assert b"scratch" in liboec.oec_last_error()
+
+
+def _noalloc(liboec, dtype, d, got, n):
+    ins = (L.FieldDesc * 4)(*[x.desc() for x in d])
+    outs = (L.FieldDesc * 2)(*[x.desc() for x in got])
+    return liboec.oec_hdiff_vadvc_apply_noalloc(L.F64 if dtype == "f64" else L.F32, ins, outs, L.I64x3(0, 0, 0),
+                                                L.I64x3(*n), 2.0, C.c_void_p(torch.cuda.current_stream().cuda_stream))
+
+
+def test_noalloc_takes_no_device_memory_at_a_new_size(liboec):
+    """A first call at a new domain size leaves the device's free memory as it
+    was (every field is allocated beforehand); the same first apply through
+    oec_program_apply allocates its scratch, which the same measurement sees."""
+    from paper_2005_13014_gb300.api import Program, device_field
+    h = 3
+    fields = {}
+    for n in ((64, 64, 20), (128, 96, 40)):
+        f = inputs.hdiff_vadvc_fields(*n, h, seed=5)
+        fields[n] = ([device_field(f[k], h, "f64") for k in ("u", "v", "w", "coeff")],
+                     [device_field(np.zeros_like(f["u"]), h, "f64") for _ in range(2)],
+                     [device_field(np.zeros_like(f["u"]), h, "f64") for _ in range(2)])
+    a, b = (64, 64, 20), (128, 96, 40)
+    assert _noalloc(liboec, "f64", fields[a][0], fields[a][1], a) == 0   # device code loaded, address looked up
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    assert _noalloc(liboec, "f64", fields[b][0], fields[b][1], b) == 0, liboec.oec_last_error()
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert free1 == free0
+    prog = Program(programs.HDIFF_VADVC, "f64")
+    prog.set_schedule(**dict(prog.schedule, sweep=0, slabs=0))
+    prog.apply(fields[b][0], fields[b][2], (0, 0, 0), b, (h, h, h), [2.0])
+    torch.cuda.synchronize()
+    free2 = torch.cuda.mem_get_info()[0]
+    assert free2 < free1   # 40 B per point of scratch: about 20 MB
+    for g, r in zip(fields[b][1], fields[b][2]):
+        assert torch.equal(g.tensor, r.tensor)
