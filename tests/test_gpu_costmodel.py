@@ -157,7 +157,10 @@ def test_trained_model_gains_over_the_paper_default():
     """Train the cost model on the autotuner's timings of 32 random programs and
     pick schedules for 16 unseen ones on the 256x256x80 FP32 domain: the picks
     must beat the paper's policy without a model (inline everything, one fixed
-    tile, no tuning) and come close to exhaustive autotuning."""
+    tile, no tuning) and come close to exhaustive autotuning; timing the
+    model's three best-ranked candidates must do about as well as the best
+    single schedule of the training programs (the honest non-learned rival:
+    on one domain shape one schedule nearly fits all programs)."""
     from paper_2005_13014_gb300 import costmodel as CM
     shape = (256, 256, 80)
     cands, train, _ = CM.measure_dags(list(range(30000, 30032)), shape, "f32", reps=3, threads=16)
@@ -168,11 +171,15 @@ def test_trained_model_gains_over_the_paper_default():
     m.fit(torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda(), epochs=150, batch=256, lr=1e-3)
     dflt = [x for x, c in enumerate(cands) if c["fusion"] == 0 and c["tile_i"] == 64 and c["tile_j"] == 4
             and c["unroll"] == 1][0]
-    r_model, r_default = [], []
+    fixed = CM.best_fixed(np.stack([t for _, t in train]))
+    r_model, r_model3, r_default, r_fixed = [], [], [], []
     for f, t in test:
         t = np.where(t > 0, t, np.inf)
-        order, _ = CM.select(m, torch.from_numpy(f.astype(np.float32)).cuda(), k=1)
+        order, _ = CM.select(m, torch.from_numpy(f.astype(np.float32)).cuda(), k=3)
         r_model.append(t[order[0]] / t.min() - 1)
+        r_model3.append(min(t[x] for x in order) / t.min() - 1)
         r_default.append(t[dflt] / t.min() - 1)
+        r_fixed.append(t[fixed] / t.min() - 1)
     assert np.mean(r_model) < np.mean(r_default)
     assert np.median(r_model) < 0.10
+    assert np.mean(r_model3) <= np.mean(r_fixed) + 0.015, (np.mean(r_model3), np.mean(r_fixed))
