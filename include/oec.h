@@ -133,7 +133,8 @@ typedef struct oec_schedule {
   int32_t arith;         /* OEC_ARITH_*                                                   */
   int32_t index_bits;    /* OEC_INDEX_AUTO (0) or OEC_INDEX_64 (64)                       */
   int32_t sweep;         /* column sweep of the stage-by-stage hdiff+vadvc form:
-                            OEC_SWEEP_PAIR (0) or OEC_SWEEP_SPLIT (1); 0 elsewhere        */
+                            OEC_SWEEP_PAIR (0), OEC_SWEEP_SPLIT (1), OEC_SWEEP_SEGMENTS4
+                            (4) or OEC_SWEEP_SEGMENTS8 (8); 0 elsewhere                  */
   int32_t slabs;         /* stage-by-stage hdiff+vadvc: the domain's j-rows in this many
                             slabs (0 or 1: one), each slab's column sweep on a stream of
                             its own once that slab's hdiff is done, overlapping the
@@ -150,6 +151,16 @@ typedef struct oec_schedule {
  * rounding (the same operations per field). */
 #define OEC_SWEEP_PAIR 0
 #define OEC_SWEEP_SPLIT 1
+/* OEC_SWEEP_SEGMENTS4 / 8: the partitioned Thomas solve. Each column is cut
+ * into 4 or 8 segments of consecutive levels, one thread each; a segment
+ * eliminates downwards carrying its coupling to the level below it, then
+ * substitutes upwards; the first and last rows of the column's segments form
+ * a small reduced system, solved by every thread of the column; then every
+ * thread forms its rows' solution. More threads per column, each with a
+ * shorter dependent chain, for about a quarter more operations. Same results
+ * up to rounding. */
+#define OEC_SWEEP_SEGMENTS4 4
+#define OEC_SWEEP_SEGMENTS8 8
 
 /* Width of the element offsets that kernels form from their fields' base
  * pointers (the paper's index type, §V-B and §VII-C). OEC_INDEX_AUTO: the

@@ -100,8 +100,10 @@ bool schedule_ok(int kind, const oec_schedule& s, std::string& why) {
     return false;
   }
   const bool staged_hv = kind == OEC_KIND_HDIFF_VADVC && s.fusion == OEC_FUSE_NONE;
-  if (s.sweep != OEC_SWEEP_PAIR && !(staged_hv && s.sweep == OEC_SWEEP_SPLIT)) {
-    why = "sweep: OEC_SWEEP_PAIR (0), or OEC_SWEEP_SPLIT (1) for the stage-by-stage hdiff+vadvc form";
+  const bool sweep_ok = s.sweep == OEC_SWEEP_SPLIT || s.sweep == OEC_SWEEP_SEGMENTS4 || s.sweep == OEC_SWEEP_SEGMENTS8;
+  if (s.sweep != OEC_SWEEP_PAIR && !(staged_hv && sweep_ok)) {
+    why = "sweep: OEC_SWEEP_PAIR (0), or OEC_SWEEP_SPLIT (1), OEC_SWEEP_SEGMENTS4 (4), OEC_SWEEP_SEGMENTS8 (8) for "
+          "the stage-by-stage hdiff+vadvc form";
     return false;
   }
   if (s.slabs != 0 && !(staged_hv && s.slabs >= 1 && s.slabs <= 16)) {

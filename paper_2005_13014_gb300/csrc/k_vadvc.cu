@@ -804,7 +804,7 @@ Layout layout(const oec_schedule& s, int dtype, const Dom& d) {
   l.thomas = 0;
   if (s.fusion == OEC_FUSE_NONE) {
     // column scratch: g, e_u, e_v per point; the split sweep keeps g, e per field
-    l.ud = align_up((s.sweep == OEC_SWEEP_SPLIT ? 4 : 3) * rsize() * pts, 256);
+    l.ud = align_up((s.sweep == OEC_SWEEP_PAIR ? 3 : 4) * rsize() * pts, 256);
     l.vd = align_up(l.ud + csize(dtype, s.arith) * pts, 256);
     l.total = align_up(l.vd + csize(dtype, s.arith) * pts, 256);
   } else {
@@ -828,6 +828,14 @@ cudaError_t launch_sweep(const oec_schedule& s, const Dom& d, const HV<typename 
   // 32-bit offsets: the fields' (as for the producer) and the column
   // scratch's (3 or 4 values per point) all fit
   const bool o32 = use_int32(s, d) && 4 * ncol * d.nk < INT32_MAX;
+  if (s.sweep == OEC_SWEEP_SEGMENTS4 || s.sweep == OEC_SWEEP_SEGMENTS8) {
+    cudaError_t e = hdiff_vadvc_segments_launch(s.sweep, std::is_same<typename P::S, double>::value ? OEC_F64 : OEC_F32,
+                                                s.arith, d, p.u, p.v, p.w, p.coeff, p.uo, p.vo, ud, vd, dtr, scr, o32,
+                                                st);
+    if (e != cudaSuccess) return e;
+    launched(st);
+    return cudaSuccess;
+  }
   if (s.sweep == OEC_SWEEP_SPLIT) {
     const unsigned grid = (unsigned)((ncol + 15) / 16);
 #define OEC_SPLIT(P2, OFF) hv_thomas_split_kernel<P, DEPTH, P2, OFF><<<grid, 64, 0, st>>>(p, ud, vd, dtr, scr)
@@ -907,7 +915,7 @@ cudaError_t run(const oec_schedule& s, int dtype, const Dom& d, const HV<typenam
   SlabStreams* ss = nullptr;
   cudaError_t e = slab_streams(&ss);
   if (e != cudaSuccess) return e;
-  const int per = (s.sweep == OEC_SWEEP_SPLIT) ? 4 : 3;   // column scratch values per point
+  const int per = (s.sweep == OEC_SWEEP_PAIR) ? 3 : 4;    // column scratch values per point
   const size_t plane = size_t(d.ni) * d.nk;                // points per row of the domain, all levels
   // one thread at a time enqueues onto the shared slab streams and events
   // (an event is re-recorded by the next apply only after this one's waits)

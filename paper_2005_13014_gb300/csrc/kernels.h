@@ -82,6 +82,13 @@ size_t hdiff_vadvc_scratch_bytes(const oec_schedule& s, int dtype, const Dom& d)
 cudaError_t hdiff_vadvc_launch(const oec_schedule& s, int dtype, const Dom& d, const void* u, const void* v,
                                const void* w, const void* coeff, void* u_out, void* v_out, double dtr,
                                void* scratch, cudaStream_t st);
+// the partitioned column sweep (k_vadvc_seg.cu): nseg = 4 or 8 segments per
+// column; ud, vd hdiff(u), hdiff(v) in the compute type over the domain
+// layout; scr 4 recurrence values per point
+cudaError_t hdiff_vadvc_segments_launch(int nseg, int dtype, int arith, const Dom& d, const void* u, const void* v,
+                                        const void* w, const void* coeff, void* u_out, void* v_out,
+                                        const void* ud, const void* vd, double dtr, void* scr, bool o32,
+                                        cudaStream_t st);
 // batched persistent form (ensembles of domains)
 size_t hdiff_vadvc_batch_slot_elems(const oec_schedule& s, int nk_max);
 int hdiff_vadvc_batch_blocks_per_sm(const oec_schedule& s, int dtype);

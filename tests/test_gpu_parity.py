@@ -449,6 +449,29 @@ def test_hdiff_vadvc_split_sweep(n, dtype, arith):
     assert _hv_case(n, 3, dtype, sched) <= TOL[dtype]
 
 
+@pytest.mark.parametrize("nseg", [4, 8])
+@pytest.mark.parametrize("n", [(37, 23, 11), (33, 5, 1), (33, 5, 2), (33, 5, 3), (31, 7, 5), (30, 9, 9),
+                               (16, 16, 137), (20, 12, 256), (33, 5, 1001), (1, 1, 80), (128, 128, 80)], ids=str)
+@pytest.mark.parametrize("dtype,arith", [("f64", 2), ("f64", 1), ("f64", 0), ("f32", 0), ("f32", 1)])
+def test_hdiff_vadvc_partitioned_sweep(n, dtype, arith, nseg):
+    """The partitioned column solve (4 or 8 segments per column, a reduced
+    system over the segments' first and last rows), including columns with
+    fewer levels than segments (empty segments) and long columns."""
+    if (dtype, arith) != ("f64", 2) and n[2] in (1001, 256):
+        pytest.skip("long columns: the fixed-point producer case covers them")
+    sched = dict(fusion=1, tile_i=32, tile_j=8, k_chunk=4, arith=arith, sweep=nseg)
+    assert _hv_case(n, 3, dtype, sched) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("nseg", [4, 8])
+@pytest.mark.parametrize("dtr", [2.0, 0.5, 3.0, 1.0 / 3.0])
+def test_hdiff_vadvc_partitioned_sweep_dtr_and_slabs(nseg, dtr):
+    sched = dict(fusion=1, tile_i=32, tile_j=8, k_chunk=4, arith=2, sweep=nseg)
+    assert _hv_case((37, 23, 11), 3, "f64", sched, dtr=dtr) <= TOL["f64"]
+    sched["slabs"] = 3
+    assert _hv_case((37, 23, 11), 3, "f64", sched, dtr=dtr) <= TOL["f64"]
+
+
 @pytest.mark.parametrize("sweep", [0, 1])
 @pytest.mark.parametrize("slabs", [2, 3, 4, 8, 16])
 @pytest.mark.parametrize("n", [(37, 23, 11), (33, 5, 2), (40, 17, 9)], ids=str)
@@ -488,7 +511,7 @@ def test_schedule_fields_sweep_and_slabs_are_validated():
     from paper_2005_13014_gb300._lib import OecError
     p = Program(programs.HDIFF_VADVC, "f64")
     for bad in (dict(fusion=0, tile_i=16, tile_j=4, sweep=1), dict(fusion=1, slabs=17), dict(fusion=1, sweep=2),
-                dict(fusion=1, slabs=-1)):
+                dict(fusion=1, slabs=-1), dict(fusion=1, sweep=16), dict(fusion=0, tile_i=16, tile_j=4, sweep=4)):
         with pytest.raises(OecError):
             p.set_schedule(**bad)
     q = Program(programs.HDIFF, "f64")
