@@ -177,10 +177,11 @@ def _kernel_source_hash(files):
     return h.hexdigest()[:16]
 
 
-def _ncu_figure(kernel, key):
+def _ncu_figure(kernel, key, sched=None):
     """A per-launch figure (dram_bytes_per_launch, warp_instructions_per_launch)
     of a kernel from its committed ncu summary, if the summary was taken on
-    the current source of that kernel."""
+    the current source of that kernel and, when it names one, with the same
+    schedule."""
     if not kernel["profile"]:
         return None
     try:
@@ -191,11 +192,16 @@ def _ncu_figure(kernel, key):
     t = re.search(key + r":\s*([0-9]+)", text)
     if not m or not t or m.group(1) != _kernel_source_hash(kernel["src"]):
         return None
+    c = re.search(r"captured_schedule:\s*(\{.*\})", text)
+    if c and sched is not None:
+        want = json.loads(c.group(1))
+        if any(sched.get(k) != v for k, v in want.items()):
+            return None
     return int(t.group(1))
 
 
-def _ncu_traffic(kernel):
-    return _ncu_figure(kernel, "dram_bytes_per_launch")
+def _ncu_traffic(kernel, sched=None):
+    return _ncu_figure(kernel, "dram_bytes_per_launch", sched)
 
 
 def _quartiles(x):
@@ -507,7 +513,7 @@ def run_gpu(args):
     sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz") or 2070.0
     issue = []
     for x, k in enumerate(kernels):
-        inst = _ncu_figure(k, "warp_instructions_per_launch")
+        inst = _ncu_figure(k, "warp_instructions_per_launch", sched)
         if inst is not None:
             cap = SMS * ISSUE_PER_SM * sm_mhz * 1e6 * float(k_med[x]) * 1e-3
             issue.append({"kernel": k["name"], "warp_instructions": inst, "frac_of_issue_peak": inst / cap,
@@ -523,7 +529,7 @@ def run_gpu(args):
                    "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU",
                    "autotune_ms": tuning},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                     "traffic": _ncu_traffic(kd), "kernel": kd["name"], "kernel_ms_median": kd_ms,
+                     "traffic": _ncu_traffic(kd, sched), "kernel": kd["name"], "kernel_ms_median": kd_ms,
                      "kernel_algorithmic_bytes": kd_bytes, "kernel_fields": list(kd["fields"]),
                      "peak_source": peak_source,
                      "step": {"achieved": step_gbs, "frac": step_gbs / hbm_peak, "algorithmic_bytes": step_bytes,
@@ -535,7 +541,7 @@ def run_gpu(args):
                                          "integer and FP32 pipes (config.arith), so no FP64 peak applies"},
         "native_f64": native,
         "kernels": [{"name": k["name"], **_quartiles(per_kernel[:, x]), "share": float(k_med[x] / k_med.sum()),
-                     "traffic": _ncu_traffic(k)} for x, k in enumerate(kernels)],
+                     "traffic": _ncu_traffic(k, sched)} for x, k in enumerate(kernels)],
         "kernel_sum_ms": dict(_quartiles(step_ms), note="attribution pass after the timed region: events around "
                               "every kernel of every step"),
         "e2e": {"value": e2e_value, "unit": "grid-points/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
