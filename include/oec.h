@@ -319,6 +319,35 @@ OEC_API int oec_program_apply_host(oec_program_t p, const oec_field_desc* in, in
                                    const double* params, int n_params, void* cuda_stream);
 
 /*
+ * Captured applies (no counterpart in the paper, which times kernels launched
+ * one by one): oec_program_capture records one oec_program_apply with these
+ * arguments into a CUDA graph and instantiates it; oec_graph_launch enqueues
+ * that graph on a stream, one launch per apply, so a loop of applies with
+ * fixed fields pays one launch instead of one per kernel and no argument
+ * marshalling. The graph reads and writes the fields' memory at the addresses
+ * given at capture (their contents may change between launches) and the
+ * program's scratch as it was then: while a program has live graphs, an apply
+ * that would need a larger scratch fails with OEC_ERR_UNSUPPORTED; destroy
+ * the graphs first (and before destroying the program). The capture runs on
+ * a private stream in relaxed capture mode, so the program's scratch and, for
+ * generated programs, its module are set up eagerly during the call (call
+ * oec_program_prepare first to compile outside it); kernel timing is off
+ * inside the capture. Argument errors are those of oec_program_apply; the
+ * capture itself: OEC_ERR_CUDA. Synchronous with respect to the host (returns
+ * once the graph is instantiated); nothing runs on the GPU.
+ */
+typedef struct oec_graph* oec_graph_t;
+OEC_API int oec_program_capture(oec_program_t p, const oec_field_desc* in, int n_in, const oec_field_desc* out,
+                                int n_out, const int64_t lb[3], const int64_t ub[3], const int64_t halo[3],
+                                const double* params, int n_params, oec_graph_t* graph);
+/* Enqueue one launch of a captured apply on cuda_stream (asynchronous).
+ * Errors: OEC_ERR_INVALID_ARG, OEC_ERR_CUDA. */
+OEC_API int oec_graph_launch(oec_graph_t graph, void* cuda_stream);
+/* Kernels one launch of the graph runs. */
+OEC_API int oec_graph_kernel_count(oec_graph_t graph);
+OEC_API void oec_graph_destroy(oec_graph_t graph);
+
+/*
  * Compile and load the generated kernels of a program without a hand-written
  * kernel for a domain extent and field j/k strides (what the first apply at
  * that shape would do), so that applies and stream capture that follow

@@ -85,6 +85,11 @@ def lib():
                                         I64x3, I64x3, I64x3, C.POINTER(C.c_double), C.c_int, P]),
         "oec_program_apply_host": (C.c_int, [P, C.POINTER(FieldDesc), C.c_int, C.POINTER(FieldDesc), C.c_int,
                                              I64x3, I64x3, I64x3, C.POINTER(C.c_double), C.c_int, P]),
+        "oec_program_capture": (C.c_int, [P, C.POINTER(FieldDesc), C.c_int, C.POINTER(FieldDesc), C.c_int,
+                                          I64x3, I64x3, I64x3, C.POINTER(C.c_double), C.c_int, C.POINTER(P)]),
+        "oec_graph_launch": (C.c_int, [P, P]),
+        "oec_graph_kernel_count": (C.c_int, [P]),
+        "oec_graph_destroy": (None, [P]),
         "oec_tunedb_open": (C.c_int, [C.c_char_p, C.POINTER(P)]),
         "oec_tunedb_save": (C.c_int, [P, C.c_char_p]),
         "oec_tunedb_count": (C.c_int, [P]),

@@ -170,6 +170,41 @@ class BoundApply:
             L.check(rc)
 
 
+class CapturedApply:
+    """One program apply captured into a CUDA graph (Program.capture): each
+    call launches it on a stream. The fields must outlive it; destroy it
+    (close, or drop it) before the program."""
+
+    def __init__(self, prog, inputs, outputs, lb, ub, halo, params):
+        self._h = None
+        self._keep = (prog, list(inputs), list(outputs))
+        ins = (L.FieldDesc * max(1, len(inputs)))(*[f.desc() for f in inputs])
+        outs = (L.FieldDesc * max(1, len(outputs)))(*[f.desc() for f in outputs])
+        par = (C.c_double * max(1, len(params)))(*params)
+        h = C.c_void_p()
+        L.check(L.lib().oec_program_capture(prog._h, ins, len(inputs), outs, len(outputs), L.I64x3(*lb), L.I64x3(*ub),
+                                            L.I64x3(*halo), par, len(params), C.byref(h)))
+        self._h = h
+        self.kernel_count = L.lib().oec_graph_kernel_count(h)
+
+    def __call__(self, stream=None):
+        if stream is None:
+            stream = _torch().cuda.current_stream().cuda_stream
+        elif hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        rc = L.lib().oec_graph_launch(self._h, C.c_void_p(stream))
+        if rc:
+            L.check(rc)
+
+    def close(self):
+        if self._h is not None:
+            L.lib().oec_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+
 class Program:
     """A compiled stencil program (liboec handle)."""
 
@@ -247,6 +282,11 @@ class Program:
         foreign call, for loops where the per-call marshalling of ``apply``
         would cost more than a short kernel)."""
         return BoundApply(self, inputs, outputs, lb, ub, halo, params, stream)
+
+    def capture(self, inputs, outputs, lb, ub, halo, params=()):
+        """Capture one apply with these fields into a CUDA graph; calling the
+        result launches it (one launch per apply, no argument marshalling)."""
+        return CapturedApply(self, inputs, outputs, lb, ub, halo, params)
 
     def launch_count(self) -> int:
         """Kernels launched by the most recent apply."""

@@ -197,6 +197,9 @@ int ensure_scratch(oec_program* p, size_t bytes) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   if (p->scratch && p->scratch_bytes >= bytes && p->scratch_dev == dev) return OEC_OK;
+  if (p->scratch && p->graphs > 0)
+    return fail(OEC_ERR_UNSUPPORTED, "the program's scratch is used by %d captured apply graph(s): destroy them "
+                "before applying at a larger domain", p->graphs);
   if (p->scratch) {
     int cur = dev;
     cudaSetDevice(p->scratch_dev);
@@ -629,6 +632,87 @@ int oec_program_kernel_times(oec_program_t p, float* ms, int cap, int* n_applies
   p->ev_count.clear();
   p->ev_used = 0;
   return OEC_OK;
+}
+
+}  // extern "C"
+
+// ---- captured applies ----------------------------------------------------
+
+struct oec_graph {
+  oec_program* prog = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int kernels = 0;
+};
+
+extern "C" {
+
+int oec_program_capture(oec_program_t p, const oec_field_desc* in, int n_in, const oec_field_desc* out, int n_out,
+                        const int64_t lb[3], const int64_t ub[3], const int64_t halo[3], const double* params,
+                        int n_params, oec_graph_t* graph) {
+  clear_error();
+  if (!p || !graph) return fail(OEC_ERR_INVALID_ARG, "null program or graph handle");
+  *graph = nullptr;
+  cudaStream_t cs = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+  const bool timing = p->timing;
+  p->timing = false;
+  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+  int rc = OEC_OK;
+  cudaGraph_t g = nullptr;
+  if (e == cudaSuccess) {
+    rc = oec_program_apply(p, in, n_in, out, n_out, lb, ub, halo, params, n_params, cs);
+    const std::string msg = rc ? oec_last_error() : "";
+    e = cudaStreamEndCapture(cs, &g);
+    if (rc) fail(rc, "%s", msg.c_str());   // the apply's error, not the capture's
+  }
+  p->timing = timing;
+  cudaStreamDestroy(cs);
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return cuda_fail(e, "stream capture of the apply");
+  }
+  cudaGraphExec_t x = nullptr;
+  e = cudaGraphInstantiate(&x, g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return cuda_fail(e, "cudaGraphInstantiate");
+  }
+  oec_graph* h = new (std::nothrow) oec_graph();
+  if (!h) {
+    cudaGraphExecDestroy(x);
+    cudaGraphDestroy(g);
+    return fail(OEC_ERR_INVALID_ARG, "out of host memory");
+  }
+  h->prog = p;
+  h->graph = g;
+  h->exec = x;
+  h->kernels = p->last_launches;
+  ++p->graphs;
+  *graph = h;
+  return OEC_OK;
+}
+
+int oec_graph_launch(oec_graph_t graph, void* cuda_stream) {
+  clear_error();
+  if (!graph) return fail(OEC_ERR_INVALID_ARG, "null graph");
+  const cudaError_t e = cudaGraphLaunch(graph->exec, (cudaStream_t)cuda_stream);
+  return e == cudaSuccess ? OEC_OK : cuda_fail(e, "cudaGraphLaunch");
+}
+
+int oec_graph_kernel_count(oec_graph_t graph) { return graph ? graph->kernels : 0; }
+
+void oec_graph_destroy(oec_graph_t graph) {
+  if (!graph) return;
+  cudaGraphExecDestroy(graph->exec);
+  cudaGraphDestroy(graph->graph);
+  if (graph->prog) --graph->prog->graphs;
+  delete graph;
 }
 
 }  // extern "C"

@@ -31,6 +31,7 @@ struct oec_program {
   std::vector<int> ev_first, ev_count;
   int last_launches = 0;
   int last_timed = 0;      // timing events recorded after the apply's first (kernels or groups)
+  int graphs = 0;          // live captured applies (oec_program_capture) using the scratch
   // oec_program_apply_host: two sets of device staging buffers (inputs then
   // outputs, bytes[x] each), the input-copy streams and the sets' events
   static constexpr int kCopyStreams = 1;
