@@ -620,8 +620,10 @@ OEC_API int oec_program_autotune_model(oec_program_t p, oec_costmodel_t m, const
  *   out[2]  u_out, v_out, written over [lb, ub)
  *   dtr     the scalar parameter of the vertical advection
  * Limit, for a domain of ni x nj x nk points: the staged form needs
- * 40 * ni * nj * nk bytes in FP64 (32 in FP32), each of its two parts rounded
- * up to 256 bytes; beyond 64 MiB the fused form needs
+ * 24 * ceil16(ni * nj) * nk + 16 * ni * nj * nk bytes in FP64 and
+ * 24 * ceil16(ni * nj) * nk + 8 * ni * nj * nk in FP32, each of its two parts
+ * rounded up to 256 bytes (40 and 32 bytes per point when ni * nj is a
+ * multiple of 16); beyond 64 MiB the fused form needs
  * 24 * ceil16(ni) * ceil4(nj) * nk bytes (ceilN: rounded up to a multiple of
  * N); a domain whose fused form needs more than 64 MiB is rejected with
  * OEC_ERR_UNSUPPORTED before anything is enqueued. The first call on each

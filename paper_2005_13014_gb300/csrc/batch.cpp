@@ -71,7 +71,7 @@ cudaError_t record_staged(const oec_batch* b, char* scratch, const std::vector<c
   cudaError_t e = cudaSuccess;
   for (const StagedMember& m : b->staged_members) {
     cudaError_t r = oec::hdiff_vadvc_launch(b->sched, b->dtype, m.d, m.u, m.v, m.w, m.coeff, m.uo, m.vo, b->dtr,
-                                            scratch + m.scratch_off, streams[m.stream % streams.size()]);
+                                            scratch + m.scratch_off, streams[m.stream % streams.size()], true);
     if (e == cudaSuccess) e = r;
   }
   return e;

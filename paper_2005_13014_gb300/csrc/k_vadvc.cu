@@ -362,10 +362,20 @@ template <> __device__ __forceinline__ df64 wsum<df64, double>(double a, double 
 // wrote; the one barrier separates the two uses of the ring. DTR_P2: dtr is a
 // power of two in float range, so dtr * phi is an exact scaling (for
 // double-float, two float multiplies instead of a pair product).
-template <class P, int NC, int DEPTH, bool DTR_P2, class Off>
+// L2 use: the scratch rows have a pitch of ncolp columns (a multiple of 16),
+// so each 128-byte line of scratch (16 columns of one value at one level)
+// belongs to one half-warp. The DISCARD form (for scratch larger than L2;
+// scr 128-byte aligned) stores scratch with evict-last priority and reads
+// and writes the streamed fields with evict-first priority, so that the
+// recurrence values of the columns in flight stay in L2 until the back
+// substitution reads them, and then drops those lines from L2 without
+// writing them back, four back steps (12 lines of a half-warp, one per lane)
+// at a time. The values of a half's last step are used from registers and
+// not stored.
+template <class P, int NC, int DEPTH, bool DTR_P2, class Off, bool DISCARD>
 __global__ void __launch_bounds__(2 * NC) hv_thomas_kernel(HV<typename P::S> p, const typename P::C* __restrict__ ud,
                                                            const typename P::C* __restrict__ vd, double dtr_d,
-                                                           typename P::R* __restrict__ scr) {
+                                                           typename P::R* __restrict__ scr, int64_t ncolp) {
   typedef typename P::S S;
   typedef typename P::C C;
   typedef typename P::R R;
@@ -382,6 +392,20 @@ __global__ void __launch_bounds__(2 * NC) hv_thomas_kernel(HV<typename P::S> p, 
   const int64_t ncol = (int64_t)p.ni * p.nj;
   const int64_t col = (int64_t)blockIdx.x * NC + (t >> 5) * 16 + (lane & 15);
   const bool active = col < ncol;   // inactive threads only join the barrier and the exchange
+  // the active lanes of this thread's half-warp (they share scratch lines)
+  const unsigned hmask = __ballot_sync(0xFFFFFFFFu, active) & (0xFFFFu << (lane & 16));
+  uint64_t keep = 0, stream = 0;
+  if (DISCARD) {
+    keep = l2_evict_last();
+    stream = l2_evict_first();
+  }
+  // loads and stores with the L2 priorities in the DISCARD form, plain otherwise
+  auto ld_async = [&](auto* dst, const auto* src, uint64_t pol) {
+    if (DISCARD) cp_async_l2(dst, src, pol); else cp_async(dst, src);
+  };
+  auto st_g = [&](auto* dst, auto v, uint64_t pol) {
+    if (DISCARD) st_l2(dst, v, pol); else *dst = v;
+  };
   const int i = active ? int(col % p.ni) : 0, j = active ? int(col / p.ni) : 0;
   const int nk = p.nk, mid = (nk + 1) / 2;
   const int nsteps = active ? (down ? nk - mid : mid) : 0;
@@ -391,7 +415,7 @@ __global__ void __launch_bounds__(2 * NC) hv_thomas_kernel(HV<typename P::S> p, 
   const int64_t cbase = (int64_t)j * p.sj + i;
   const S* __restrict__ wcol = p.w + cbase;
   // element offsets per level in Off (32-bit when every offset fits)
-  const Off ncol_o = (Off)ncol, col_o = (Off)col, sk_o = (Off)p.sk;
+  const Off ncol_o = (Off)ncol, ncolp_o = (Off)ncolp, col_o = (Off)col, sk_o = (Off)p.sk;
   // level of step s, and the level whose w gives the edge behind step s
   // (the edge between levels k-1 and k belongs to w at level k)
   auto lev = [&](int st) { return down ? nk - 1 - st : st; };
@@ -401,12 +425,12 @@ __global__ void __launch_bounds__(2 * NC) hv_thomas_kernel(HV<typename P::S> p, 
       const int sl = st % DEPTH, k = lev(st), kw = wlev(st);
       if (k >= 0 && k < nk) {
         const Off o = (Off)k * ncol_o + col_o;
-        cp_async(&su[sl][t], ud + o);
-        cp_async(&sv[sl][t], vd + o);
+        ld_async(&su[sl][t], ud + o, stream);
+        ld_async(&sv[sl][t], vd + o, stream);
       }
       if (kw < nk) {
-        cp_async(&sw0[sl][t], wcol + (Off)kw * sk_o);
-        cp_async(&sw1[sl][t], wcol + (Off)kw * sk_o + 1);
+        ld_async(&sw0[sl][t], wcol + (Off)kw * sk_o, stream);
+        ld_async(&sw1[sl][t], wcol + (Off)kw * sk_o + 1, stream);
       }
     }
     cp_async_commit();
@@ -452,17 +476,19 @@ __global__ void __launch_bounds__(2 * NC) hv_thomas_kernel(HV<typename P::S> p, 
   }
   // elimination of the row of step st (step 0 needs no special case:
   // beta = 0 and g = 0 make m = b exactly)
-  auto eliminate = [&](int st) {
+  auto eliminate = [&](int st, bool store) {
     const R rb = cvt<R>(beta);
     const R m = subf(cvt<R>(b), rb * g);
     const R inv = rcp_pivot(m);
     g = cvt<R>(gamma) * inv;
     eu = subf(cvt<R>(ru), rb * eu) * inv;
     ev = subf(cvt<R>(rv), rb * ev) * inv;
-    R* sp = scr + ((Off)lev(st) * 3 * ncol_o + col_o);
-    sp[0] = g;
-    sp[ncol_o] = eu;
-    sp[2 * ncol_o] = ev;
+    if (store) {
+      R* sp = scr + ((Off)lev(st) * 3 * ncolp_o + col_o);
+      st_g(sp, g, keep);
+      st_g(sp + ncolp_o, eu, keep);
+      st_g(sp + 2 * ncolp_o, ev, keep);
+    }
   };
   // row of step st+1 (it has a level behind; hi: it has one ahead)
   auto build_next = [&](int st, bool hi) {
@@ -499,12 +525,12 @@ __global__ void __launch_bounds__(2 * NC) hv_thomas_kernel(HV<typename P::S> p, 
   for (; st + 1 < nsteps; ++st) {
     issue(st + DEPTH - 1);
     cp_async_wait<DEPTH - 3>();   // slot st+2 has landed
-    eliminate(st);
+    eliminate(st, true);
     build_next(st, true);
   }
   if (st < nsteps) {
     issue(st + DEPTH - 1);
-    eliminate(st);
+    eliminate(st, false);
   }
   cp_async_wait<0>();
   // the halves meet: x_lo = x_{mid-1} (upward half's last row), x_hi = x_mid
@@ -529,10 +555,10 @@ __global__ void __launch_bounds__(2 * NC) hv_thomas_kernel(HV<typename P::S> p, 
     const int sb = nsteps - 2 - mm;
     if (sb >= 0) {
       const int sl = mm % DEPTH;
-      const R* sp = scr + ((Off)lev(sb) * 3 * ncol_o + col_o);
+      const R* sp = scr + ((Off)lev(sb) * 3 * ncolp_o + col_o);
       cp_async(&sg[sl][t], sp);
-      cp_async(&seu[sl][t], sp + ncol_o);
-      cp_async(&sev[sl][t], sp + 2 * ncol_o);
+      cp_async(&seu[sl][t], sp + ncolp_o);
+      cp_async(&sev[sl][t], sp + 2 * ncolp_o);
     }
     cp_async_commit();
   };
@@ -541,20 +567,30 @@ __global__ void __launch_bounds__(2 * NC) hv_thomas_kernel(HV<typename P::S> p, 
   for (int mm = 0; mm < DEPTH - 1; ++mm) issue_b(mm);
   Off o = (Off)lev(nsteps - 1) * sk_o + (Off)cbase;
   const Off ostep = down ? sk_o : -sk_o;   // outwards
-  p.uo[o] = cvt<S>(xu);
-  p.vo[o] = cvt<S>(xv);
+  st_g(p.uo + o, cvt<S>(xu), stream);
+  st_g(p.vo + o, cvt<S>(xv), stream);
+  // the half-warp's first column: its scratch lines start there. Lane l < 12
+  // of the half drops the line of value l % 3 of back step first + l / 3.
+  const int lh = lane & 15;
+  const R* hline = scr + (col_o - (Off)lh);
+  auto drop4 = [&](int first, int n) {
+    __syncwarp(hmask);   // every lane of the half has its copies of these steps
+    if (lh < 3 * n) l2_discard(hline + ((Off)lev(nsteps - 2 - (first + lh / 3)) * 3 + lh % 3) * ncolp_o);
+  };
 #pragma unroll 4
   for (int mm = 0; mm < nsteps - 1; ++mm) {
     issue_b(mm + DEPTH - 1);
     cp_async_wait<DEPTH - 1>();   // back step mm's values have landed
     const int sl = mm % DEPTH;
+    if (DISCARD && (mm & 3) == 3) drop4(mm - 3, 4);
     const R gk = sg[sl][t];
     xu = subf(seu[sl][t], gk * xu);
     xv = subf(sev[sl][t], gk * xv);
     o += ostep;
-    p.uo[o] = cvt<S>(xu);
-    p.vo[o] = cvt<S>(xv);
+    st_g(p.uo + o, cvt<S>(xu), stream);
+    st_g(p.vo + o, cvt<S>(xv), stream);
   }
+  if (DISCARD && ((nsteps - 1) & 3)) drop4((nsteps - 1) & ~3, (nsteps - 1) & 3);
   cp_async_wait<0>();
 }
 
@@ -795,6 +831,20 @@ int occupancy_of(const oec_schedule& s) {
   return 1;
 }
 
+// the pair sweep drops its read scratch lines from L2 when its scratch is
+// larger than this
+constexpr size_t kDiscardAboveBytes = size_t(48) << 20;
+
+// scratch row pitch of the pair sweep: the columns rounded up to 16, so that
+// a 128-byte line of 8-byte values holds one half-warp's columns only
+int64_t pair_pitch(int64_t ncol) { return (ncol + 15) / 16 * 16; }
+
+// column-scratch elements (recurrence values) of one slab of `rows` j-rows
+size_t sweep_scratch_elems(const oec_schedule& s, const Dom& d, int rows) {
+  const int64_t ncol = (int64_t)d.ni * rows;
+  return s.sweep == OEC_SWEEP_PAIR ? size_t(3) * pair_pitch(ncol) * d.nk : size_t(4) * ncol * d.nk;
+}
+
 struct Layout {
   size_t thomas, ud, vd, total;
 };
@@ -803,8 +853,12 @@ Layout layout(const oec_schedule& s, int dtype, const Dom& d) {
   Layout l;
   l.thomas = 0;
   if (s.fusion == OEC_FUSE_NONE) {
-    // column scratch: g, e_u, e_v per point; the split sweep keeps g, e per field
-    l.ud = align_up((s.sweep == OEC_SWEEP_PAIR ? 3 : 4) * rsize() * pts, 256);
+    // column scratch: g, e_u, e_v per point (pair sweep; each slab's rows
+    // padded to 16 columns), the split and partitioned sweeps keep g, e per
+    // field
+    const int ns = std::min(std::max(s.slabs, 1), std::min(d.nj, kMaxSlabs));
+    const size_t pad = ns > 1 ? size_t(3) * 16 * ns * d.nk : 0;   // slab starts on 128 bytes
+    l.ud = align_up(rsize() * (sweep_scratch_elems(s, d, d.nj) + pad), 256);
     l.vd = align_up(l.ud + csize(dtype, s.arith) * pts, 256);
     l.total = align_up(l.vd + csize(dtype, s.arith) * pts, 256);
   } else {
@@ -819,7 +873,7 @@ Layout layout(const oec_schedule& s, int dtype, const Dom& d) {
 template <class P>
 cudaError_t launch_sweep(const oec_schedule& s, const Dom& d, const HV<typename P::S>& p,
                          const typename P::C* ud, const typename P::C* vd, typename P::R* scr, double dtr,
-                         cudaStream_t st) {
+                         cudaStream_t st, bool batch_member = false) {
   typedef typename P::C C;
   constexpr int NC = 32, DEPTH = 16;   // pair sweep: 64 threads, two warps of 16 columns
   const int64_t ncol = (int64_t)d.ni * d.nj;
@@ -827,7 +881,7 @@ cudaError_t launch_sweep(const oec_schedule& s, const Dom& d, const HV<typename 
   const bool p2 = std::is_same<C, df64>::value && std::frexp(dtr, &e2) == 0.5 && e2 > -120 && e2 < 120;
   // 32-bit offsets: the fields' (as for the producer) and the column
   // scratch's (3 or 4 values per point) all fit
-  const bool o32 = use_int32(s, d) && 4 * ncol * d.nk < INT32_MAX;
+  const bool o32 = use_int32(s, d) && 4 * pair_pitch(ncol) * d.nk < INT32_MAX;
   if (s.sweep == OEC_SWEEP_SEGMENTS4 || s.sweep == OEC_SWEEP_SEGMENTS8) {
     cudaError_t e = hdiff_vadvc_segments_launch(s.sweep, std::is_same<typename P::S, double>::value ? OEC_F64 : OEC_F32,
                                                 s.arith, d, p.u, p.v, p.w, p.coeff, p.uo, p.vo, ud, vd, dtr, scr, o32,
@@ -847,12 +901,21 @@ cudaError_t launch_sweep(const oec_schedule& s, const Dom& d, const HV<typename 
 #undef OEC_SPLIT
   } else {
     const unsigned grid = (unsigned)((ncol + NC - 1) / NC);
-#define OEC_PAIR(P2, OFF) hv_thomas_kernel<P, NC, DEPTH, P2, OFF><<<grid, 2 * NC, 0, st>>>(p, ud, vd, dtr, scr)
+    // the L2 form pays for batch members whose scratch cannot stay in L2
+    // anyway (on smaller domains, and for one apply alone, its few extra
+    // instructions per step cost more than the traffic it saves)
+    const bool discard = batch_member && (uintptr_t)scr % 128 == 0 &&
+                         size_t(24) * pair_pitch(ncol) * d.nk > kDiscardAboveBytes;
+#define OEC_PAIR(P2, OFF, D) \
+  hv_thomas_kernel<P, NC, DEPTH, P2, OFF, D><<<grid, 2 * NC, 0, st>>>(p, ud, vd, dtr, scr, pair_pitch(ncol))
+#define OEC_PAIR_D(P2, OFF) \
+  if (discard) { OEC_PAIR(P2, OFF, true); } else { OEC_PAIR(P2, OFF, false); }
     if (p2) {
-      if (o32) { OEC_PAIR(true, int); } else { OEC_PAIR(true, int64_t); }
+      if (o32) { OEC_PAIR_D(true, int); } else { OEC_PAIR_D(true, int64_t); }
     } else {
-      if (o32) { OEC_PAIR(false, int); } else { OEC_PAIR(false, int64_t); }
+      if (o32) { OEC_PAIR_D(false, int); } else { OEC_PAIR_D(false, int64_t); }
     }
+#undef OEC_PAIR_D
 #undef OEC_PAIR
   }
   launched(st);
@@ -895,7 +958,7 @@ cudaError_t slab_streams(SlabStreams** out) {
 
 template <class P>
 cudaError_t run(const oec_schedule& s, int dtype, const Dom& d, const HV<typename P::S>& p, double dtr, char* scratch,
-                cudaStream_t st) {
+                cudaStream_t st, bool batch_member) {
   typedef typename P::S S;
   typedef typename P::C C;
   typedef typename P::R R;
@@ -908,15 +971,15 @@ cudaError_t run(const oec_schedule& s, int dtype, const Dom& d, const HV<typenam
   if (ns == 1) {
     cudaError_t e = hdiff_to_compute(s, dtype, d, p.u, p.v, p.coeff, ud, vd, st);
     if (e != cudaSuccess) return e;
-    return launch_sweep<P>(s, d, p, ud, vd, scr, dtr, st);
+    return launch_sweep<P>(s, d, p, ud, vd, scr, dtr, st, batch_member);
   }
   // slab pipeline: slab x holds the rows [j0, j1) with its own compact
   // hdiff(u), hdiff(v) and column scratch (the same bytes in total)
   SlabStreams* ss = nullptr;
   cudaError_t e = slab_streams(&ss);
   if (e != cudaSuccess) return e;
-  const int per = (s.sweep == OEC_SWEEP_PAIR) ? 3 : 4;    // column scratch values per point
   const size_t plane = size_t(d.ni) * d.nk;                // points per row of the domain, all levels
+  size_t soff = 0;                                         // this slab's column scratch (elements)
   // one thread at a time enqueues onto the shared slab streams and events
   // (an event is re-recorded by the next apply only after this one's waits)
   std::lock_guard<std::mutex> lock(g_slab_mu);
@@ -932,8 +995,8 @@ cudaError_t run(const oec_schedule& s, int dtype, const Dom& d, const HV<typenam
     e = hdiff_to_compute(s, dtype, ds, ps.u, ps.v, ps.coeff, ud + before, vd + before, st);
     if (e == cudaSuccess) e = cudaEventRecord(ss->ev[x + 1], st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(ss->side[x], ss->ev[x + 1], 0);
-    if (e == cudaSuccess)
-      e = launch_sweep<P>(s, ds, ps, ud + before, vd + before, scr + per * before, dtr, ss->side[x]);
+    if (e == cudaSuccess) e = launch_sweep<P>(s, ds, ps, ud + before, vd + before, scr + soff, dtr, ss->side[x]);
+    soff += (sweep_scratch_elems(s, ds, ds.nj) + 15) / 16 * 16;   // next slab's lines start on 128 bytes
     if (e == cudaSuccess) e = cudaEventRecord(ss->done[x], ss->side[x]);
   }
   for (int x = 0; e == cudaSuccess && x < ns; ++x) e = cudaStreamWaitEvent(st, ss->done[x], 0);
@@ -962,16 +1025,18 @@ size_t hdiff_vadvc_scratch_bytes(const oec_schedule& s, int dtype, const Dom& d)
 
 cudaError_t hdiff_vadvc_launch(const oec_schedule& s, int dtype, const Dom& d, const void* u, const void* v,
                                const void* w, const void* coeff, void* u_out, void* v_out, double dtr, void* scratch,
-                               cudaStream_t st) {
+                               cudaStream_t st, bool batch_member) {
   const bool df = s.arith >= 1;   // arith 2: fixed-point hdiff producer, double-float column
   if (dtype == OEC_F64) {
     HV<double> p{(const double*)u, (const double*)v, (const double*)w, (const double*)coeff,
                  (double*)u_out, (double*)v_out, d.ni, d.nj, d.nk, d.sj, d.sk};
-    return df ? run<P64D>(s, dtype, d, p, dtr, (char*)scratch, st) : run<P64>(s, dtype, d, p, dtr, (char*)scratch, st);
+    return df ? run<P64D>(s, dtype, d, p, dtr, (char*)scratch, st, batch_member)
+              : run<P64>(s, dtype, d, p, dtr, (char*)scratch, st, batch_member);
   }
   HV<float> p{(const float*)u, (const float*)v, (const float*)w, (const float*)coeff,
               (float*)u_out, (float*)v_out, d.ni, d.nj, d.nk, d.sj, d.sk};
-  return df ? run<P32D>(s, dtype, d, p, dtr, (char*)scratch, st) : run<P32>(s, dtype, d, p, dtr, (char*)scratch, st);
+  return df ? run<P32D>(s, dtype, d, p, dtr, (char*)scratch, st, batch_member)
+            : run<P32>(s, dtype, d, p, dtr, (char*)scratch, st, batch_member);
 }
 
 size_t hdiff_vadvc_batch_slot_elems(const oec_schedule& s, int nk_max) {

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <cstring>
 
 namespace oec {
 
@@ -21,6 +22,49 @@ __device__ __forceinline__ void cp_async(T* smem, const T* gmem) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"((int)sizeof(T)) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+
+// L2 eviction priorities (createpolicy): values that are read again soon
+// (a column sweep's own recurrence values) stay while streamed fields, read
+// or written once, leave first.
+__device__ __forceinline__ uint64_t l2_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;\n" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t l2_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(p));
+  return p;
+}
+// cp_async with an L2 eviction priority
+template <typename T>
+__device__ __forceinline__ void cp_async_l2(T* smem, const T* gmem, uint64_t pol) {
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8 || sizeof(T) == 16, "cp.async copies 4, 8 or 16 bytes");
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], %2, %3;\n" ::"r"(s), "l"(gmem),
+               "n"((int)sizeof(T)), "l"(pol)
+               : "memory");
+}
+// store of a 4- or 8-byte value with an L2 eviction priority
+template <typename T>
+__device__ __forceinline__ void st_l2(T* gmem, const T& v, uint64_t pol) {
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte stores");
+  const size_t g = __cvta_generic_to_global(gmem);
+  if (sizeof(T) == 8) {
+    unsigned long long b;
+    memcpy(&b, &v, 8);
+    asm volatile("st.global.L2::cache_hint.b64 [%0], %1, %2;\n" ::"l"(g), "l"(b), "l"(pol) : "memory");
+  } else {
+    unsigned b;
+    memcpy(&b, &v, 4);
+    asm volatile("st.global.L2::cache_hint.b32 [%0], %1, %2;\n" ::"l"(g), "r"(b), "l"(pol) : "memory");
+  }
+}
+// drop the 128-byte L2 line at p (128-byte aligned) without writing it back:
+// for scratch that nothing reads again. Its contents become undefined.
+__device__ __forceinline__ void l2_discard(const void* p) {
+  asm volatile("discard.global.L2 [%0], 128;\n" ::"l"(__cvta_generic_to_global(p)) : "memory");
+}
 // wait until at most N of this thread's committed groups are still pending
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }

@@ -22,8 +22,9 @@
 namespace {
 
 // 64 MiB. The staged form needs 40 bytes per grid point in FP64 (hdiff(u),
-// hdiff(v) as double-float pairs, and g, e_u, e_v of the sweep) and 32 in FP32
-// (each rounded up to 256 bytes): up to 1,677,721 / 2,097,152 points. The
+// hdiff(v) as double-float pairs, and g, e_u, e_v of the sweep, whose rows are
+// padded to a multiple of 16 columns) and 32 in FP32 (each part rounded up to
+// 256 bytes): up to 1,677,721 / 2,097,152 points. The
 // fused form needs 24 * ceil16(ni) * ceil4(nj) * nk bytes (c', d'_u, d'_v per
 // column of its 16 x 4 tiles).
 constexpr size_t kNoallocScratchBytes = size_t(64) << 20;

@@ -121,3 +121,42 @@ def test_batch_config_ensemble_32_members_f32():
         gu = o[0].interior(lb, ub).cpu().numpy().astype(np.float64)
         gv = o[1].interior(lb, ub).cpu().numpy().astype(np.float64)
         assert max(rel_err(gu, ru), rel_err(gv, rv)) <= TOL["f32"]
+
+
+@pytest.mark.parametrize("dtype,arith", [("f32", 1), ("f64", 2), ("f32", 0)])
+def test_staged_batch_l2_sweep_on_large_members(dtype, arith):
+    """Batch members whose column scratch exceeds 48 MB run the column sweep's
+    L2 form (recurrence values kept in L2 with evict-last priority and dropped
+    once read, four back steps at a time). Column counts that are not multiples
+    of 16 and odd level counts (halves of unequal length, partial groups of
+    four back steps) give, member by member, the bits of the single applies,
+    which use the plain sweep; sampled column blocks match the oracle."""
+    from paper_2005_13014_gb300.api import Batch, Program, device_field
+    h = 3
+    shapes = [(1001, 300, 23), (517, 333, 37), (700, 120, 80), (37, 23, 11)]
+    prog = Program(programs.HDIFF_VADVC, dtype)
+    prog.set_schedule(fusion=1, tile_i=32, tile_j=8, k_chunk=4, arith=arith)
+    ms = _members(dtype, h, shapes=shapes, seed=300)
+    batch = Batch(prog, [(d, o, (0, 0, 0), n, (h, h, h)) for (_, d, o, n) in ms], [2.0])
+    rng = np.random.default_rng(11)
+    for graph in (True, False):
+        for (_, _, o, _) in ms:
+            for t in o:
+                t.tensor.fill_(3.0)
+        batch.apply(graph=graph)
+        torch.cuda.synchronize()
+        for (f, d, o, n) in ms:
+            single = [device_field(np.full_like(f["u"], 3.0), h, dtype) for _ in range(2)]
+            prog.apply(d, single, (0, 0, 0), n, (h, h, h), [2.0])
+            torch.cuda.synchronize()
+            for a, b in zip(o, single):
+                assert torch.equal(a.tensor, b.tensor)
+            del single
+    for (f, d, o, n) in ms:
+        i0, j0 = int(rng.integers(0, n[0] - 8)), int(rng.integers(0, n[1] - 8))
+        lb, ub = (i0, j0, 0), (i0 + 8, j0 + 8, n[2])
+        G = {k: S.Grid.storage(v, h) for k, v in f.items()}
+        ru, rv = S.hdiff_vadvc(G["u"], G["v"], G["w"], G["coeff"], lb, ub, 2.0)
+        gu = o[0].interior(lb, ub).cpu().numpy().astype(np.float64)
+        gv = o[1].interior(lb, ub).cpu().numpy().astype(np.float64)
+        assert max(rel_err(gu, ru), rel_err(gv, rv)) <= TOL[dtype]
