@@ -909,8 +909,10 @@ def run_testset(args):
 
 def run_ensemble(args):
     """32 uneven hdiff+vadvc members, FP32: one batch graph (fused: one
-    persistent launch; staged: concurrent per-member chains; form, tile and
-    arith picked by timing) vs 32 separate applies, plain and graph-captured."""
+    persistent launch of tile sweeps; staged on the warp-row producer: one
+    persistent launch of producer and column-sweep items; other staged
+    schedules: concurrent per-member chains; form, tile and arith picked by
+    timing) vs 32 separate applies, plain and graph-captured."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -935,8 +937,9 @@ def run_ensemble(args):
         prog.set_schedule(**c)
         b = Batch(prog, members, [2.0])
         ms = _timed(lambda _: b.apply(), 5, 2, stream)
-        form = "fused" if c["fusion"] == 0 else f"staged_kc{c['k_chunk']}"
-        tune[f"{form}_{c['tile_i']}x{c['tile_j']}_arith{c['arith']}"] = ms
+        form = "fused" if c["fusion"] == 0 else (
+            ("staged_persistent" if b.n_items > len(members) else "staged_chains") + f"_kc{c['k_chunk']}")
+        tune[f"{form}_{c['tile_i']}x{c['tile_j']}_u{c['unroll']}_st{c['staging']}_arith{c['arith']}"] = ms
         if best is None or ms < best[0]:
             best = (ms, c)
         del b
@@ -957,7 +960,9 @@ def run_ensemble(args):
     ms_sep_graph = _timed(lambda _: g.replay(), args.steps, 3, torch.cuda.current_stream())
     out = {"workload": "ensemble of 32 hdiff+vadvc members, FP32, halo 3, rows 16-byte aligned", "members": shapes,
            "points": pts,
-           "form": "fused persistent launch" if best[1]["fusion"] == 0 else "staged: concurrent member chains",
+           "form": ("fused persistent launch" if best[1]["fusion"] == 0 else
+                    "staged persistent launch (producer and column-sweep items)" if batch.n_items > len(members)
+                    else "staged: concurrent member chains"),
            "schedule": best[1], "tuning_ms": tune,
            "batched_graph": {"ms": ms_graph, "gpoints_per_s": pts / ms_graph / 1e6},
            "batched_direct": {"ms": ms_direct, "gpoints_per_s": pts / ms_direct / 1e6},

@@ -498,6 +498,13 @@ OEC_API int oec_device_status(void* cuda_stream);
  * reports OEC_ERR_TIMEOUT. No copies are involved; the GPU context stays
  * usable. Errors: OEC_ERR_INVALID_ARG, OEC_ERR_CUDA. */
 OEC_API int oec_device_wait_selftest(int polls, void* cuda_stream);
+/* The same for the persistent staged batch's wait on its per-row-block
+ * counters (see oec_batch_create): launch the batch kernel on one column-sweep
+ * item whose counter nothing releases; its wait gives up after `polls` polls
+ * (1..65536), records a timeout and skips the item, so the next
+ * oec_device_status reports OEC_ERR_TIMEOUT. Synchronises cuda_stream before
+ * returning. Errors: OEC_ERR_INVALID_ARG, OEC_ERR_CUDA. */
+OEC_API int oec_batch_wait_selftest(int polls, void* cuda_stream);
 OEC_API int oec_program_launch_count(oec_program_t p);
 OEC_API int oec_program_set_timing(oec_program_t p, int enable);
 OEC_API int oec_program_kernel_times(oec_program_t p, float* ms, int cap, int* n_applies, int* n_kernels);
@@ -521,12 +528,20 @@ typedef struct oec_batch_member {
  * - one CTA per resident slot on every SM - pulls (member, tile) items from an
  * atomic counter and runs the fused column sweep with the program's tile
  * shape and arithmetic; the counter reset and the launch are captured into
- * the graph. With a staged schedule (OEC_FUSE_NONE) every member's producer
- * and column-sweep launches form an independent branch of the graph (members
- * on up to 16 forked streams, largest first to the least-loaded one), so the
- * members' sweeps run concurrently. Device memory: the work table, the
- * counter and per-CTA scratch, or each staged member's scratch, owned by the
- * batch. The program and every member's fields must outlive the batch.
+ * the graph. With a staged schedule (OEC_FUSE_NONE) on FP32 fields with the
+ * warp-row producer (OEC_STAGE_WARP, unroll 1 or 2, the pair column sweep)
+ * and every member's rows 16-byte aligned (u, v, coeff at the domain corner,
+ * j/k strides, ni a multiple of 4): one persistent kernel takes, in ticket
+ * order, producer items (a block of 4 x unroll rows of one member: hdiff of
+ * u and v into the member's buffers) and column-sweep items (64 columns of
+ * one member), a sweep item waiting - bounded, see oec_batch_wait_selftest -
+ * on counters of the row blocks it needs; the counters' reset and the launch
+ * are captured into the graph. Other staged schedules: every member's
+ * producer and column-sweep launches form an independent branch of the graph
+ * (members on up to 16 forked streams, largest first to the least-loaded
+ * one), so the members' sweeps run concurrently. Device memory: the work
+ * table, the counters and per-CTA or per-member scratch, owned by the batch.
+ * The program and every member's fields must outlive the batch.
  * params: the program's scalars. Errors: as oec_program_apply, and
  * OEC_ERR_UNSUPPORTED for other program kinds.
  */
@@ -534,9 +549,11 @@ OEC_API int oec_batch_create(oec_program_t p, const oec_batch_member* members, i
                              int n_params, oec_batch_t* out);
 /* Launch the captured graph on cuda_stream (asynchronous). */
 OEC_API int oec_batch_apply(oec_batch_t b, void* cuda_stream);
-/* Launch the persistent kernel directly (no graph) on cuda_stream. */
+/* The same work without the graph on cuda_stream: the persistent kernel(s)
+ * launched directly, or the staged members' launches one after another. */
 OEC_API int oec_batch_apply_direct(oec_batch_t b, void* cuda_stream);
-/* Work items (tiles) and persistent CTAs of a batch. */
+/* Work items (tiles, or producer and sweep items; staged chains: members) and
+ * persistent CTAs (staged chains: streams) of a batch. */
 OEC_API int oec_batch_info(oec_batch_t b, int* n_items, int* n_ctas);
 /* Free the batch (NULL is a no-op); waits for its device work to finish. */
 OEC_API void oec_batch_destroy(oec_batch_t b);

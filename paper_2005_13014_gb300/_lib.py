@@ -104,6 +104,7 @@ def lib():
         "oec_program_algorithmic_bytes": (C.c_int, [P, I64x3, I64x3, C.POINTER(C.c_int64)]),
         "oec_device_status": (C.c_int, [P]),
         "oec_device_wait_selftest": (C.c_int, [C.c_int, P]),
+        "oec_batch_wait_selftest": (C.c_int, [C.c_int, P]),
         "oec_costmodel_save": (C.c_int, [P, C.c_char_p]),
         "oec_costmodel_load": (C.c_int, [C.c_char_p, C.POINTER(P)]),
         "oec_program_autotune_model": (C.c_int, [P, P, C.POINTER(FieldDesc), C.c_int, C.POINTER(FieldDesc), C.c_int,

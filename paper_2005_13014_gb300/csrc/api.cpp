@@ -589,6 +589,14 @@ int oec_device_wait_selftest(int polls, void* cuda_stream) {
   return OEC_OK;
 }
 
+int oec_batch_wait_selftest(int polls, void* cuda_stream) {
+  clear_error();
+  if (polls < 1 || polls > 65536) return fail(OEC_ERR_INVALID_ARG, "polls must be in 1..65536");
+  const cudaError_t e = pstaged_wait_selftest_launch((unsigned)polls, (cudaStream_t)cuda_stream);
+  if (e != cudaSuccess) return cuda_fail(e, "batch wait self-test");
+  return OEC_OK;
+}
+
 int oec_device_status(void* cuda_stream) {
   clear_error();
   unsigned n = 0;

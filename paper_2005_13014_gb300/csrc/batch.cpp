@@ -1,6 +1,9 @@
 // batch.cpp - ensembles of domains, captured into one CUDA graph
 // (include/oec.h, oec_batch_*). Fused schedules: one persistent launch over
-// the (member, tile) work items of every member. Staged schedules: every
+// the (member, tile) work items of every member. Staged schedules with FP32
+// fields on the warp-row producer (rows 16-byte aligned): one persistent
+// launch over producer and column-sweep items of every member, the sweeps
+// waiting (bounded) on per-row-block counters. Other staged schedules: every
 // member's producer + column-sweep chain is an independent branch of the
 // graph (members spread over up to 16 forked streams), so the members' column
 // sweeps - latency-bound, with few warps each - run concurrently and fill the
@@ -8,6 +11,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
+#include <deque>
 #include <new>
 #include <numeric>
 #include <vector>
@@ -38,6 +43,13 @@ struct oec_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int dev = 0;
+  // persistent staged form: one launch over every member's items
+  bool persistent = false;
+  oec::PSLaunch ps{};
+  oec::PSMember* d_psm = nullptr;
+  oec::PSItem* d_items = nullptr;
+  int* d_done = nullptr;
+  int n_done = 0;
 };
 
 namespace {
@@ -47,12 +59,15 @@ void release(oec_batch* b) {
   int cur = 0;
   cudaGetDevice(&cur);
   cudaSetDevice(b->dev);
-  if (b->exec || b->d_members) cudaDeviceSynchronize();
+  if (b->exec || b->d_members || b->d_items) cudaDeviceSynchronize();
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->d_members) cudaFree(b->d_members);
   if (b->d_counter) cudaFree(b->d_counter);
   if (b->d_scratch) cudaFree(b->d_scratch);
+  if (b->d_psm) cudaFree(b->d_psm);
+  if (b->d_items) cudaFree(b->d_items);
+  if (b->d_done) cudaFree(b->d_done);
   cudaSetDevice(cur);
   delete b;
 }
@@ -75,6 +90,138 @@ cudaError_t record_staged(const oec_batch* b, char* scratch, const std::vector<c
     if (e == cudaSuccess) e = r;
   }
   return e;
+}
+
+// counters reset, then the persistent launch
+cudaError_t record_pstaged(const oec_batch* b, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_done, 0, sizeof(int) * std::max(1, b->n_done), st);
+  if (e == cudaSuccess) e = oec::hdiff_vadvc_pstaged_launch(b->sched, b->ps, st);
+  return e;
+}
+
+// Members the persistent form can run: rows 16-byte aligned at the domain
+// corner for the warp-row producer (pointers, j/k strides, and ni for its
+// hdiff(u), hdiff(v) buffers).
+bool pstaged_aligned(const oec_batch* b) {
+  for (const StagedMember& m : b->staged_members) {
+    const uintptr_t a = (uintptr_t)m.u | (uintptr_t)m.v | (uintptr_t)m.coeff;
+    if (a % 16 != 0 || m.d.sj % 4 != 0 || m.d.sk % 4 != 0 || m.d.ni % 4 != 0) return false;
+  }
+  return true;
+}
+
+// The persistent staged form: the member table, the work items in ticket
+// order, and a graph of (reset counters, one launch). Producer items go row
+// block by row block, member after member; a sweep item (64 columns) follows
+// once every row block it needs has its producer items at least `lag` tickets
+// back (two per resident CTA), so that its rows are usually done and still in
+// L2 when it starts.
+int build_pstaged(oec_batch* b) {
+  using namespace oec;
+  const oec_schedule& s = b->sched;
+  const int U = s.unroll, rows = 4 * U;
+  constexpr int W = 128, COLS = 64;   // producer columns per CTA (32 lanes x 4 floats), sweep columns
+  std::vector<PSMember> tab;
+  bool o32 = true, discard = false;
+  int row_base = 0;
+  for (const StagedMember& sm : b->staged_members) {
+    PSMember m{};
+    const Dom& d = sm.d;
+    size_t ud = 0, vd = 0;
+    hdiff_vadvc_scratch_parts(s, b->dtype, d, &ud, &vd);
+    char* scr = (char*)b->d_scratch + sm.scratch_off;
+    m.u = sm.u; m.v = sm.v; m.w = sm.w; m.coeff = sm.coeff; m.uo = sm.uo; m.vo = sm.vo;
+    m.ud = scr + ud; m.vd = scr + vd; m.scr = scr;
+    m.sj = d.sj; m.sk = d.sk;
+    const int64_t ncol = (int64_t)d.ni * d.nj;
+    m.ncolp = hdiff_vadvc_pair_pitch(ncol);
+    m.ni = d.ni; m.nj = d.nj; m.nk = d.nk;
+    m.kchunk = (s.k_chunk <= 0 || s.k_chunk > d.nk) ? d.nk : s.k_chunk;
+    m.nkz = (d.nk + m.kchunk - 1) / m.kchunk;
+    m.row_base = row_base;
+    row_base += (d.nj + rows - 1) / rows;
+    m.need = ((d.ni + W - 1) / W) * 2 * m.nkz;
+    o32 = o32 && use_int32(s, d) && 4 * m.ncolp * d.nk < INT32_MAX;
+    discard = discard || size_t(24) * m.ncolp * d.nk > hdiff_vadvc_discard_above_bytes();
+    tab.push_back(m);
+  }
+  PSLaunch& L = b->ps;
+  L.unroll = U;
+  L.o32 = o32;
+  L.discard = discard;
+  L.dtr = b->dtr;
+  L.polls = 1u << 22;
+  int sms = 0, per_sm = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->dev);
+  if (e == cudaSuccess) e = hdiff_vadvc_pstaged_blocks_per_sm(s, L, &per_sm);
+  if (e != cudaSuccess) return cuda_fail(e, "persistent batch occupancy");
+  if (per_sm < 1) return fail(OEC_ERR_UNSUPPORTED, "persistent batch kernel does not fit on an SM");
+  const int64_t lag = 2 * (int64_t)sms * per_sm;
+  // items in ticket order
+  std::vector<PSItem> items;
+  struct Pending { int m, g, lo, hi; int64_t dep; };
+  std::deque<Pending> ready;
+  auto flush = [&](bool all) {
+    while (!ready.empty() && (all || ready.front().dep + lag <= (int64_t)items.size())) {
+      const Pending& q = ready.front();
+      items.push_back(PSItem{~q.m, q.g, q.lo, q.hi});
+      ready.pop_front();
+    }
+  };
+  for (int mi = 0; mi < (int)tab.size(); ++mi) {
+    const PSMember& m = tab[mi];
+    const int64_t ncol = (int64_t)m.ni * m.nj;
+    const int tx = (m.ni + W - 1) / W, ty = (m.nj + rows - 1) / rows;
+    int64_t g = 0;
+    const int64_t groups = (ncol + COLS - 1) / COLS;
+    for (int by = 0; by < ty; ++by) {
+      for (int bz = 0; bz < 2 * m.nkz; ++bz)
+        for (int bx = 0; bx < tx; ++bx) {
+          items.push_back(PSItem{mi, bx, by, bz});
+          flush(false);
+        }
+      // the sweep groups whose rows all lie in row blocks 0..by
+      const int64_t dep = (int64_t)items.size() - 1;
+      for (; g < groups; ++g) {
+        const int64_t c0 = g * COLS, c1 = std::min(ncol, c0 + COLS) - 1;
+        const int lo = int(c0 / m.ni) / rows, hi = int(c1 / m.ni) / rows;
+        if (hi > by) break;
+        ready.push_back(Pending{mi, (int)g, lo, hi, dep});
+      }
+    }
+  }
+  flush(true);
+  if (items.size() > (size_t)INT32_MAX) return fail(OEC_ERR_UNSUPPORTED, "more than 2^31 batch items");
+  L.n_items = (int)items.size();
+  L.grid = (int)std::min<int64_t>(L.n_items, (int64_t)sms * per_sm);
+  b->n_done = row_base;
+  e = cudaMalloc(&b->d_psm, sizeof(PSMember) * tab.size());
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_items, sizeof(PSItem) * items.size());
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_done, sizeof(int) * std::max(1, b->n_done));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_psm, tab.data(), sizeof(PSMember) * tab.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_items, items.data(), sizeof(PSItem) * items.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "persistent batch tables");
+  L.members = b->d_psm;
+  L.items = b->d_items;
+  L.ticket = b->d_counter;
+  L.done = b->d_done;
+  L.timeouts = wait_timeout_counter();
+  if (!L.timeouts) return fail(OEC_ERR_CUDA, "device wait counter not found");
+  b->persistent = true;
+  cudaStream_t cap = nullptr;
+  e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t r = record_pstaged(b, cap);
+    e = cudaStreamEndCapture(cap, &b->graph);
+    if (e == cudaSuccess) e = r;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+  if (cap) cudaStreamDestroy(cap);
+  if (e != cudaSuccess) return cuda_fail(e, "persistent batch capture");
+  return OEC_OK;
 }
 
 int create_staged(oec_program* p, const std::vector<oec::HVMember>& tab, double dtr, oec_batch_t* out) {
@@ -106,6 +253,12 @@ int create_staged(oec_program* p, const std::vector<oec::HVMember>& tab, double 
   }
   cudaError_t e = cudaMalloc(&b->d_scratch, std::max<size_t>(off, 256));
   if (e != cudaSuccess) { release(b); return cuda_fail(e, "batch scratch"); }
+  if (hdiff_vadvc_pstaged_ok(b->sched, b->dtype) && pstaged_aligned(b)) {   // one persistent launch
+    const int rc = build_pstaged(b);
+    if (rc) { release(b); return rc; }
+    *out = b;
+    return OEC_OK;
+  }
   cudaStream_t cap = nullptr;
   std::vector<cudaStream_t> streams(b->n_streams, nullptr);
   std::vector<cudaEvent_t> ev(b->n_streams + 1, nullptr);
@@ -260,6 +413,10 @@ int oec_batch_apply_direct(oec_batch_t b, void* stream) {
   clear_error();
   NvtxRange range("oec_batch_apply_direct");
   if (!b) return fail(OEC_ERR_INVALID_ARG, "null batch");
+  if (b->persistent) {   // counters reset and the launch, on the caller's stream
+    cudaError_t e = record_pstaged(b, (cudaStream_t)stream);
+    return e == cudaSuccess ? OEC_OK : cuda_fail(e, "batch launch");
+  }
   if (b->staged) {   // the same launches, one after another on the caller's stream
     cudaError_t e = record_staged(b, (char*)b->d_scratch, std::vector<cudaStream_t>{(cudaStream_t)stream});
     return e == cudaSuccess ? OEC_OK : cuda_fail(e, "batch launch");
@@ -272,6 +429,11 @@ int oec_batch_apply_direct(oec_batch_t b, void* stream) {
 int oec_batch_info(oec_batch_t b, int* n_items, int* n_ctas) {
   clear_error();
   if (!b || !n_items || !n_ctas) return fail(OEC_ERR_INVALID_ARG, "null argument");
+  if (b->persistent) {
+    *n_items = b->ps.n_items;
+    *n_ctas = b->ps.grid;
+    return OEC_OK;
+  }
   *n_items = b->staged ? (int)b->staged_members.size() : b->launch.total_items;
   *n_ctas = b->staged ? b->n_streams : b->launch.grid;
   return OEC_OK;

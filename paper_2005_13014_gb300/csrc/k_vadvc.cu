@@ -29,6 +29,7 @@
 #include "kcommon.cuh"
 #include "kernels.h"
 #include "k_vadvc.cuh"
+#include "k_hdiff_vec.cuh"
 
 namespace oec {
 namespace {
@@ -372,17 +373,26 @@ template <> __device__ __forceinline__ df64 wsum<df64, double>(double a, double 
 // writing them back, four back steps (12 lines of a half-warp, one per lane)
 // at a time. The values of a half's last step are used from registers and
 // not stored.
+// shared-memory ring of one block of the column sweep (bytes)
+template <class P, int NC, int DEPTH>
+__host__ __device__ constexpr size_t thomas_ring_bytes() {
+  constexpr size_t FB = size_t(DEPTH) * 2 * NC * (2 * sizeof(typename P::C) + 2 * sizeof(typename P::S));
+  constexpr size_t BB = size_t(DEPTH) * 2 * NC * 3 * sizeof(typename P::R);
+  return FB > BB ? FB : BB;
+}
+
+// One block of the column sweep: NC columns (2 NC threads), the block-th
+// group of NC columns of the domain; ring: thomas_ring_bytes() of shared
+// memory, 16-byte aligned.
 template <class P, int NC, int DEPTH, bool DTR_P2, class Off, bool DISCARD>
-__global__ void __launch_bounds__(2 * NC) hv_thomas_kernel(HV<typename P::S> p, const typename P::C* __restrict__ ud,
-                                                           const typename P::C* __restrict__ vd, double dtr_d,
-                                                           typename P::R* __restrict__ scr, int64_t ncolp) {
+__device__ __forceinline__ void hv_thomas_block(const HV<typename P::S>& p, const typename P::C* __restrict__ ud,
+                                                const typename P::C* __restrict__ vd, double dtr_d,
+                                                typename P::R* __restrict__ scr, int64_t ncolp, int64_t block,
+                                                unsigned char* ring) {
   typedef typename P::S S;
   typedef typename P::C C;
   typedef typename P::R R;
   constexpr int NT = 2 * NC;
-  constexpr size_t FB = size_t(DEPTH) * NT * (2 * sizeof(C) + 2 * sizeof(S));
-  constexpr size_t BB = size_t(DEPTH) * NT * 3 * sizeof(R);
-  __shared__ __align__(16) unsigned char ring[FB > BB ? FB : BB];
   C(*su)[NT] = reinterpret_cast<C(*)[NT]>(ring);
   C(*sv)[NT] = su + DEPTH;
   S(*sw0)[NT] = reinterpret_cast<S(*)[NT]>(sv + DEPTH);
@@ -390,7 +400,7 @@ __global__ void __launch_bounds__(2 * NC) hv_thomas_kernel(HV<typename P::S> p, 
   const int t = threadIdx.x, lane = t & 31;
   const bool down = lane >= 16;
   const int64_t ncol = (int64_t)p.ni * p.nj;
-  const int64_t col = (int64_t)blockIdx.x * NC + (t >> 5) * 16 + (lane & 15);
+  const int64_t col = block * NC + (t >> 5) * 16 + (lane & 15);
   const bool active = col < ncol;   // inactive threads only join the barrier and the exchange
   // the active lanes of this thread's half-warp (they share scratch lines)
   const unsigned hmask = __ballot_sync(0xFFFFFFFFu, active) & (0xFFFFu << (lane & 16));
@@ -592,6 +602,14 @@ __global__ void __launch_bounds__(2 * NC) hv_thomas_kernel(HV<typename P::S> p, 
   }
   if (DISCARD && ((nsteps - 1) & 3)) drop4((nsteps - 1) & ~3, (nsteps - 1) & 3);
   cp_async_wait<0>();
+}
+
+template <class P, int NC, int DEPTH, bool DTR_P2, class Off, bool DISCARD>
+__global__ void __launch_bounds__(2 * NC) hv_thomas_kernel(HV<typename P::S> p, const typename P::C* __restrict__ ud,
+                                                           const typename P::C* __restrict__ vd, double dtr_d,
+                                                           typename P::R* __restrict__ scr, int64_t ncolp) {
+  __shared__ __align__(16) unsigned char ring[thomas_ring_bytes<P, NC, DEPTH>()];
+  hv_thomas_block<P, NC, DEPTH, DTR_P2, Off, DISCARD>(p, ud, vd, dtr_d, scr, ncolp, blockIdx.x, ring);
 }
 
 // The same column sweep with the two fields in separate warps (schedule
@@ -922,6 +940,98 @@ cudaError_t launch_sweep(const oec_schedule& s, const Dom& d, const HV<typename 
   return cudaGetLastError();
 }
 
+// ---- persistent staged batch ------------------------------------------------
+// Every CTA (128 threads) takes work items in ticket order from an atomic
+// counter until none is left. A producer item is one CTA of the warp-row hdiff
+// kernel for one member (both fields into its hdiff(u), hdiff(v) buffers);
+// when it is done its thread 0 releases one count on the member's row-block
+// counter. A sweep item is one block of 64 columns of the column sweep; its
+// thread 0 first waits until the counters of the row blocks those columns
+// need are complete. Tickets put every producer item that a sweep item needs
+// before it, and producer items never wait, so every wait ends without any
+// assumption on which CTAs are resident: the items it waits for were taken by
+// running CTAs. The host orders the items so that a sweep item comes well
+// after its producers (the rows in between stay in L2). A wait is bounded: it
+// gives up after `polls` polls, counts a timeout and skips the item.
+constexpr int kPSDepth = 16;    // column sweep ring depth
+constexpr int kPSCols = 64;     // columns per sweep item (128 threads)
+
+__device__ __forceinline__ bool ps_wait_geq(const int* p, int need, unsigned polls) {
+  for (unsigned n = 0; n < polls; ++n) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+    if (v >= need) return true;
+    __nanosleep(256);
+  }
+  return false;
+}
+
+template <class P, int U, class Off, bool DISCARD>
+__global__ void __launch_bounds__(2 * kPSCols) hv_pstaged_kernel(PSLaunch L) {
+  typedef typename P::S S;
+  typedef typename P::C C;
+  typedef typename P::R R;
+  extern __shared__ __align__(16) unsigned char ps_ring[];
+  __shared__ int s_item, s_ok;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(L.ticket, 1);
+    __syncthreads();
+    const int it = s_item;
+    if (it >= L.n_items) break;
+    const PSItem item = L.items[it];
+    if (item.x >= 0) {   // producer
+      const PSMember& m = L.members[item.x];
+      hdiff_vec_block<P, U, Off, 2, true>((const S*)m.u, (const S*)m.coeff, (S*)m.ud, m.ni, m.nj, m.nk, m.sj, m.sk,
+                                          m.kchunk, m.ni, (int64_t)m.ni * m.nj, m.nkz, (const S*)m.v, (S*)m.vd,
+                                          item.y, item.z, item.w);
+      __syncthreads();   // every store of this item is issued
+      if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(L.done + m.row_base + item.z, 1);
+      }
+    } else {             // column sweep
+      const PSMember& m = L.members[~item.x];
+      if (threadIdx.x == 0) {
+        bool ok = true;
+        for (int b = item.z; ok && b <= item.w; ++b) ok = ps_wait_geq(L.done + m.row_base + b, m.need, L.polls);
+        if (!ok) atomicAdd(L.timeouts, 1u);
+        s_ok = ok;
+      }
+      __syncthreads();
+      if (s_ok) {
+        const HV<S> p{(const S*)m.u, (const S*)m.v, (const S*)m.w, (const S*)m.coeff, (S*)m.uo, (S*)m.vo,
+                      m.ni, m.nj, m.nk, m.sj, m.sk};
+        hv_thomas_block<P, kPSCols, kPSDepth, false, Off, DISCARD>(p, (const C*)m.ud, (const C*)m.vd, L.dtr,
+                                                                   (R*)m.scr, m.ncolp, item.y, ps_ring);
+      }
+    }
+    __syncthreads();   // s_item, s_ok and the ring are free for the next item
+  }
+}
+
+template <class P>
+cudaError_t pstaged_dispatch(const PSLaunch& L, bool query, int* per_sm, cudaStream_t st) {
+  const size_t smem = thomas_ring_bytes<P, kPSCols, kPSDepth>();
+#define OEC_PS(U, OFF, D)                                                                            \
+  {                                                                                                   \
+    auto k = hv_pstaged_kernel<P, U, OFF, D>;                                                        \
+    /* the ring and the item slots together pass 48 KB: opt in */                                    \
+    cudaError_t ea = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+    if (ea != cudaSuccess) return ea;                                                                 \
+    if (query) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k, 2 * kPSCols, smem);   \
+    k<<<L.grid, 2 * kPSCols, smem, st>>>(L);                                                          \
+    return cudaGetLastError();                                                                        \
+  }
+#define OEC_PS_D(U, OFF) \
+  if (L.discard) OEC_PS(U, OFF, true) else OEC_PS(U, OFF, false)
+#define OEC_PS_O(U) \
+  if (L.o32) { OEC_PS_D(U, int) } else { OEC_PS_D(U, int64_t) }
+  if (L.unroll == 2) { OEC_PS_O(2) } else { OEC_PS_O(1) }
+#undef OEC_PS_O
+#undef OEC_PS_D
+#undef OEC_PS
+}
+
 // The staged form's slab streams and their events (one set per device, made
 // on first use): with slabs > 1 the producer of every slab runs on the
 // caller's stream and the column sweep of slab s on stream s once producer s
@@ -1037,6 +1147,78 @@ cudaError_t hdiff_vadvc_launch(const oec_schedule& s, int dtype, const Dom& d, c
               (float*)u_out, (float*)v_out, d.ni, d.nj, d.nk, d.sj, d.sk};
   return df ? run<P32D>(s, dtype, d, p, dtr, (char*)scratch, st, batch_member)
             : run<P32>(s, dtype, d, p, dtr, (char*)scratch, st, batch_member);
+}
+
+bool hdiff_vadvc_pstaged_ok(const oec_schedule& s, int dtype) {
+  return dtype == OEC_F32 && s.fusion == OEC_FUSE_NONE && s.staging == OEC_STAGE_WARP &&
+         (s.unroll == 1 || s.unroll == 2) && s.sweep == OEC_SWEEP_PAIR && (s.arith == 0 || s.arith == 1);
+}
+
+void hdiff_vadvc_scratch_parts(const oec_schedule& s, int dtype, const Dom& d, size_t* ud, size_t* vd) {
+  const Layout l = layout(s, dtype, d);
+  *ud = l.ud;
+  *vd = l.vd;
+}
+
+int64_t hdiff_vadvc_pair_pitch(int64_t ncol) { return pair_pitch(ncol); }
+
+size_t hdiff_vadvc_discard_above_bytes() { return kDiscardAboveBytes; }
+
+cudaError_t hdiff_vadvc_pstaged_blocks_per_sm(const oec_schedule& s, const PSLaunch& L, int* per_sm) {
+  return s.arith == 1 ? pstaged_dispatch<P32D>(L, true, per_sm, nullptr)
+                      : pstaged_dispatch<P32>(L, true, per_sm, nullptr);
+}
+
+cudaError_t hdiff_vadvc_pstaged_launch(const oec_schedule& s, const PSLaunch& L, cudaStream_t st) {
+  cudaError_t e = s.arith == 1 ? pstaged_dispatch<P32D>(L, false, nullptr, st)
+                               : pstaged_dispatch<P32>(L, false, nullptr, st);
+  if (e == cudaSuccess) launched(st);
+  return e;
+}
+
+// Give-up path of the persistent batch's wait: one sweep item whose row-block
+// counter nothing releases (no producer items), so its wait gives up after
+// `polls` polls, counts a timeout and skips the item. The buffers are valid
+// for the 4-column domain the item names, though nothing reads them.
+cudaError_t pstaged_wait_selftest_launch(unsigned polls, cudaStream_t st) {
+  constexpr size_t kRegion = 256, kBytes = 16 * kRegion;
+  char* buf = nullptr;
+  cudaError_t e = cudaMalloc(&buf, kBytes);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(buf, 0, kBytes, st);
+  PSMember m{};
+  auto at = [&](int r) { return (void*)(buf + (r + 1) * kRegion); };   // a region, room before it
+  m.u = at(0); m.v = at(1); m.w = at(2); m.coeff = at(3); m.uo = at(4); m.vo = at(5);
+  m.ud = at(6); m.vd = at(7); m.scr = at(8);
+  m.sj = 4; m.sk = 4; m.ncolp = 16;
+  m.ni = 4; m.nj = 1; m.nk = 1; m.kchunk = 1; m.nkz = 1;
+  m.row_base = 0;
+  m.need = 1;
+  const PSItem item{~0, 0, 0, 0};
+  PSMember* dm = (PSMember*)(buf + 12 * kRegion);
+  PSItem* di = (PSItem*)(buf + 13 * kRegion);
+  int* ticket = (int*)(buf + 14 * kRegion);
+  int* done = (int*)(buf + 15 * kRegion);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dm, &m, sizeof(m), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(di, &item, sizeof(item), cudaMemcpyHostToDevice, st);
+  PSLaunch L{};
+  L.members = dm;
+  L.items = di;
+  L.n_items = 1;
+  L.ticket = ticket;
+  L.done = done;
+  L.timeouts = wait_timeout_counter();
+  L.polls = polls;
+  L.dtr = 2.0;
+  L.grid = 1;
+  L.unroll = 1;
+  L.o32 = true;
+  L.discard = false;
+  if (e == cudaSuccess && !L.timeouts) e = cudaErrorInvalidSymbol;
+  if (e == cudaSuccess) e = pstaged_dispatch<P32D>(L, false, nullptr, st);
+  const cudaError_t e2 = cudaStreamSynchronize(st);   // the host copies' sources and the buffer outlive the kernel
+  cudaFree(buf);
+  return e != cudaSuccess ? e : e2;
 }
 
 size_t hdiff_vadvc_batch_slot_elems(const oec_schedule& s, int nk_max) {

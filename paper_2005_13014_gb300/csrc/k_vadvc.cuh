@@ -34,4 +34,41 @@ struct HVBatchLaunch {
   int grid;                 // persistent CTAs
 };
 
+// Persistent staged batch (FP32 fields, vector-row producer): one member in
+// the device-side table. Pointers at the domain's lower corner; ud, vd, scr
+// are the member's hdiff(u), hdiff(v) buffers (domain layout) and column
+// scratch (row pitch ncolp).
+struct PSMember {
+  const void *u, *v, *w, *coeff;
+  void *uo, *vo;
+  void *ud, *vd, *scr;
+  int64_t sj, sk, ncolp;
+  int ni, nj, nk, kchunk, nkz;
+  int row_base;   // this member's first row-block counter
+  int need;       // producer items per row block (tiles along i x 2 fields x nkz)
+  int pad;
+};
+
+// One work item, in ticket order: x = member for a producer item (bx, by, bz
+// = y, z, w: the warp-row kernel's block indices), or ~member for a sweep item
+// (y = group of 64 columns, z..w = the row blocks it needs).
+struct PSItem {
+  int x, y, z, w;
+};
+
+struct PSLaunch {
+  const PSMember* members;   // device memory
+  const PSItem* items;       // device memory, n_items entries
+  int n_items;
+  int* ticket;               // device int, zero before the launch
+  int* done;                 // device ints, one per (member, row block), zero before the launch
+  unsigned* timeouts;        // device counter of waits that gave up
+  unsigned polls;            // poll limit of one wait
+  double dtr;
+  int grid;
+  int unroll;                // rows per warp of the producer (1 or 2)
+  bool o32;                  // every member's offsets fit 32 bits
+  bool discard;              // the column sweep's L2 form
+};
+
 }  // namespace oec

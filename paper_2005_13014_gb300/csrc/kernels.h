@@ -93,6 +93,21 @@ cudaError_t hdiff_vadvc_segments_launch(int nseg, int dtype, int arith, const Do
                                         const void* w, const void* coeff, void* u_out, void* v_out,
                                         const void* ud, const void* vd, double dtr, void* scr, bool o32,
                                         cudaStream_t st);
+// persistent staged batch (FP32 fields, vector-row producer; k_vadvc.cu):
+// whether a schedule has it, a member's hdiff(u) / hdiff(v) offsets in its
+// scratch, the column scratch row pitch, the scratch size above which the
+// column sweep takes its L2 form, the CTAs per SM, and the launch
+bool hdiff_vadvc_pstaged_ok(const oec_schedule& s, int dtype);
+void hdiff_vadvc_scratch_parts(const oec_schedule& s, int dtype, const Dom& d, size_t* ud, size_t* vd);
+int64_t hdiff_vadvc_pair_pitch(int64_t ncol);
+size_t hdiff_vadvc_discard_above_bytes();
+cudaError_t hdiff_vadvc_pstaged_blocks_per_sm(const oec_schedule& s, const PSLaunch& L, int* per_sm);
+cudaError_t hdiff_vadvc_pstaged_launch(const oec_schedule& s, const PSLaunch& L, cudaStream_t st);
+// the persistent batch's give-up path: one sweep item whose counter is never
+// released; waits for the kernel before returning
+cudaError_t pstaged_wait_selftest_launch(unsigned polls, cudaStream_t st);
+// device counter of bounded waits that gave up (k_hdiff_vec.cu)
+unsigned* wait_timeout_counter();
 // batched persistent form (ensembles of domains)
 size_t hdiff_vadvc_batch_slot_elems(const oec_schedule& s, int nk_max);
 int hdiff_vadvc_batch_blocks_per_sm(const oec_schedule& s, int dtype);

@@ -138,6 +138,8 @@ def test_apply_host_validation_without_gpu(liboec):
 def test_wait_selftest_validation_without_gpu(liboec):
     assert L.lib().oec_device_wait_selftest(0, None) == -1
     assert L.lib().oec_device_wait_selftest(70000, None) == -1
+    assert L.lib().oec_batch_wait_selftest(0, None) == -1
+    assert L.lib().oec_batch_wait_selftest(70000, None) == -1
 
 
 def test_bad_schedule_rejected(liboec):

@@ -128,6 +128,22 @@ def test_bounded_wait_gives_up_and_is_reported():
     assert lib.oec_device_wait_selftest(0, None) == -1
 
 
+def test_batch_counter_wait_gives_up_and_is_reported():
+    """The persistent staged batch's bounded wait on its row-block counters: a
+    sweep item whose counter nothing releases gives up after its poll limit,
+    skips the item, is reported once by oec_device_status, and the context
+    keeps working."""
+    from paper_2005_13014_gb300 import _lib as L
+    lib = L.lib()
+    assert lib.oec_device_status(None) == 0
+    assert lib.oec_batch_wait_selftest(64, None) == 0
+    assert lib.oec_device_status(None) == -10   # OEC_ERR_TIMEOUT
+    assert "gave up" in lib.oec_last_error().decode()
+    assert lib.oec_device_status(None) == 0
+    t = torch.ones(1024, device="cuda")
+    assert float((t * 3).sum()) == 3072.0
+
+
 def test_injected_scratch_allocation_failure(monkeypatch):
     """OEC_FAULT=alloc: an apply that needs scratch returns OEC_ERR_CUDA with
     the reason and enqueues nothing; without it the same program runs and
