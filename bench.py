@@ -147,7 +147,8 @@ def _kernels_of(sched):
                  "fields": ("u", "v", "w", "coeff", "u_out", "v_out"), "profile": None}]
     sweep = "hv_thomas_split_kernel" if sched.get("sweep", 0) == 1 else "hv_thomas_kernel"
     hd = "hdiff_fixed_kernel" if arith == 2 else "hdiff_smem_kernel"
-    return [{"name": hd, "src": ["k_hdiff.cu", "fixedpt.cuh"] + common, "flops": FLOPS_HDIFF, "fields": ("u", "v", "coeff"),
+    hsrc = ["k_hdiff.cu", "k_hdiff_fixed.cuh", "fixedpt.cuh"] if arith == 2 else ["k_hdiff.cu"]
+    return [{"name": hd, "src": hsrc + common, "flops": FLOPS_HDIFF, "fields": ("u", "v", "coeff"),
              "profile": f"{hd}_f64_2fields_128x128x80.md" if arith == 2 else None},
             {"name": sweep, "src": ["k_vadvc.cu"] + common, "flops": FLOPS_COLUMN,
              "fields": ("w", "u_out", "v_out"),
