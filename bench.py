@@ -148,8 +148,10 @@ def _kernels_of(sched):
     sweep = "hv_thomas_split_kernel" if sched.get("sweep", 0) == 1 else "hv_thomas_kernel"
     hd = "hdiff_fixed_kernel" if arith == 2 else "hdiff_smem_kernel"
     hsrc = ["k_hdiff.cu", "k_hdiff_fixed.cuh", "fixedpt.cuh"] if arith == 2 else ["k_hdiff.cu"]
+    rows = sched.get("unroll", 1)   # the producer's rows per thread: a summary of its own
     return [{"name": hd, "src": hsrc + common, "flops": FLOPS_HDIFF, "fields": ("u", "v", "coeff"),
-             "profile": f"{hd}_f64_2fields_128x128x80.md" if arith == 2 else None},
+             "profile": (f"{hd}_f64_2fields_128x128x80" + (f"_{rows}rows" if rows != 1 else "") + ".md")
+             if arith == 2 else None},
             {"name": sweep, "src": ["k_vadvc.cu"] + common, "flops": FLOPS_COLUMN,
              "fields": ("w", "u_out", "v_out"),
              "profile": f"{sweep}_f64_128x128x80.md" if arith == 2 else None}]

@@ -893,7 +893,11 @@ cudaError_t launch_sweep(const oec_schedule& s, const Dom& d, const HV<typename 
                          const typename P::C* ud, const typename P::C* vd, typename P::R* scr, double dtr,
                          cudaStream_t st, bool batch_member = false) {
   typedef typename P::C C;
-  constexpr int NC = 32, DEPTH = 16;   // pair sweep: 64 threads, two warps of 16 columns
+  // pair sweep: 64 threads, two warps of 16 columns. Ring depth: with FP64
+  // fields 8 levels (measured at 128x128x80: 34.8 us against 36.9 us at 16 and
+  // 38.9 at 4; larger FP64 domains 1-3% faster too), with FP32 fields 16
+  // (512x512x137: 8 levels 4% slower)
+  constexpr int NC = 32, DEPTH = std::is_same<typename P::S, double>::value ? 8 : 16, DEPTH_SPLIT = 16;
   const int64_t ncol = (int64_t)d.ni * d.nj;
   int e2 = 0;
   const bool p2 = std::is_same<C, df64>::value && std::frexp(dtr, &e2) == 0.5 && e2 > -120 && e2 < 120;
@@ -910,7 +914,7 @@ cudaError_t launch_sweep(const oec_schedule& s, const Dom& d, const HV<typename 
   }
   if (s.sweep == OEC_SWEEP_SPLIT) {
     const unsigned grid = (unsigned)((ncol + 15) / 16);
-#define OEC_SPLIT(P2, OFF) hv_thomas_split_kernel<P, DEPTH, P2, OFF><<<grid, 64, 0, st>>>(p, ud, vd, dtr, scr)
+#define OEC_SPLIT(P2, OFF) hv_thomas_split_kernel<P, DEPTH_SPLIT, P2, OFF><<<grid, 64, 0, st>>>(p, ud, vd, dtr, scr)
     if (p2) {
       if (o32) { OEC_SPLIT(true, int); } else { OEC_SPLIT(true, int64_t); }
     } else {
@@ -953,7 +957,7 @@ cudaError_t launch_sweep(const oec_schedule& s, const Dom& d, const HV<typename 
 // running CTAs. The host orders the items so that a sweep item comes well
 // after its producers (the rows in between stay in L2). A wait is bounded: it
 // gives up after `polls` polls, counts a timeout and skips the item.
-constexpr int kPSDepth = 16;    // column sweep ring depth
+constexpr int kPSDepth = 8;     // column sweep ring depth (16: 1.4-5% slower)
 constexpr int kPSCols = 64;     // columns per sweep item (128 threads)
 
 __device__ __forceinline__ bool ps_wait_geq(const int* p, int need, unsigned polls) {
@@ -1015,7 +1019,7 @@ cudaError_t pstaged_dispatch(const PSLaunch& L, bool query, int* per_sm, cudaStr
 #define OEC_PS(U, OFF, D)                                                                            \
   {                                                                                                   \
     auto k = hv_pstaged_kernel<P, U, OFF, D>;                                                        \
-    /* the ring and the item slots together pass 48 KB: opt in */                                    \
+    /* the ring and the item slots may pass 48 KB: opt in */                                          \
     cudaError_t ea = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
     if (ea != cudaSuccess) return ea;                                                                 \
     if (query) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k, 2 * kPSCols, smem);   \
