@@ -895,9 +895,12 @@ cudaError_t launch_sweep(const oec_schedule& s, const Dom& d, const HV<typename 
   typedef typename P::C C;
   // pair sweep: 64 threads, two warps of 16 columns. Ring depth: with FP64
   // fields 8 levels (measured at 128x128x80: 34.8 us against 36.9 us at 16 and
-  // 38.9 at 4; larger FP64 domains 1-3% faster too), with FP32 fields 16
-  // (512x512x137: 8 levels 4% slower)
-  constexpr int NC = 32, DEPTH = std::is_same<typename P::S, double>::value ? 8 : 16, DEPTH_SPLIT = 16;
+  // 38.9 at 4; larger FP64 domains 1-3% faster too); with FP32 fields 16
+  // (512x512x137: 8 levels 4% slower), or 12 when every CTA of the 16-level
+  // ring would be resident at once (128x128x80: 26.3 us against 27.6 at 16)
+  constexpr bool f64 = std::is_same<typename P::S, double>::value;
+  constexpr int NC = 32, DEPTH = f64 ? 8 : 16, DEPTH_SMALL = f64 ? 8 : 12, DEPTH_SPLIT = 16;
+  constexpr int64_t kSmallCols = 152 * 7 * NC;
   const int64_t ncol = (int64_t)d.ni * d.nj;
   int e2 = 0;
   const bool p2 = std::is_same<C, df64>::value && std::frexp(dtr, &e2) == 0.5 && e2 > -120 && e2 < 120;
@@ -928,10 +931,17 @@ cudaError_t launch_sweep(const oec_schedule& s, const Dom& d, const HV<typename 
     // instructions per step cost more than the traffic it saves)
     const bool discard = batch_member && (uintptr_t)scr % 128 == 0 &&
                          size_t(24) * pair_pitch(ncol) * d.nk > kDiscardAboveBytes;
-#define OEC_PAIR(P2, OFF, D) \
-  hv_thomas_kernel<P, NC, DEPTH, P2, OFF, D><<<grid, 2 * NC, 0, st>>>(p, ud, vd, dtr, scr, pair_pitch(ncol))
-#define OEC_PAIR_D(P2, OFF) \
-  if (discard) { OEC_PAIR(P2, OFF, true); } else { OEC_PAIR(P2, OFF, false); }
+    const bool small = ncol <= kSmallCols;
+#define OEC_PAIR(P2, OFF, D, DP) \
+  hv_thomas_kernel<P, NC, DP, P2, OFF, D><<<grid, 2 * NC, 0, st>>>(p, ud, vd, dtr, scr, pair_pitch(ncol))
+#define OEC_PAIR_D(P2, OFF)                      \
+  if (discard) {                                 \
+    OEC_PAIR(P2, OFF, true, DEPTH);              \
+  } else if (small) {                            \
+    OEC_PAIR(P2, OFF, false, DEPTH_SMALL);       \
+  } else {                                       \
+    OEC_PAIR(P2, OFF, false, DEPTH);             \
+  }
     if (p2) {
       if (o32) { OEC_PAIR_D(true, int); } else { OEC_PAIR_D(true, int64_t); }
     } else {
