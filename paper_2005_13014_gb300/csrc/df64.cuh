@@ -104,13 +104,18 @@ __device__ __forceinline__ df64 df_rcp(df64 b) {
 }
 
 // 1 / b seeded by the hardware's approximate reciprocal (rcp.approx.ftz.f32,
-// relative error about 2^-23), then the same Newton step: error about 2^-45.
-// For b.hi normal and below 2^126 (the column recurrence's pivots).
+// relative error about 2^-23), then one Newton step x0 + x0 r. The residual
+// r = 1 - b x0 is of order 2^-23, so it is formed in single floats by two
+// FMAs: 1 - b.hi x0 is exact before its one rounding, and b.lo x0 is added by
+// the second. Error about 2^-44 (in exact arithmetic, with seeds one ulp off,
+// the same as the residual formed as a double-float product and difference,
+// in 7 float operations instead of 22). For b.hi normal and below 2^126 (the
+// column recurrence's pivots).
 __device__ __forceinline__ df64 df_rcp_approx_seed(df64 b) {
   float x0;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(x0) : "f"(b.hi));
-  const df64 r = df_sub_fast(df64{1.0f, 0.0f}, df_mulf(b, x0));
-  return df_norm(x0, __fmul_rn(r.hi, x0));
+  const float r = __fmaf_rn(-b.lo, x0, __fmaf_rn(-b.hi, x0, 1.0f));
+  return df_norm(x0, __fmul_rn(x0, r));
 }
 
 __device__ __forceinline__ bool df_gt0(df64 a) { return a.hi > 0.0f; }   // sign of a normalised pair
