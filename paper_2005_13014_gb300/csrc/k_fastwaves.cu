@@ -56,25 +56,27 @@ __device__ __forceinline__ C fw_out(C uin, C dt, C tens, C pg, C fx, C rho_n, C 
 template <class P>
 __device__ __forceinline__ typename P::C ld(const typename P::S* q) { return cvt<typename P::C>(ldg(q)); }
 
-template <class P>
-__device__ __forceinline__ typename P::C ppgk_at(const FW<typename P::S>& p, int64_t o) {
-  return fw_ppgk(ld<P>(p.wgtfac + o), ld<P>(p.pp + o), ld<P>(p.pp + o - p.sk));
+// element offsets o of type Off (int where every offset of the domain fits)
+template <class P, class Off>
+__device__ __forceinline__ typename P::C ppgk_at(const FW<typename P::S>& p, Off o) {
+  return fw_ppgk(ld<P>(p.wgtfac + o), ld<P>(p.pp + o), ld<P>(p.pp + (o - (Off)p.sk)));
 }
-template <class P>
-__device__ __forceinline__ typename P::C div_at(const FW<typename P::S>& p, int64_t o) {
+template <class P, class Off>
+__device__ __forceinline__ typename P::C div_at(const FW<typename P::S>& p, Off o) {
   const typename P::S* u = p.u_in + o;
   const typename P::S* v = p.v_in + o;
+  const Off sj = (Off)p.sj;
   return fw_d4(ld<P>(u - 2), ld<P>(u - 1), ld<P>(u + 1), ld<P>(u + 2)) +
-         fw_d4(ld<P>(v - 2 * p.sj), ld<P>(v - p.sj), ld<P>(v + p.sj), ld<P>(v + 2 * p.sj));
+         fw_d4(ld<P>(v - 2 * sj), ld<P>(v - sj), ld<P>(v + sj), ld<P>(v + 2 * sj));
 }
 
-template <class P>
-__device__ __forceinline__ void fw_point(const FW<typename P::S>& p, int64_t o, typename P::C pc, typename P::C pc_e,
+template <class P, class Off>
+__device__ __forceinline__ void fw_point(const FW<typename P::S>& p, Off o, typename P::C pc, typename P::C pc_e,
                                          typename P::C pc_n, typename P::C dv, typename P::C dv_e, typename P::C dv_n,
                                          typename P::C dt, typename P::C alpha) {
   typedef typename P::C C;
   typedef typename P::S S;
-  const int64_t sj = p.sj, sk = p.sk;
+  const Off sj = (Off)p.sj, sk = (Off)p.sk;
   const C pp = ld<P>(p.pp + o), h = ld<P>(p.hhl + o), h1 = ld<P>(p.hhl + o + sk);
   const C ppgu = fw_pgrad(ld<P>(p.pp + o + 1), pp, pc_e, pc, h1, h, ld<P>(p.hhl + o + 1 + sk), ld<P>(p.hhl + o + 1));
   const C ppgv = fw_pgrad(ld<P>(p.pp + o + sj), pp, pc_n, pc, h1, h, ld<P>(p.hhl + o + sj + sk), ld<P>(p.hhl + o + sj));
@@ -504,7 +506,7 @@ __global__ void __launch_bounds__(TI * TJ) fw_tma_kernel(const __grid_constant__
     for (int k = failed_at; k < issued_to; ++k) mbar_wait(smem_u32(&bars[(k - k0) % D]), (unsigned)(((k - k0) / D) & 1));
 }
 
-template <class P, int TI, int TJ>
+template <class P, int TI, int TJ, class Off>
 __global__ void __launch_bounds__(TI * TJ) fw_smem_kernel(FW<typename P::S> p, double dt_d, double alpha_d, int kchunk) {
   typedef typename P::C T;
   const T dt = kd<T>(dt_d), alpha = kd<T>(alpha_d);
@@ -516,19 +518,19 @@ __global__ void __launch_bounds__(TI * TJ) fw_smem_kernel(FW<typename P::S> p, d
   const int i0 = blockIdx.x * TI, j0 = blockIdx.y * TJ;
   const int k0 = blockIdx.z * kchunk, k1 = min(p.nk, k0 + kchunk);
   const int vi = min(TI, p.ni - i0), vj = min(TJ, p.nj - j0);
-  const int64_t tile = (int64_t)j0 * p.sj + i0;
+  const Off sj = (Off)p.sj, sk = (Off)p.sk, tile = (Off)j0 * sj + i0;
   int cur = 0;
   for (int idx = tid; idx < PI * PJ; idx += NT) {
     const int b = idx / PI, a = idx - b * PI;
-    if (a < vi + 1 && b < vj + 1) s_pk[cur][b][a] = ppgk_at<P>(p, (int64_t)k0 * p.sk + tile + (int64_t)b * p.sj + a);
+    if (a < vi + 1 && b < vj + 1) s_pk[cur][b][a] = ppgk_at<P>(p, (Off)k0 * sk + tile + (Off)b * sj + a);
   }
   for (int k = k0; k < k1; ++k) {
     __syncthreads();
     for (int idx = tid; idx < PI * PJ; idx += NT) {
       const int b = idx / PI, a = idx - b * PI;
       if (a < vi + 1 && b < vj + 1) {
-        const int64_t o = (int64_t)k * p.sk + tile + (int64_t)b * p.sj + a;
-        const T pk1 = ppgk_at<P>(p, o + p.sk);
+        const Off o = (Off)k * sk + tile + (Off)b * sj + a;
+        const T pk1 = ppgk_at<P>(p, o + sk);
         s_pc[b][a] = pk1 - s_pk[cur][b][a];
         s_pk[cur ^ 1][b][a] = pk1;
         s_dv[b][a] = div_at<P>(p, o);
@@ -536,7 +538,7 @@ __global__ void __launch_bounds__(TI * TJ) fw_smem_kernel(FW<typename P::S> p, d
     }
     __syncthreads();
     if (tx < vi && ty < vj) {
-      const int64_t o = (int64_t)k * p.sk + tile + (int64_t)ty * p.sj + tx;
+      const Off o = (Off)k * sk + tile + (Off)ty * sj + tx;
       fw_point<P>(p, o, s_pc[ty][tx], s_pc[ty][tx + 1], s_pc[ty + 1][tx], s_dv[ty][tx], s_dv[ty][tx + 1],
                   s_dv[ty + 1][tx], dt, alpha);
     }
@@ -619,6 +621,8 @@ bool offsets_fit_fw(const Dom& d) {
   const int64_t lo = -(d.sk + 3 * d.sj + 3);
   return hi < INT32_MAX && lo > INT32_MIN;
 }
+// 32-bit offsets unless the schedule asks for 64-bit ones or they do not fit
+bool fw_int32(const oec_schedule& s, const Dom& d) { return s.index_bits != OEC_INDEX_64 && offsets_fit_fw(d); }
 
 // tiles of the TMA-staged kernel (TI a multiple of 16 elements keeps every
 // box corner on a 16-byte boundary)
@@ -657,7 +661,7 @@ cudaError_t run_fw_tma(const oec_schedule& s, const Dom& d, const TmaField* tf, 
     cudaFuncSetAttribute(fw_tma_kernel<P, TI, TJ, int64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)G::SMEM);
   });
-  if (offsets_fit_fw(d))
+  if (fw_int32(s, d))
     fw_tma_kernel<P, TI, TJ, int><<<g, TI * TJ, G::SMEM, st>>>(mp, p, dt, alpha, kc, timeouts);
   else
     fw_tma_kernel<P, TI, TJ, int64_t><<<g, TI * TJ, G::SMEM, st>>>(mp, p, dt, alpha, kc, timeouts);
@@ -700,7 +704,7 @@ cudaError_t dispatch(const oec_schedule& s, const Dom& d, const FW<typename P::S
 #define X(a, b)                                                                                       \
   if (s.tile_i == a && s.tile_j == b) {                                                               \
     dim3 g(ceil_div(d.ni, a), ceil_div(d.nj, b), ceil_div(d.nk, kc));                                 \
-    if (offsets_fit_fw(d))                                                                            \
+    if (fw_int32(s, d))                                                                            \
       fw_tile_kernel<P, a, b, int><<<g, a * b, 0, st>>>(p, dt, alpha, kc);                            \
     else                                                                                              \
       fw_tile_kernel<P, a, b, int64_t><<<g, a * b, 0, st>>>(p, dt, alpha, kc);                        \
@@ -715,7 +719,7 @@ cudaError_t dispatch(const oec_schedule& s, const Dom& d, const FW<typename P::S
     const int kc = kchunk_of(s, d.nk);
     dim3 b(s.tile_i, s.tile_j);
     dim3 g(ceil_div(d.ni, s.tile_i), ceil_div(d.nj, s.tile_j), ceil_div(d.nk, kc));
-    if (offsets_fit_fw(d))
+    if (fw_int32(s, d))
       fw_stream_kernel<P, int><<<g, b, 0, st>>>(p, dt, alpha, kc);
     else
       fw_stream_kernel<P, int64_t><<<g, b, 0, st>>>(p, dt, alpha, kc);
@@ -727,7 +731,11 @@ cudaError_t dispatch(const oec_schedule& s, const Dom& d, const FW<typename P::S
 #define X(a, b)                                                                                 \
   if (s.tile_i == a && s.tile_j == b) {                                                         \
     dim3 g(ceil_div(d.ni, a), ceil_div(d.nj, b), ceil_div(d.nk, kc));                           \
-    fw_smem_kernel<P, a, b><<<g, a * b, 0, st>>>(p, dt, alpha, kc); launched(st);                              \
+    if (fw_int32(s, d))                                                                      \
+      fw_smem_kernel<P, a, b, int><<<g, a * b, 0, st>>>(p, dt, alpha, kc);                      \
+    else                                                                                        \
+      fw_smem_kernel<P, a, b, int64_t><<<g, a * b, 0, st>>>(p, dt, alpha, kc);                  \
+    launched(st);                                                                               \
     return cudaGetLastError();                                                                  \
   }
     OEC_FW_TILES(X)

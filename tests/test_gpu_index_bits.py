@@ -94,3 +94,25 @@ def test_generated_offset_widths_agree(seed, dtype):
         for x, y, name in zip(a, b, prog.outputs):
             assert np.array_equal(x, y)
             assert rel_err(x, ref[name]) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype,arith", [("f64", 0), ("f64", 1), ("f32", 0)])
+@pytest.mark.parametrize("sched", [dict(fusion=0, staging=1, tile_i=32, tile_j=8, k_chunk=4),
+                                   dict(fusion=0, staging=2, tile_i=64, tile_j=4, k_chunk=8),
+                                   dict(fusion=0, staging=2, tile_i=32, tile_j=8, unroll=2, k_chunk=4),
+                                   dict(fusion=0, staging=4, tile_i=32, tile_j=4, k_chunk=8)], ids=str)
+def test_fastwaves_offset_widths_agree(dtype, arith, sched):
+    """The fastwaves kernels (shared-memory tile, k-streaming, k-streaming with
+    shared u/v windows, TMA boxes): 64-bit offsets forced give the bits of
+    the automatic (32-bit) form, within tolerance of the oracle."""
+    n, h = (37, 29, 7), 3
+    f = inputs.fastwaves_fields(*n, h, seed=71)
+    g = {k: _round(v, dtype) for k, v in f.items()}
+    s = dict(sched, arith=arith)
+    a, b = _both_widths(programs.FASTWAVES, dtype, s, g, inputs.FASTWAVES_NAMES, n, h, params=(0.5, 0.0625),
+                        align=16, n_out=2)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    G = {k: S.Grid.storage(v, h) for k, v in g.items()}
+    ru, rv = S.fastwaves(G, (0, 0, 0), n, 0.5, 0.0625)
+    assert max(rel_err(a[0], ru), rel_err(a[1], rv)) <= TOL[dtype]
