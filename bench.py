@@ -164,9 +164,8 @@ ARITH_NAMES = {0: "native binary64 throughout",
 
 
 def _field_bytes(name, n=N, es=8):
-    """Algorithmic bytes of one field of hdiff+vadvc (SURVEY-style access
-    boxes: u, v with the i/j halo of 2, w with the i+1 column, the rest the
-    domain)."""
+    """Algorithmic bytes of one field of hdiff+vadvc over its access box (u, v
+    with the i/j halo of 2, w with the i+1 column, the rest the domain)."""
     ni, nj, nk = n
     pts = {"u": (ni + 4) * (nj + 4) * nk, "v": (ni + 4) * (nj + 4) * nk, "w": (ni + 1) * nj * nk}
     return pts.get(name, ni * nj * nk) * es

@@ -606,7 +606,8 @@ OEC_API int oec_costmodel_load(const char* path, oec_costmodel_t* out);
  * takes the best-ranked valid candidate untimed, top_k > 0 times the top_k
  * best-ranked as oec_program_autotune does (reps applies each; fields as for
  * oec_program_apply, outputs overwritten) and takes the fastest, with
- * exhaustive oec_program_autotune as the reference it is judged against.
+ * exhaustive oec_program_autotune as the reference its choices are measured
+ * against.
  * Sets the program's schedule; *best = the pick's index in the candidate
  * list; pred (may be NULL) receives the n_cand predictions. Synchronises
  * cuda_stream. Errors: as oec_program_features and oec_program_autotune, and
