@@ -388,7 +388,7 @@ def run_gpu(args):
         cands = prog.candidates()
         times, best = prog.autotune(d0, o0, lb, ub, halo, [DTR], candidates=cands, reps=5, stream=stream)
         tuning = {json.dumps(c, sort_keys=True): round(t, 4) for c, t in zip(cands, times)}
-        top = [cands[x] for x in np.argsort(times)[:4]]
+        top = [cands[x] for x in np.argsort(times) if times[x] > 0][:4]
         refined = []
         for c in top:
             prog.set_schedule(**c)
@@ -678,8 +678,20 @@ def _run_program(prog_name, dtype, arith, steps, schedule=None, cache=None, size
     if schedule:
         prog.set_schedule(**schedule)
     else:
+        # every candidate timed on one set, then the four fastest re-timed by
+        # replaying captured applies over the rotating sets, the fastest kept
         cands = [dict(c, index_bits=index_bits) for c in prog.candidates() if c["arith"] == arith]
-        prog.autotune(ins, outs, (0, 0, 0), n, (h, h, h), params, candidates=cands, reps=5)
+        times, _ = prog.autotune(ins, outs, (0, 0, 0), n, (h, h, h), params, candidates=cands, reps=5)
+        top = [cands[x] for x in np.argsort(times) if times[x] > 0][:4]   # timed candidates only
+        refined = []
+        for c in top:
+            prog.set_schedule(**c)
+            gs = [prog.capture(*sets[x], (0, 0, 0), n, (h, h, h), params) for x in range(n_sets)]
+            refined.append(_timed(lambda x: gs[x % n_sets](stream), max(20, 2 * n_sets), 2 * n_sets, stream))
+            for g in gs:
+                g.close()
+        if top:
+            prog.set_schedule(**top[int(np.argmin(refined))])
     # direct: one C-ABI call per apply from Python (host overhead included),
     # arguments marshalled per call (apply) and once (bind)
     ms_direct = _timed(lambda x: prog.apply(*sets[x % n_sets], (0, 0, 0), n, (h, h, h), params), steps, 3, stream)

@@ -151,6 +151,13 @@ typedef struct oec_schedule {
  * rounding (the same operations per field). */
 #define OEC_SWEEP_PAIR 0
 #define OEC_SWEEP_SPLIT 1
+/* With FP32 fields, the warp-row producer (OEC_STAGE_WARP, unroll 1 or 2,
+ * rows 16-byte aligned), OEC_SWEEP_PAIR, slabs 0 or 1 and at least 65,536
+ * columns, oec_program_apply runs the stage-by-stage form as one persistent
+ * launch: CTAs take producer items (a block of 4 x unroll rows) and column
+ * sweep items (64 columns) in a fixed ticket order, a sweep item waiting
+ * (bounded, see oec_device_status) until the producer items of its rows are
+ * done. Same results as the two kernels bit for bit. */
 /* OEC_SWEEP_SEGMENTS4 / 8: the partitioned Thomas solve. Each column is cut
  * into 4 or 8 segments of consecutive levels, one thread each; a segment
  * eliminates downwards carrying its coupling to the level below it, then
@@ -641,7 +648,9 @@ OEC_API int oec_program_autotune_model(oec_program_t p, oec_costmodel_t m, const
  * 24 * ceil16(ni * nj) * nk + 16 * ni * nj * nk bytes in FP64 and
  * 24 * ceil16(ni * nj) * nk + 8 * ni * nj * nk in FP32, each of its two parts
  * rounded up to 256 bytes (40 and 32 bytes per point when ni * nj is a
- * multiple of 16); beyond 64 MiB the fused form needs
+ * multiple of 16; FP32 domains of at least 65,536 columns add
+ * 4 * (ceil(nj / 4) + 1) bytes of counters, rounded up to 256); beyond 64 MiB
+ * the fused form needs
  * 24 * ceil16(ni) * ceil4(nj) * nk bytes (ceilN: rounded up to a multiple of
  * N); a domain whose fused form needs more than 64 MiB is rejected with
  * OEC_ERR_UNSUPPORTED before anything is enqueued. The first call on each

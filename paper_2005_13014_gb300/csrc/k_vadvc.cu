@@ -21,6 +21,7 @@
 // Batched form: a persistent kernel pulls (member, tile) items of an ensemble
 // of domains from an atomic counter and runs the fused tile sweep on each.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <mutex>
 #include <type_traits>
@@ -863,8 +864,16 @@ size_t sweep_scratch_elems(const oec_schedule& s, const Dom& d, int rows) {
   return s.sweep == OEC_SWEEP_PAIR ? size_t(3) * pair_pitch(ncol) * d.nk : size_t(4) * ncol * d.nk;
 }
 
+// one FP32 domain of at least this many columns runs the staged form as one
+// persistent launch (measured: 512x512x137 68.8 against 56.8 G points/s,
+// 256x256x80 60.4 against 57.9; on smaller domains the two kernels)
+constexpr int64_t kPSSingleMinCols = 65536;
+bool pstaged_single_ok(const oec_schedule& s, int dtype, const Dom& d) {
+  return hdiff_vadvc_pstaged_ok(s, dtype) && s.slabs <= 1 && (int64_t)d.ni * d.nj >= kPSSingleMinCols;
+}
+
 struct Layout {
-  size_t thomas, ud, vd, total;
+  size_t thomas, ud, vd, counters, total;
 };
 Layout layout(const oec_schedule& s, int dtype, const Dom& d) {
   const size_t pts = size_t(d.ni) * d.nj * d.nk;
@@ -878,11 +887,14 @@ Layout layout(const oec_schedule& s, int dtype, const Dom& d) {
     const size_t pad = ns > 1 ? size_t(3) * 16 * ns * d.nk : 0;   // slab starts on 128 bytes
     l.ud = align_up(rsize() * (sweep_scratch_elems(s, d, d.nj) + pad), 256);
     l.vd = align_up(l.ud + csize(dtype, s.arith) * pts, 256);
-    l.total = align_up(l.vd + csize(dtype, s.arith) * pts, 256);
+    l.counters = align_up(l.vd + csize(dtype, s.arith) * pts, 256);
+    // the persistent single-domain form's row-block counters and ticket
+    const size_t nc = pstaged_single_ok(s, dtype, d) ? size_t(ceil_div(d.nj, 4 * s.unroll)) + 1 : 0;
+    l.total = align_up(l.counters + sizeof(int) * nc, 256);
   } else {
     // one slot of 3 x nk x (TI*TJ) recurrence values per tile
     const size_t tiles = size_t(ceil_div(d.ni, s.tile_i)) * ceil_div(d.nj, s.tile_j);
-    l.ud = l.vd = l.total = align_up(3 * rsize() * tiles * d.nk * s.tile_i * s.tile_j, 256);
+    l.ud = l.vd = l.counters = l.total = align_up(3 * rsize() * tiles * d.nk * s.tile_i * s.tile_j, 256);
   }
   return l;
 }
@@ -980,6 +992,37 @@ __device__ __forceinline__ bool ps_wait_geq(const int* p, int need, unsigned pol
   return false;
 }
 
+// One domain's ticket order in closed form (PSLaunch without tables). Column
+// group g (columns 64g .. 64g+63) needs the row blocks of its first and last
+// column; it is placed after the producer items of row block hi + lag, where
+// hi is its last column's row block, or after the last block. Row block b
+// then starts at ticket b * per_block + before(b), where before(b) counts the
+// groups whose last column lies in a row block below b - lag.
+__device__ __forceinline__ int64_t ps_groups_before(const PSLaunch& L, int b) {
+  if (b >= L.blocks) return L.groups;
+  const int h = b - 1 - L.lag;
+  if (h < 0) return 0;
+  const int64_t lim = (int64_t)(h + 1) * L.rows * L.single.ni;   // first column beyond row block h
+  if (lim >= (int64_t)L.single.ni * L.single.nj) return L.groups;
+  return lim / kPSCols;   // groups whose last column (64g + 63) lies below lim
+}
+
+__device__ PSItem ps_decode(const PSLaunch& L, int t) {
+  auto start = [&](int b) { return (int64_t)b * L.per_block + ps_groups_before(L, b); };
+  int lo = 0, hi = L.blocks - 1;   // the row block b with start(b) <= t < start(b + 1)
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (start(mid) <= t) lo = mid; else hi = mid - 1;
+  }
+  const int b = lo;
+  const int64_t r = t - start(b);
+  if (r < L.per_block) return PSItem{0, int(r % L.tiles_i), b, int(r / L.tiles_i)};
+  const int64_t g = ps_groups_before(L, b) + (r - L.per_block);
+  const int64_t ncol = (int64_t)L.single.ni * L.single.nj;
+  const int64_t c1 = min(g * kPSCols + kPSCols - 1, ncol - 1);
+  return PSItem{~0, int(g), int((g * kPSCols) / L.single.ni) / L.rows, int(c1 / L.single.ni) / L.rows};
+}
+
 template <class P, int U, class Off, bool DISCARD>
 __global__ void __launch_bounds__(2 * kPSCols) hv_pstaged_kernel(PSLaunch L) {
   typedef typename P::S S;
@@ -987,14 +1030,18 @@ __global__ void __launch_bounds__(2 * kPSCols) hv_pstaged_kernel(PSLaunch L) {
   typedef typename P::R R;
   extern __shared__ __align__(16) unsigned char ps_ring[];
   __shared__ int s_item, s_ok;
+  __shared__ PSItem s_pi;
   for (;;) {
-    if (threadIdx.x == 0) s_item = atomicAdd(L.ticket, 1);
+    if (threadIdx.x == 0) {
+      s_item = atomicAdd(L.ticket, 1);
+      if (s_item < L.n_items) s_pi = L.items ? L.items[s_item] : ps_decode(L, s_item);
+    }
     __syncthreads();
     const int it = s_item;
     if (it >= L.n_items) break;
-    const PSItem item = L.items[it];
+    const PSItem item = s_pi;
     if (item.x >= 0) {   // producer
-      const PSMember& m = L.members[item.x];
+      const PSMember& m = L.items ? L.members[item.x] : L.single;
       hdiff_vec_block<P, U, Off, 2, true>((const S*)m.u, (const S*)m.coeff, (S*)m.ud, m.ni, m.nj, m.nk, m.sj, m.sk,
                                           m.kchunk, m.ni, (int64_t)m.ni * m.nj, m.nkz, (const S*)m.v, (S*)m.vd,
                                           item.y, item.z, item.w);
@@ -1004,7 +1051,7 @@ __global__ void __launch_bounds__(2 * kPSCols) hv_pstaged_kernel(PSLaunch L) {
         atomicAdd(L.done + m.row_base + item.z, 1);
       }
     } else {             // column sweep
-      const PSMember& m = L.members[~item.x];
+      const PSMember& m = L.items ? L.members[~item.x] : L.single;
       if (threadIdx.x == 0) {
         bool ok = true;
         for (int b = item.z; ok && b <= item.w; ++b) ok = ps_wait_geq(L.done + m.row_base + b, m.need, L.polls);
@@ -1044,6 +1091,71 @@ cudaError_t pstaged_dispatch(const PSLaunch& L, bool query, int* per_sm, cudaStr
 #undef OEC_PS_O
 #undef OEC_PS_D
 #undef OEC_PS
+}
+
+// One FP32 domain as a persistent staged launch (the closed-form ticket order
+// of ps_decode, no tables): false in *ran when the fields' rows are not
+// 16-byte aligned (the two kernels run then).
+template <class P>
+cudaError_t pstaged_single_launch(const oec_schedule& s, const Dom& d, const HV<float>& p, float* ud, float* vd,
+                                  typename P::R* scr, int* counters, double dtr, cudaStream_t st, bool* ran) {
+  *ran = false;
+  const bool aligned = ((uintptr_t)p.u | (uintptr_t)p.v | (uintptr_t)p.coeff | (uintptr_t)ud | (uintptr_t)vd) % 16 == 0 &&
+                       d.sj % 4 == 0 && d.sk % 4 == 0 && d.ni % 4 == 0;
+  if (!aligned) return cudaSuccess;
+  PSLaunch L{};
+  PSMember& m = L.single;
+  m.u = p.u; m.v = p.v; m.w = p.w; m.coeff = p.coeff; m.uo = p.uo; m.vo = p.vo;
+  m.ud = ud; m.vd = vd; m.scr = scr;
+  m.sj = d.sj; m.sk = d.sk;
+  const int64_t ncol = (int64_t)d.ni * d.nj;
+  m.ncolp = pair_pitch(ncol);
+  m.ni = d.ni; m.nj = d.nj; m.nk = d.nk;
+  m.kchunk = (s.k_chunk <= 0 || s.k_chunk > d.nk) ? d.nk : s.k_chunk;
+  m.nkz = ceil_div(d.nk, m.kchunk);
+  m.row_base = 0;
+  L.tiles_i = ceil_div(d.ni, 128);   // 32 lanes x 4 floats
+  m.need = L.tiles_i * 2 * m.nkz;
+  L.per_block = m.need;
+  L.rows = 4 * s.unroll;
+  L.blocks = ceil_div(d.nj, L.rows);
+  L.groups = (int)((ncol + kPSCols - 1) / kPSCols);
+  const int64_t n_items = (int64_t)L.blocks * L.per_block + L.groups;
+  L.timeouts = wait_timeout_counter();
+  if (n_items > INT32_MAX / 2 || !L.timeouts) return cudaSuccess;
+  L.n_items = (int)n_items;
+  L.unroll = s.unroll;
+  L.o32 = use_int32(s, d) && 4 * m.ncolp * d.nk < INT32_MAX;
+  L.discard = (uintptr_t)scr % 128 == 0 && size_t(24) * m.ncolp * d.nk > kDiscardAboveBytes;
+  L.dtr = dtr;
+  L.polls = 1u << 22;
+  L.done = counters;
+  L.ticket = counters + L.blocks;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  // CTAs per SM of this kernel form, looked up once per device
+  static std::atomic<int> cache[8][64];
+  const int form = (L.unroll - 1) * 4 + (L.o32 ? 2 : 0) + (L.discard ? 1 : 0);
+  int per_sm = dev < 64 ? cache[form][dev].load() : 0;
+  if (per_sm <= 0) {
+    e = pstaged_dispatch<P>(L, true, &per_sm, nullptr);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaSuccess;
+    if (dev < 64) cache[form][dev].store(per_sm);
+  }
+  L.grid = (int)std::min<int64_t>(n_items, (int64_t)per_sm * sms);
+  // a group follows its last producers by about two resident CTAs' worth of items
+  const int64_t per_row_block = L.per_block + std::max<int64_t>(1, (int64_t)L.rows * d.ni / kPSCols);
+  L.lag = (int)std::min<int64_t>(L.blocks, (2 * (int64_t)L.grid + per_row_block - 1) / per_row_block);
+  e = cudaMemsetAsync(counters, 0, sizeof(int) * (size_t)(L.blocks + 1), st);
+  if (e == cudaSuccess) e = pstaged_dispatch<P>(L, false, nullptr, st);
+  if (e == cudaSuccess) {
+    *ran = true;
+    launched(st);
+  }
+  return e;
 }
 
 // The staged form's slab streams and their events (one set per device, made
@@ -1093,6 +1205,15 @@ cudaError_t run(const oec_schedule& s, int dtype, const Dom& d, const HV<typenam
   R* scr = (R*)(scratch + l.thomas);
   const int ns = std::min(std::max(s.slabs, 1), std::min(d.nj, kMaxSlabs));
   if (ns == 1) {
+    if constexpr (std::is_same<typename P::S, float>::value) {
+      // a large FP32 domain: producer and column sweep in one persistent launch
+      if (!batch_member && pstaged_single_ok(s, dtype, d)) {
+        bool ran = false;
+        cudaError_t e = pstaged_single_launch<P>(s, d, p, (float*)ud, (float*)vd, scr, (int*)(scratch + l.counters),
+                                                 dtr, st, &ran);
+        if (e != cudaSuccess || ran) return e;
+      }
+    }
     cudaError_t e = hdiff_to_compute(s, dtype, d, p.u, p.v, p.coeff, ud, vd, st);
     if (e != cudaSuccess) return e;
     return launch_sweep<P>(s, d, p, ud, vd, scr, dtr, st, batch_member);

@@ -57,8 +57,8 @@ struct PSItem {
 };
 
 struct PSLaunch {
-  const PSMember* members;   // device memory
-  const PSItem* items;       // device memory, n_items entries
+  const PSMember* members;   // device memory (a batch), or null: one domain, `single`
+  const PSItem* items;       // device memory, n_items entries, or null: one domain's closed-form order
   int n_items;
   int* ticket;               // device int, zero before the launch
   int* done;                 // device ints, one per (member, row block), zero before the launch
@@ -69,6 +69,16 @@ struct PSLaunch {
   int unroll;                // rows per warp of the producer (1 or 2)
   bool o32;                  // every member's offsets fit 32 bits
   bool discard;              // the column sweep's L2 form
+  // one domain without tables: ticket order row block by row block, each
+  // block's producer items followed by the column groups whose last row lies
+  // `lag` row blocks back (the remaining groups after the last block)
+  PSMember single;
+  int tiles_i;               // producer CTAs along i
+  int per_block;             // producer items per row block (tiles_i x 2 fields x chunks)
+  int blocks;                // row blocks (rows each)
+  int rows;                  // rows per row block (4 x unroll)
+  int groups;                // column groups of 64
+  int lag;                   // row blocks between a group's last producers and the group
 };
 
 }  // namespace oec

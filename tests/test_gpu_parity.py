@@ -596,3 +596,52 @@ def test_hdiff_vadvc_staged_dtr(dtype, arith, dtr):
     if arith == 2:   # the split sweep and the slab pipeline
         sched = dict(fusion=1, tile_i=32, tile_j=8, k_chunk=4, arith=2, sweep=1, slabs=4)
         assert _hv_case((37, 23, 11), 3, dtype, sched, dtr=dtr) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("n", [(256, 256, 8), (268, 250, 5), (512, 128, 3), (1024, 64, 2), (256, 257, 1)], ids=str)
+@pytest.mark.parametrize("unroll,k_chunk,arith", [(1, 4, 1), (2, 0, 1), (1, 20, 0), (2, 3, 0)])
+def test_hdiff_vadvc_f32_persistent_single_domain(n, unroll, k_chunk, arith):
+    """FP32 fields on the warp-row producer with at least 65,536 columns: the
+    producer and the column sweep run as one persistent launch whose tickets
+    follow a closed-form order (producer items of a row block, then the
+    column groups a lag of row blocks back). Partial row blocks, partial
+    column groups, 1-level columns, the threshold itself (1024x64): the bits
+    of the two-kernel form with the one-field-per-thread sweep (the same
+    operations per field), sampled blocks within tolerance of the oracle, no
+    bounded wait given up, also when replayed from a captured graph."""
+    from paper_2005_13014_gb300 import _lib as L
+    from paper_2005_13014_gb300.api import Program, device_field
+    h = 3
+    f = inputs.hdiff_vadvc_fields(*n, h, seed=91)
+    g = {k: _round(v, "f32") for k, v in f.items()}
+    d = [device_field(g[k], h, "f32", align_bytes=16) for k in ("u", "v", "w", "coeff")]
+    res = []
+    for sweep in (0, 1):
+        p = Program(programs.HDIFF_VADVC, "f32")
+        p.set_schedule(fusion=1, staging=3, tile_i=32, tile_j=4 * unroll, unroll=unroll, k_chunk=k_chunk, arith=arith,
+                       sweep=sweep)
+        o = [device_field(np.full_like(g["u"], 5.0), h, "f32", align_bytes=16) for _ in range(2)]
+        p.apply(d, o, (0, 0, 0), n, (h, h, h), [2.0])
+        if sweep == 0:
+            assert p.launch_count() == 1   # one persistent launch
+            cg = [device_field(np.full_like(g["u"], 5.0), h, "f32", align_bytes=16) for _ in range(2)]
+            gr = p.capture(d, cg, (0, 0, 0), n, (h, h, h), [2.0])
+            gr()
+            gr()
+            torch.cuda.synchronize()
+            gr.close()
+            for a, b in zip(o, cg):
+                assert torch.equal(a.tensor, b.tensor)
+        torch.cuda.synchronize()
+        res.append(o)
+    for a, b in zip(*res):
+        assert torch.equal(a.tensor, b.tensor)
+    assert L.lib().oec_device_status(None) == 0
+    rng = np.random.default_rng(3)
+    i0, j0 = int(rng.integers(0, n[0] - 8)), int(rng.integers(0, n[1] - 8))
+    lb, ub = (i0, j0, 0), (i0 + 8, j0 + 8, n[2])
+    G = {k: S.Grid.storage(v, h) for k, v in g.items()}
+    ru, rv = S.hdiff_vadvc(G["u"], G["v"], G["w"], G["coeff"], lb, ub, 2.0)
+    gu = res[0][0].interior(lb, ub).cpu().numpy().astype(np.float64)
+    gv = res[0][1].interior(lb, ub).cpu().numpy().astype(np.float64)
+    assert max(rel_err(gu, ru), rel_err(gv, rv)) <= TOL["f32"]
