@@ -1,6 +1,6 @@
 // k_hdiff_fixed.cuh - the exact fixed-point FP64 hdiff tile (arith 2): one
-// CTA's block body, used by the fixed-point hdiff kernel (k_hdiff.cu) and by
-// the pipelined hdiff+vadvc kernel (k_vadvc.cu). Arithmetic in fixedpt.cuh.
+// CTA's block body, used by the fixed-point hdiff kernel (k_hdiff.cu).
+// Arithmetic in fixedpt.cuh.
 #pragma once
 
 #include "arith.cuh"
