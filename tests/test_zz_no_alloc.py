@@ -83,6 +83,32 @@ def test_noalloc_bits_of_the_schedule_it_runs(liboec, dtype, n, sched):
         assert torch.equal(g.tensor, r.tensor)
 
 
+@pytest.mark.parametrize("n", [(256, 256, 24), (260, 256, 7)], ids=str)
+def test_noalloc_f32_persistent_single_domain(liboec, n):
+    """FP32 fields with 16-byte aligned rows and at least 65,536 columns: the
+    default schedule (warp-row producer) runs as one persistent launch whose
+    row-block counters and ticket sit in the fixed scratch after the column
+    scratch and the hdiff planes (50.3 MB at 256x256x24). Bit for bit the
+    apply with that schedule, twice in a row (the counters are reset by
+    every call), and no bounded wait given up."""
+    from paper_2005_13014_gb300.api import Program, device_field
+    h = 3
+    prog = Program(programs.HDIFF_VADVC, "f32")
+    prog.set_schedule(**dict(prog.schedule, sweep=0, slabs=0))
+    f = inputs.hdiff_vadvc_fields(*n, h, seed=78)
+    d = [device_field(f[k], h, "f32", align_bytes=16) for k in ("u", "v", "w", "coeff")]
+    ref = [device_field(np.zeros_like(f["u"]), h, "f32", align_bytes=16) for _ in range(2)]
+    prog.apply(d, ref, (0, 0, 0), n, (h, h, h), [2.0])
+    assert prog.launch_count() == 1   # the persistent form
+    for call in range(2):
+        got = [device_field(np.full_like(f["u"], 7.0), h, "f32", align_bytes=16) for _ in range(2)]
+        assert _noalloc(liboec, "f32", d, got, n) == 0, liboec.oec_last_error()
+        torch.cuda.synchronize()
+        for g, r in zip(got, ref):
+            assert torch.equal(g.interior((0, 0, 0), n), r.interior((0, 0, 0), n)), f"call {call}"
+    assert liboec.oec_device_status(None) == 0
+
+
 @pytest.mark.parametrize("n", [(2796203, 1, 1), (128, 128, 171)], ids=str)
 def test_noalloc_rejects_oversized_domain(liboec, n):
     # more than the fixed 64 MiB even in the fused form (24 * ceil16(ni) *
