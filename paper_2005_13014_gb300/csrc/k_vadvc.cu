@@ -1042,7 +1042,12 @@ __global__ void __launch_bounds__(2 * kPSCols) hv_pstaged_kernel(PSLaunch L) {
     const PSItem item = s_pi;
     if (item.x >= 0) {   // producer
       const PSMember& m = L.items ? L.members[item.x] : L.single;
-      hdiff_vec_block<P, U, Off, 2, true>((const S*)m.u, (const S*)m.coeff, (S*)m.ud, m.ni, m.nj, m.nk, m.sj, m.sk,
+      // one register window (the next level loads after this one's rows):
+      // with two, the 2-row producer's registers hold the kernel at three
+      // CTAs per SM (164 registers); with one, four (125), and the column
+      // sweep items' chains gain the warps (512x512x80: 71.6 against 68.9 G
+      // points/s; 32-member ensemble 1.78 against 1.85 ms)
+      hdiff_vec_block<P, U, Off, 1, true>((const S*)m.u, (const S*)m.coeff, (S*)m.ud, m.ni, m.nj, m.nk, m.sj, m.sk,
                                           m.kchunk, m.ni, (int64_t)m.ni * m.nj, m.nkz, (const S*)m.v, (S*)m.vd,
                                           item.y, item.z, item.w);
       __syncthreads();   // every store of this item is issued
