@@ -270,9 +270,9 @@ OEC_API int oec_program_input_range(oec_program_t p, int index, const int64_t lb
  * k-chunk). Values outside the supported set give OEC_ERR_UNSUPPORTED and
  * leave the schedule unchanged. A new program starts with the library's
  * default schedule for its kind and dtype (hdiff+vadvc: the staged form the
- * autotuner picks at 128x128x80 - FP64 fixed-point producer 32x8 with 4
- * levels per CTA, FP32 vector-row producer with 20 levels per CTA, both with
- * the double-float column sweep).
+ * autotuner picks at 128x128x80 - FP64 fixed-point producer 32x16 with 2
+ * rows per thread and 2 levels per CTA, FP32 vector-row producer with 20
+ * levels per CTA, both with the double-float column sweep).
  */
 OEC_API int oec_program_set_schedule(oec_program_t p, const oec_schedule* s);
 OEC_API int oec_program_get_schedule(oec_program_t p, oec_schedule* s);

@@ -67,13 +67,15 @@ oec_schedule default_schedule(int kind, int dtype) {
       break;
     case OEC_KIND_HDIFF_VADVC:
       // the staged form the autotuner picks at 128x128x80: FP64 fixed-point
-      // producer 32x8, 4 levels per CTA; FP32 vector-row producer (REGS on
-      // unaligned fields), 20 levels per CTA; double-float column sweep
+      // producer 32x16 with 2 rows per thread, 2 levels per CTA; FP32
+      // vector-row producer (REGS on unaligned fields), 20 levels per CTA;
+      // double-float column sweep
       s.fusion = OEC_FUSE_NONE;
       s.staging = dtype == OEC_F64 ? OEC_STAGE_REGS : OEC_STAGE_WARP;
       s.tile_i = 32;
-      s.tile_j = dtype == OEC_F64 ? 8 : 4;
-      s.k_chunk = dtype == OEC_F64 ? 4 : 20;
+      s.tile_j = dtype == OEC_F64 ? 16 : 4;
+      s.unroll = dtype == OEC_F64 ? 2 : 1;
+      s.k_chunk = dtype == OEC_F64 ? 2 : 20;
       s.arith = dtype == OEC_F64 ? OEC_ARITH_FIXED : OEC_ARITH_DOUBLE_FLOAT;
       break;
     case OEC_KIND_FASTWAVES:

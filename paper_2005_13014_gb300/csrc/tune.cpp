@@ -58,12 +58,16 @@ std::vector<oec_schedule> candidates(const oec_program* p) {
       // staged: the tile is the hdiff producer's (FP64: the SMEM tile kernel,
       // staging unused; FP32: the REGS kernel, and the SMEM one at 64 x 4)
       if (p->dtype == OEC_F64) {
+        // the fixed-point producer also with 2 and 3 levels per CTA: at
+        // 128x128x80 its CTAs then fill the SMs in whole waves (32x16 tiles,
+        // 2 rows per thread, 2 levels: 62.7 against 65.2 us per step at 4)
         for (int a : {2, 1, 0})
           for (auto t : {std::pair<int, int>{32, 4}, {32, 8}, {64, 4}, {64, 8}, {128, 4}})
-            for (int kc : {4, 8}) c.push_back(mk(OEC_FUSE_NONE, 0, t.first, t.second, 1, kc, a));
+            for (int kc : {2, 3, 4, 8})
+              if (a == 2 || kc >= 4) c.push_back(mk(OEC_FUSE_NONE, 0, t.first, t.second, 1, kc, a));
         // the fixed-point producer with several rows per thread
         for (auto t : {std::array<int, 3>{32, 8, 2}, {32, 16, 1}, {32, 16, 2}, {32, 16, 4}, {64, 8, 2}})
-          for (int kc : {4, 8}) c.push_back(mk(OEC_FUSE_NONE, 0, t[0], t[1], t[2], kc, 2));
+          for (int kc : {2, 3, 4, 8}) c.push_back(mk(OEC_FUSE_NONE, 0, t[0], t[1], t[2], kc, 2));
 
       } else {
         for (int a : {1, 0}) {

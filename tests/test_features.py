@@ -15,7 +15,7 @@ def test_candidate_sets(liboec):
     assert len(_prog(inputs.random_dag(10000)).candidates()) == 108
     assert len(_prog(programs.HDIFF, "f64", generic=False).candidates()) == 233
     assert len(_prog(programs.HDIFF, "f32", generic=False).candidates()) == 95
-    assert len(_prog(programs.HDIFF_VADVC, "f64", generic=False).candidates()) == 52
+    assert len(_prog(programs.HDIFF_VADVC, "f64", generic=False).candidates()) == 72
     c = _prog(programs.FASTWAVES, "f64", generic=False).candidates()
     assert len(c) == 152 and {x["arith"] for x in c} == {0, 1}
 

@@ -534,11 +534,22 @@ def test_hdiff_vadvc_staged_producer_tiles(dtype, arith, tile, kc):
     assert _hv_case((37, 23, 11), 3, dtype, sched) <= TOL[dtype]
 
 
+@pytest.mark.parametrize("kc", [2, 3, 4])
 @pytest.mark.parametrize("tile", [(32, 8, 2), (32, 16, 1), (32, 16, 2), (32, 16, 4), (64, 8, 2)], ids=str)
-def test_hdiff_vadvc_staged_fixed_rows_per_thread(tile):
-    sched = dict(fusion=1, tile_i=tile[0], tile_j=tile[1], unroll=tile[2], k_chunk=4, arith=2)
+def test_hdiff_vadvc_staged_fixed_rows_per_thread(tile, kc):
+    sched = dict(fusion=1, tile_i=tile[0], tile_j=tile[1], unroll=tile[2], k_chunk=kc, arith=2)
     assert _hv_case((37, 23, 11), 3, "f64", sched) <= TOL["f64"]
     assert _hv_case((128, 128, 80), 3, "f64", sched) <= TOL["f64"]
+
+
+@pytest.mark.parametrize("kc", [2, 3])
+@pytest.mark.parametrize("tile", [(32, 4), (32, 8), (64, 4), (64, 8), (128, 4)], ids=str)
+def test_hdiff_vadvc_staged_fixed_short_chunks(tile, kc):
+    """The fixed-point producer with 2 or 3 levels per CTA (the tuner's
+    shortest chunks; 11 levels leave a partial last chunk), one row per
+    thread."""
+    sched = dict(fusion=1, tile_i=tile[0], tile_j=tile[1], k_chunk=kc, arith=2)
+    assert _hv_case((37, 23, 11), 3, "f64", sched) <= TOL["f64"]
 
 
 @pytest.mark.parametrize("unroll", [1, 2, 4])
