@@ -512,6 +512,24 @@ OEC_API int oec_device_wait_selftest(int polls, void* cuda_stream);
  * oec_device_status reports OEC_ERR_TIMEOUT. Synchronises cuda_stream before
  * returning. Errors: OEC_ERR_INVALID_ARG, OEC_ERR_CUDA. */
 OEC_API int oec_batch_wait_selftest(int polls, void* cuda_stream);
+/* The ticket order of the persistent launch that runs one FP32 domain of
+ * ni x nj x nk points (warp-row producer with `unroll` rows per warp, 1 or 2;
+ * `k_chunk` levels per producer item, 0 or more than nk: all) when `grid`
+ * CTAs are resident, computed on the host exactly as the kernel's CTAs
+ * decode their tickets. No GPU is used. For ticket t, items[4t..4t+3] hold
+ * (x, y, z, w): x = 0 for a producer item (y its tile along i, z its row
+ * block, w its level chunk, plus the number of chunks for the second field),
+ * x = -1 for a column-sweep item (y its group of 64 columns, z..w the row
+ * blocks whose producer items it waits for). The order is what keeps every
+ * bounded wait of the launch finite without assuming which CTAs are
+ * resident: each sweep item comes after all the producer items it waits for,
+ * and producer items never wait. *n_items receives the ticket count; items
+ * is written only when cap >= 4 x that count (items may be null to query).
+ * Errors: OEC_ERR_INVALID_ARG (a size or grid below 1, unroll not 1 or 2,
+ * more tickets than an int holds). The paper has no counterpart: this is a
+ * diagnostic of the library's own scheduling. */
+OEC_API int oec_pstaged_ticket_order(int32_t ni, int32_t nj, int32_t nk, int32_t unroll, int32_t k_chunk,
+                                     int32_t grid, int32_t* items, int64_t cap, int64_t* n_items);
 OEC_API int oec_program_launch_count(oec_program_t p);
 OEC_API int oec_program_set_timing(oec_program_t p, int enable);
 OEC_API int oec_program_kernel_times(oec_program_t p, float* ms, int cap, int* n_applies, int* n_kernels);

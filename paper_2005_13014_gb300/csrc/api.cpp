@@ -599,6 +599,23 @@ int oec_batch_wait_selftest(int polls, void* cuda_stream) {
   return OEC_OK;
 }
 
+int oec_pstaged_ticket_order(int32_t ni, int32_t nj, int32_t nk, int32_t unroll, int32_t k_chunk, int32_t grid,
+                             int32_t* items, int64_t cap, int64_t* n_items) {
+  clear_error();
+  if (!n_items) return fail(OEC_ERR_INVALID_ARG, "n_items is null");
+  if (ni < 1 || nj < 1 || nk < 1) return fail(OEC_ERR_INVALID_ARG, "domain sizes must be at least 1");
+  if (unroll != 1 && unroll != 2) return fail(OEC_ERR_INVALID_ARG, "unroll must be 1 or 2");
+  if (grid < 1) return fail(OEC_ERR_INVALID_ARG, "grid must be at least 1");
+  oec_schedule s{};
+  s.unroll = unroll;
+  s.k_chunk = k_chunk;
+  const Dom d{ni, nj, nk, ni, (int64_t)ni * nj};
+  const int64_t n = hdiff_vadvc_pstaged_order(s, d, grid, items, cap);
+  if (n < 0) return fail(OEC_ERR_INVALID_ARG, "the launch would take more tickets than an int holds");
+  *n_items = n;
+  return OEC_OK;
+}
+
 int oec_device_status(void* cuda_stream) {
   clear_error();
   unsigned n = 0;

@@ -998,7 +998,7 @@ __device__ __forceinline__ bool ps_wait_geq(const int* p, int need, unsigned pol
 // hi is its last column's row block, or after the last block. Row block b
 // then starts at ticket b * per_block + before(b), where before(b) counts the
 // groups whose last column lies in a row block below b - lag.
-__device__ __forceinline__ int64_t ps_groups_before(const PSLaunch& L, int b) {
+__host__ __device__ inline int64_t ps_groups_before(const PSLaunch& L, int b) {
   if (b >= L.blocks) return L.groups;
   const int h = b - 1 - L.lag;
   if (h < 0) return 0;
@@ -1007,7 +1007,7 @@ __device__ __forceinline__ int64_t ps_groups_before(const PSLaunch& L, int b) {
   return lim / kPSCols;   // groups whose last column (64g + 63) lies below lim
 }
 
-__device__ PSItem ps_decode(const PSLaunch& L, int t) {
+__host__ __device__ PSItem ps_decode(const PSLaunch& L, int t) {
   auto start = [&](int b) { return (int64_t)b * L.per_block + ps_groups_before(L, b); };
   int lo = 0, hi = L.blocks - 1;   // the row block b with start(b) <= t < start(b + 1)
   while (lo < hi) {
@@ -1019,7 +1019,7 @@ __device__ PSItem ps_decode(const PSLaunch& L, int t) {
   if (r < L.per_block) return PSItem{0, int(r % L.tiles_i), b, int(r / L.tiles_i)};
   const int64_t g = ps_groups_before(L, b) + (r - L.per_block);
   const int64_t ncol = (int64_t)L.single.ni * L.single.nj;
-  const int64_t c1 = min(g * kPSCols + kPSCols - 1, ncol - 1);
+  const int64_t c1 = g * kPSCols + kPSCols - 1 < ncol - 1 ? g * kPSCols + kPSCols - 1 : ncol - 1;
   return PSItem{~0, int(g), int((g * kPSCols) / L.single.ni) / L.rows, int(c1 / L.single.ni) / L.rows};
 }
 
@@ -1098,6 +1098,37 @@ cudaError_t pstaged_dispatch(const PSLaunch& L, bool query, int* per_sm, cudaStr
 #undef OEC_PS
 }
 
+// The closed-form plan of one FP32 domain's persistent launch: levels per
+// producer item, producer items per row block (tiles along i x 2 fields x
+// level chunks), row blocks of 4 x unroll rows, 64-column groups and the
+// ticket count; false when the tickets do not fit an int.
+bool ps_single_plan(const oec_schedule& s, const Dom& d, PSLaunch& L) {
+  PSMember& m = L.single;
+  m.ni = d.ni; m.nj = d.nj; m.nk = d.nk;
+  m.kchunk = (s.k_chunk <= 0 || s.k_chunk > d.nk) ? d.nk : s.k_chunk;
+  m.nkz = ceil_div(d.nk, m.kchunk);
+  m.row_base = 0;
+  L.tiles_i = ceil_div(d.ni, 128);   // 32 lanes x 4 floats
+  m.need = L.tiles_i * 2 * m.nkz;
+  L.per_block = m.need;
+  L.rows = 4 * s.unroll;
+  L.blocks = ceil_div(d.nj, L.rows);
+  const int64_t ncol = (int64_t)d.ni * d.nj;
+  L.groups = (int)((ncol + kPSCols - 1) / kPSCols);
+  const int64_t n_items = (int64_t)L.blocks * L.per_block + L.groups;
+  if (n_items > INT32_MAX / 2) return false;
+  L.n_items = (int)n_items;
+  L.unroll = s.unroll;
+  return true;
+}
+
+// the lag for `grid` resident CTAs: a group follows its last producers by
+// about two resident CTAs' worth of items
+int ps_single_lag(const PSLaunch& L, int grid) {
+  const int64_t per_row_block = L.per_block + std::max<int64_t>(1, (int64_t)L.rows * L.single.ni / kPSCols);
+  return (int)std::min<int64_t>(L.blocks, (2 * (int64_t)grid + per_row_block - 1) / per_row_block);
+}
+
 // One FP32 domain as a persistent staged launch (the closed-form ticket order
 // of ps_decode, no tables): false in *ran when the fields' rows are not
 // 16-byte aligned (the two kernels run then).
@@ -1115,21 +1146,10 @@ cudaError_t pstaged_single_launch(const oec_schedule& s, const Dom& d, const HV<
   m.sj = d.sj; m.sk = d.sk;
   const int64_t ncol = (int64_t)d.ni * d.nj;
   m.ncolp = pair_pitch(ncol);
-  m.ni = d.ni; m.nj = d.nj; m.nk = d.nk;
-  m.kchunk = (s.k_chunk <= 0 || s.k_chunk > d.nk) ? d.nk : s.k_chunk;
-  m.nkz = ceil_div(d.nk, m.kchunk);
-  m.row_base = 0;
-  L.tiles_i = ceil_div(d.ni, 128);   // 32 lanes x 4 floats
-  m.need = L.tiles_i * 2 * m.nkz;
-  L.per_block = m.need;
-  L.rows = 4 * s.unroll;
-  L.blocks = ceil_div(d.nj, L.rows);
-  L.groups = (int)((ncol + kPSCols - 1) / kPSCols);
-  const int64_t n_items = (int64_t)L.blocks * L.per_block + L.groups;
+  if (!ps_single_plan(s, d, L)) return cudaSuccess;
+  const int64_t n_items = L.n_items;
   L.timeouts = wait_timeout_counter();
-  if (n_items > INT32_MAX / 2 || !L.timeouts) return cudaSuccess;
-  L.n_items = (int)n_items;
-  L.unroll = s.unroll;
+  if (!L.timeouts) return cudaSuccess;
   L.o32 = use_int32(s, d) && 4 * m.ncolp * d.nk < INT32_MAX;
   L.discard = (uintptr_t)scr % 128 == 0 && size_t(24) * m.ncolp * d.nk > kDiscardAboveBytes;
   L.dtr = dtr;
@@ -1151,9 +1171,7 @@ cudaError_t pstaged_single_launch(const oec_schedule& s, const Dom& d, const HV<
     if (dev < 64) cache[form][dev].store(per_sm);
   }
   L.grid = (int)std::min<int64_t>(n_items, (int64_t)per_sm * sms);
-  // a group follows its last producers by about two resident CTAs' worth of items
-  const int64_t per_row_block = L.per_block + std::max<int64_t>(1, (int64_t)L.rows * d.ni / kPSCols);
-  L.lag = (int)std::min<int64_t>(L.blocks, (2 * (int64_t)L.grid + per_row_block - 1) / per_row_block);
+  L.lag = ps_single_lag(L, L.grid);
   e = cudaMemsetAsync(counters, 0, sizeof(int) * (size_t)(L.blocks + 1), st);
   if (e == cudaSuccess) e = pstaged_dispatch<P>(L, false, nullptr, st);
   if (e == cudaSuccess) {
@@ -1287,6 +1305,21 @@ cudaError_t hdiff_vadvc_launch(const oec_schedule& s, int dtype, const Dom& d, c
               (float*)u_out, (float*)v_out, d.ni, d.nj, d.nk, d.sj, d.sk};
   return df ? run<P32D>(s, dtype, d, p, dtr, (char*)scratch, st, batch_member)
             : run<P32>(s, dtype, d, p, dtr, (char*)scratch, st, batch_member);
+}
+
+int64_t hdiff_vadvc_pstaged_order(const oec_schedule& s, const Dom& d, int grid, int32_t* items, int64_t cap) {
+  PSLaunch L{};
+  if (grid < 1 || !ps_single_plan(s, d, L)) return -1;
+  L.lag = ps_single_lag(L, grid);
+  if (items && cap >= 4 * (int64_t)L.n_items)
+    for (int t = 0; t < L.n_items; ++t) {
+      const PSItem it = ps_decode(L, t);
+      items[4 * (int64_t)t] = it.x;
+      items[4 * (int64_t)t + 1] = it.y;
+      items[4 * (int64_t)t + 2] = it.z;
+      items[4 * (int64_t)t + 3] = it.w;
+    }
+  return L.n_items;
 }
 
 bool hdiff_vadvc_pstaged_ok(const oec_schedule& s, int dtype) {

@@ -102,6 +102,12 @@ void hdiff_vadvc_scratch_parts(const oec_schedule& s, int dtype, const Dom& d, s
 int64_t hdiff_vadvc_pair_pitch(int64_t ncol);
 size_t hdiff_vadvc_discard_above_bytes();
 cudaError_t hdiff_vadvc_pstaged_blocks_per_sm(const oec_schedule& s, const PSLaunch& L, int* per_sm);
+// The ticket order of one FP32 domain's persistent staged launch for `grid`
+// resident CTAs, computed on the host: per ticket (x, y, z, w) as the kernel
+// decodes it (x >= 0: producer item y, row block z, level chunk and field w;
+// x < 0: column group y needing row blocks z..w). Returns the ticket count
+// (items written when cap >= 4 x count), -1 when the plan does not fit.
+int64_t hdiff_vadvc_pstaged_order(const oec_schedule& s, const Dom& d, int grid, int32_t* items, int64_t cap);
 cudaError_t hdiff_vadvc_pstaged_launch(const oec_schedule& s, const PSLaunch& L, cudaStream_t st);
 // the persistent batch's give-up path: one sweep item whose counter is never
 // released; waits for the kernel before returning
