@@ -530,6 +530,19 @@ OEC_API int oec_batch_wait_selftest(int polls, void* cuda_stream);
  * diagnostic of the library's own scheduling. */
 OEC_API int oec_pstaged_ticket_order(int32_t ni, int32_t nj, int32_t nk, int32_t unroll, int32_t k_chunk,
                                      int32_t grid, int32_t* items, int64_t cap, int64_t* n_items);
+/* The same for a persistent staged batch (see oec_batch_create) of
+ * n_members FP32 domains, sizes[3m..3m+2] = (ni, nj, nk) of member m in
+ * order, when a column group is placed `lag` tickets after the last producer
+ * item it waits for (the batch uses twice the resident CTAs). Host only, no
+ * GPU. For ticket t, items[4t..4t+3] hold (x, y, z, w): x = m >= 0 for a
+ * producer item of member m (y its tile along i, z its row block, w its
+ * level chunk, plus the number of chunks for the second field), x = -1 - m
+ * for a column group y of member m waiting for its row blocks z..w.
+ * *n_items receives the ticket count; items is written only when cap >= 4 x
+ * that count. Errors: OEC_ERR_INVALID_ARG (no members, a size below 1,
+ * unroll not 1 or 2, lag below 0). The paper has no counterpart. */
+OEC_API int oec_batch_ticket_order(int32_t n_members, const int32_t* sizes, int32_t unroll, int32_t k_chunk,
+                                   int64_t lag, int32_t* items, int64_t cap, int64_t* n_items);
 OEC_API int oec_program_launch_count(oec_program_t p);
 OEC_API int oec_program_set_timing(oec_program_t p, int enable);
 OEC_API int oec_program_kernel_times(oec_program_t p, float* ms, int cap, int* n_applies, int* n_kernels);

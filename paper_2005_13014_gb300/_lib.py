@@ -107,6 +107,8 @@ def lib():
         "oec_batch_wait_selftest": (C.c_int, [C.c_int, P]),
         "oec_pstaged_ticket_order": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                                C.POINTER(C.c_int32), C.c_int64, C.POINTER(C.c_int64)]),
+        "oec_batch_ticket_order": (C.c_int, [C.c_int32, C.POINTER(C.c_int32), C.c_int32, C.c_int32, C.c_int64,
+                                             C.POINTER(C.c_int32), C.c_int64, C.POINTER(C.c_int64)]),
         "oec_costmodel_save": (C.c_int, [P, C.c_char_p]),
         "oec_costmodel_load": (C.c_int, [C.c_char_p, C.POINTER(P)]),
         "oec_program_autotune_model": (C.c_int, [P, P, C.POINTER(FieldDesc), C.c_int, C.POINTER(FieldDesc), C.c_int,

@@ -117,11 +117,62 @@ bool pstaged_aligned(const oec_batch* b) {
 // once every row block it needs has its producer items at least `lag` tickets
 // back (two per resident CTA), so that its rows are usually done and still in
 // L2 when it starts.
+// The items of a persistent staged batch in ticket order. Per member, row
+// block by row block (4 x unroll rows): the block's producer items (level
+// chunk and field, then tile of 128 columns along i), and every 64-column
+// group whose columns all lie in the blocks placed so far becomes ready with
+// the ticket of the block's last producer item; a ready group is placed once
+// `lag` more items follow that ticket, the rest at the end. So every group
+// comes after all producer items it waits for, and producer items wait for
+// nothing.
+std::vector<oec::PSItem> batch_ticket_order(const std::vector<oec::Dom>& doms, int unroll, int k_chunk,
+                                            int64_t lag) {
+  using oec::PSItem;
+  constexpr int W = 128, COLS = 64;   // producer columns per CTA (32 lanes x 4 floats), sweep columns
+  const int rows = 4 * unroll;
+  std::vector<PSItem> items;
+  struct Pending { int m, g, lo, hi; int64_t dep; };
+  std::deque<Pending> ready;
+  auto flush = [&](bool all) {
+    while (!ready.empty() && (all || ready.front().dep + lag <= (int64_t)items.size())) {
+      const Pending& q = ready.front();
+      items.push_back(PSItem{~q.m, q.g, q.lo, q.hi});
+      ready.pop_front();
+    }
+  };
+  for (int mi = 0; mi < (int)doms.size(); ++mi) {
+    const oec::Dom& d = doms[mi];
+    const int kchunk = (k_chunk <= 0 || k_chunk > d.nk) ? d.nk : k_chunk;
+    const int nkz = (d.nk + kchunk - 1) / kchunk;
+    const int64_t ncol = (int64_t)d.ni * d.nj;
+    const int tx = (d.ni + W - 1) / W, ty = (d.nj + rows - 1) / rows;
+    int64_t g = 0;
+    const int64_t groups = (ncol + COLS - 1) / COLS;
+    for (int by = 0; by < ty; ++by) {
+      for (int bz = 0; bz < 2 * nkz; ++bz)
+        for (int bx = 0; bx < tx; ++bx) {
+          items.push_back(PSItem{mi, bx, by, bz});
+          flush(false);
+        }
+      // the sweep groups whose rows all lie in row blocks 0..by
+      const int64_t dep = (int64_t)items.size() - 1;
+      for (; g < groups; ++g) {
+        const int64_t c0 = g * COLS, c1 = std::min(ncol, c0 + COLS) - 1;
+        const int lo = int(c0 / d.ni) / rows, hi = int(c1 / d.ni) / rows;
+        if (hi > by) break;
+        ready.push_back(Pending{mi, (int)g, lo, hi, dep});
+      }
+    }
+  }
+  flush(true);
+  return items;
+}
+
 int build_pstaged(oec_batch* b) {
   using namespace oec;
   const oec_schedule& s = b->sched;
   const int U = s.unroll, rows = 4 * U;
-  constexpr int W = 128, COLS = 64;   // producer columns per CTA (32 lanes x 4 floats), sweep columns
+  constexpr int W = 128;   // producer columns per CTA (32 lanes x 4 floats)
   std::vector<PSMember> tab;
   bool o32 = true, discard = false;
   int row_base = 0;
@@ -158,40 +209,9 @@ int build_pstaged(oec_batch* b) {
   if (e != cudaSuccess) return cuda_fail(e, "persistent batch occupancy");
   if (per_sm < 1) return fail(OEC_ERR_UNSUPPORTED, "persistent batch kernel does not fit on an SM");
   const int64_t lag = 2 * (int64_t)sms * per_sm;
-  // items in ticket order
-  std::vector<PSItem> items;
-  struct Pending { int m, g, lo, hi; int64_t dep; };
-  std::deque<Pending> ready;
-  auto flush = [&](bool all) {
-    while (!ready.empty() && (all || ready.front().dep + lag <= (int64_t)items.size())) {
-      const Pending& q = ready.front();
-      items.push_back(PSItem{~q.m, q.g, q.lo, q.hi});
-      ready.pop_front();
-    }
-  };
-  for (int mi = 0; mi < (int)tab.size(); ++mi) {
-    const PSMember& m = tab[mi];
-    const int64_t ncol = (int64_t)m.ni * m.nj;
-    const int tx = (m.ni + W - 1) / W, ty = (m.nj + rows - 1) / rows;
-    int64_t g = 0;
-    const int64_t groups = (ncol + COLS - 1) / COLS;
-    for (int by = 0; by < ty; ++by) {
-      for (int bz = 0; bz < 2 * m.nkz; ++bz)
-        for (int bx = 0; bx < tx; ++bx) {
-          items.push_back(PSItem{mi, bx, by, bz});
-          flush(false);
-        }
-      // the sweep groups whose rows all lie in row blocks 0..by
-      const int64_t dep = (int64_t)items.size() - 1;
-      for (; g < groups; ++g) {
-        const int64_t c0 = g * COLS, c1 = std::min(ncol, c0 + COLS) - 1;
-        const int lo = int(c0 / m.ni) / rows, hi = int(c1 / m.ni) / rows;
-        if (hi > by) break;
-        ready.push_back(Pending{mi, (int)g, lo, hi, dep});
-      }
-    }
-  }
-  flush(true);
+  std::vector<Dom> doms;
+  for (const StagedMember& sm : b->staged_members) doms.push_back(sm.d);
+  const std::vector<PSItem> items = batch_ticket_order(doms, U, s.k_chunk, lag);
   if (items.size() > (size_t)INT32_MAX) return fail(OEC_ERR_UNSUPPORTED, "more than 2^31 batch items");
   L.n_items = (int)items.size();
   L.grid = (int)std::min<int64_t>(L.n_items, (int64_t)sms * per_sm);
@@ -424,6 +444,35 @@ int oec_batch_apply_direct(oec_batch_t b, void* stream) {
   cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(int), (cudaStream_t)stream);
   if (e == cudaSuccess) e = hdiff_vadvc_batch_launch(b->sched, b->dtype, b->launch, (cudaStream_t)stream);
   return e == cudaSuccess ? OEC_OK : cuda_fail(e, "batch launch");
+}
+
+int oec_batch_ticket_order(int32_t n_members, const int32_t* sizes, int32_t unroll, int32_t k_chunk, int64_t lag,
+                           int32_t* items, int64_t cap, int64_t* n_items) {
+  clear_error();
+  if (!n_items || !sizes || n_members < 1) return fail(OEC_ERR_INVALID_ARG, "n_members, sizes or n_items invalid");
+  if (unroll != 1 && unroll != 2) return fail(OEC_ERR_INVALID_ARG, "unroll must be 1 or 2");
+  if (lag < 0) return fail(OEC_ERR_INVALID_ARG, "lag must be at least 0");
+  std::vector<oec::Dom> doms;
+  for (int m = 0; m < n_members; ++m) {
+    const int32_t* z = sizes + 3 * (int64_t)m;
+    if (z[0] < 1 || z[1] < 1 || z[2] < 1) return fail(OEC_ERR_INVALID_ARG, "member %d: sizes must be at least 1", m);
+    doms.push_back(oec::Dom{z[0], z[1], z[2], z[0], (int64_t)z[0] * z[1]});
+  }
+  std::vector<oec::PSItem> order;
+  try {
+    order = batch_ticket_order(doms, unroll, k_chunk, lag);
+  } catch (const std::bad_alloc&) {
+    return fail(OEC_ERR_INVALID_ARG, "too many items");
+  }
+  *n_items = (int64_t)order.size();
+  if (items && cap >= 4 * (int64_t)order.size())
+    for (size_t t = 0; t < order.size(); ++t) {
+      items[4 * t] = order[t].x;
+      items[4 * t + 1] = order[t].y;
+      items[4 * t + 2] = order[t].z;
+      items[4 * t + 3] = order[t].w;
+    }
+  return OEC_OK;
 }
 
 int oec_batch_info(oec_batch_t b, int* n_items, int* n_ctas) {
